@@ -1,0 +1,239 @@
+"""CPU reference for the split-precision (emulated) products -- TEST INFRASTRUCTURE.
+
+Only the tests, the smoke check and the benchmark's CPU-baseline leg may import
+this module. The GPU library never calls it and shares no code with it.
+
+The paper itself measures only the plain FP64 triple loop (Sec. III, Sec. V);
+it prints no emulation scheme. The two emulated modes below restate published
+methods from their mathematics:
+
+* FP64-accuracy ("fp64_emu"): the error-free splitting of a matrix product of
+  Ozaki, Ogita, Oishi and Rump (2012), in the integer-slice form of Ootomo,
+  Ozaki and Yokota (2024): after a power-of-two scaling per row of A and per
+  column of B, every entry becomes an integer R (the scaled value rounded to
+  t*s bits), written as s signed radix-2^t digits ("slices"). Slice products
+  are integer matrix products; products whose digit levels add to more than
+  s+1 are dropped; the kept levels are recombined with their powers of two.
+* FP32-accuracy ("fp32_emu"): three bfloat16 slices per entry, each the
+  round-to-nearest bfloat16 of the residual left by the slices before it, and
+  the six slice products whose slice indices add to at most 2.
+
+Notation (row-major, A is m x k, B is k x n):
+  t      digit width in bits (8 here: every digit fits in a bfloat16 exactly)
+  s      number of slices
+  E_i    scale exponent of row i of A; F_j of column j of B
+  R      integer representation of a scaled entry
+  sigma_p  slice p (p = 1 .. s), an integer with |sigma_p| <= 2^(t-1)
+  L_d    level-d product sum_{p+q=d} sigma^A_p . sigma^B_q  (d = 2 .. s+1)
+
+Readings taken where no source fixes the detail (each is listed in the design
+notes):
+  * E_i = floor(log2 max_k |a_ik|) + 2 for FP64-accuracy, so |a/2^E| < 1/2 and
+    every balanced digit stays within [-2^(t-1), 2^(t-1)]; +1 for FP32-accuracy.
+    A zero row (or column) takes E = 0 and all-zero slices.
+  * R = round-half-even(a * 2^(t*s - E)); the digits are its balanced radix-2^t
+    expansion, taken from the least significant digit up, with the top digit
+    keeping whatever remains.
+  * The emulated FP64-accuracy result is the exactly computed kept sum, rounded
+    once to the nearest double.
+
+Integer work uses numpy int64 (exact: |R| < 2^62) or Python integers.
+Every function is plain and unblocked so it can be checked against the method
+by eye.
+"""
+from __future__ import annotations
+
+from fractions import Fraction
+import math
+
+import numpy as np
+
+T_BITS = 8  # digit width t
+
+
+# ---------------------------------------------------------------------------
+# Step 1: power-of-two scale exponents (per row of A, per column of B)
+# ---------------------------------------------------------------------------
+def _floor_log2(x: float) -> int:
+    """floor(log2 x) for a finite x > 0, exact (frexp gives x = f*2^e, f in [1/2,1))."""
+    f, e = math.frexp(x)
+    return e - 1
+
+
+def row_exponents(A: np.ndarray, offset: int) -> np.ndarray:
+    """E_i = floor(log2 max_k |a_ik|) + offset; 0 for an all-zero row.
+
+    offset is 2 for the FP64-accuracy digits and 1 for the FP32-accuracy slices.
+    """
+    A = np.asarray(A, dtype=np.float64)
+    m = A.shape[0]
+    E = np.zeros(m, dtype=np.int64)
+    for i in range(m):
+        mx = float(np.max(np.abs(A[i]))) if A.shape[1] else 0.0
+        if mx > 0.0:
+            E[i] = _floor_log2(mx) + offset
+    return E
+
+
+def col_exponents(B: np.ndarray, offset: int) -> np.ndarray:
+    """F_j = floor(log2 max_k |b_kj|) + offset; 0 for an all-zero column."""
+    return row_exponents(np.asarray(B, dtype=np.float64).T, offset)
+
+
+def has_nonfinite(X: np.ndarray) -> bool:
+    return not bool(np.all(np.isfinite(X)))
+
+
+# ---------------------------------------------------------------------------
+# Step 2 (FP64-accuracy): integer representation and balanced digits
+# ---------------------------------------------------------------------------
+def integer_repr(A: np.ndarray, E: np.ndarray, s: int, t: int = T_BITS) -> np.ndarray:
+    """R_ik = round-half-even(a_ik * 2^(t*s - E_i)) as int64 (rows scaled by E)."""
+    A = np.asarray(A, dtype=np.float64)
+    shift = (t * s - np.asarray(E, dtype=np.int64))[:, None]
+    scaled = np.ldexp(A, shift)            # exact: a power-of-two scaling
+    R = np.rint(scaled)                    # numpy rint rounds half to even
+    assert np.all(np.abs(R) <= 2.0 ** (t * s - 1)), "scaled entry out of range"
+    return R.astype(np.int64)
+
+
+def balanced_digits(R: np.ndarray, s: int, t: int = T_BITS) -> np.ndarray:
+    """Digits sigma[p-1] (p = 1..s, most significant first) with
+    R = sum_p sigma_p * 2^(t*(s-p)); sigma_p in [-2^(t-1), 2^(t-1)) for p >= 2
+    and |sigma_1| <= 2^(t-1)."""
+    R = np.asarray(R, dtype=np.int64).copy()
+    half = 1 << (t - 1)
+    base = 1 << t
+    sig = np.zeros((s,) + R.shape, dtype=np.int64)
+    for p in range(s, 1, -1):                  # least significant digit first
+        d = np.mod(R + half, base) - half      # balanced remainder
+        sig[p - 1] = d
+        R = (R - d) >> t                       # exact division by 2^t
+    sig[0] = R
+    return sig
+
+
+def fp64_slices_A(A: np.ndarray, s: int, t: int = T_BITS):
+    """(E, sigma) for A: sigma has shape (s, m, k)."""
+    E = row_exponents(A, 2)
+    return E, balanced_digits(integer_repr(A, E, s, t), s, t)
+
+
+def fp64_slices_B(B: np.ndarray, s: int, t: int = T_BITS):
+    """(F, sigma) for B: sigma has shape (s, k, n) (column j scaled by F_j)."""
+    F = col_exponents(B, 2)
+    RT = integer_repr(np.asarray(B, dtype=np.float64).T, F, s, t)   # (n, k)
+    return F, np.transpose(balanced_digits(RT, s, t), (0, 2, 1))     # (s, k, n)
+
+
+# ---------------------------------------------------------------------------
+# Step 3 (FP64-accuracy): level products of the slices
+# ---------------------------------------------------------------------------
+def level_products(sigA: np.ndarray, sigB: np.ndarray, s: int) -> np.ndarray:
+    """L[d-2] = sum_{p+q=d} sigma^A_p @ sigma^B_q for d = 2..s+1 (int64, exact).
+
+    numpy's integer matmul is exact while |L| < 2^63 (here |L| <= k*s*2^14)."""
+    m, n = sigA.shape[1], sigB.shape[2]
+    L = np.zeros((s, m, n), dtype=np.int64)
+    for d in range(2, s + 2):
+        for p in range(1, d):
+            q = d - p
+            if p > s or q > s:
+                continue
+            L[d - 2] += sigA[p - 1] @ sigB[q - 1]
+    return L
+
+
+# ---------------------------------------------------------------------------
+# Step 4 (FP64-accuracy): recombination, rounded once to double
+# ---------------------------------------------------------------------------
+def recombine_exact(L: np.ndarray, E: np.ndarray, F: np.ndarray, s: int,
+                    t: int = T_BITS) -> np.ndarray:
+    """C_ij = RN( 2^(E_i+F_j) * sum_{d=2}^{s+1} 2^(-t d) L_d[i,j] ).
+
+    The sum is formed exactly as the integer X = sum_d 2^(t(s+1-d)) L_d (Python
+    integers), then X * 2^(E_i+F_j-t(s+1)) is rounded once (Fraction -> float
+    rounds to nearest-even, subnormals included)."""
+    m, n = L.shape[1], L.shape[2]
+    C = np.zeros((m, n), dtype=np.float64)
+    for i in range(m):
+        for j in range(n):
+            X = 0
+            for d in range(2, s + 2):
+                X += int(L[d - 2, i, j]) << (t * (s + 1 - d))
+            e = int(E[i]) + int(F[j]) - t * (s + 1)
+            C[i, j] = float(Fraction(X) * (Fraction(2) ** e))
+    return C
+
+
+def gemm_fp64_emu(A: np.ndarray, B: np.ndarray, s: int, t: int = T_BITS) -> np.ndarray:
+    """The FP64-accuracy emulated product, steps 1-4 in order."""
+    E, sA = fp64_slices_A(A, s, t)
+    F, sB = fp64_slices_B(B, s, t)
+    L = level_products(sA, sB, s)
+    return recombine_exact(L, E, F, s, t)
+
+
+# ---------------------------------------------------------------------------
+# FP32-accuracy: three bfloat16 slices
+# ---------------------------------------------------------------------------
+def bf16_round(x: np.ndarray) -> np.ndarray:
+    """Round doubles to the nearest bfloat16 value (ties to even), returned as
+    doubles. bfloat16 keeps 8 significant bits and float32's exponent range;
+    below 2^-126 its spacing is the subnormal step 2^-133."""
+    x = np.asarray(x, dtype=np.float64)
+    out = np.zeros_like(x)
+    nz = x != 0.0
+    _, e = np.frexp(x[nz])                       # |x| in [2^(e-1), 2^e)
+    ulp_exp = np.maximum(e - 8, -133)            # spacing of bfloat16 there
+    out[nz] = np.ldexp(np.rint(np.ldexp(x[nz], -ulp_exp)), ulp_exp)
+    return out
+
+
+def fp32_slices(R: np.ndarray):
+    """a0 = bf16(r), a1 = bf16(r - a0), a2 = bf16(r - a0 - a1); the residuals
+    are exact in double (each slice is within a factor two of its residual)."""
+    a0 = bf16_round(R)
+    r1 = R - a0
+    a1 = bf16_round(r1)
+    r2 = r1 - a1
+    a2 = bf16_round(r2)
+    return np.stack([a0, a1, a2])
+
+
+def fp32_slices_A(A: np.ndarray):
+    E = row_exponents(A, 1)
+    r = np.ldexp(np.asarray(A, dtype=np.float64), -E[:, None])
+    return E, fp32_slices(r)
+
+
+def fp32_slices_B(B: np.ndarray):
+    F = col_exponents(B, 1)
+    r = np.ldexp(np.asarray(B, dtype=np.float64), -F[None, :])
+    return F, fp32_slices(r)
+
+
+FP32_PAIRS = [(0, 0), (0, 1), (1, 0), (0, 2), (1, 1), (2, 0)]
+
+
+def gemm_fp32_emu(A: np.ndarray, B: np.ndarray) -> np.ndarray:
+    """sum over the six pairs (p, q), p+q <= 2, of slice products, scaled back.
+
+    Products of bfloat16 values are exact in double; the k-sums here are in
+    double, so this is the FP32-accuracy value without the float32 rounding the
+    tensor cores add."""
+    E, sA = fp32_slices_A(A)
+    F, sB = fp32_slices_B(B)
+    acc = np.zeros((sA.shape[1], sB.shape[2]))
+    for p, q in FP32_PAIRS:
+        acc += sA[p] @ sB[q]
+    return np.ldexp(np.ldexp(acc, E[:, None]), F[None, :])
+
+
+# ---------------------------------------------------------------------------
+# Acceptance bound (componentwise)
+# ---------------------------------------------------------------------------
+def gamma(k: int, mode: str) -> float:
+    """gamma = 4k*2^-53 for FP64-accuracy modes, 4k*2^-24 for FP32-accuracy."""
+    u = 2.0 ** -53 if mode in ("fp64", "fp64_emu") else 2.0 ** -24
+    return 4.0 * max(k, 1) * u
