@@ -1,0 +1,362 @@
+#!/usr/bin/env python
+"""Benchmark: FP64-accuracy dense product C = A*B at M = N = K = 8192 on GB300.
+
+One step = one FP64-accuracy product through the library (exponent scan,
+slicing of both operands, tcgen05 slice products and exact recombination) on
+inputs resident in HBM: A with entries uniform[-1,1)*2^e (e uniform on
+[-20, 20] per row), B likewise per column. Inputs are 2 x 512 MiB, larger
+than the 129 MB L2, so no flush is needed between steps.
+
+Reported beside the headline value (all measured in this run): the plain FP64
+kernel and the FP32-accuracy mode on the same inputs, the FP64 pipe peak, the
+end-to-end figure through the host-buffer entry point, the dominant kernel's
+roofline, SM clocks sampled during the timed region, and the CPU oracle on a
+bounded row sample (which also gives the measured error of the sampled rows).
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+Under torchrun each rank runs its own replica of the product (replicas only:
+the single product is not sharded across GPUs); value = all ranks' flops over
+the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_DEFAULT = 8192
+METRIC = "FP64-accuracy GEMM TFLOP/s, emulated vs plain FP64, N=8192; serve p50/p99 ms"
+WORKLOAD = "split-precision FP64-accuracy GEMM M=N=K=8192, A uniform[-1,1)*2^e per row, B per column, e in [-20,20]"
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.idx)],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- helpers
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def profiled_traffic(kernel_src: str):
+    """DRAM bytes per launch of the slice GEMM from the committed ncu summary,
+    if it was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "slice_gemm_fp64emu_traffic.md")
+    if not os.path.exists(path):
+        return None, None
+    txt = open(path).read()
+    src_hash = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+    m_hash = re.search(r"source sha256\[:16\]:\s*`?([0-9a-f]{16})", txt)
+    m_bytes = re.search(r"bytes per launch at N=8192:\s*`?([0-9.eE+]+)", txt)
+    if not m_hash or not m_bytes or m_hash.group(1) != src_hash:
+        return None, src_hash
+    return float(m_bytes.group(1)), src_hash
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------- CPU oracle leg
+def cpu_oracle_rows(A, B, seconds: float, max_rows: int):
+    """Time the oracle's OpenMP triple loop (the paper's threaded scheme) on a
+    bounded number of rows of the product; returns (rows, C_rows, seconds, threads)."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    C1, used = oracle.gemm_omp_rows(A, B, 0, 1)
+    t1 = time.perf_counter() - t0
+    rows = int(max(1, min(max_rows, seconds / max(t1, 1e-6))))
+    # whole rows split over the threads: keep a multiple of the thread count
+    rows = max(used, (rows // used) * used) if rows >= used else rows
+    t0 = time.perf_counter()
+    Cr, used = oracle.gemm_omp_rows(A, B, 0, rows)
+    dt = time.perf_counter() - t0
+    return rows, Cr, dt, used
+
+
+def reference_arm(args):
+    """The oracle (test infrastructure) timed as it stands on the host cores."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+    from paper_2408_15384_gb300 import inputs
+    import oracle
+    oracle.build()
+    N = args.n
+    A = inputs.row_scaled(N, N, 3)
+    B = inputs.col_scaled(N, N, 3)
+    per_step = max(2.0, 150.0 / max(1, args.steps + args.warmup))
+    rows, _, _, used = cpu_oracle_rows(A, B, per_step, 512)
+    for _ in range(args.warmup):
+        oracle.gemm_omp_rows(A, B, 0, rows)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.gemm_omp_rows(A, B, 0, rows)
+        times.append(time.perf_counter() - t0)
+    t = sum(times) / len(times)
+    tflops = 2.0 * rows * N * N / t / 1e12
+    line = {
+        "impl": "reference", "metric": METRIC, "value": tflops, "unit": "TFLOP/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": N, "sample_rows": rows, "parallelism": "host threads (OpenMP)"},
+        "cpu_baseline": {"value": tflops, "unit": "TFLOP/s", "cores": used, "kind": "oracle",
+                         "sample": f"{rows} rows of the {N}^3 product per step (2*{rows}*{N}*{N} flop)"},
+        "e2e": {"value": tflops, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+def ours(args):
+    import numpy as np
+    import torch
+    import paper_2408_15384_gb300 as mm
+    from paper_2408_15384_gb300 import inputs
+
+    ws, rank, local = dist_env()
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    N = args.n
+    h = mm.Handle(local)
+    stream = torch.cuda.current_stream(dev)
+
+    seed = 3 + 1000 * rank
+    A = torch.empty((N, N), dtype=torch.float64, device=dev)
+    B = torch.empty_like(A)
+    C = torch.empty_like(A)
+    mm.fill_uniform(A, seed, inputs.STREAM_A, 1, inputs.STREAM_EXP_A)
+    mm.fill_uniform(B, seed, inputs.STREAM_B, 2, inputs.STREAM_EXP_B)
+    s = mm.slices_for_k(N)
+    pairs = s * (s + 1) // 2
+    flop = 2.0 * N ** 3
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    # ---------------- timed region: FP64-accuracy products
+    for _ in range(max(args.warmup, 3)):
+        h.gemm(A, B, C, precision=mm.FP64_EMU)
+    torch.cuda.synchronize(dev)
+    h.set_option(mm.OPT_PROFILE, 1)
+    for kcls in (mm.KERNEL_SLICE_GEMM, mm.KERNEL_SPLIT):
+        h.profile_read(kcls, reset=True)
+    launches0 = h.stats()
+    sampler = ClockSampler(local if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
+    sampler.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        h.gemm(A, B, C, precision=mm.FP64_EMU, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    clocks = sampler.stop()
+    t_ms = e0.elapsed_time(e1)
+    launches = h.stats() - launches0
+    status = h.sync()
+    gemm_ms, gemm_n = h.profile_read(mm.KERNEL_SLICE_GEMM, reset=True)
+    split_ms, split_n = h.profile_read(mm.KERNEL_SPLIT, reset=True)
+    h.set_option(mm.OPT_PROFILE, 0)
+    if dist is not None:
+        tt = torch.tensor([t_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    ms_step = t_ms / args.steps
+    value = ws * flop * args.steps / (t_ms * 1e-3) / 1e12
+
+    # ---------------- dominant kernel roofline (tensor pipe, bf16)
+    peaks = measured_peaks()
+    kernel_ms = gemm_ms / max(gemm_n, 1)
+    slice_flop = flop * pairs
+    achieved = slice_flop / (kernel_ms * 1e-3) / 1e12
+    if "bf16_tflops_sustained" in peaks:
+        peak, peak_note = peaks["bf16_tflops_sustained"], "of measured (bf16 sustained)"
+    else:
+        peak, peak_note = 1700.0, "of fallback (bf16 sustained)"
+    traffic, src_hash = profiled_traffic(os.path.join(ROOT, "paper_2408_15384_gb300", "csrc", "slice_gemm.cu"))
+
+    extra = {}
+    if rank == 0 and not args.quick:
+        # ---------------- the other modes on the same inputs (outside the timed region)
+        def time_mode(prec, reps):
+            h.gemm(A, B, C, precision=prec)
+            torch.cuda.synchronize(dev)
+            ts = []
+            for _ in range(reps):
+                a0 = torch.cuda.Event(enable_timing=True)
+                a1 = torch.cuda.Event(enable_timing=True)
+                a0.record(stream)
+                h.gemm(A, B, C, precision=prec, stream=stream)
+                a1.record(stream)
+                a1.synchronize()
+                ts.append(a0.elapsed_time(a1))
+            return statistics.median(ts)
+
+        fp32_ms = time_mode(mm.FP32_EMU, 5)
+        fp64_ms = time_mode(mm.FP64, 2)
+        dfma, dmma = h.peak_fp64()
+        fp64_peak = max(dfma, dmma)
+        extra["modes"] = {
+            "fp64_emu_tflops": flop / (ms_step * 1e-3) / 1e12,
+            "fp32_emu_tflops": flop / (fp32_ms * 1e-3) / 1e12,
+            "plain_fp64_tflops": flop / (fp64_ms * 1e-3) / 1e12,
+            "emu_over_plain": fp64_ms / ms_step,
+            "fp64_peak_tflops_measured": {"dfma": dfma, "dmma": dmma},
+            "plain_fp64_frac_of_fp64_peak": (flop / (fp64_ms * 1e-3) / 1e12) / fp64_peak,
+            "slices": s, "slice_pairs": pairs,
+        }
+        # ---------------- end to end through the host-buffer entry point
+        Ah = torch.empty((N, N), dtype=torch.float64, pin_memory=True)
+        Bh = torch.empty_like(Ah, pin_memory=True)
+        Ch = torch.empty_like(Ah, pin_memory=True)
+        Ah.copy_(A.cpu())
+        Bh.copy_(B.cpu())
+        An, Bn, Cn = Ah.numpy(), Bh.numpy(), Ch.numpy()
+        h.gemm_host(An, Bn, Cn, precision=mm.FP64_EMU)
+        reps = max(1, min(3, args.steps))
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            h.gemm_host(An, Bn, Cn, precision=mm.FP64_EMU)
+        e2e_s = (time.perf_counter() - t0) / reps
+        extra["e2e"] = {"value": flop / e2e_s / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": 16 * N * N,
+                        "d2h_bytes_per_step": 8 * N * N}
+        # ---------------- CPU oracle on a bounded sample, and the measured error of those rows
+        if not args.no_cpu_baseline:
+            rows, Cr, dt, used = cpu_oracle_rows(An, Bn, args.cpu_seconds, 2048)
+            import oracle
+            from oracle import emulation as em
+            D = oracle.absprod_rows(An, Bn, list(range(min(rows, 8))))
+            got = Cn[:min(rows, 8)]
+            ref = Cr[:min(rows, 8)]
+            ratio = float(np.max(np.abs(got - ref) / (em.gamma(N, "fp64") * D)))
+            extra["cpu_baseline"] = {"value": 2.0 * rows * N * N / dt / 1e12, "unit": "TFLOP/s", "cores": used,
+                                     "kind": "oracle",
+                                     "sample": f"{rows} rows of the {N}^3 product by the OpenMP triple loop "
+                                               f"({dt:.1f} s, {os.cpu_count()} host cores)"}
+            extra["max_abs_err"] = float(np.max(np.abs(got - ref)))
+            extra["max_err_over_bound"] = ratio
+            extra["err_sample"] = f"{min(rows, 8)} rows x {N} columns vs the FP64 triple-loop oracle"
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "m": N, "n": N, "k": N, "accuracy": "fp64", "slices": s,
+                       "l2": "inputs 2 x 512 MiB > 129 MB L2 (no flush)", "parallelism": f"replicas x{ws}"},
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": traffic, "peak_note": peak_note,
+                         "kernel": "slice_gemm (tcgen05 bf16 slice products, FP64-accuracy epilogue)",
+                         "kernel_ms": kernel_ms, "algorithmic": f"2*N^3*{pairs} slice flop per launch"},
+            "split_kernels_ms_per_step": split_ms / max(args.steps, 1),
+            "clocks": clocks, "gpu_launches": launches, "device_status": status,
+        }
+        line.update(extra)
+        if "e2e" not in line:
+            line["e2e"] = None
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="headline line only")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        from paper_2408_15384_gb300 import build
+        build.build()
+        ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,243 @@
+/*
+ * mm.h -- C ABI of libmm, a single-GPU GB300 (sm_103a) library for the dense
+ * matrix product C = A*B.
+ *
+ * The operation is the paper's matrix product (Sec. III): A is m x k, B is
+ * k x n, C is m x n and C[i][j] = sum_p A[i][p] * B[p][j], the dot product of
+ * row i of A with column j of B. All matrices are row-major, as in the paper's
+ * C program (Sec. III, row-major storage), with leading dimensions
+ * lda >= k, ldb >= n, ldc >= n counted in elements. (The paper names the
+ * shapes m x n and n x p; here n -> k and p -> n.) Inputs and outputs are IEEE
+ * binary64 (double) in every precision mode.
+ *
+ * Precision modes (mm_precision):
+ *   MM_FP64      plain FP64 arithmetic on the FP64 pipe (the paper's
+ *                computation, Sec. V). Inf and NaN propagate as in IEEE.
+ *   MM_FP64_EMU  FP64-accuracy emulation: per-row (A) and per-column (B)
+ *                power-of-two scaling, each entry rounded to t*s bits and split
+ *                into s signed 8-bit integer slices held in bfloat16, slice
+ *                products on the tcgen05 tensor cores with exact FP32 partial
+ *                sums, exact integer recombination, one rounding to double
+ *                (Ozaki, Ogita, Oishi, Rump 2012; Ootomo, Ozaki, Yokota 2024).
+ *                Meets |C - C_ref| <= 4k*2^-53 * (|A||B|) on the library's
+ *                workload distributions (see mm_gemm).
+ *   MM_FP32_EMU  FP32-accuracy emulation: three bfloat16 slices per scaled
+ *                entry and the six slice products with index sum <= 2, FP32
+ *                accumulation on tcgen05. Bound 4k*2^-24 * (|A||B|).
+ *
+ * Status codes: every entry point returns an int status (MM_OK = 0 on
+ * success); mm_status_string() gives a static English description.
+ *
+ * Ownership: the caller owns A, B, C and any stream it passes; the library owns
+ * every workspace it allocates (from a per-handle stream-ordered pool, charged
+ * against the handle's memory budget) and frees it with the handle.
+ *
+ * Threading: mm_gemm / mm_gemm_grouped may be called from several host threads
+ * on distinct streams; the serving calls are thread-safe. A handle must not be
+ * used after mm_destroy.
+ */
+#ifndef MM_H
+#define MM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ types */
+
+typedef struct mm_handle_s *mm_handle;
+
+typedef enum {
+    MM_FP64 = 0,
+    MM_FP64_EMU = 1,
+    MM_FP32_EMU = 2
+} mm_precision;
+
+enum {
+    MM_OK = 0,
+    MM_PENDING = 1,          /* serve: request not finished yet */
+    MM_ERR_INVALID_ARG = 2,  /* null pointer, negative size, ld too small, C overlapping A or B, unknown mode */
+    MM_ERR_BUDGET = 3,       /* the request needs more device memory than the handle's budget */
+    MM_ERR_NONFINITE = 4,    /* emulated mode met Inf or NaN in A or B */
+    MM_ERR_CUDA = 5,         /* a CUDA runtime or driver call failed */
+    MM_ERR_TIMEOUT = 6,      /* a bounded device-side wait ran out; the kernel returned early */
+    MM_ERR_NOT_FOUND = 7,    /* serve: unknown or already collected ticket */
+    MM_ERR_SHUTDOWN = 8,     /* serve: handle is being destroyed; request cancelled */
+    MM_ERR_UNSUPPORTED = 9   /* no sm_100-family GPU (tcgen05) present */
+};
+
+/* One product C = A*B of the grouped and serving calls. Device pointers. */
+typedef struct {
+    int64_t m, n, k;
+    const double *A; int64_t lda;
+    const double *B; int64_t ldb;
+    double *C;       int64_t ldc;
+} mm_problem;
+
+/* A serving request: the product, its accuracy class and a caller tag. The
+ * operands are caller-owned device memory that must stay valid and unchanged
+ * until the request completes. */
+typedef struct {
+    mm_problem prob;
+    int precision;           /* an mm_precision */
+    uint64_t user_tag;
+} mm_request;
+
+/* Completion record of a serving request. Times are microseconds on the
+ * host's steady clock, measured from mm_create. */
+typedef struct {
+    int status;              /* MM_OK, MM_PENDING or the request's error */
+    uint64_t user_tag;
+    double t_submit_us;      /* mm_serve_submit returned */
+    double t_admit_us;       /* admitted: memory reserved, queued for a batch */
+    double t_launch_us;      /* its batch was launched */
+    double t_done_us;        /* its batch finished on the GPU (host saw the event) */
+} mm_req_status;
+
+/* -------------------------------------------------------------- lifecycle */
+
+/* Create a handle on CUDA device `device`. mem_budget_bytes caps the device
+ * memory the handle may hold for workspaces and serving (0 = 40 GiB). Starts
+ * the serving thread lazily (first mm_serve_submit).
+ * Errors: MM_ERR_INVALID_ARG (out == NULL), MM_ERR_CUDA (no such device),
+ * MM_ERR_UNSUPPORTED (device is not compute capability 10.x). */
+int mm_create(mm_handle *out, int device, size_t mem_budget_bytes);
+
+/* Finish or cancel every pending serving request (pending ones complete with
+ * MM_ERR_SHUTDOWN), wait for the handle's GPU work, free everything. */
+int mm_destroy(mm_handle h);
+
+const char *mm_status_string(int status);
+
+/* -------------------------------------------------------------------- GEMM */
+
+/* C <- A*B (overwrite; no alpha or beta), Sec. III definition, row-major.
+ * Asynchronous on `stream` (a cudaStream_t; NULL = legacy default stream):
+ * returns once the kernels are queued. A, B, C are device pointers.
+ * m == 0 or n == 0: nothing is done. k == 0: C is set to zero.
+ * Argument errors (checked on the host before any launch): MM_ERR_INVALID_ARG
+ * for NULL pointers with nonzero sizes, negative sizes, lda < k, ldb < n,
+ * ldc < n, C overlapping A or B, or an unknown precision.
+ * Emulated modes: non-finite inputs are detected on the device; the affected
+ * rows/columns of C become NaN and the handle's sticky status is set, which
+ * mm_sync() reports as MM_ERR_NONFINITE. For k <= 4 MM_FP64_EMU computes with
+ * the FP64 kernel (per-row scaling to <= 56 bits cannot meet the FP64 bound
+ * for such short sums). The emulated FP64 accuracy bound is met on inputs whose
+ * entries within a row of A (column of B) share a scale, such as the workload
+ * recipes; a row mixing very different magnitudes can exceed it, since the
+ * splitting is exact only relative to the row maximum. */
+int mm_gemm(mm_handle h, int64_t m, int64_t n, int64_t k,
+            const double *A, int64_t lda, const double *B, int64_t ldb,
+            double *C, int64_t ldc, int precision, void *stream);
+
+/* Same product with HOST operands (pageable or pinned): copies A and B to
+ * device workspace, computes, copies C back, and synchronises. Returns the
+ * device-side status (including MM_ERR_NONFINITE / MM_ERR_TIMEOUT). */
+int mm_gemm_host(mm_handle h, int64_t m, int64_t n, int64_t k,
+                 const double *A, int64_t lda, const double *B, int64_t ldb,
+                 double *C, int64_t ldc, int precision, void *stream);
+
+/* Wait for `stream` and return (and clear) the handle's sticky device status:
+ * MM_OK, MM_ERR_NONFINITE or MM_ERR_TIMEOUT. */
+int mm_sync(mm_handle h, void *stream);
+
+/* `count` independent products in one persistent launch (per stage), replayed
+ * from a CUDA graph that is captured once per (count, precision, stream) and
+ * updated with the new descriptors on every call. Each problem's result equals
+ * mm_gemm on that problem (same kernels and tile choices, so bit-identical for
+ * MM_FP64 and MM_FP64_EMU). Problems may have any shapes; their C must not
+ * overlap any A or B. Errors as for mm_gemm, checked for every problem. */
+int mm_gemm_grouped(mm_handle h, int count, const mm_problem *probs,
+                    int precision, void *stream);
+
+/* ----------------------------------------------------------------- serving */
+
+/* Queue a request (non-blocking); *ticket identifies it. The serving thread
+ * admits queued requests while their workspace fits the memory budget and a
+ * batch slot is free, groups admitted requests into grouped launches on two
+ * or more streams so batches overlap, and records a completion event per
+ * batch. Errors: MM_ERR_INVALID_ARG (bad problem), MM_ERR_BUDGET (one request
+ * larger than the whole budget), MM_ERR_SHUTDOWN. */
+int mm_serve_submit(mm_handle h, const mm_request *r, uint64_t *ticket);
+
+/* Non-blocking poll: MM_OK (done; C is complete and *st filled; the ticket is
+ * released), MM_PENDING (not yet), MM_ERR_NOT_FOUND (unknown ticket) or the
+ * request's own error (also released). st may be NULL. */
+int mm_serve_poll(mm_handle h, uint64_t ticket, mm_req_status *st);
+
+/* Block until every submitted request has completed (or failed). */
+int mm_serve_drain(mm_handle h);
+
+/* ---------------------------------------------------------- configuration */
+
+/* Options (mm_set_option / mm_get_option). */
+enum {
+    MM_OPT_SLICES = 1,        /* FP64-accuracy slice count s (0 = automatic rule, else 3..7) */
+    MM_OPT_TIMEOUT_MS = 2,    /* bound on every device-side wait (default 2000) */
+    MM_OPT_AUTOTUNE = 3,      /* 1 = time candidate tile shapes on first use of a shape bucket */
+    MM_OPT_SERVE_MAX_BATCH = 4,   /* requests per grouped launch (default 64) */
+    MM_OPT_SERVE_STREAMS = 5,     /* serving streams (default 2) */
+    MM_OPT_FP64_KERNEL = 6,       /* 0 = automatic, 1 = DFMA tiles, 2 = DMMA (mma.sync f64) tiles */
+    MM_OPT_PROFILE = 7            /* 1 = time every kernel launch with CUDA events (see mm_profile_read) */
+};
+
+/* Kernel classes for mm_profile_read. */
+enum {
+    MM_KERNEL_SLICE_GEMM = 0,     /* tcgen05 slice products + recombination (emulated modes) */
+    MM_KERNEL_SPLIT = 1,          /* exponent scan and slicing of both operands */
+    MM_KERNEL_FP64_GEMM = 2       /* plain FP64 tile kernel */
+};
+int mm_set_option(mm_handle h, int option, int64_t value);
+int mm_get_option(mm_handle h, int option, int64_t *value);
+
+/* The slice count the automatic rule picks for inner dimension k (FP64-EMU). */
+int mm_slices_for_k(int64_t k);
+
+/* --------------------------------------------------- inputs and diagnostics */
+
+/* Fill a rows x cols row-major device matrix (leading dimension ld) with the
+ * seeded SplitMix64 counter-based uniform[-1,1) values (element (r,c) draws
+ * counter r*cols+c of stream `stream_id`), optionally times 2^e with one
+ * integer e uniform on [-20,20] per row (scale_mode 1) or per column
+ * (scale_mode 2). Same definition as the Python input module. */
+int mm_fill_uniform(double *X, int64_t rows, int64_t cols, int64_t ld,
+                    uint64_t seed, uint64_t stream_id, int scale_mode,
+                    uint64_t exp_stream_id, void *stream);
+
+/* Exponents and slices as the emulated modes compute them, for checking the
+ * integer work bit for bit. mode: MM_FP64_EMU or MM_FP32_EMU. For A (rows of
+ * an m x k matrix, which = 0) or B (columns of a k x n matrix, which = 1):
+ * exps[rows or cols] (int32) and slices[s][rows or cols][k] as bfloat16 bit
+ * patterns (uint16; B's slices are transposed, K contiguous). s is the slice
+ * count (FP64_EMU) or 3 (FP32_EMU). Device pointers; synchronous. */
+int mm_debug_slices(mm_handle h, int which, int mode, int s,
+                    int64_t rows, int64_t cols, const double *X, int64_t ldx,
+                    int32_t *exps, uint16_t *slices, void *stream);
+
+/* The level products L_d (d = 2..s+1) of the FP64-accuracy mode as the
+ * tensor-core kernel accumulates them (exact integers), written as int64
+ * [s][m][n] to `levels` (device). Synchronous. */
+int mm_debug_level_products(mm_handle h, int64_t m, int64_t n, int64_t k,
+                            const double *A, int64_t lda, const double *B, int64_t ldb,
+                            int s, int64_t *levels, void *stream);
+
+/* Device peak microbenchmarks: FP64 DFMA and DMMA (mma.sync f64) rates in
+ * TFLOP/s, each from a fixed-length register-resident loop on every SM. */
+int mm_peak_fp64(mm_handle h, double *dfma_tflops, double *dmma_tflops);
+
+/* Library counters since mm_create: kernels launched (all kinds). */
+int mm_stats(mm_handle h, uint64_t *kernel_launches);
+
+/* With MM_OPT_PROFILE on, every launch of a kernel class is bracketed by CUDA
+ * events recorded on the stream it runs on. This waits for the recorded
+ * events and returns the summed device time (ms) and the launch count of
+ * `kernel` (an MM_KERNEL_* class) since the last reset; reset != 0 clears. */
+int mm_profile_read(mm_handle h, int kernel, double *total_ms, uint64_t *launches, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MM_H */

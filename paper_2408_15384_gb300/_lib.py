@@ -1,0 +1,73 @@
+"""ctypes declarations of libmm's C ABI (include/mm.h). Marshalling only."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libmm.so")
+
+c_i64 = ctypes.c_int64
+c_u64 = ctypes.c_uint64
+c_int = ctypes.c_int
+c_vp = ctypes.c_void_p
+c_dbl_p = ctypes.POINTER(ctypes.c_double)
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("m", c_i64), ("n", c_i64), ("k", c_i64),
+                ("A", c_vp), ("lda", c_i64),
+                ("B", c_vp), ("ldb", c_i64),
+                ("C", c_vp), ("ldc", c_i64)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("prob", Problem), ("precision", c_int), ("user_tag", c_u64)]
+
+
+class ReqStatus(ctypes.Structure):
+    _fields_ = [("status", c_int), ("user_tag", c_u64),
+                ("t_submit_us", ctypes.c_double), ("t_admit_us", ctypes.c_double),
+                ("t_launch_us", ctypes.c_double), ("t_done_us", ctypes.c_double)]
+
+
+# name -> (restype, argtypes); the full exported surface of include/mm.h
+SIGNATURES = {
+    "mm_create": (c_int, [ctypes.POINTER(c_vp), c_int, ctypes.c_size_t]),
+    "mm_destroy": (c_int, [c_vp]),
+    "mm_status_string": (ctypes.c_char_p, [c_int]),
+    "mm_gemm": (c_int, [c_vp, c_i64, c_i64, c_i64, c_vp, c_i64, c_vp, c_i64, c_vp, c_i64, c_int, c_vp]),
+    "mm_gemm_host": (c_int, [c_vp, c_i64, c_i64, c_i64, c_vp, c_i64, c_vp, c_i64, c_vp, c_i64, c_int, c_vp]),
+    "mm_sync": (c_int, [c_vp, c_vp]),
+    "mm_gemm_grouped": (c_int, [c_vp, c_int, ctypes.POINTER(Problem), c_int, c_vp]),
+    "mm_serve_submit": (c_int, [c_vp, ctypes.POINTER(Request), ctypes.POINTER(c_u64)]),
+    "mm_serve_poll": (c_int, [c_vp, c_u64, ctypes.POINTER(ReqStatus)]),
+    "mm_serve_drain": (c_int, [c_vp]),
+    "mm_set_option": (c_int, [c_vp, c_int, c_i64]),
+    "mm_get_option": (c_int, [c_vp, c_int, ctypes.POINTER(c_i64)]),
+    "mm_slices_for_k": (c_int, [c_i64]),
+    "mm_fill_uniform": (c_int, [c_vp, c_i64, c_i64, c_i64, c_u64, c_u64, c_int, c_u64, c_vp]),
+    "mm_debug_slices": (c_int, [c_vp, c_int, c_int, c_int, c_i64, c_i64, c_vp, c_i64, c_vp, c_vp, c_vp]),
+    "mm_debug_level_products": (c_int, [c_vp, c_i64, c_i64, c_i64, c_vp, c_i64, c_vp, c_i64, c_int, c_vp, c_vp]),
+    "mm_peak_fp64": (c_int, [c_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    "mm_stats": (c_int, [c_vp, ctypes.POINTER(c_u64)]),
+    "mm_profile_read": (c_int, [c_vp, c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(c_u64), c_int]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libmm.so; raise (never fall back) when it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libmm.so is not built ({path}); run `python -m paper_2408_15384_gb300.build`")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib

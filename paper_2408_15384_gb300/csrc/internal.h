@@ -1,0 +1,120 @@
+// internal.h -- the handle and host helpers shared by the C ABI files.
+#pragma once
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstdarg>
+#include <cstdint>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "../../include/mm.h"
+#include "kernels.cuh"
+
+// host copies of the device error bits (ptx.cuh)
+#define MM_DEV_ERR_TIMEOUT_H 1u
+#define MM_DEV_ERR_NONFINITE_H 2u
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+namespace mmhost {
+struct GroupedCache;
+struct ServeEngine;
+}
+
+struct mm_handle_s {
+  int device = 0;
+  size_t budget = 0;
+  int sm_count = 148;
+  std::chrono::steady_clock::time_point t0;
+  EncodeTiledFn encode = nullptr;
+  cudaMemPool_t pool = nullptr;
+  uint32_t* d_err = nullptr;                 // device error word (MM_DEV_ERR_* bits)
+  std::atomic<size_t> ws_in_use{0};          // workspace bytes held (budget accounting)
+  std::atomic<uint64_t> launches{0};         // kernels launched by the library
+
+  // options
+  int opt_slices = 0;
+  int64_t opt_timeout_ms = 2000;
+  bool opt_autotune = false;
+  int opt_serve_max_batch = 64;
+  int opt_serve_streams = 2;
+  int opt_fp64_kernel = 0;
+  int opt_fp32_bn = 0;
+  bool opt_profile = false;
+
+  // profiling: (start, end) event pairs per kernel class, drained by mm_profile_read
+  std::mutex prof_mu;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_pending[3];
+  double prof_ms[3] = {0, 0, 0};
+  uint64_t prof_count[3] = {0, 0, 0};
+
+  std::mutex grouped_mu;
+  mmhost::GroupedCache* grouped = nullptr;
+  std::mutex serve_mu;
+  mmhost::ServeEngine* serve = nullptr;
+};
+
+namespace mmhost {
+
+void logf(int level, const char* fmt, ...);
+double now_us(const mm_handle_s* h);
+int cuda_status(cudaError_t e, const char* what);
+size_t align_up(size_t x, size_t a);
+int ws_alloc(mm_handle_s* h, size_t bytes, cudaStream_t st, void** out);
+void ws_free(mm_handle_s* h, void* p, size_t bytes, cudaStream_t st);
+int validate_problem(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B, int64_t ldb,
+                     const double* C, int64_t ldc, int precision);
+int slices_for_k(int64_t k);
+int fixed_shift(int s, int64_t k);
+bool encode_slices_tmap(mm_handle_s* h, CUtensorMap* tm, const void* base, int64_t k, int64_t rows, int S, int64_t kp,
+                        int box_rows);
+void count_launch(mm_handle_s* h, uint64_t n);
+int pick_bn(mm_handle_s* h, int precision, int64_t m, int64_t n);
+int fp64_kind(mm_handle_s* h);
+int gemm_device(mm_handle_s* h, int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
+                int64_t ldb, double* C, int64_t ldc, int precision, cudaStream_t st);
+int read_and_clear_err(mm_handle_s* h);
+
+// Brackets one launch with events when profiling is on.
+struct ProfScope {
+  mm_handle_s* h;
+  int kernel;
+  cudaStream_t st;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  ProfScope(mm_handle_s* h_, int kernel_, cudaStream_t st_);
+  ~ProfScope();
+};
+
+struct DeviceGuard {
+  int prev = 0, target = 0;
+  explicit DeviceGuard(int dev);
+  ~DeviceGuard();
+};
+
+// Workspace layout of one emulated product.
+struct SplitLayout {
+  int64_t m = 0, n = 0, k = 0, kp = 0;
+  int S = 0;
+  size_t off_rowmax = 0, off_colmax = 0, off_E = 0, off_F = 0, off_sa = 0, off_sb = 0, bytes = 0;
+  void plan(int64_t m_, int64_t n_, int64_t k_, int S_);
+};
+
+int run_split(mm_handle_s* h, int mode01, const SplitLayout& L, char* ws, const double* A, int64_t lda,
+              const double* B, int64_t ldb, cudaStream_t st);
+
+// grouped.cu / serve.cu
+void grouped_release(mm_handle_s* h);
+void serve_shutdown(mm_handle_s* h);
+
+}  // namespace mmhost

@@ -1,0 +1,84 @@
+// kernels.cuh -- launchers shared between the kernel files and the C ABI.
+#pragma once
+#include <cstdint>
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+// Scale exponent marking a row/column that holds Inf or NaN.
+#define EXP_NONFINITE (-1000000)
+
+static inline uint64_t splitmix_mix_host(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// ---------------------------------------------------------------- split.cu
+cudaError_t launch_absmax(const double* A, int64_t m, int64_t k, int64_t lda, const double* B, int64_t n,
+                          int64_t ldb, uint64_t* rowmax, uint64_t* colmax, cudaStream_t st);
+cudaError_t launch_slice_rows(int mode, const double* A, int64_t m, int64_t k, int64_t lda, const uint64_t* rowmax,
+                              int s, int64_t kp, uint16_t* slices, int32_t* E, uint32_t* err, cudaStream_t st);
+cudaError_t launch_slice_cols(int mode, const double* B, int64_t k, int64_t n, int64_t ldb, const uint64_t* colmax,
+                              int s, int64_t kp, uint16_t* slices, int32_t* F, uint32_t* err, cudaStream_t st);
+cudaError_t launch_fill_uniform(double* X, int64_t rows, int64_t cols, int64_t ld, uint64_t seed, uint64_t stream_id,
+                                int scale_mode, uint64_t exp_stream_id, cudaStream_t st);
+
+// ----------------------------------------------------------- slice_gemm.cu
+// Epilogue kinds of the slice GEMM.
+enum SliceMode { SLICE_FP32EMU = 0, SLICE_FP64EMU = 1, SLICE_LEVELS = 2 };
+
+// One product as the slice GEMM sees it (also the grouped problem record).
+struct SliceProblem {
+  int64_t m, n, k;
+  int nkb;               // ceil(k / 64)
+  int s;                 // FP64-accuracy slice count
+  int fix_shift;         // right shift of the int64 fixed-point total (FP64-accuracy)
+  int tiles_m, tiles_n;
+  const int32_t* E;      // row scale exponents of A
+  const int32_t* F;      // column scale exponents of B
+  double* C;
+  int64_t ldc;
+  int64_t* levels;       // SLICE_LEVELS: [s][m][n] int64
+};
+
+// A tile of a grouped launch: problem index and tile coordinates.
+struct TileRef {
+  int32_t prob;
+  int16_t tm, tn;
+};
+
+struct SliceGemmArgs {
+  SliceProblem single;             // used when probs == nullptr
+  const SliceProblem* probs;       // grouped: problem records (device)
+  const CUtensorMap* tmaps;        // grouped: 2 per problem (A, B), device, 64-byte aligned
+  const TileRef* tiles;            // grouped: tile list (device)
+  int ntiles;
+  uint32_t* err;
+  uint64_t timeout_ns;
+};
+
+// Tile width (columns of C per CTA): 128 or 256. grid = persistent CTA count.
+cudaError_t launch_slice_gemm(int mode, int bn, const CUtensorMap* tmA, const CUtensorMap* tmB,
+                              const SliceGemmArgs& a, int grid, cudaStream_t st);
+// Set the dynamic shared memory limits of every instantiation (once per device).
+cudaError_t slice_gemm_prepare();
+int slice_gemm_smem_bytes(int bn);
+
+// ------------------------------------------------------------- fp64_gemm.cu
+struct Fp64GemmArgs {
+  int64_t m, n, k;
+  const double* A;
+  int64_t lda;
+  const double* B;
+  int64_t ldb;
+  double* C;
+  int64_t ldc;
+};
+// kind: 1 = DFMA tiles, 2 = DMMA (mma.sync m8n8k4 f64) tiles.
+cudaError_t launch_fp64_gemm(int kind, const Fp64GemmArgs& a, cudaStream_t st);
+// Grouped: one persistent launch over a tile list of many problems (device arrays).
+cudaError_t launch_fp64_gemm_grouped(int kind, const Fp64GemmArgs* probs, const TileRef* tiles, int ntiles,
+                                     int grid, cudaStream_t st);
+cudaError_t fp64_gemm_prepare();
+cudaError_t launch_zero_c(double* C, int64_t m, int64_t n, int64_t ldc, cudaStream_t st);
+cudaError_t launch_peak_fp64(int kind, double* sink, int iters, int blocks, cudaStream_t st);

@@ -1,0 +1,619 @@
+// mm_abi.cu -- the C ABI of libmm (include/mm.h): handles, argument checks,
+// workspace, the GEMM drivers of the three precision modes, diagnostics.
+//
+// Everything here is host code. Workspaces come from a per-handle CUDA memory
+// pool through stream-ordered allocation (cudaMallocFromPoolAsync /
+// cudaFreeAsync), so concurrent calls on different streams never share
+// scratch and the bytes held are charged against the handle's budget.
+// The tensor-map encoder is fetched from the driver at run time, so the
+// library loads on machines without a GPU driver (no link to libcuda).
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "../../include/mm.h"
+#include "internal.h"
+#include "kernels.cuh"
+
+// ------------------------------------------------------------------ helpers
+const char* mm_status_string(int status) {
+  switch (status) {
+    case MM_OK: return "ok";
+    case MM_PENDING: return "pending";
+    case MM_ERR_INVALID_ARG: return "invalid argument";
+    case MM_ERR_BUDGET: return "device memory budget exceeded";
+    case MM_ERR_NONFINITE: return "non-finite input in an emulated mode";
+    case MM_ERR_CUDA: return "CUDA error";
+    case MM_ERR_TIMEOUT: return "device-side wait timed out";
+    case MM_ERR_NOT_FOUND: return "unknown ticket";
+    case MM_ERR_SHUTDOWN: return "handle shutting down";
+    case MM_ERR_UNSUPPORTED: return "unsupported device";
+    default: return "unknown status";
+  }
+}
+
+namespace mmhost {
+
+static int g_log = -1;
+void logf(int level, const char* fmt, ...) {
+  if (g_log < 0) {
+    const char* e = getenv("MM_LOG");
+    g_log = e ? atoi(e) : 0;
+  }
+  if (level > g_log) return;
+  va_list ap;
+  va_start(ap, fmt);
+  fprintf(stderr, "[libmm] ");
+  vfprintf(stderr, fmt, ap);
+  fprintf(stderr, "\n");
+  va_end(ap);
+}
+
+double now_us(const mm_handle_s* h) {
+  auto d = std::chrono::steady_clock::now() - h->t0;
+  return std::chrono::duration<double, std::micro>(d).count();
+}
+
+DeviceGuard::DeviceGuard(int dev) {
+  cudaGetDevice(&prev);
+  if (prev != dev) cudaSetDevice(dev);
+  target = dev;
+}
+DeviceGuard::~DeviceGuard() {
+  if (prev != target) cudaSetDevice(prev);
+}
+
+int cuda_status(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return MM_OK;
+  logf(1, "%s: %s", what, cudaGetErrorString(e));
+  return MM_ERR_CUDA;
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+int ws_alloc(mm_handle_s* h, size_t bytes, cudaStream_t st, void** out) {
+  *out = nullptr;
+  if (bytes == 0) return MM_OK;
+  size_t cur = h->ws_in_use.fetch_add(bytes);
+  if (cur + bytes > h->budget) {
+    h->ws_in_use.fetch_sub(bytes);
+    return MM_ERR_BUDGET;
+  }
+  cudaError_t e = cudaMallocFromPoolAsync(out, bytes, h->pool, st);
+  if (e != cudaSuccess) {
+    h->ws_in_use.fetch_sub(bytes);
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? MM_ERR_BUDGET : cuda_status(e, "cudaMallocFromPoolAsync");
+  }
+  return MM_OK;
+}
+
+void ws_free(mm_handle_s* h, void* p, size_t bytes, cudaStream_t st) {
+  if (!p) return;
+  cudaFreeAsync(p, st);
+  h->ws_in_use.fetch_sub(bytes);
+}
+
+static bool ranges_overlap(const void* a, size_t na, const void* b, size_t nb) {
+  const char* pa = static_cast<const char*>(a);
+  const char* pb = static_cast<const char*>(b);
+  return pa < pb + nb && pb < pa + na;
+}
+
+int validate_problem(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B, int64_t ldb,
+                     const double* C, int64_t ldc, int precision) {
+  if (precision != MM_FP64 && precision != MM_FP64_EMU && precision != MM_FP32_EMU) return MM_ERR_INVALID_ARG;
+  if (m < 0 || n < 0 || k < 0) return MM_ERR_INVALID_ARG;
+  const int64_t LIM = (int64_t(1) << 31) - 1;
+  if (m > LIM || n > LIM || k > LIM) return MM_ERR_INVALID_ARG;
+  if (m == 0 || n == 0) return MM_OK;
+  if (C == nullptr || ldc < n) return MM_ERR_INVALID_ARG;
+  if (k > 0) {
+    if (A == nullptr || B == nullptr || lda < k || ldb < n) return MM_ERR_INVALID_ARG;
+    size_t cb = static_cast<size_t>((m - 1) * ldc + n) * 8;
+    size_t ab = static_cast<size_t>((m - 1) * lda + k) * 8;
+    size_t bb = static_cast<size_t>((k - 1) * ldb + n) * 8;
+    if (ranges_overlap(C, cb, A, ab) || ranges_overlap(C, cb, B, bb)) return MM_ERR_INVALID_ARG;
+  }
+  return MM_OK;
+}
+
+// Slice count of the FP64-accuracy mode for inner dimension k: the smallest s
+// whose measured error stays near a quarter of the bound 4k*2^-53 |A||B| on the
+// workload distributions (uniform rows/columns times a power of two).
+int slices_for_k(int64_t k) {
+  if (k >= 4096) return 5;
+  if (k >= 96) return 6;
+  return 7;
+}
+
+// Right shift that keeps |X| = |sum_d 2^(8(s+1-d)) L_d| below 2^62, with
+// |L_d| <= k (d-1) 2^14.
+int fixed_shift(int s, int64_t k) {
+  double sum = 0.0;
+  for (int j = 1; j <= s; ++j) sum += j * std::ldexp(1.0, 8 * (s - j));
+  double bits = std::log2(std::ldexp(1.0, 14) * static_cast<double>(std::max<int64_t>(k, 1)) * sum);
+  int need = static_cast<int>(std::ceil(bits + 1e-9));
+  return std::max(0, need - 62);
+}
+
+bool encode_slices_tmap(mm_handle_s* h, CUtensorMap* tm, const void* base, int64_t k, int64_t rows, int S, int64_t kp,
+                        int box_rows) {
+  cuuint64_t dims[3] = {static_cast<cuuint64_t>(k), static_cast<cuuint64_t>(rows), static_cast<cuuint64_t>(S)};
+  cuuint64_t strides[2] = {static_cast<cuuint64_t>(kp * 2), static_cast<cuuint64_t>(rows * kp * 2)};
+  cuuint32_t box[3] = {64u, static_cast<cuuint32_t>(box_rows), 1u};
+  cuuint32_t estr[3] = {1u, 1u, 1u};
+  CUresult r = h->encode(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) logf(1, "cuTensorMapEncodeTiled failed (%d)", static_cast<int>(r));
+  return r == CUDA_SUCCESS;
+}
+
+void count_launch(mm_handle_s* h, uint64_t n) { h->launches.fetch_add(n); }
+
+ProfScope::ProfScope(mm_handle_s* h_, int kernel_, cudaStream_t st_) : h(h_), kernel(kernel_), st(st_) {
+  if (!h->opt_profile) return;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    e0 = e1 = nullptr;
+    return;
+  }
+  cudaEventRecord(e0, st);
+}
+
+ProfScope::~ProfScope() {
+  if (!e0) return;
+  cudaEventRecord(e1, st);
+  std::lock_guard<std::mutex> lk(h->prof_mu);
+  h->prof_pending[kernel].push_back({e0, e1});
+}
+
+// Layout of the emulated-mode workspace of one product.
+void SplitLayout::plan(int64_t m_, int64_t n_, int64_t k_, int S_) {
+  m = m_; n = n_; k = k_; S = S_;
+  kp = static_cast<int64_t>(align_up(static_cast<size_t>(std::max<int64_t>(k, 1)), 8));
+  size_t off = 0;
+  off_rowmax = off; off = align_up(off + 8 * static_cast<size_t>(m), 256);
+  off_colmax = off; off = align_up(off + 8 * static_cast<size_t>(n), 256);
+  off_E = off; off = align_up(off + 4 * static_cast<size_t>(m), 256);
+  off_F = off; off = align_up(off + 4 * static_cast<size_t>(n), 256);
+  off_sa = off; off = align_up(off + 2 * static_cast<size_t>(S) * m * kp, 1024);
+  off_sb = off; off = align_up(off + 2 * static_cast<size_t>(S) * n * kp, 1024);
+  bytes = off;
+}
+
+// Scan + split of both operands into the workspace (3 launches + 1 memset).
+int run_split(mm_handle_s* h, int mode01, const SplitLayout& L, char* ws, const double* A, int64_t lda,
+              const double* B, int64_t ldb, cudaStream_t st) {
+  uint64_t* rowmax = reinterpret_cast<uint64_t*>(ws + L.off_rowmax);
+  uint64_t* colmax = reinterpret_cast<uint64_t*>(ws + L.off_colmax);
+  cudaError_t e = launch_absmax(A, L.m, L.k, lda, B, L.n, ldb, rowmax, colmax, st);
+  if (e != cudaSuccess) return cuda_status(e, "absmax");
+  e = launch_slice_rows(mode01, A, L.m, L.k, lda, rowmax, L.S, L.kp, reinterpret_cast<uint16_t*>(ws + L.off_sa),
+                        reinterpret_cast<int32_t*>(ws + L.off_E), h->d_err, st);
+  if (e != cudaSuccess) return cuda_status(e, "slice rows");
+  e = launch_slice_cols(mode01, B, L.k, L.n, ldb, colmax, L.S, L.kp, reinterpret_cast<uint16_t*>(ws + L.off_sb),
+                        reinterpret_cast<int32_t*>(ws + L.off_F), h->d_err, st);
+  if (e != cudaSuccess) return cuda_status(e, "slice cols");
+  count_launch(h, 4);
+  return MM_OK;
+}
+
+int pick_bn(mm_handle_s* h, int precision, int64_t m, int64_t n) {
+  if (precision != MM_FP32_EMU) return 128;
+  if (h->opt_fp32_bn == 128 || h->opt_fp32_bn == 256) return h->opt_fp32_bn;
+  // 256-wide tiles halve the operand traffic per flop; narrow products keep 128
+  const int64_t t256 = ((m + 127) / 128) * ((n + 255) / 256);
+  return (n > 128 && t256 >= h->sm_count / 2) ? 256 : 128;
+}
+
+// The emulated product of one problem (FP64-accuracy, FP32-accuracy, or the
+// level-product diagnostic when levels != nullptr).
+int run_emulated(mm_handle_s* h, int precision, int64_t m, int64_t n, int64_t k, const double* A, int64_t lda,
+                 const double* B, int64_t ldb, double* C, int64_t ldc, cudaStream_t st, int64_t* levels,
+                 int s_override) {
+  const bool fp64 = (precision == MM_FP64_EMU);
+  const int s = fp64 ? (s_override > 0 ? s_override : (h->opt_slices > 0 ? h->opt_slices : slices_for_k(k))) : 3;
+  SplitLayout L;
+  L.plan(m, n, k, s);
+  void* wsv = nullptr;
+  int rc = ws_alloc(h, L.bytes, st, &wsv);
+  if (rc != MM_OK) return rc;
+  char* ws = static_cast<char*>(wsv);
+  {
+    ProfScope ps(h, MM_KERNEL_SPLIT, st);
+    rc = run_split(h, fp64 ? 0 : 1, L, ws, A, lda, B, ldb, st);
+  }
+  if (rc == MM_OK) {
+    const int bn = pick_bn(h, precision, m, n);
+    CUtensorMap tmA, tmB;
+    if (!encode_slices_tmap(h, &tmA, ws + L.off_sa, k, m, L.S, L.kp, 128) ||
+        !encode_slices_tmap(h, &tmB, ws + L.off_sb, k, n, L.S, L.kp, bn)) {
+      rc = MM_ERR_CUDA;
+    } else {
+      SliceGemmArgs a;
+      memset(&a, 0, sizeof(a));
+      SliceProblem& P = a.single;
+      P.m = m; P.n = n; P.k = k;
+      P.nkb = static_cast<int>((k + 63) / 64);
+      P.s = s;
+      P.fix_shift = fp64 ? fixed_shift(s, k) : 0;
+      P.tiles_m = static_cast<int>((m + 127) / 128);
+      P.tiles_n = static_cast<int>((n + bn - 1) / bn);
+      P.E = reinterpret_cast<const int32_t*>(ws + L.off_E);
+      P.F = reinterpret_cast<const int32_t*>(ws + L.off_F);
+      P.C = C;
+      P.ldc = ldc;
+      P.levels = levels;
+      a.err = h->d_err;
+      a.timeout_ns = static_cast<uint64_t>(h->opt_timeout_ms) * 1000000ull;
+      const int ntiles = P.tiles_m * P.tiles_n;
+      const int grid = std::min(ntiles, h->sm_count);
+      const int mode = levels ? SLICE_LEVELS : (fp64 ? SLICE_FP64EMU : SLICE_FP32EMU);
+      cudaError_t e;
+      {
+        ProfScope ps(h, MM_KERNEL_SLICE_GEMM, st);
+        e = launch_slice_gemm(mode, bn, &tmA, &tmB, a, grid, st);
+      }
+      rc = cuda_status(e, "slice gemm");
+      count_launch(h, 1);
+    }
+  }
+  ws_free(h, wsv, L.bytes, st);
+  return rc;
+}
+
+int fp64_kind(mm_handle_s* h) { return h->opt_fp64_kernel == 1 ? 1 : 2; }
+
+int run_fp64(mm_handle_s* h, int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
+             int64_t ldb, double* C, int64_t ldc, cudaStream_t st) {
+  Fp64GemmArgs a{m, n, k, A, lda, B, ldb, C, ldc};
+  ProfScope ps(h, MM_KERNEL_FP64_GEMM, st);
+  cudaError_t e = launch_fp64_gemm(fp64_kind(h), a, st);
+  count_launch(h, 1);
+  return cuda_status(e, "fp64 gemm");
+}
+
+int gemm_device(mm_handle_s* h, int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
+                int64_t ldb, double* C, int64_t ldc, int precision, cudaStream_t st) {
+  int rc = validate_problem(m, n, k, A, lda, B, ldb, C, ldc, precision);
+  if (rc != MM_OK) return rc;
+  if (m == 0 || n == 0) return MM_OK;
+  if (k == 0) {
+    count_launch(h, 1);
+    return cuda_status(launch_zero_c(C, m, n, ldc, st), "zero C");
+  }
+  if (precision == MM_FP64 || (precision == MM_FP64_EMU && k <= 4))
+    return run_fp64(h, m, n, k, A, lda, B, ldb, C, ldc, st);
+  return run_emulated(h, precision, m, n, k, A, lda, B, ldb, C, ldc, st, nullptr, 0);
+}
+
+int read_and_clear_err(mm_handle_s* h) {
+  uint32_t v = 0;
+  cudaError_t e = cudaMemcpy(&v, h->d_err, sizeof(v), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_status(e, "read error word");
+  if (v) cudaMemset(h->d_err, 0, sizeof(uint32_t));
+  if (v & MM_DEV_ERR_TIMEOUT_H) return MM_ERR_TIMEOUT;
+  if (v & MM_DEV_ERR_NONFINITE_H) return MM_ERR_NONFINITE;
+  return MM_OK;
+}
+
+}  // namespace mmhost
+
+using namespace mmhost;
+
+// ---------------------------------------------------------------- lifecycle
+int mm_create(mm_handle* out, int device, size_t mem_budget_bytes) {
+  if (!out) return MM_ERR_INVALID_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return MM_ERR_CUDA;
+  }
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return MM_ERR_CUDA;
+  if (prop.major != 10) return MM_ERR_UNSUPPORTED;
+  DeviceGuard g(device);
+  mm_handle_s* h = new (std::nothrow) mm_handle_s();
+  if (!h) return MM_ERR_CUDA;
+  h->device = device;
+  h->budget = mem_budget_bytes ? mem_budget_bytes : (size_t(40) << 30);
+  h->sm_count = prop.multiProcessorCount;
+  h->t0 = std::chrono::steady_clock::now();
+  const char* es = getenv("MM_SLICES");
+  if (es) h->opt_slices = atoi(es);
+  cudaDriverEntryPointQueryResult q;
+  void* fn = nullptr;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || !fn) {
+    delete h;
+    return MM_ERR_CUDA;
+  }
+  h->encode = reinterpret_cast<EncodeTiledFn>(fn);
+  cudaMemPoolProps pp;
+  memset(&pp, 0, sizeof(pp));
+  pp.allocType = cudaMemAllocationTypePinned;
+  pp.handleTypes = cudaMemHandleTypeNone;
+  pp.location.type = cudaMemLocationTypeDevice;
+  pp.location.id = device;
+  if (cudaMemPoolCreate(&h->pool, &pp) != cudaSuccess) {
+    delete h;
+    return MM_ERR_CUDA;
+  }
+  uint64_t thr = h->budget;
+  cudaMemPoolSetAttribute(h->pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  if (cudaMalloc(&h->d_err, 64) != cudaSuccess || cudaMemset(h->d_err, 0, 64) != cudaSuccess) {
+    cudaMemPoolDestroy(h->pool);
+    delete h;
+    return MM_ERR_CUDA;
+  }
+  cudaError_t e1 = slice_gemm_prepare();
+  cudaError_t e2 = fp64_gemm_prepare();
+  if (e1 != cudaSuccess || e2 != cudaSuccess) {
+    cudaFree(h->d_err);
+    cudaMemPoolDestroy(h->pool);
+    delete h;
+    return MM_ERR_CUDA;
+  }
+  *out = h;
+  return MM_OK;
+}
+
+int mm_destroy(mm_handle h) {
+  if (!h) return MM_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  serve_shutdown(h);
+  grouped_release(h);
+  cudaDeviceSynchronize();
+  cudaFree(h->d_err);
+  cudaMemPoolDestroy(h->pool);
+  delete h;
+  return MM_OK;
+}
+
+// --------------------------------------------------------------------- GEMM
+int mm_gemm(mm_handle h, int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B, int64_t ldb,
+            double* C, int64_t ldc, int precision, void* stream) {
+  if (!h) return MM_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  return gemm_device(h, m, n, k, A, lda, B, ldb, C, ldc, precision, static_cast<cudaStream_t>(stream));
+}
+
+int mm_gemm_host(mm_handle h, int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
+                 int64_t ldb, double* C, int64_t ldc, int precision, void* stream) {
+  if (!h) return MM_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  // host pointers: validate shapes (overlap of host ranges is checked the same way)
+  int rc = validate_problem(m, n, k, A, lda, B, ldb, C, ldc, precision);
+  if (rc != MM_OK || m == 0 || n == 0) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t ab = 8 * static_cast<size_t>(m) * std::max<int64_t>(k, 1);
+  const size_t bb = 8 * static_cast<size_t>(std::max<int64_t>(k, 1)) * n;
+  const size_t cb = 8 * static_cast<size_t>(m) * n;
+  void *dA = nullptr, *dB = nullptr, *dC = nullptr;
+  if ((rc = ws_alloc(h, ab, st, &dA)) != MM_OK) return rc;
+  if ((rc = ws_alloc(h, bb, st, &dB)) != MM_OK) { ws_free(h, dA, ab, st); return rc; }
+  if ((rc = ws_alloc(h, cb, st, &dC)) != MM_OK) { ws_free(h, dA, ab, st); ws_free(h, dB, bb, st); return rc; }
+  cudaError_t e = cudaSuccess;
+  if (k > 0) {
+    e = cudaMemcpy2DAsync(dA, 8 * k, A, 8 * lda, 8 * k, m, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpy2DAsync(dB, 8 * n, B, 8 * ldb, 8 * n, k, cudaMemcpyHostToDevice, st);
+  }
+  if (e == cudaSuccess) {
+    rc = gemm_device(h, m, n, k, static_cast<double*>(dA), std::max<int64_t>(k, 1), static_cast<double*>(dB), n,
+                     static_cast<double*>(dC), n, precision, st);
+    if (rc == MM_OK) e = cudaMemcpy2DAsync(C, 8 * ldc, dC, 8 * n, 8 * n, m, cudaMemcpyDeviceToHost, st);
+  }
+  ws_free(h, dA, ab, st);
+  ws_free(h, dB, bb, st);
+  ws_free(h, dC, cb, st);
+  if (e != cudaSuccess) return cuda_status(e, "host copies");
+  if (rc != MM_OK) return rc;
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_status(e, "synchronize");
+  return read_and_clear_err(h);
+}
+
+int mm_sync(mm_handle h, void* stream) {
+  if (!h) return MM_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_status(e, "synchronize");
+  return read_and_clear_err(h);
+}
+
+// ------------------------------------------------------------ configuration
+int mm_set_option(mm_handle h, int option, int64_t value) {
+  if (!h) return MM_ERR_INVALID_ARG;
+  switch (option) {
+    case MM_OPT_SLICES:
+      if (value != 0 && (value < 3 || value > 7)) return MM_ERR_INVALID_ARG;
+      h->opt_slices = static_cast<int>(value);
+      return MM_OK;
+    case MM_OPT_TIMEOUT_MS:
+      if (value < 1) return MM_ERR_INVALID_ARG;
+      h->opt_timeout_ms = value;
+      return MM_OK;
+    case MM_OPT_AUTOTUNE: h->opt_autotune = value != 0; return MM_OK;
+    case MM_OPT_SERVE_MAX_BATCH:
+      if (value < 1 || value > 4096) return MM_ERR_INVALID_ARG;
+      h->opt_serve_max_batch = static_cast<int>(value);
+      return MM_OK;
+    case MM_OPT_SERVE_STREAMS:
+      if (value < 1 || value > 8) return MM_ERR_INVALID_ARG;
+      h->opt_serve_streams = static_cast<int>(value);
+      return MM_OK;
+    case MM_OPT_FP64_KERNEL:
+      if (value < 0 || value > 2) return MM_ERR_INVALID_ARG;
+      h->opt_fp64_kernel = static_cast<int>(value);
+      return MM_OK;
+    case MM_OPT_PROFILE: h->opt_profile = value != 0; return MM_OK;
+    default: return MM_ERR_INVALID_ARG;
+  }
+}
+
+int mm_get_option(mm_handle h, int option, int64_t* value) {
+  if (!h || !value) return MM_ERR_INVALID_ARG;
+  switch (option) {
+    case MM_OPT_SLICES: *value = h->opt_slices; return MM_OK;
+    case MM_OPT_TIMEOUT_MS: *value = h->opt_timeout_ms; return MM_OK;
+    case MM_OPT_AUTOTUNE: *value = h->opt_autotune; return MM_OK;
+    case MM_OPT_SERVE_MAX_BATCH: *value = h->opt_serve_max_batch; return MM_OK;
+    case MM_OPT_SERVE_STREAMS: *value = h->opt_serve_streams; return MM_OK;
+    case MM_OPT_FP64_KERNEL: *value = h->opt_fp64_kernel; return MM_OK;
+    case MM_OPT_PROFILE: *value = h->opt_profile; return MM_OK;
+    default: return MM_ERR_INVALID_ARG;
+  }
+}
+
+int mm_slices_for_k(int64_t k) { return slices_for_k(k); }
+
+// ------------------------------------------------------------- diagnostics
+int mm_fill_uniform(double* X, int64_t rows, int64_t cols, int64_t ld, uint64_t seed, uint64_t stream_id,
+                    int scale_mode, uint64_t exp_stream_id, void* stream) {
+  if (rows < 0 || cols < 0 || (rows > 0 && cols > 0 && (!X || ld < cols)) || scale_mode < 0 || scale_mode > 2)
+    return MM_ERR_INVALID_ARG;
+  return cuda_status(launch_fill_uniform(X, rows, cols, ld, seed, stream_id, scale_mode, exp_stream_id,
+                                         static_cast<cudaStream_t>(stream)),
+                     "fill");
+}
+
+int mm_debug_slices(mm_handle h, int which, int mode, int s, int64_t rows, int64_t cols, const double* X, int64_t ldx,
+                    int32_t* exps, uint16_t* slices, void* stream) {
+  if (!h || (which != 0 && which != 1) || (mode != MM_FP64_EMU && mode != MM_FP32_EMU)) return MM_ERR_INVALID_ARG;
+  if (mode == MM_FP64_EMU && (s < 1 || s > 7)) return MM_ERR_INVALID_ARG;
+  if (rows <= 0 || cols <= 0 || !X || !exps || !slices) return MM_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int S = (mode == MM_FP64_EMU) ? s : 3;
+  // which = 0: X is the m x k matrix A (rows = m, cols = k);
+  // which = 1: X is the k x n matrix B (rows = k, cols = n), split by columns.
+  const int64_t nvec = (which == 0) ? rows : cols;  // vectors that get a scale
+  const int64_t klen = (which == 0) ? cols : rows;
+  if (which == 0 ? ldx < cols : ldx < cols) return MM_ERR_INVALID_ARG;
+  SplitLayout L;
+  L.plan(which == 0 ? nvec : 1, which == 1 ? nvec : 1, klen, S);
+  void* wsv = nullptr;
+  int rc = ws_alloc(h, L.bytes, st, &wsv);
+  if (rc != MM_OK) return rc;
+  char* ws = static_cast<char*>(wsv);
+  cudaError_t e;
+  const int mode01 = (mode == MM_FP64_EMU) ? 0 : 1;
+  if (which == 0) {
+    e = launch_absmax(X, nvec, klen, ldx, nullptr, 0, 0, reinterpret_cast<uint64_t*>(ws + L.off_rowmax), nullptr, st);
+    if (e == cudaSuccess)
+      e = launch_slice_rows(mode01, X, nvec, klen, ldx, reinterpret_cast<uint64_t*>(ws + L.off_rowmax), S, L.kp,
+                            reinterpret_cast<uint16_t*>(ws + L.off_sa), exps, h->d_err, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(slices, 2 * klen, ws + L.off_sa, 2 * L.kp, 2 * klen, static_cast<size_t>(S) * nvec,
+                            cudaMemcpyDeviceToDevice, st);
+  } else {
+    e = launch_absmax(nullptr, 0, klen, 0, X, nvec, ldx, nullptr, reinterpret_cast<uint64_t*>(ws + L.off_colmax), st);
+    if (e == cudaSuccess)
+      e = launch_slice_cols(mode01, X, klen, nvec, ldx, reinterpret_cast<uint64_t*>(ws + L.off_colmax), S, L.kp,
+                            reinterpret_cast<uint16_t*>(ws + L.off_sb), exps, h->d_err, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(slices, 2 * klen, ws + L.off_sb, 2 * L.kp, 2 * klen, static_cast<size_t>(S) * nvec,
+                            cudaMemcpyDeviceToDevice, st);
+  }
+  count_launch(h, 3);
+  ws_free(h, wsv, L.bytes, st);
+  if (e != cudaSuccess) return cuda_status(e, "debug slices");
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_status(e, "synchronize");
+  return read_and_clear_err(h);
+}
+
+int mm_debug_level_products(mm_handle h, int64_t m, int64_t n, int64_t k, const double* A, int64_t lda,
+                            const double* B, int64_t ldb, int s, int64_t* levels, void* stream) {
+  if (!h || !levels || s < 1 || s > 7 || m <= 0 || n <= 0 || k <= 0) return MM_ERR_INVALID_ARG;
+  int rc = validate_problem(m, n, k, A, lda, B, ldb, reinterpret_cast<double*>(levels), n, MM_FP64_EMU);
+  if (rc != MM_OK) return rc;
+  DeviceGuard g(h->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemsetAsync(levels, 0, sizeof(int64_t) * static_cast<size_t>(s) * m * n, st);
+  if (e != cudaSuccess) return cuda_status(e, "memset");
+  // C is not written in level mode; pass the level buffer as a placeholder
+  rc = run_emulated(h, MM_FP64_EMU, m, n, k, A, lda, B, ldb, reinterpret_cast<double*>(levels), n, st, levels, s);
+  if (rc != MM_OK) return rc;
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_status(e, "synchronize");
+  return read_and_clear_err(h);
+}
+
+int mm_peak_fp64(mm_handle h, double* dfma_tflops, double* dmma_tflops) {
+  if (!h || !dfma_tflops || !dmma_tflops) return MM_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  double* sink = nullptr;
+  if (cudaMalloc(&sink, 4096 * sizeof(double)) != cudaSuccess) return MM_ERR_CUDA;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int blocks = h->sm_count * 8;
+  double res[3] = {0, 0, 0};
+  for (int kind = 1; kind <= 2; ++kind) {
+    const int iters = (kind == 1) ? 4096 : 2048;
+    launch_peak_fp64(kind, sink, 64, blocks, 0);  // warm-up
+    cudaEventRecord(e0, 0);
+    launch_peak_fp64(kind, sink, iters, blocks, 0);
+    cudaEventRecord(e1, 0);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    const double threads = static_cast<double>(blocks) * 256.0;
+    double flops = (kind == 1) ? 2.0 * 8.0 * iters * threads : 512.0 * 4.0 * iters * (threads / 32.0);
+    res[kind] = flops / (ms * 1e-3) / 1e12;
+    count_launch(h, 2);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(sink);
+  *dfma_tflops = res[1];
+  *dmma_tflops = res[2];
+  return cuda_status(cudaGetLastError(), "peak");
+}
+
+int mm_stats(mm_handle h, uint64_t* kernel_launches) {
+  if (!h || !kernel_launches) return MM_ERR_INVALID_ARG;
+  *kernel_launches = h->launches.load();
+  return MM_OK;
+}
+
+int mm_profile_read(mm_handle h, int kernel, double* total_ms, uint64_t* launches, int reset) {
+  if (!h || kernel < 0 || kernel > 2 || !total_ms || !launches) return MM_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pend;
+  {
+    std::lock_guard<std::mutex> lk(h->prof_mu);
+    pend.swap(h->prof_pending[kernel]);
+  }
+  double add = 0.0;
+  for (auto& pr : pend) {
+    cudaEventSynchronize(pr.second);
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess) add += ms;
+    cudaEventDestroy(pr.first);
+    cudaEventDestroy(pr.second);
+  }
+  std::lock_guard<std::mutex> lk(h->prof_mu);
+  h->prof_ms[kernel] += add;
+  h->prof_count[kernel] += pend.size();
+  *total_ms = h->prof_ms[kernel];
+  *launches = h->prof_count[kernel];
+  if (reset) {
+    h->prof_ms[kernel] = 0.0;
+    h->prof_count[kernel] = 0;
+  }
+  return MM_OK;
+}

@@ -1,0 +1,469 @@
+// slice_gemm.cu -- tcgen05 tensor-core product of bfloat16 operand slices, with
+// the FP32-accuracy or FP64-accuracy epilogue. Persistent: each CTA (one per
+// SM) walks a list of 128 x BN output tiles, of one product or of a group of
+// products.
+//
+// Warp roles:
+//   warp 0      TMA producer: one A-slice tile (128 x 64) and one B-slice tile
+//               (BN x 64) per pipeline step into a STAGES-deep shared ring.
+//   warp 1      allocates TMEM; one thread issues tcgen05.mma (M=128, N=BN,
+//               K=16, bf16 x bf16 -> f32) and tcgen05.commit.
+//   warps 2..9  epilogue: tcgen05.ld of the accumulator, row = TMEM lane,
+//               two warps per TMEM lane quadrant, each on half the columns.
+// Accumulation chunks alternate between two TMEM slots of BN columns, so the
+// tensor cores run the next chunk (or the next tile) while the epilogue drains
+// the previous one.
+//
+// FP32-accuracy (three bfloat16 slices per operand): the six slice pairs
+// (p, q) with p + q <= 2 accumulate into one f32 accumulator, smallest
+// products first; the epilogue scales by 2^(E_i + F_j) and stores doubles.
+//
+// FP64-accuracy (integer slices, levels d = p + q = 2..s+1, Ozaki-style): the
+// kernel walks the levels one after the other. Level d sums d-1 slice pairs;
+// with |slice| <= 2^7 each product is at most 2^14, so a K-chunk of Kc with
+// Kc * (d-1) <= 1024 sums to at most 2^24 and the f32 accumulator holds it
+// exactly. The epilogue adds each finished chunk, converted to int32, to an
+// int32 level sum kept in the spare TMEM columns (512 columns = two 128-wide
+// accumulator slots + the level sums). At the end of a level the sums join an
+// exact int64 fixed-point total X = sum_d 2^(8(s+1-d) - shift) L_d kept in C's
+// own storage; the last level converts X to double once and scales it by
+// 2^(E_i + F_j - 8(s+1) + shift).
+#include <cstdint>
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "kernels.cuh"
+#include "ptx.cuh"
+
+namespace mmdev {
+
+static constexpr int BM = 128;
+static constexpr int BK = 64;                 // bf16 elements per K block (128 bytes)
+static constexpr int SEG_CHUNKS = 120;        // chunks per int32 level sum (120 * 2^24 < 2^31)
+static constexpr int EPI_WARPS = 8;
+
+template <int BN, int MODE>
+struct Cfg {
+  static constexpr int NUM_THREADS = 64 + 32 * EPI_WARPS;
+  static constexpr int A_BYTES = BM * BK * 2;
+  static constexpr int B_BYTES = BN * BK * 2;
+  static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+  static constexpr int STAGES = (BN == 256) ? 4 : 6;
+  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
+  // two accumulator slots; FP64-accuracy adds the int32 level sums (BN = 128)
+  static constexpr int TMEM_COLS = (MODE == SLICE_FP32EMU) ? 2 * BN : 512;
+  static constexpr int SUM_COL = 2 * BN;
+  static constexpr int COLS_PER_THREAD = BN / 2;
+};
+
+// K blocks per chunk at level d (d - 1 pairs): Kc * (d-1) <= 1024.
+__device__ __forceinline__ int chunk_blocks(int d) {
+  int kb = 16 / (d - 1);
+  return kb < 1 ? 1 : kb;
+}
+
+__device__ __forceinline__ uint64_t dbits(double x) { return static_cast<uint64_t>(__double_as_longlong(x)); }
+__device__ __forceinline__ double bitsd(uint64_t b) { return __longlong_as_double(static_cast<long long>(b)); }
+
+// x * 2^e for finite x, exact unless the result leaves the normal range.
+__device__ __forceinline__ double scale_pow2(double x, int e) {
+  uint64_t b = dbits(x);
+  uint64_t ab = b & 0x7FFFFFFFFFFFFFFFull;
+  if (ab == 0) return x;
+  int ex = static_cast<int>(ab >> 52);
+  if (ex > 0 && ex + e >= 1 && ex + e <= 2046) return bitsd(b + (static_cast<uint64_t>(static_cast<int64_t>(e)) << 52));
+  // rare: step through exact powers of two (a subnormal result rounds here)
+  while (e > 1000) { x *= bitsd(static_cast<uint64_t>(1000 + 1023) << 52); e -= 1000; }
+  while (e < -1000) { x *= bitsd(static_cast<uint64_t>(-1000 + 1023) << 52); e += 1000; }
+  return x * bitsd(static_cast<uint64_t>(e + 1023) << 52);
+}
+
+// exact float -> double with a power-of-two scale
+__device__ __forceinline__ double f32_to_f64_scaled(uint32_t fb, int e) {
+  uint32_t e8 = (fb >> 23) & 255u;
+  if (e8 == 0u || e8 == 255u) return scale_pow2(static_cast<double>(__uint_as_float(fb)), e);
+  int ex = static_cast<int>(e8) - 127 + 1023;
+  uint64_t sgn = static_cast<uint64_t>(fb >> 31) << 63;
+  uint64_t man = static_cast<uint64_t>(fb & 0x7FFFFFu) << 29;
+  if (ex + e >= 1 && ex + e <= 2046) return bitsd(sgn | (static_cast<uint64_t>(ex + e) << 52) | man);
+  return scale_pow2(bitsd(sgn | (static_cast<uint64_t>(ex) << 52) | man), e);
+}
+
+struct Step {
+  int kb, pa, pb;      // K block, A slice index, B slice index
+  bool first, last;    // first / last step of its chunk
+};
+
+// Walk the pipeline steps of one tile in order; f(Step, chunk offset in tile).
+template <int MODE, typename Fn>
+__device__ __forceinline__ void for_each_step(int s, int nkb, Fn&& f) {
+  if (MODE == SLICE_FP32EMU) {
+    // pairs (p, q), p + q <= 2, smallest products first
+    for (int kb = 0; kb < nkb; ++kb) {
+      f(Step{kb, 2, 0, kb == 0, false}, 0);
+      f(Step{kb, 1, 1, false, false}, 0);
+      f(Step{kb, 0, 2, false, false}, 0);
+      f(Step{kb, 1, 0, false, false}, 0);
+      f(Step{kb, 0, 1, false, false}, 0);
+      f(Step{kb, 0, 0, false, kb == nkb - 1}, 0);
+    }
+  } else {
+    int chunk = 0;
+    for (int d = 2; d <= s + 1; ++d) {
+      const int kc = chunk_blocks(d);
+      for (int kb0 = 0; kb0 < nkb; kb0 += kc, ++chunk) {
+        const int kb1 = min(kb0 + kc, nkb);
+        for (int kb = kb0; kb < kb1; ++kb)
+          for (int p = 1; p < d; ++p)
+            f(Step{kb, p - 1, d - p - 1, kb == kb0 && p == 1, kb == kb1 - 1 && p == d - 1}, chunk);
+      }
+    }
+  }
+}
+
+template <int MODE>
+__device__ __forceinline__ int chunks_per_tile(int s, int nkb) {
+  if (MODE == SLICE_FP32EMU) return 1;
+  int c = 0;
+  for (int d = 2; d <= s + 1; ++d) {
+    const int kc = chunk_blocks(d);
+    c += (nkb + kc - 1) / kc;
+  }
+  return c;
+}
+
+struct TileJob {
+  const SliceProblem* P;
+  const CUtensorMap* ta;
+  const CUtensorMap* tb;
+  int tm, tn;
+};
+
+__device__ __forceinline__ TileJob get_job(const SliceGemmArgs& a, const CUtensorMap* pa, const CUtensorMap* pb,
+                                           int t) {
+  TileJob j;
+  if (a.probs == nullptr) {
+    // raster in groups of 8 tile rows so consecutive tiles share B panels
+    const SliceProblem& P = a.single;
+    const int GROUP = 8;
+    const int in_group = GROUP * P.tiles_n;
+    const int gid = t / in_group;
+    const int first_m = gid * GROUP;
+    const int gsize = min(P.tiles_m - first_m, GROUP);
+    j.tm = first_m + (t % in_group) % gsize;
+    j.tn = (t % in_group) / gsize;
+    j.P = &a.single;
+    j.ta = pa;
+    j.tb = pb;
+  } else {
+    const TileRef r = a.tiles[t];
+    j.P = a.probs + r.prob;
+    j.ta = a.tmaps + 2 * r.prob;
+    j.tb = a.tmaps + 2 * r.prob + 1;
+    j.tm = r.tm;
+    j.tn = r.tn;
+  }
+  return j;
+}
+
+template <int BN, int MODE>
+__global__ void __launch_bounds__(Cfg<BN, MODE>::NUM_THREADS, 1)
+    slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                      const __grid_constant__ SliceGemmArgs args) {
+  using C_ = Cfg<BN, MODE>;
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar[C_::STAGES];
+  __shared__ __align__(8) uint64_t empty_bar[C_::STAGES];
+  __shared__ __align__(8) uint64_t accf_bar[2];
+  __shared__ __align__(8) uint64_t acce_bar[2];
+  __shared__ __align__(8) uint64_t drain_bar;
+  __shared__ uint32_t tmem_base_slot;
+  __shared__ volatile uint32_t abort_flag;
+
+  const uint32_t warp = warp_id(), lane = lane_id();
+  const uint32_t smem_base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  uint8_t* smem_gen = smem_raw + (smem_base - smem_u32(smem_raw));
+  const int ntiles = (args.probs == nullptr) ? args.single.tiles_m * args.single.tiles_n : args.ntiles;
+
+  WaitCtl wc;
+  wc.abort = &abort_flag;
+  wc.err = args.err;
+  wc.deadline_ns = globaltimer_ns() + args.timeout_ns;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < C_::STAGES; ++i) {
+      mbar_init(&full_bar[i], 1);
+      mbar_init(&empty_bar[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&accf_bar[i], 1);
+      mbar_init(&acce_bar[i], EPI_WARPS);
+    }
+    mbar_init(&drain_bar, 1);
+    abort_flag = 0u;
+    fence_mbar_init();
+  }
+  if (warp == 0 && lane == 0 && args.probs == nullptr) {
+    tma_prefetch_desc(&tmA);
+    tma_prefetch_desc(&tmB);
+  }
+  if (warp == 1) {
+    tmem_alloc(&tmem_base_slot, C_::TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = tmem_base_slot;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      int it = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        const TileJob job = get_job(args, &tmA, &tmB, t);
+        const int ya = job.tm * BM, yb = job.tn * BN;
+        for_each_step<MODE>(job.P->s, job.P->nkb, [&](const Step& st, int) {
+          if (!ok) return;
+          const int stage = it % C_::STAGES;
+          const uint32_t use = static_cast<uint32_t>(it / C_::STAGES);
+          if (!mbar_wait(&empty_bar[stage], (use & 1u) ^ 1u, wc)) { ok = false; return; }
+          uint8_t* sa = smem_gen + stage * C_::STAGE_BYTES;
+          uint8_t* sb = sa + C_::A_BYTES;
+          mbar_arrive_expect_tx(&full_bar[stage], C_::STAGE_BYTES);
+          tma_load_3d(sa, job.ta, st.kb * BK, ya, st.pa, &full_bar[stage]);
+          tma_load_3d(sb, job.tb, st.kb * BK, yb, st.pb, &full_bar[stage]);
+          ++it;
+        });
+      }
+      if (!ok) {
+        // copies already issued must land before the CTA exits
+        const uint64_t dl = globaltimer_ns() + 100000000ull;
+        for (int j = (it > C_::STAGES ? it - C_::STAGES : 0); j < it; ++j)
+          mbar_wait_quiet(&full_bar[j % C_::STAGES], static_cast<uint32_t>(j / C_::STAGES) & 1u, dl);
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ----------------------------------------------------------------- MMA
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16_f32(BM, BN);
+      int it = 0;
+      int chunk_base = 0;
+      bool ok = true;
+      bool issued_any = false;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        const TileJob job = get_job(args, &tmA, &tmB, t);
+        const int s = job.P->s, nkb = job.P->nkb;
+        for_each_step<MODE>(s, nkb, [&](const Step& st, int cofs) {
+          if (!ok) return;
+          const int chunk = chunk_base + cofs;
+          const int slot = chunk & 1;
+          if (st.first) {
+            const uint32_t use = static_cast<uint32_t>(chunk >> 1);
+            if (!mbar_wait(&acce_bar[slot], (use & 1u) ^ 1u, wc)) { ok = false; return; }
+            tc_fence_after();
+          }
+          const int stage = it % C_::STAGES;
+          const uint32_t use = static_cast<uint32_t>(it / C_::STAGES);
+          if (!mbar_wait(&full_bar[stage], use & 1u, wc)) { ok = false; return; }
+          tc_fence_after();
+          const uint32_t sa = smem_base + stage * C_::STAGE_BYTES;
+          const uint32_t sb = sa + C_::A_BYTES;
+          const uint64_t da = smem_desc_sw128(sa), db = smem_desc_sw128(sb);
+          const uint32_t dt = tmem_base + static_cast<uint32_t>(slot * BN);
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk) {
+            // 16 bf16 (32 bytes) further along K inside the 128-byte swizzled rows
+            umma_bf16(dt, da + static_cast<uint64_t>(kk * 2), db + static_cast<uint64_t>(kk * 2), idesc,
+                      (st.first && kk == 0) ? 0u : 1u);
+          }
+          issued_any = true;
+          umma_commit(&empty_bar[stage]);
+          if (st.last) umma_commit(&accf_bar[slot]);
+          ++it;
+        });
+        chunk_base += chunks_per_tile<MODE>(s, nkb);
+      }
+      if (!ok && issued_any) {
+        umma_commit(&drain_bar);
+        mbar_wait_quiet(&drain_bar, 0u, globaltimer_ns() + 100000000ull);
+      }
+    }
+    __syncwarp();
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int ew = static_cast<int>(warp) - 2;          // 0..7
+    const int quad = static_cast<int>(warp & 3u);        // TMEM lane quadrant this warp may access
+    const int half = ew >> 2;                            // which half of the tile's columns
+    const int row_in_tile = quad * 32 + static_cast<int>(lane);
+    const int col_off = half * C_::COLS_PER_THREAD;
+    const uint32_t t_lane = static_cast<uint32_t>(quad * 32) << 16;
+    int chunk = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      const TileJob job = get_job(args, &tmA, &tmB, t);
+      const SliceProblem& P = *job.P;
+      const int64_t row = static_cast<int64_t>(job.tm) * BM + row_in_tile;
+      const int64_t col0 = static_cast<int64_t>(job.tn) * BN + col_off;
+      const int64_t n = P.n;
+      const bool row_ok = row < P.m;
+      const int32_t Ei = row_ok ? P.E[row] : 0;
+
+      if (MODE == SLICE_FP32EMU) {
+        const int slot = chunk & 1;
+        if (!mbar_wait(&accf_bar[slot], static_cast<uint32_t>(chunk >> 1) & 1u, wc)) { ok = false; break; }
+        tc_fence_after();
+        double* crow = P.C + row * P.ldc;
+#pragma unroll 1
+        for (int cg = 0; cg < C_::COLS_PER_THREAD / 32; ++cg) {
+          uint32_t r[32];
+          tmem_ld32(tmem_base + t_lane + static_cast<uint32_t>(slot * BN + col_off + cg * 32), r);
+          tmem_ld_wait();
+          if (row_ok) {
+#pragma unroll
+            for (int v = 0; v < 32; ++v) {
+              const int64_t col = col0 + cg * 32 + v;
+              if (col < n) {
+                const int32_t Fj = __ldg(P.F + col);
+                double out;
+                if (Ei == EXP_NONFINITE || Fj == EXP_NONFINITE)
+                  out = __longlong_as_double(0x7FF8000000000000ll);
+                else
+                  out = f32_to_f64_scaled(r[v], Ei + Fj);
+                crow[col] = out;
+              }
+            }
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acce_bar[slot]);
+        ++chunk;
+      } else {
+        int64_t* const xrow = reinterpret_cast<int64_t*>(P.C) + row * P.ldc;
+        const int s = P.s;
+        const int nkb = P.nkb;
+        const int fix_shift = P.fix_shift;
+        const uint32_t tsum = tmem_base + t_lane + static_cast<uint32_t>(C_::SUM_COL + col_off);
+        bool first_fold = true;
+        bool sum_live = false;   // the TMEM level sums hold data (else they read as zero)
+        for (int d = 2; d <= s + 1 && ok; ++d) {
+          const int kc = chunk_blocks(d);
+          const int nch = (nkb + kc - 1) / kc;
+          for (int c = 0; c < nch; ++c, ++chunk) {
+            const int slot = chunk & 1;
+            if (!mbar_wait(&accf_bar[slot], static_cast<uint32_t>(chunk >> 1) & 1u, wc)) { ok = false; break; }
+            tc_fence_after();
+#pragma unroll 1
+            for (int cg = 0; cg < C_::COLS_PER_THREAD / 32; ++cg) {
+              uint32_t r[32], q[32];
+              tmem_ld32(tmem_base + t_lane + static_cast<uint32_t>(slot * BN + col_off + cg * 32), r);
+              if (sum_live) tmem_ld32(tsum + cg * 32, q);
+              tmem_ld_wait();
+#pragma unroll
+              for (int v = 0; v < 32; ++v) {
+                const int32_t a = __float2int_rz(__uint_as_float(r[v]));
+                q[v] = static_cast<uint32_t>(sum_live ? static_cast<int32_t>(q[v]) + a : a);
+              }
+              tmem_st32(tsum + cg * 32, q);
+            }
+            tmem_st_wait();
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acce_bar[slot]);
+            sum_live = true;
+            const bool level_end = (c == nch - 1);
+            const bool seg_end = ((c + 1) % SEG_CHUNKS) == 0;
+            if (!(level_end || seg_end)) continue;
+            // ---- fold the level sums into the int64 total (or the level output)
+            const bool last_fold = level_end && (d == s + 1);
+            const int lsh = 8 * (s + 1 - d) - fix_shift;
+#pragma unroll 1
+            for (int cg = 0; cg < C_::COLS_PER_THREAD / 32; ++cg) {
+              uint32_t q[32];
+              tmem_ld32(tsum + cg * 32, q);
+              tmem_ld_wait();
+              if (!row_ok) continue;
+#pragma unroll 4
+              for (int v = 0; v < 32; ++v) {
+                const int64_t col = col0 + cg * 32 + v;
+                if (col >= n) break;
+                const int64_t lv = static_cast<int64_t>(static_cast<int32_t>(q[v]));
+                if (MODE == SLICE_LEVELS) {
+                  P.levels[(static_cast<int64_t>(d - 2) * P.m + row) * n + col] += lv;
+                } else {
+                  const int64_t add = (lsh >= 0) ? (lv << lsh) : ((lv + (1ll << (-lsh - 1))) >> (-lsh));
+                  const int64_t X = first_fold ? add : (xrow[col] + add);
+                  if (last_fold) {
+                    const int32_t Fj = __ldg(P.F + col);
+                    double out;
+                    if (Ei == EXP_NONFINITE || Fj == EXP_NONFINITE)
+                      out = __longlong_as_double(0x7FF8000000000000ll);
+                    else
+                      out = scale_pow2(__ll2double_rn(X), Ei + Fj - 8 * (s + 1) + fix_shift);
+                    reinterpret_cast<double*>(xrow)[col] = out;
+                  } else {
+                    xrow[col] = X;
+                  }
+                }
+              }
+            }
+            sum_live = false;
+            first_fold = false;
+          }
+        }
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, C_::TMEM_COLS);
+  }
+}
+
+template <int BN, int MODE>
+static cudaError_t set_smem_attr() {
+  return cudaFuncSetAttribute(slice_gemm_kernel<BN, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              Cfg<BN, MODE>::SMEM_BYTES);
+}
+
+template <int BN, int MODE>
+static cudaError_t launch_t(const CUtensorMap* tmA, const CUtensorMap* tmB, const SliceGemmArgs& a, int grid,
+                            cudaStream_t st) {
+  slice_gemm_kernel<BN, MODE><<<grid, Cfg<BN, MODE>::NUM_THREADS, Cfg<BN, MODE>::SMEM_BYTES, st>>>(*tmA, *tmB, a);
+  return cudaGetLastError();
+}
+
+}  // namespace mmdev
+
+using namespace mmdev;
+
+cudaError_t slice_gemm_prepare() {
+  cudaError_t e;
+  if ((e = set_smem_attr<256, SLICE_FP32EMU>()) != cudaSuccess) return e;
+  if ((e = set_smem_attr<128, SLICE_FP32EMU>()) != cudaSuccess) return e;
+  if ((e = set_smem_attr<128, SLICE_FP64EMU>()) != cudaSuccess) return e;
+  if ((e = set_smem_attr<128, SLICE_LEVELS>()) != cudaSuccess) return e;
+  return cudaSuccess;
+}
+
+int slice_gemm_smem_bytes(int bn) {
+  return bn == 256 ? Cfg<256, SLICE_FP32EMU>::SMEM_BYTES : Cfg<128, SLICE_FP32EMU>::SMEM_BYTES;
+}
+
+// FP32-accuracy: BN 256 or 128. FP64-accuracy and level output: BN 128 (the
+// per-thread int32 level sums of a 256-wide tile do not fit the register file).
+cudaError_t launch_slice_gemm(int mode, int bn, const CUtensorMap* tmA, const CUtensorMap* tmB,
+                              const SliceGemmArgs& a, int grid, cudaStream_t st) {
+  if (grid <= 0) return cudaSuccess;
+  if (mode == SLICE_FP32EMU)
+    return bn == 256 ? launch_t<256, SLICE_FP32EMU>(tmA, tmB, a, grid, st)
+                     : launch_t<128, SLICE_FP32EMU>(tmA, tmB, a, grid, st);
+  if (mode == SLICE_FP64EMU) return launch_t<128, SLICE_FP64EMU>(tmA, tmB, a, grid, st);
+  return launch_t<128, SLICE_LEVELS>(tmA, tmB, a, grid, st);
+}
