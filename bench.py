@@ -129,12 +129,13 @@ def cpu_oracle_rows(A, B, seconds: float, max_rows: int):
     bounded number of rows of the product; returns (rows, C_rows, seconds, threads)."""
     import oracle
     oracle.build()
+    # one row per thread first, to size the sample
+    _, used = oracle.gemm_omp_rows(A, B, 0, 1)
     t0 = time.perf_counter()
-    C1, used = oracle.gemm_omp_rows(A, B, 0, 1)
+    _, used = oracle.gemm_omp_rows(A, B, 0, used)
     t1 = time.perf_counter() - t0
-    rows = int(max(1, min(max_rows, seconds / max(t1, 1e-6))))
-    # whole rows split over the threads: keep a multiple of the thread count
-    rows = max(used, (rows // used) * used) if rows >= used else rows
+    reps = int(max(1, min(max_rows // used, seconds / max(t1, 1e-6))))
+    rows = reps * used
     t0 = time.perf_counter()
     Cr, used = oracle.gemm_omp_rows(A, B, 0, rows)
     dt = time.perf_counter() - t0
@@ -217,7 +218,11 @@ def ours(args):
     for kcls in (mm.KERNEL_SLICE_GEMM, mm.KERNEL_SPLIT):
         h.profile_read(kcls, reset=True)
     launches0 = h.stats()
-    sampler = ClockSampler(local if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        gpu_id = str(local)
+    sampler = ClockSampler(gpu_id)
     sampler.start()
     time.sleep(0.3)
     barrier()

@@ -54,6 +54,8 @@ def _mat(t, name):
     import torch
     if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or t.dim() != 2 or not t.is_cuda:
         raise TypeError(f"{name} must be a 2-D torch.float64 CUDA tensor")
+    if t.numel() == 0:
+        return t.data_ptr(), t.shape[0], t.shape[1], max(t.shape[1], 1)
     if t.shape[1] > 1 and t.stride(1) != 1:
         raise ValueError(f"{name} must have unit column stride (row-major)")
     ld = t.stride(0) if t.shape[0] > 1 else max(t.shape[1], 1)

@@ -81,12 +81,9 @@ __device__ __forceinline__ void store_tiles(Fp64Smem& sm, int buf, const double 
   }
 }
 
+// One 128 x 128 tile of C = A*B with its top-left corner at (m0, n0).
 template <int KIND>
-__global__ void __launch_bounds__(FTHREADS) fp64_gemm_kernel(const Fp64GemmArgs a) {
-  extern __shared__ __align__(16) uint8_t fsm_raw[];
-  Fp64Smem& sm = *reinterpret_cast<Fp64Smem*>(fsm_raw);
-  const int64_t m0 = static_cast<int64_t>(blockIdx.y) * FT;
-  const int64_t n0 = static_cast<int64_t>(blockIdx.x) * FT;
+__device__ __forceinline__ void fp64_tile(const Fp64GemmArgs& a, int64_t m0, int64_t n0, Fp64Smem& sm) {
   const bool vecA = ((a.lda & 1) == 0) && ((reinterpret_cast<uintptr_t>(a.A) & 15u) == 0);
   const bool vecB = ((a.ldb & 1) == 0) && ((reinterpret_cast<uintptr_t>(a.B) & 15u) == 0);
   const int t = threadIdx.x;
@@ -185,6 +182,31 @@ __global__ void __launch_bounds__(FTHREADS) fp64_gemm_kernel(const Fp64GemmArgs 
   }
 }
 
+template <int KIND>
+__global__ void __launch_bounds__(FTHREADS) fp64_gemm_kernel(const Fp64GemmArgs a) {
+  extern __shared__ __align__(16) uint8_t fsm_raw[];
+  Fp64Smem& sm = *reinterpret_cast<Fp64Smem*>(fsm_raw);
+  fp64_tile<KIND>(a, static_cast<int64_t>(blockIdx.y) * FT, static_cast<int64_t>(blockIdx.x) * FT, sm);
+}
+
+// Grouped: a persistent grid walks the tile list of many products; the tile
+// count is read from device memory so a captured graph can be replayed with
+// new work.
+template <int KIND>
+__global__ void __launch_bounds__(FTHREADS) fp64_grouped_kernel(const Fp64GemmArgs* __restrict__ probs,
+                                                                const TileRef* __restrict__ tiles,
+                                                                const int* __restrict__ ntiles_dev) {
+  extern __shared__ __align__(16) uint8_t fsm_raw[];
+  Fp64Smem& sm = *reinterpret_cast<Fp64Smem*>(fsm_raw);
+  const int nt = *ntiles_dev;
+  for (int t = blockIdx.x; t < nt; t += gridDim.x) {
+    const TileRef r = tiles[t];
+    const Fp64GemmArgs a = probs[r.prob];
+    fp64_tile<KIND>(a, static_cast<int64_t>(r.tm) * FT, static_cast<int64_t>(r.tn) * FT, sm);
+    __syncthreads();
+  }
+}
+
 __global__ void zero_c_kernel(double* C, int64_t m, int64_t n, int64_t ldc) {
   int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   int64_t total = m * n;
@@ -237,8 +259,22 @@ using namespace mmdev;
 cudaError_t fp64_gemm_prepare() {
   const int smem = static_cast<int>(sizeof(Fp64Smem));
   cudaError_t e = cudaFuncSetAttribute(fp64_gemm_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(fp64_gemm_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(fp64_gemm_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(fp64_grouped_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(fp64_grouped_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  return e;
+}
+
+int fp64_tile_size() { return FT; }
+
+cudaError_t launch_fp64_grouped(int kind, const Fp64GemmArgs* probs, const TileRef* tiles, const int* ntiles_dev,
+                                int grid, cudaStream_t st) {
+  const int smem = static_cast<int>(sizeof(Fp64Smem));
+  if (kind == 1)
+    fp64_grouped_kernel<1><<<grid, FTHREADS, smem, st>>>(probs, tiles, ntiles_dev);
+  else
+    fp64_grouped_kernel<2><<<grid, FTHREADS, smem, st>>>(probs, tiles, ntiles_dev);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_fp64_gemm(int kind, const Fp64GemmArgs& a, cudaStream_t st) {

@@ -115,6 +115,7 @@ int run_split(mm_handle_s* h, int mode01, const SplitLayout& L, char* ws, const 
 
 // grouped.cu / serve.cu
 void grouped_release(mm_handle_s* h);
+int grouped_run(mm_handle_s* h, int count, const mm_problem* probs, int precision, cudaStream_t st);
 void serve_shutdown(mm_handle_s* h);
 
 }  // namespace mmhost

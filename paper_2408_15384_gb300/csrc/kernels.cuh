@@ -23,6 +23,33 @@ cudaError_t launch_slice_cols(int mode, const double* B, int64_t k, int64_t n, i
 cudaError_t launch_fill_uniform(double* X, int64_t rows, int64_t cols, int64_t ld, uint64_t seed, uint64_t stream_id,
                                 int scale_mode, uint64_t exp_stream_id, cudaStream_t st);
 
+// Grouped splitting: per-problem record of one emulated product's operands and
+// workspace.
+struct GroupedSplit {
+  int64_t m, n, k, lda, ldb, kp;
+  const double* A;
+  const double* B;
+  int s;                  // slices (FP64-accuracy) or 3
+  int pad;
+  uint64_t* rowmax;
+  uint64_t* colmax;
+  int32_t* E;
+  int32_t* F;
+  uint16_t* slA;
+  uint16_t* slB;
+};
+// Virtual block offsets: off[kind][p] = first block of problem p for kernel
+// kind (0 row max, 1 column max, 2 slice rows, 3 slice cols); off[kind][count]
+// = total. Arrays of count+1 int64 in device memory.
+struct GroupedSplitArgs {
+  const GroupedSplit* probs;
+  const int64_t* off[4];
+  const int* count_dev;
+  uint32_t* err;
+};
+// mode01: 0 FP64-accuracy digits, 1 FP32-accuracy slices. grid: persistent blocks.
+cudaError_t launch_grouped_split(int mode01, const GroupedSplitArgs& a, int grid, cudaStream_t st);
+
 // ----------------------------------------------------------- slice_gemm.cu
 // Epilogue kinds of the slice GEMM.
 enum SliceMode { SLICE_FP32EMU = 0, SLICE_FP64EMU = 1, SLICE_LEVELS = 2 };
@@ -52,7 +79,7 @@ struct SliceGemmArgs {
   const SliceProblem* probs;       // grouped: problem records (device)
   const CUtensorMap* tmaps;        // grouped: 2 per problem (A, B), device, 64-byte aligned
   const TileRef* tiles;            // grouped: tile list (device)
-  int ntiles;
+  const int* ntiles_dev;           // grouped: tile count (device)
   uint32_t* err;
   uint64_t timeout_ns;
 };
@@ -76,9 +103,11 @@ struct Fp64GemmArgs {
 };
 // kind: 1 = DFMA tiles, 2 = DMMA (mma.sync m8n8k4 f64) tiles.
 cudaError_t launch_fp64_gemm(int kind, const Fp64GemmArgs& a, cudaStream_t st);
-// Grouped: one persistent launch over a tile list of many problems (device arrays).
-cudaError_t launch_fp64_gemm_grouped(int kind, const Fp64GemmArgs* probs, const TileRef* tiles, int ntiles,
-                                     int grid, cudaStream_t st);
+// Grouped: one persistent launch over a tile list of many problems (device
+// arrays; the tile count is read from device memory).
+cudaError_t launch_fp64_grouped(int kind, const Fp64GemmArgs* probs, const TileRef* tiles, const int* ntiles_dev,
+                                int grid, cudaStream_t st);
+int fp64_tile_size();
 cudaError_t fp64_gemm_prepare();
 cudaError_t launch_zero_c(double* C, int64_t m, int64_t n, int64_t ldc, cudaStream_t st);
 cudaError_t launch_peak_fp64(int kind, double* sink, int iters, int blocks, cudaStream_t st);

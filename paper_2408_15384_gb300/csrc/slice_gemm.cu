@@ -22,12 +22,12 @@
 // kernel walks the levels one after the other. Level d sums d-1 slice pairs;
 // with |slice| <= 2^7 each product is at most 2^14, so a K-chunk of Kc with
 // Kc * (d-1) <= 1024 sums to at most 2^24 and the f32 accumulator holds it
-// exactly. The epilogue adds each finished chunk, converted to int32, to an
-// int32 level sum kept in the spare TMEM columns (512 columns = two 128-wide
-// accumulator slots + the level sums). At the end of a level the sums join an
-// exact int64 fixed-point total X = sum_d 2^(8(s+1-d) - shift) L_d kept in C's
-// own storage; the last level converts X to double once and scales it by
-// 2^(E_i + F_j - 8(s+1) + shift).
+// exactly. The epilogue converts each finished chunk to integers and adds it,
+// shifted by its level weight, to an exact int64 fixed-point total
+// X = sum_d 2^(8(s+1-d) - shift) L_d kept in TMEM (512 columns = two 128-wide
+// accumulator slots + the low and high 32-bit planes of X). After the last
+// chunk of the tile X is converted to double once, scaled by
+// 2^(E_i + F_j - 8(s+1) + shift) and stored: C is written exactly once.
 #include <cstdint>
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -39,7 +39,6 @@ namespace mmdev {
 
 static constexpr int BM = 128;
 static constexpr int BK = 64;                 // bf16 elements per K block (128 bytes)
-static constexpr int SEG_CHUNKS = 120;        // chunks per int32 level sum (120 * 2^24 < 2^31)
 static constexpr int EPI_WARPS = 8;
 
 template <int BN, int MODE>
@@ -50,9 +49,10 @@ struct Cfg {
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
   static constexpr int STAGES = (BN == 256) ? 4 : 6;
   static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
-  // two accumulator slots; FP64-accuracy adds the int32 level sums (BN = 128)
+  // two accumulator slots; FP64-accuracy adds the int64 total's planes (BN = 128)
   static constexpr int TMEM_COLS = (MODE == SLICE_FP32EMU) ? 2 * BN : 512;
-  static constexpr int SUM_COL = 2 * BN;
+  static constexpr int XLO_COL = 2 * BN;
+  static constexpr int XHI_COL = 3 * BN;
   static constexpr int COLS_PER_THREAD = BN / 2;
 };
 
@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(Cfg<BN, MODE>::NUM_THREADS, 1)
   const uint32_t warp = warp_id(), lane = lane_id();
   const uint32_t smem_base = (smem_u32(smem_raw) + 1023u) & ~1023u;
   uint8_t* smem_gen = smem_raw + (smem_base - smem_u32(smem_raw));
-  const int ntiles = (args.probs == nullptr) ? args.single.tiles_m * args.single.tiles_n : args.ntiles;
+  const int ntiles = (args.probs == nullptr) ? args.single.tiles_m * args.single.tiles_n : *args.ntiles_dev;
 
   WaitCtl wc;
   wc.abort = &abort_flag;
@@ -342,76 +342,74 @@ __global__ void __launch_bounds__(Cfg<BN, MODE>::NUM_THREADS, 1)
         if (lane == 0) mbar_arrive(&acce_bar[slot]);
         ++chunk;
       } else {
-        int64_t* const xrow = reinterpret_cast<int64_t*>(P.C) + row * P.ldc;
+        double* const crow = P.C + row * P.ldc;
         const int s = P.s;
         const int nkb = P.nkb;
         const int fix_shift = P.fix_shift;
-        const uint32_t tsum = tmem_base + t_lane + static_cast<uint32_t>(C_::SUM_COL + col_off);
-        bool first_fold = true;
-        bool sum_live = false;   // the TMEM level sums hold data (else they read as zero)
+        const uint32_t txlo = tmem_base + t_lane + static_cast<uint32_t>(C_::XLO_COL + col_off);
+        const uint32_t txhi = tmem_base + t_lane + static_cast<uint32_t>(C_::XHI_COL + col_off);
+        bool fresh = true;   // X holds nothing yet (reads as zero)
         for (int d = 2; d <= s + 1 && ok; ++d) {
           const int kc = chunk_blocks(d);
           const int nch = (nkb + kc - 1) / kc;
+          // weight of level d in the fixed-point total (level output: unweighted)
+          const int lsh = (MODE == SLICE_LEVELS) ? 0 : 8 * (s + 1 - d) - fix_shift;
+          if (MODE == SLICE_LEVELS) fresh = true;
           for (int c = 0; c < nch; ++c, ++chunk) {
             const int slot = chunk & 1;
+            const bool level_end = (c == nch - 1);
+            const bool out = (MODE == SLICE_LEVELS) ? level_end : (level_end && d == s + 1);
             if (!mbar_wait(&accf_bar[slot], static_cast<uint32_t>(chunk >> 1) & 1u, wc)) { ok = false; break; }
             tc_fence_after();
 #pragma unroll 1
-            for (int cg = 0; cg < C_::COLS_PER_THREAD / 32; ++cg) {
-              uint32_t r[32], q[32];
-              tmem_ld32(tmem_base + t_lane + static_cast<uint32_t>(slot * BN + col_off + cg * 32), r);
-              if (sum_live) tmem_ld32(tsum + cg * 32, q);
+            for (int cg = 0; cg < C_::COLS_PER_THREAD / 16; ++cg) {
+              uint32_t r[16], lo[16], hi[16];
+              tmem_ld16(tmem_base + t_lane + static_cast<uint32_t>(slot * BN + col_off + cg * 16), r);
+              if (!fresh) {
+                tmem_ld16(txlo + cg * 16, lo);
+                tmem_ld16(txhi + cg * 16, hi);
+              } else {
+#pragma unroll
+                for (int v = 0; v < 16; ++v) lo[v] = hi[v] = 0u;
+              }
               tmem_ld_wait();
 #pragma unroll
-              for (int v = 0; v < 32; ++v) {
-                const int32_t a = __float2int_rz(__uint_as_float(r[v]));
-                q[v] = static_cast<uint32_t>(sum_live ? static_cast<int32_t>(q[v]) + a : a);
+              for (int v = 0; v < 16; ++v) {
+                const int64_t a = static_cast<int64_t>(__float2int_rz(__uint_as_float(r[v])));
+                const int64_t add = (lsh >= 0) ? (a << lsh) : ((a + (1ll << (-lsh - 1))) >> (-lsh));
+                const int64_t X = static_cast<int64_t>((static_cast<uint64_t>(hi[v]) << 32) | lo[v]) + add;
+                lo[v] = static_cast<uint32_t>(static_cast<uint64_t>(X));
+                hi[v] = static_cast<uint32_t>(static_cast<uint64_t>(X) >> 32);
               }
-              tmem_st32(tsum + cg * 32, q);
-            }
-            tmem_st_wait();
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&acce_bar[slot]);
-            sum_live = true;
-            const bool level_end = (c == nch - 1);
-            const bool seg_end = ((c + 1) % SEG_CHUNKS) == 0;
-            if (!(level_end || seg_end)) continue;
-            // ---- fold the level sums into the int64 total (or the level output)
-            const bool last_fold = level_end && (d == s + 1);
-            const int lsh = 8 * (s + 1 - d) - fix_shift;
-#pragma unroll 1
-            for (int cg = 0; cg < C_::COLS_PER_THREAD / 32; ++cg) {
-              uint32_t q[32];
-              tmem_ld32(tsum + cg * 32, q);
-              tmem_ld_wait();
-              if (!row_ok) continue;
+              if (!out) {
+                tmem_st16(txlo + cg * 16, lo);
+                tmem_st16(txhi + cg * 16, hi);
+              } else if (row_ok) {
 #pragma unroll 4
-              for (int v = 0; v < 32; ++v) {
-                const int64_t col = col0 + cg * 32 + v;
-                if (col >= n) break;
-                const int64_t lv = static_cast<int64_t>(static_cast<int32_t>(q[v]));
-                if (MODE == SLICE_LEVELS) {
-                  P.levels[(static_cast<int64_t>(d - 2) * P.m + row) * n + col] += lv;
-                } else {
-                  const int64_t add = (lsh >= 0) ? (lv << lsh) : ((lv + (1ll << (-lsh - 1))) >> (-lsh));
-                  const int64_t X = first_fold ? add : (xrow[col] + add);
-                  if (last_fold) {
-                    const int32_t Fj = __ldg(P.F + col);
-                    double out;
-                    if (Ei == EXP_NONFINITE || Fj == EXP_NONFINITE)
-                      out = __longlong_as_double(0x7FF8000000000000ll);
-                    else
-                      out = scale_pow2(__ll2double_rn(X), Ei + Fj - 8 * (s + 1) + fix_shift);
-                    reinterpret_cast<double*>(xrow)[col] = out;
-                  } else {
-                    xrow[col] = X;
+                for (int v = 0; v < 16; ++v) {
+                  const int64_t col = col0 + cg * 16 + v;
+                  if (col < n) {
+                    const int64_t X = static_cast<int64_t>((static_cast<uint64_t>(hi[v]) << 32) | lo[v]);
+                    if (MODE == SLICE_LEVELS) {
+                      P.levels[(static_cast<int64_t>(d - 2) * P.m + row) * n + col] = X;
+                    } else {
+                      const int32_t Fj = __ldg(P.F + col);
+                      double o;
+                      if (Ei == EXP_NONFINITE || Fj == EXP_NONFINITE)
+                        o = __longlong_as_double(0x7FF8000000000000ll);
+                      else
+                        o = scale_pow2(__ll2double_rn(X), Ei + Fj - 8 * (s + 1) + fix_shift);
+                      crow[col] = o;
+                    }
                   }
                 }
               }
             }
-            sum_live = false;
-            first_fold = false;
+            if (!out) tmem_st_wait();
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acce_bar[slot]);
+            fresh = false;
           }
         }
       }

@@ -164,15 +164,13 @@ __device__ __forceinline__ void fp32_slices3(uint64_t bits, int E, uint16_t* out
   out[2] = bf16_rne_take(M, e);
 }
 
-// -------------------------------------------------------------- scan kernels
-// One warp per row: maximum of |a| bits over the row.
-__global__ void row_absmax_kernel(const double* __restrict__ A, int64_t m, int64_t k, int64_t lda,
-                                  uint64_t* __restrict__ rowmax) {
-  int64_t row = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (row >= m) return;
+// ---------------------------------------------------------- kernel bodies
+// Row maximum of |a| bits for one row by one warp.
+__device__ __forceinline__ void row_absmax_body(const double* __restrict__ A, int64_t k, int64_t lda, int64_t row,
+                                                uint64_t* __restrict__ rowmax) {
   const double* a = A + row * lda;
   uint64_t mx = 0;
-  uint32_t lane = threadIdx.x & 31u;
+  const uint32_t lane = threadIdx.x & 31u;
   int64_t c = lane;
   for (; c + 96 < k; c += 128) {
     uint64_t v0 = dbits(__ldg(a + c)) & ABS_MASK, v1 = dbits(__ldg(a + c + 32)) & ABS_MASK;
@@ -181,49 +179,36 @@ __global__ void row_absmax_kernel(const double* __restrict__ A, int64_t m, int64
   }
   for (; c < k; c += 32) mx = max(mx, dbits(__ldg(a + c)) & ABS_MASK);
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) mx = max(mx, static_cast<uint64_t>(__shfl_xor_sync(0xffffffffu, static_cast<unsigned long long>(mx), o)));
+  for (int o = 16; o > 0; o >>= 1)
+    mx = max(mx, static_cast<uint64_t>(__shfl_xor_sync(0xffffffffu, static_cast<unsigned long long>(mx), o)));
   if (lane == 0) rowmax[row] = mx;
 }
 
-// Column maxima of B (k x n): thread per column over a range of rows, merged
-// with atomicMax (colmax must be zeroed first).
-__global__ void col_absmax_kernel(const double* __restrict__ B, int64_t k, int64_t n, int64_t ldb,
-                                  int64_t rows_per_block, unsigned long long* __restrict__ colmax) {
-  int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (j >= n) return;
-  int64_t r0 = static_cast<int64_t>(blockIdx.y) * rows_per_block;
-  int64_t r1 = min(k, r0 + rows_per_block);
+// Column maximum of |b| bits for column j over rows [r0, r1), merged with atomicMax.
+__device__ __forceinline__ void col_absmax_body(const double* __restrict__ B, int64_t ldb, int64_t j, int64_t r0,
+                                                int64_t r1, unsigned long long* __restrict__ colmax) {
   uint64_t mx = 0;
   for (int64_t r = r0; r < r1; ++r) mx = max(mx, dbits(__ldg(B + r * ldb + j)) & ABS_MASK);
   if (mx) atomicMax(colmax + j, static_cast<unsigned long long>(mx));
 }
 
-// ------------------------------------------------------------ slice kernels
-// A (m x k, rows scaled): thread handles 8 consecutive entries of one row.
-// Writes slices [S][m][kp] (bf16 bits), E[m]; raises NONFINITE in err.
+// Slices of 8 consecutive entries A[row][c0 .. c0+8) (rows scaled by E).
 template <int MODE>  // 0: FP64-accuracy digits, 1: FP32-accuracy bf16 slices
-__global__ void slice_rows_kernel(const double* __restrict__ A, int64_t m, int64_t k, int64_t lda,
-                                  const uint64_t* __restrict__ rowmax, int s, int64_t kp,
-                                  uint16_t* __restrict__ slices, int32_t* __restrict__ E,
-                                  uint32_t* __restrict__ err) {
-  int64_t row = blockIdx.x;
-  int64_t c0 = (static_cast<int64_t>(blockIdx.y) * blockDim.x + threadIdx.x) * 8;
-  if (row >= m || c0 >= k) return;
-  uint64_t mx = rowmax[row];
-  int32_t Ei = exponent_from_max(mx, MODE == 0 ? 2 : 1);
+__device__ __forceinline__ void slice_rows_body(const double* __restrict__ A, int64_t m, int64_t k, int64_t lda,
+                                                const uint64_t* __restrict__ rowmax, int s, int64_t kp,
+                                                uint16_t* __restrict__ slices, int32_t* __restrict__ E,
+                                                uint32_t* __restrict__ err, int64_t row, int64_t c0) {
+  const uint64_t mx = rowmax[row];
+  const int32_t Ei = exponent_from_max(mx, MODE == 0 ? 2 : 1);
   if (c0 == 0) {
     E[row] = Ei;
     if (Ei == EXP_NONFINITE) atomicOr(err, MM_DEV_ERR_NONFINITE);
   }
   const double* a = A + row * lda + c0;
   uint64_t vb[8];
-  int cnt = static_cast<int>((k - c0) < 8 ? (k - c0) : 8);
+  const int cnt = static_cast<int>((k - c0) < 8 ? (k - c0) : 8);
 #pragma unroll
-  for (int u = 0; u < 8; ++u) vb[u] = (u < cnt) ? dbits(__ldg(a + u)) : 0ull;
-  if (Ei == EXP_NONFINITE) {
-#pragma unroll
-    for (int u = 0; u < 8; ++u) vb[u] = 0ull;
-  }
+  for (int u = 0; u < 8; ++u) vb[u] = (u < cnt && Ei != EXP_NONFINITE) ? dbits(__ldg(a + u)) : 0ull;
   const int S = (MODE == 0) ? s : 3;
   const size_t plane = static_cast<size_t>(m) * kp;
   uint16_t dig[8][8];
@@ -235,7 +220,7 @@ __global__ void slice_rows_kernel(const double* __restrict__ A, int64_t m, int64
       fp32_slices3(vb[u], Ei, dig[u]);
   }
   uint16_t* dst = slices + row * kp + c0;
-  bool vec = (cnt == 8) && ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0);
+  const bool vec = (cnt == 8) && ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0);
   for (int p = 0; p < S; ++p) {
     uint16_t* d = dst + p * plane;
     if (vec) {
@@ -251,20 +236,18 @@ __global__ void slice_rows_kernel(const double* __restrict__ A, int64_t m, int64
   }
 }
 
-// B (k x n, columns scaled) -> slices [S][n][kp], transposed through shared
-// memory: a block covers 64 rows (k) x 32 columns (n) of B.
+// Slices of the 64 (k) x 32 (n) block of B at (k0, n0), transposed through
+// shared memory into [S][n][kp]. Needs 256 threads; contains __syncthreads.
 template <int MODE>
-__global__ void __launch_bounds__(256) slice_cols_kernel(const double* __restrict__ B, int64_t k, int64_t n,
-                                                         int64_t ldb, const uint64_t* __restrict__ colmax, int s,
-                                                         int64_t kp, uint16_t* __restrict__ slices,
-                                                         int32_t* __restrict__ F, uint32_t* __restrict__ err) {
+__device__ __forceinline__ void slice_cols_body(const double* __restrict__ B, int64_t k, int64_t n, int64_t ldb,
+                                                const uint64_t* __restrict__ colmax, int s, int64_t kp,
+                                                uint16_t* __restrict__ slices, int32_t* __restrict__ F,
+                                                uint32_t* __restrict__ err, int64_t k0, int64_t n0) {
   __shared__ uint64_t tile[64][33];
   __shared__ int32_t fexp[32];
-  int64_t k0 = static_cast<int64_t>(blockIdx.y) * 64;
-  int64_t n0 = static_cast<int64_t>(blockIdx.x) * 32;
-  int t = threadIdx.x;
+  const int t = threadIdx.x;
   if (t < 32) {
-    int64_t j = n0 + t;
+    const int64_t j = n0 + t;
     int32_t Fj = 0;
     if (j < n) {
       Fj = exponent_from_max(colmax[j], MODE == 0 ? 2 : 1);
@@ -275,47 +258,143 @@ __global__ void __launch_bounds__(256) slice_cols_kernel(const double* __restric
     }
     fexp[t] = Fj;
   }
-  // load 64 x 32 doubles: thread -> row t/4, columns (t%4)*8 .. +8
   {
-    int r = t >> 2, cb = (t & 3) * 8;
-    int64_t gr = k0 + r;
+    // load 64 x 32 doubles: thread -> row t/4, columns (t%4)*8 .. +8
+    const int r = t >> 2, cb = (t & 3) * 8;
+    const int64_t gr = k0 + r;
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-      int64_t gc = n0 + cb + u;
+      const int64_t gc = n0 + cb + u;
       tile[r][cb + u] = (gr < k && gc < n) ? dbits(__ldg(B + gr * ldb + gc)) : 0ull;
     }
   }
   __syncthreads();
   // compute: thread -> column t/8, k sub-range (t%8)*8 .. +8
-  int jl = t >> 3, kb = (t & 7) * 8;
-  int64_t j = n0 + jl, c0 = k0 + kb;
-  if (j >= n || c0 >= k) return;
-  int32_t Fj = fexp[jl];
-  int cnt = static_cast<int>((k - c0) < 8 ? (k - c0) : 8);
-  const int S = (MODE == 0) ? s : 3;
-  uint16_t dig[8][8];
+  const int jl = t >> 3, kb = (t & 7) * 8;
+  const int64_t j = n0 + jl, c0 = k0 + kb;
+  if (j < n && c0 < k) {
+    const int32_t Fj = fexp[jl];
+    const int cnt = static_cast<int>((k - c0) < 8 ? (k - c0) : 8);
+    const int S = (MODE == 0) ? s : 3;
+    uint16_t dig[8][8];
 #pragma unroll
-  for (int u = 0; u < 8; ++u) {
-    uint64_t b = (Fj == EXP_NONFINITE) ? 0ull : tile[kb + u][jl];
-    if (MODE == 0)
-      fp64_digits(b, 8 * s - Fj, s, dig[u]);
-    else
-      fp32_slices3(b, Fj, dig[u]);
+    for (int u = 0; u < 8; ++u) {
+      const uint64_t b = (Fj == EXP_NONFINITE) ? 0ull : tile[kb + u][jl];
+      if (MODE == 0)
+        fp64_digits(b, 8 * s - Fj, s, dig[u]);
+      else
+        fp32_slices3(b, Fj, dig[u]);
+    }
+    const size_t plane = static_cast<size_t>(n) * kp;
+    uint16_t* dst = slices + j * kp + c0;
+    const bool vec = (cnt == 8) && ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0);
+    for (int p = 0; p < S; ++p) {
+      uint16_t* d = dst + p * plane;
+      if (vec) {
+        uint4 w;
+        w.x = dig[0][p] | (static_cast<uint32_t>(dig[1][p]) << 16);
+        w.y = dig[2][p] | (static_cast<uint32_t>(dig[3][p]) << 16);
+        w.z = dig[4][p] | (static_cast<uint32_t>(dig[5][p]) << 16);
+        w.w = dig[6][p] | (static_cast<uint32_t>(dig[7][p]) << 16);
+        *reinterpret_cast<uint4*>(d) = w;
+      } else {
+        for (int u = 0; u < cnt; ++u) d[u] = dig[u][p];
+      }
+    }
   }
-  const size_t plane = static_cast<size_t>(n) * kp;
-  uint16_t* dst = slices + j * kp + c0;
-  bool vec = (cnt == 8) && ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0);
-  for (int p = 0; p < S; ++p) {
-    uint16_t* d = dst + p * plane;
-    if (vec) {
-      uint4 w;
-      w.x = dig[0][p] | (static_cast<uint32_t>(dig[1][p]) << 16);
-      w.y = dig[2][p] | (static_cast<uint32_t>(dig[3][p]) << 16);
-      w.z = dig[4][p] | (static_cast<uint32_t>(dig[5][p]) << 16);
-      w.w = dig[6][p] | (static_cast<uint32_t>(dig[7][p]) << 16);
-      *reinterpret_cast<uint4*>(d) = w;
+  __syncthreads();  // the tile is reused by the next block of a persistent loop
+}
+
+// -------------------------------------------------- single-product kernels
+__global__ void row_absmax_kernel(const double* __restrict__ A, int64_t m, int64_t k, int64_t lda,
+                                  uint64_t* __restrict__ rowmax) {
+  const int64_t row = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (row < m) row_absmax_body(A, k, lda, row, rowmax);
+}
+
+__global__ void col_absmax_kernel(const double* __restrict__ B, int64_t k, int64_t n, int64_t ldb,
+                                  int64_t rows_per_block, unsigned long long* __restrict__ colmax) {
+  const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const int64_t r0 = static_cast<int64_t>(blockIdx.y) * rows_per_block;
+  col_absmax_body(B, ldb, j, r0, min(k, r0 + rows_per_block), colmax);
+}
+
+template <int MODE>
+__global__ void slice_rows_kernel(const double* __restrict__ A, int64_t m, int64_t k, int64_t lda,
+                                  const uint64_t* __restrict__ rowmax, int s, int64_t kp,
+                                  uint16_t* __restrict__ slices, int32_t* __restrict__ E,
+                                  uint32_t* __restrict__ err) {
+  const int64_t row = blockIdx.x;
+  const int64_t c0 = (static_cast<int64_t>(blockIdx.y) * blockDim.x + threadIdx.x) * 8;
+  if (row < m && c0 < k) slice_rows_body<MODE>(A, m, k, lda, rowmax, s, kp, slices, E, err, row, c0);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(256) slice_cols_kernel(const double* __restrict__ B, int64_t k, int64_t n,
+                                                         int64_t ldb, const uint64_t* __restrict__ colmax, int s,
+                                                         int64_t kp, uint16_t* __restrict__ slices,
+                                                         int32_t* __restrict__ F, uint32_t* __restrict__ err) {
+  slice_cols_body<MODE>(B, k, n, ldb, colmax, s, kp, slices, F, err, static_cast<int64_t>(blockIdx.y) * 64,
+                        static_cast<int64_t>(blockIdx.x) * 32);
+}
+
+// --------------------------------------------------------- grouped kernels
+// Problem of virtual block vb: the last p with off[p] <= vb (binary search).
+__device__ __forceinline__ int find_problem(const int64_t* __restrict__ off, int count, int64_t vb) {
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(off + mid) <= vb) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Phase 1: row maxima (8 rows per block) then column maxima (256 columns x
+// 256 rows per block) of every problem.
+__global__ void __launch_bounds__(256) grouped_absmax_kernel(const GroupedSplitArgs a) {
+  const int count = *a.count_dev;
+  const int64_t t0 = a.off[0][count], t1 = a.off[1][count];
+  for (int64_t vb = blockIdx.x; vb < t0 + t1; vb += gridDim.x) {
+    if (vb < t0) {
+      const int p = find_problem(a.off[0], count, vb);
+      const GroupedSplit& g = a.probs[p];
+      const int64_t row = (vb - a.off[0][p]) * 8 + (threadIdx.x >> 5);
+      if (row < g.m) row_absmax_body(g.A, g.k, g.lda, row, g.rowmax);
     } else {
-      for (int u = 0; u < cnt; ++u) d[u] = dig[u][p];
+      const int64_t v = vb - t0;
+      const int p = find_problem(a.off[1], count, v);
+      const GroupedSplit& g = a.probs[p];
+      const int64_t lb = v - a.off[1][p];
+      const int64_t ncb = (g.n + 255) / 256;
+      const int64_t j = (lb % ncb) * 256 + threadIdx.x, r0 = (lb / ncb) * 256;
+      if (j < g.n) col_absmax_body(g.B, g.ldb, j, r0, min(g.k, r0 + 256), reinterpret_cast<unsigned long long*>(g.colmax));
+    }
+  }
+}
+
+// Phase 2: slices of every row of A (2048 entries per block) then of every
+// 64 x 32 block of B.
+template <int MODE>
+__global__ void __launch_bounds__(256) grouped_slice_kernel(const GroupedSplitArgs a) {
+  const int count = *a.count_dev;
+  const int64_t t2 = a.off[2][count], t3 = a.off[3][count];
+  for (int64_t vb = blockIdx.x; vb < t2 + t3; vb += gridDim.x) {
+    if (vb < t2) {
+      const int p = find_problem(a.off[2], count, vb);
+      const GroupedSplit& g = a.probs[p];
+      const int64_t lb = vb - a.off[2][p];
+      const int64_t nkc = (g.k + 2047) / 2048;
+      const int64_t row = lb / nkc, c0 = (lb % nkc) * 2048 + threadIdx.x * 8;
+      if (row < g.m && c0 < g.k) slice_rows_body<MODE>(g.A, g.m, g.k, g.lda, g.rowmax, g.s, g.kp, g.slA, g.E, a.err, row, c0);
+    } else {
+      const int64_t v = vb - t2;
+      const int p = find_problem(a.off[3], count, v);
+      const GroupedSplit& g = a.probs[p];
+      const int64_t lb = v - a.off[3][p];
+      const int64_t nnb = (g.n + 31) / 32;
+      slice_cols_body<MODE>(g.B, g.k, g.n, g.ldb, g.colmax, g.s, g.kp, g.slB, g.F, a.err, (lb / nnb) * 64,
+                            (lb % nnb) * 32);
     }
   }
 }
@@ -393,6 +472,17 @@ cudaError_t launch_slice_cols(int mode, const double* B, int64_t k, int64_t n, i
     slice_cols_kernel<0><<<grd, blk, 0, st>>>(B, k, n, ldb, colmax, s, kp, slices, F, err);
   else
     slice_cols_kernel<1><<<grd, blk, 0, st>>>(B, k, n, ldb, colmax, s, kp, slices, F, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grouped_split(int mode01, const GroupedSplitArgs& a, int grid, cudaStream_t st) {
+  grouped_absmax_kernel<<<grid, 256, 0, st>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (mode01 == 0)
+    grouped_slice_kernel<0><<<grid, 256, 0, st>>>(a);
+  else
+    grouped_slice_kernel<1><<<grid, 256, 0, st>>>(a);
   return cudaGetLastError();
 }
 
