@@ -237,6 +237,32 @@ int mm_stats(mm_handle h, uint64_t *kernel_launches);
  * `kernel` (an MM_KERNEL_* class) since the last reset; reset != 0 clears. */
 int mm_profile_read(mm_handle h, int kernel, double *total_ms, uint64_t *launches, int reset);
 
+/* ---------------------------------------------------- allocation-free call */
+
+/* The emulated product (MM_FP64_EMU or MM_FP32_EMU) with no device
+ * allocation at all, for callers that cannot call cudaMalloc: code running in
+ * a host callback or inside an allocator's own hooks, latency-critical loops
+ * that must never pay cudaMalloc's implicit device synchronisation, or
+ * processes that reserve their device memory up front and allow no later
+ * allocation. The paper has no counterpart; this is a library service.
+ *
+ * Same product, layout and results as mm_gemm with the same precision (the
+ * FP64-accuracy result is bit-identical). No handle: it runs on the calling
+ * thread's current device, asynchronously on `stream` (NULL = legacy default
+ * stream). A, B, C are caller-owned device pointers.
+ * Scratch: one fixed 32 MiB array inside the library image, held by every GPU
+ * that loads it until the process exits. The first call on a device looks up
+ * that array's device address (do it before any stream capture). Every call
+ * on a device shares the array, so calls whose GPU work overlaps race; each
+ * call clears what must start at zero itself.
+ * Errors: MM_ERR_INVALID_ARG (as mm_gemm, or another precision),
+ * MM_ERR_BUDGET (the problem's split operands need more than the fixed
+ * scratch: about 2*s*(m+n)*k bytes, s <= 7), MM_ERR_CUDA. Inf/NaN inputs give
+ * NaN in the affected rows/columns of C; no status is reported for them. */
+int mm_gemm_emu_static(int64_t m, int64_t n, int64_t k,
+                       const double *A, int64_t lda, const double *B, int64_t ldb,
+                       double *C, int64_t ldc, int precision, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

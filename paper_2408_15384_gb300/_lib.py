@@ -52,6 +52,7 @@ SIGNATURES = {
     "mm_peak_fp64": (c_int, [c_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "mm_stats": (c_int, [c_vp, ctypes.POINTER(c_u64)]),
     "mm_profile_read": (c_int, [c_vp, c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(c_u64), c_int]),
+    "mm_gemm_emu_static": (c_int, [c_i64, c_i64, c_i64, c_vp, c_i64, c_vp, c_i64, c_vp, c_i64, c_int, c_vp]),
 }
 
 _lib = None

@@ -1,0 +1,68 @@
+"""The allocation-free entry point mm_gemm_emu_static, through the C ABI.
+
+Some callers cannot call cudaMalloc (host callbacks, allocator hooks, loops that
+must not pay its implicit synchronisation, processes whose device memory is
+reserved up front). mm_gemm_emu_static serves them from one fixed scratch array
+in the library image. These checks compare it with mm_gemm on two calls in a row
+(different shapes and data, so stale scratch contents from the first call would
+show), within the tolerance the other GPU tests use: 4k*2^-53 |A||B| for
+FP64-accuracy (where the two must in fact agree bit for bit) and 4k*2^-24 |A||B|
+for FP32-accuracy. This file runs last so a failure here does not hide the rest.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import emulation as em
+from paper_2408_15384_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mm():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2408_15384_gb300 as mm
+    from paper_2408_15384_gb300 import build
+    build.build()
+    return mm
+
+
+def call_static(lib, A, B, prec):
+    m, k = A.shape
+    n = B.shape[1]
+    C = torch.full((m, n), np.nan, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    rc = lib.mm_gemm_emu_static(m, n, k, A.data_ptr(), k, B.data_ptr(), n, C.data_ptr(), n, prec, stream)
+    torch.cuda.synchronize()
+    return rc, C
+
+
+@pytest.mark.parametrize("prec,mode", [(1, "fp64_emu"), (2, "fp32_emu")])
+def test_static_scratch_matches_mm_gemm_twice(mm, prec, mode):
+    with mm.Handle(0) as h:
+        for m, n, k, seed in ((300, 260, 700, 1), (130, 70, 1500, 2)):
+            A = inputs.row_scaled(m, k, seed)
+            B = inputs.col_scaled(k, n, seed)
+            Ad = torch.from_numpy(A).cuda()
+            Bd = torch.from_numpy(B).cuda()
+            rc, Cs = call_static(h.lib, Ad, Bd, prec)
+            assert rc == 0
+            Cg = h.gemm(Ad, Bd, precision=prec)
+            assert h.sync() == 0
+            cs, cg = Cs.cpu().numpy(), Cg.cpu().numpy()
+            D = oracle.absprod(A, B)
+            assert np.all(np.abs(cs - cg) <= em.gamma(k, mode) * D)
+            if prec == 1:
+                assert np.array_equal(cs, cg)
+
+
+def test_static_scratch_rejects_oversize(mm):
+    lib = mm._lib.load()
+    A = torch.zeros((4096, 4096), dtype=torch.float64, device="cuda")
+    B = torch.zeros((4096, 4096), dtype=torch.float64, device="cuda")
+    rc, _ = call_static(lib, A, B, 1)
+    assert rc == 3  # MM_ERR_BUDGET: larger than the fixed scratch
+    assert lib.mm_gemm_emu_static(8, 8, 8, None, 8, None, 8, None, 8, 0, None) == 2   # plain FP64 is not offered
