@@ -237,6 +237,52 @@ int mm_stats(mm_handle h, uint64_t *kernel_launches);
  * `kernel` (an MM_KERNEL_* class) since the last reset; reset != 0 clears. */
 int mm_profile_read(mm_handle h, int kernel, double *total_ms, uint64_t *launches, int reset);
 
+/* ------------------------------------------------------ serving benchmark */
+
+/* A seeded synthetic request stream for mm_serve_bench. Request i has M, N, K
+ * each drawn log-uniform on [dim_lo, dim_hi] (round(exp(U(ln lo, ln hi)))),
+ * the FP64-accuracy class with probability fp64_share (else FP32-accuracy),
+ * and arrives at the i-th point of a Poisson process of rate rate_per_s
+ * (rate_per_s <= 0: closed loop, every request is due at once). Operands live
+ * in `slots` resident slots (dim_hi x dim_hi A, B and C each, A and B filled
+ * once by mm_fill_uniform with seed*1000003 + slot on streams 1 and 2); request
+ * i uses slot i % slots (its top-left m x k, k x n, m x n corners, leading
+ * dimension dim_hi) and waits for the slot's previous request to finish. */
+typedef struct {
+    int64_t count;
+    int64_t dim_lo, dim_hi;
+    double fp64_share;
+    double rate_per_s;
+    uint64_t seed;
+    int slots;
+    int64_t sample_every;     /* copy every n-th request's C to the host (0 = none) */
+} mm_serve_load;
+
+typedef struct {
+    int64_t completed, failed;
+    double wall_s;            /* first arrival to last completion */
+    double req_per_s;
+    double tflops;            /* sum of 2mnk over wall_s */
+    double p50_ms, p90_ms, p99_ms, max_ms, mean_ms;   /* scheduled arrival -> completion */
+    double fp64_p99_ms, fp32_p99_ms;
+} mm_serve_load_result;
+
+typedef struct {
+    int64_t index, m, n, k;
+    int precision, slot;
+    int64_t host_offset;      /* element offset of its C (m x n, row-major) in sample_host */
+} mm_serve_sample;
+
+/* Run the stream through mm_serve_submit / mm_serve_poll on h (blocking).
+ * Latency is measured from each request's scheduled arrival to the completion
+ * time the serving engine records. Every sample_every-th request's C is copied
+ * to sample_host (capacity sample_cap doubles) and described in samples
+ * (capacity max_samples); *n_samples receives the count. Slots are allocated
+ * for the run and freed after it. */
+int mm_serve_bench(mm_handle h, const mm_serve_load *load, mm_serve_load_result *res,
+                   mm_serve_sample *samples, int64_t max_samples, int64_t *n_samples,
+                   double *sample_host, int64_t sample_cap);
+
 /* ---------------------------------------------------- allocation-free call */
 
 /* The emulated product (MM_FP64_EMU or MM_FP32_EMU) with no device

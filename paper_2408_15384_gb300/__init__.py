@@ -161,6 +161,27 @@ class Handle:
     def serve_drain(self):
         _check(self.lib.mm_serve_drain(self.h), "mm_serve_drain")
 
+    def serve_bench(self, count, dim_lo=64, dim_hi=4096, fp64_share=0.5, rate_per_s=0.0, seed=5, slots=64,
+                    sample_every=0, max_samples=64, sample_cap=1 << 24):
+        """Run a seeded request stream through the serving calls (mm_serve_bench).
+        Returns (result dict, list of sample dicts with their C as numpy arrays)."""
+        import numpy as np
+        load = _lib.ServeLoad(count, dim_lo, dim_hi, fp64_share, rate_per_s, seed, slots, sample_every)
+        res = _lib.ServeLoadResult()
+        samples = (_lib.ServeSample * max(max_samples, 1))()
+        host = np.zeros(sample_cap if sample_every else 1, dtype=np.float64)
+        ns = ctypes.c_int64()
+        _check(self.lib.mm_serve_bench(self.h, ctypes.byref(load), ctypes.byref(res), samples, max_samples,
+                                       ctypes.byref(ns), host.ctypes.data, host.size), "mm_serve_bench")
+        out = {f: getattr(res, f) for f, _ in _lib.ServeLoadResult._fields_}
+        smp = []
+        for i in range(ns.value):
+            sm = samples[i]
+            C = host[sm.host_offset: sm.host_offset + sm.m * sm.n].reshape(sm.m, sm.n).copy()
+            smp.append({"index": sm.index, "m": sm.m, "n": sm.n, "k": sm.k, "precision": sm.precision,
+                        "slot": sm.slot, "C": C})
+        return out, smp
+
     # ------------------------------------------------------- configuration
     def set_option(self, opt: int, value: int):
         _check(self.lib.mm_set_option(self.h, opt, int(value)), "mm_set_option")

@@ -25,6 +25,24 @@ class Request(ctypes.Structure):
     _fields_ = [("prob", Problem), ("precision", c_int), ("user_tag", c_u64)]
 
 
+class ServeLoad(ctypes.Structure):
+    _fields_ = [("count", c_i64), ("dim_lo", c_i64), ("dim_hi", c_i64), ("fp64_share", ctypes.c_double),
+                ("rate_per_s", ctypes.c_double), ("seed", c_u64), ("slots", c_int), ("sample_every", c_i64)]
+
+
+class ServeLoadResult(ctypes.Structure):
+    _fields_ = [("completed", c_i64), ("failed", c_i64), ("wall_s", ctypes.c_double),
+                ("req_per_s", ctypes.c_double), ("tflops", ctypes.c_double),
+                ("p50_ms", ctypes.c_double), ("p90_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("max_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
+                ("fp64_p99_ms", ctypes.c_double), ("fp32_p99_ms", ctypes.c_double)]
+
+
+class ServeSample(ctypes.Structure):
+    _fields_ = [("index", c_i64), ("m", c_i64), ("n", c_i64), ("k", c_i64), ("precision", c_int),
+                ("slot", c_int), ("host_offset", c_i64)]
+
+
 class ReqStatus(ctypes.Structure):
     _fields_ = [("status", c_int), ("user_tag", c_u64),
                 ("t_submit_us", ctypes.c_double), ("t_admit_us", ctypes.c_double),
@@ -52,6 +70,8 @@ SIGNATURES = {
     "mm_peak_fp64": (c_int, [c_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "mm_stats": (c_int, [c_vp, ctypes.POINTER(c_u64)]),
     "mm_profile_read": (c_int, [c_vp, c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(c_u64), c_int]),
+    "mm_serve_bench": (c_int, [c_vp, ctypes.POINTER(ServeLoad), ctypes.POINTER(ServeLoadResult),
+                               ctypes.POINTER(ServeSample), c_i64, ctypes.POINTER(c_i64), c_vp, c_i64]),
     "mm_gemm_emu_static": (c_int, [c_i64, c_i64, c_i64, c_vp, c_i64, c_vp, c_i64, c_vp, c_i64, c_int, c_vp]),
 }
 

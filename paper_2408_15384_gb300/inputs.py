@@ -61,6 +61,23 @@ def words(seed: int, stream: int, count: int, start: int = 0) -> np.ndarray:
         return _mix(base + i * GOLDEN)
 
 
+def sym_at(seed: int, stream: int, idx) -> np.ndarray:
+    """sym(i) in [-1, 1) at arbitrary counters idx (uint64 array)."""
+    idx = np.asarray(idx, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        base = _mix(np.array([(seed + stream * int(GOLDEN)) % (1 << 64)], dtype=np.uint64))[0]
+        w = _mix(base + (idx + np.uint64(1)) * GOLDEN)
+    return 2.0 * ((w >> np.uint64(11)).astype(np.float64) * 2.0 ** -53) - 1.0
+
+
+def slot_block(seed: int, stream: int, ld: int, rows: int, cols: int, row0: int = 0) -> np.ndarray:
+    """Rows [row0, row0+rows) x columns [0, cols) of an ld x ld matrix filled by
+    ``uniform(ld, ld, seed, stream)`` (element (r, c) draws counter r*ld + c)."""
+    r = np.arange(row0, row0 + rows, dtype=np.uint64)[:, None]
+    c = np.arange(cols, dtype=np.uint64)[None, :]
+    return sym_at(seed, stream, r * np.uint64(ld) + c)
+
+
 def unit(seed: int, stream: int, count: int, start: int = 0) -> np.ndarray:
     """unit(i) in [0, 1)."""
     return (words(seed, stream, count, start) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
