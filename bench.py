@@ -193,7 +193,7 @@ def ours(args):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     N = args.n
-    h = mm.Handle(local)
+    h = mm.Handle(local, budget_bytes=40 << 30)
     stream = torch.cuda.current_stream(dev)
 
     seed = 3 + 1000 * rank
@@ -305,6 +305,9 @@ def ours(args):
         e2e_s = (time.perf_counter() - t0) / reps
         extra["e2e"] = {"value": flop / e2e_s / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": 16 * N * N,
                         "d2h_bytes_per_step": 8 * N * N}
+        # ---------------- serving: capacity (closed loop), then Poisson arrivals at 80 % of it
+        if not args.no_serve:
+            extra["serve"] = serve_leg(h, args, mm, inputs)
         # ---------------- CPU oracle on a bounded sample, and the measured error of those rows
         if not args.no_cpu_baseline:
             rows, Cr, dt, used = cpu_oracle_rows(An, Bn, args.cpu_seconds, 2048)
@@ -344,6 +347,41 @@ def ours(args):
         dist.destroy_process_group()
 
 
+def serve_leg(h, args, mm, inputs):
+    """The serving workload: M, N, K each log-uniform on [64, 4096], accuracy
+    class FP64/FP32 50:50, entries uniform[-1,1), admission under 40 GB.
+    Capacity = closed-loop completion rate; then args.serve_requests requests
+    arrive as a Poisson process at 80 % of it. Latency = scheduled arrival ->
+    completion. A few sampled outputs are checked against the CPU oracle
+    (their first two rows) when the CPU-baseline leg is on."""
+    cap_res, _ = h.serve_bench(10000, 64, 4096, 0.5, 0.0, seed=5, slots=64)
+    capacity = cap_res["req_per_s"]
+    rate = 0.8 * capacity
+    res, smp = h.serve_bench(args.serve_requests, 64, 4096, 0.5, rate, seed=6, slots=64,
+                             sample_every=max(1, args.serve_requests // 16), max_samples=16, sample_cap=1 << 26)
+    out = {"requests": args.serve_requests, "load": 0.8, "capacity_req_per_s": capacity,
+           "offered_req_per_s": rate, "achieved_req_per_s": res["req_per_s"],
+           "p50_ms": res["p50_ms"], "p90_ms": res["p90_ms"], "p99_ms": res["p99_ms"], "max_ms": res["max_ms"],
+           "fp64_class_p99_ms": res["fp64_p99_ms"], "fp32_class_p99_ms": res["fp32_p99_ms"],
+           "tflops": res["tflops"], "completed": res["completed"], "failed": res["failed"],
+           "budget_gb": 40, "dims": "log-uniform [64, 4096]", "classes": "fp64/fp32 50:50"}
+    if not args.no_cpu_baseline and smp:
+        import numpy as np
+        import oracle
+        from oracle import emulation as em
+        worst = 0.0
+        for sm in smp[:6]:
+            sd = 6 * 1000003 + sm["slot"]
+            A2 = inputs.slot_block(sd, 1, 4096, 2, sm["k"])
+            B = inputs.slot_block(sd, 2, 4096, sm["k"], sm["n"])
+            mode = "fp64_emu" if sm["precision"] == 1 else "fp32_emu"
+            D = oracle.absprod(A2, B)
+            worst = max(worst, float(np.max(np.abs(sm["C"][:2] - oracle.gemm(A2, B)) / (em.gamma(sm["k"], mode) * D))))
+        out["sampled_max_err_over_bound"] = worst
+        out["err_sample"] = f"first 2 rows of {min(len(smp), 6)} sampled requests vs the FP64 triple-loop oracle"
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -354,6 +392,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="headline line only")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
+    ap.add_argument("--serve-requests", type=int, default=100000)
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)

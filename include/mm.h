@@ -181,7 +181,11 @@ enum {
     MM_OPT_SERVE_MAX_BATCH = 4,   /* requests per grouped launch (default 64) */
     MM_OPT_SERVE_STREAMS = 5,     /* serving streams (default 2) */
     MM_OPT_FP64_KERNEL = 6,       /* 0 = automatic, 1 = DFMA tiles, 2 = DMMA (mma.sync f64) tiles */
-    MM_OPT_PROFILE = 7            /* 1 = time every kernel launch with CUDA events (see mm_profile_read) */
+    MM_OPT_PROFILE = 7,           /* 1 = time every kernel launch with CUDA events (see mm_profile_read) */
+    MM_OPT_CTA_PAIR = 8,          /* emulated products: 0 = automatic, 1 = one CTA per 128-row tile,
+                                     2 = CTA pairs (cta_group::2) on 256-row tiles */
+    MM_OPT_TILE_N = 9             /* FP64-accuracy tile width: 0 = automatic, 128 or 256 columns.
+                                     Every choice gives the same bits. */
 };
 
 /* Kernel classes for mm_profile_read. */

@@ -21,6 +21,8 @@ PRECISIONS = {"fp64": FP64, "fp64_emu": FP64_EMU, "fp32_emu": FP32_EMU}
 OK, PENDING = 0, 1
 OPT_SLICES, OPT_TIMEOUT_MS, OPT_AUTOTUNE, OPT_SERVE_MAX_BATCH, OPT_SERVE_STREAMS, OPT_FP64_KERNEL = 1, 2, 3, 4, 5, 6
 OPT_PROFILE = 7
+OPT_CTA_PAIR = 8
+OPT_TILE_N = 9
 KERNEL_SLICE_GEMM, KERNEL_SPLIT, KERNEL_FP64_GEMM = 0, 1, 2
 
 

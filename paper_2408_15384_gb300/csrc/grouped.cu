@@ -188,7 +188,7 @@ static cudaError_t launch_emu_group(mm_handle_s* h, bool fp64, const EmuLayout& 
   cudaError_t e = cudaMemsetAsync(ws, 0, colmax_cap, st);
   if (e == cudaSuccess) e = launch_grouped_split(fp64 ? 0 : 1, ga, h->sm_count * 8, st);
   if (e == cudaSuccess)
-    e = launch_slice_gemm(fp64 ? SLICE_FP64EMU : SLICE_FP32EMU, 128, &dummy, &dummy, sa, h->sm_count, st);
+    e = launch_slice_gemm(fp64 ? SLICE_FP64EMU : SLICE_FP32EMU, 128, 1, &dummy, &dummy, sa, h->sm_count, st);
   return e;
 }
 

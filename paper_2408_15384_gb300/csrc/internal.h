@@ -52,6 +52,9 @@ struct mm_handle_s {
   int opt_fp64_kernel = 0;
   int opt_fp32_bn = 0;
   bool opt_profile = false;
+  int opt_cta_pair = 0;
+  int opt_tile_n = 0;        // FP64-accuracy tile width (0 = automatic, 128, 256)
+  int max_pairs_fp32 = 0, max_pairs_fp64 = 0;   // co-resident CTA pairs of the pair kernels
 
   // profiling: (start, end) event pairs per kernel class, drained by mm_profile_read
   std::mutex prof_mu;

@@ -84,12 +84,15 @@ struct SliceGemmArgs {
   uint64_t timeout_ns;
 };
 
-// Tile width (columns of C per CTA): 128 or 256. grid = persistent CTA count.
-cudaError_t launch_slice_gemm(int mode, int bn, const CUtensorMap* tmA, const CUtensorMap* tmB,
+// bn: tile width (columns of C); cg: CTAs per tile (1, or 2 for a CTA pair on
+// 256-row tiles). grid = persistent CTA count (a multiple of 2 when cg = 2).
+// With cg = 2, tiles_m counts 256-row tiles and B's tensor map box has bn/2 rows.
+cudaError_t launch_slice_gemm(int mode, int bn, int cg, const CUtensorMap* tmA, const CUtensorMap* tmB,
                               const SliceGemmArgs& a, int grid, cudaStream_t st);
 // Set the dynamic shared memory limits of every instantiation (once per device).
 cudaError_t slice_gemm_prepare();
-int slice_gemm_smem_bytes(int bn);
+// Largest number of co-resident CTA pairs of the pair kernel for a mode.
+int slice_gemm_max_pairs(int mode);
 
 // ------------------------------------------------------------- fp64_gemm.cu
 struct Fp64GemmArgs {

@@ -235,10 +235,20 @@ int run_emulated(mm_handle_s* h, int precision, int64_t m, int64_t n, int64_t k,
     rc = run_split(h, fp64 ? 0 : 1, L, ws, A, lda, B, ldb, st);
   }
   if (rc == MM_OK) {
-    const int bn = pick_bn(h, precision, m, n);
+    // CTA pairs (256-row tiles, half of B per CTA) unless the product is one tile high
+    const int pairs_avail = fp64 ? h->max_pairs_fp64 : h->max_pairs_fp32;
+    int cg = (h->opt_cta_pair == 1) ? 1 : (h->opt_cta_pair == 2 ? 2 : (m > 128 ? 2 : 1));
+    if (pairs_avail <= 0) cg = 1;
+    // 256-wide tiles whenever the product is wider than one 128-wide tile (the
+    // tensor cores need N = 256 per MMA for full rate); FP32-accuracy pairs always 256
+    int bn;
+    if (fp64)
+      bn = (h->opt_tile_n == 128 || h->opt_tile_n == 256) ? h->opt_tile_n : (n > 128 ? 256 : 128);
+    else
+      bn = (cg == 2) ? 256 : pick_bn(h, precision, m, n);
     CUtensorMap tmA, tmB;
     if (!encode_slices_tmap(h, &tmA, ws + L.off_sa, k, m, L.S, L.kp, 128) ||
-        !encode_slices_tmap(h, &tmB, ws + L.off_sb, k, n, L.S, L.kp, bn)) {
+        !encode_slices_tmap(h, &tmB, ws + L.off_sb, k, n, L.S, L.kp, bn / cg)) {
       rc = MM_ERR_CUDA;
     } else {
       SliceGemmArgs a;
@@ -248,7 +258,7 @@ int run_emulated(mm_handle_s* h, int precision, int64_t m, int64_t n, int64_t k,
       P.nkb = static_cast<int>((k + 63) / 64);
       P.s = s;
       P.fix_shift = fp64 ? fixed_shift(s, k) : 0;
-      P.tiles_m = static_cast<int>((m + 127) / 128);
+      P.tiles_m = static_cast<int>((m + 128 * cg - 1) / (128 * cg));
       P.tiles_n = static_cast<int>((n + bn - 1) / bn);
       P.E = reinterpret_cast<const int32_t*>(ws + L.off_E);
       P.F = reinterpret_cast<const int32_t*>(ws + L.off_F);
@@ -258,12 +268,12 @@ int run_emulated(mm_handle_s* h, int precision, int64_t m, int64_t n, int64_t k,
       a.err = h->d_err;
       a.timeout_ns = static_cast<uint64_t>(h->opt_timeout_ms) * 1000000ull;
       const int ntiles = P.tiles_m * P.tiles_n;
-      const int grid = std::min(ntiles, h->sm_count);
+      const int grid = (cg == 2) ? 2 * std::min(ntiles, pairs_avail) : std::min(ntiles, h->sm_count);
       const int mode = levels ? SLICE_LEVELS : (fp64 ? SLICE_FP64EMU : SLICE_FP32EMU);
       cudaError_t e;
       {
         ProfScope ps(h, MM_KERNEL_SLICE_GEMM, st);
-        e = launch_slice_gemm(mode, bn, &tmA, &tmB, a, grid, st);
+        e = launch_slice_gemm(mode, bn, cg, &tmA, &tmB, a, grid, st);
       }
       rc = cuda_status(e, "slice gemm");
       count_launch(h, 1);
@@ -360,6 +370,8 @@ int mm_create(mm_handle* out, int device, size_t mem_budget_bytes) {
   }
   cudaError_t e1 = slice_gemm_prepare();
   cudaError_t e2 = fp64_gemm_prepare();
+  h->max_pairs_fp32 = slice_gemm_max_pairs(SLICE_FP32EMU);
+  h->max_pairs_fp64 = slice_gemm_max_pairs(SLICE_FP64EMU);
   if (e1 != cudaSuccess || e2 != cudaSuccess) {
     cudaFree(h->d_err);
     cudaMemPoolDestroy(h->pool);
@@ -459,6 +471,14 @@ int mm_set_option(mm_handle h, int option, int64_t value) {
       h->opt_fp64_kernel = static_cast<int>(value);
       return MM_OK;
     case MM_OPT_PROFILE: h->opt_profile = value != 0; return MM_OK;
+    case MM_OPT_CTA_PAIR:
+      if (value < 0 || value > 2) return MM_ERR_INVALID_ARG;
+      h->opt_cta_pair = static_cast<int>(value);
+      return MM_OK;
+    case MM_OPT_TILE_N:
+      if (value != 0 && value != 128 && value != 256) return MM_ERR_INVALID_ARG;
+      h->opt_tile_n = static_cast<int>(value);
+      return MM_OK;
     default: return MM_ERR_INVALID_ARG;
   }
 }
@@ -473,6 +493,8 @@ int mm_get_option(mm_handle h, int option, int64_t* value) {
     case MM_OPT_SERVE_STREAMS: *value = h->opt_serve_streams; return MM_OK;
     case MM_OPT_FP64_KERNEL: *value = h->opt_fp64_kernel; return MM_OK;
     case MM_OPT_PROFILE: *value = h->opt_profile; return MM_OK;
+    case MM_OPT_CTA_PAIR: *value = h->opt_cta_pair; return MM_OK;
+    case MM_OPT_TILE_N: *value = h->opt_tile_n; return MM_OK;
     default: return MM_ERR_INVALID_ARG;
   }
 }

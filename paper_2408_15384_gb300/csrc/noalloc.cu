@@ -149,6 +149,6 @@ int mm_gemm_emu_static(int64_t m, int64_t n, int64_t k, const double* A, int64_t
   a.err = err;
   a.timeout_ns = 2000ull * 1000000ull;
   const int grid = std::min(P.tiles_m * P.tiles_n, d.sm_count);
-  e = launch_slice_gemm(fp64 ? SLICE_FP64EMU : SLICE_FP32EMU, bn, &tmA, &tmB, a, grid, st);
+  e = launch_slice_gemm(fp64 ? SLICE_FP64EMU : SLICE_FP32EMU, bn, 1, &tmA, &tmB, a, grid, st);
   return cuda_status(e, "slice gemm");
 }

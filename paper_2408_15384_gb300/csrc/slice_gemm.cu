@@ -39,21 +39,32 @@ namespace mmdev {
 
 static constexpr int BM = 128;
 static constexpr int BK = 64;                 // bf16 elements per K block (128 bytes)
-static constexpr int EPI_WARPS = 8;
+static constexpr int SEG_CHUNKS = 120;        // chunks per int32 level sum (120 * 2^24 < 2^31)
 
-template <int BN, int MODE>
+// CG = CTAs per output tile: 1, or 2 for a CTA pair (cta_group::2) computing a
+// 256-row tile, each CTA holding 128 rows of A and BN/2 rows of B in shared
+// memory and its 128 rows of the accumulator in its own TMEM.
+template <int BN, int MODE, int CG>
 struct Cfg {
-  static constexpr int NUM_THREADS = 64 + 32 * EPI_WARPS;
+  // epilogue warps: 8 (two per TMEM lane quadrant); 16 for 256-wide FP64-accuracy
+  // tiles, whose threads keep their columns' int32 level sums in registers
+  static constexpr bool REG_SUMS = (BN == 256) && (MODE != SLICE_FP32EMU);
+  static constexpr int EPI_WARPS = REG_SUMS ? 16 : 8;
+  static constexpr int EPI_WARP0 = 2;
+  static constexpr int NUM_THREADS = 32 * (EPI_WARP0 + EPI_WARPS);
   static constexpr int A_BYTES = BM * BK * 2;
-  static constexpr int B_BYTES = BN * BK * 2;
+  static constexpr int B_BYTES = (BN / CG) * BK * 2;
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-  static constexpr int STAGES = (BN == 256) ? 4 : 6;
+  static constexpr int SMEM_LIMIT = 232448 - 1024 - 256;   // max dynamic smem - alignment - static
+  static constexpr int STAGES_FIT = SMEM_LIMIT / STAGE_BYTES;
+  static constexpr int STAGES = STAGES_FIT > 10 ? 10 : STAGES_FIT;
   static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
   // two accumulator slots; FP64-accuracy adds the int64 total's planes (BN = 128)
   static constexpr int TMEM_COLS = (MODE == SLICE_FP32EMU) ? 2 * BN : 512;
   static constexpr int XLO_COL = 2 * BN;
   static constexpr int XHI_COL = 3 * BN;
-  static constexpr int COLS_PER_THREAD = BN / 2;
+  static constexpr int COLS_PER_THREAD = BN / (EPI_WARPS / 4);
+  static constexpr int TILE_M = BM * CG;
 };
 
 // K blocks per chunk at level d (d - 1 pairs): Kc * (d-1) <= 1024.
@@ -166,11 +177,11 @@ __device__ __forceinline__ TileJob get_job(const SliceGemmArgs& a, const CUtenso
   return j;
 }
 
-template <int BN, int MODE>
-__global__ void __launch_bounds__(Cfg<BN, MODE>::NUM_THREADS, 1)
+template <int BN, int MODE, int CG>
+__global__ void __launch_bounds__(Cfg<BN, MODE, CG>::NUM_THREADS, 1)
     slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                       const __grid_constant__ SliceGemmArgs args) {
-  using C_ = Cfg<BN, MODE>;
+  using C_ = Cfg<BN, MODE, CG>;
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[C_::STAGES];
   __shared__ __align__(8) uint64_t empty_bar[C_::STAGES];
@@ -184,6 +195,11 @@ __global__ void __launch_bounds__(Cfg<BN, MODE>::NUM_THREADS, 1)
   const uint32_t smem_base = (smem_u32(smem_raw) + 1023u) & ~1023u;
   uint8_t* smem_gen = smem_raw + (smem_base - smem_u32(smem_raw));
   const int ntiles = (args.probs == nullptr) ? args.single.tiles_m * args.single.tiles_n : *args.ntiles_dev;
+  // tile walk: CTAs (CG = 1) or CTA pairs (CG = 2) stride over the tile list
+  const uint32_t rank = (CG == 2) ? cluster_ctarank() : 0u;
+  const int walker = (CG == 2) ? static_cast<int>(cluster_id_x()) : static_cast<int>(blockIdx.x);
+  const int walkers = (CG == 2) ? static_cast<int>(cluster_count_x()) : static_cast<int>(gridDim.x);
+  const bool leader = (rank == 0);
 
   WaitCtl wc;
   wc.abort = &abort_flag;
@@ -197,7 +213,7 @@ __global__ void __launch_bounds__(Cfg<BN, MODE>::NUM_THREADS, 1)
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&accf_bar[i], 1);
-      mbar_init(&acce_bar[i], EPI_WARPS);
+      mbar_init(&acce_bar[i], C_::EPI_WARPS * CG);   // the pair's epilogue warps all report to the leader
     }
     mbar_init(&drain_bar, 1);
     abort_flag = 0u;
@@ -208,22 +224,32 @@ __global__ void __launch_bounds__(Cfg<BN, MODE>::NUM_THREADS, 1)
     tma_prefetch_desc(&tmB);
   }
   if (warp == 1) {
-    tmem_alloc(&tmem_base_slot, C_::TMEM_COLS);
-    tmem_relinquish();
+    if constexpr (CG == 2) {
+      tmem_alloc_pair(&tmem_base_slot, C_::TMEM_COLS);   // collective: the same columns in both CTAs
+      tmem_relinquish_pair();
+    } else {
+      tmem_alloc(&tmem_base_slot, C_::TMEM_COLS);
+      tmem_relinquish();
+    }
   }
   tc_fence_before();
-  __syncthreads();
+  if constexpr (CG == 2)
+    cluster_sync_all();   // both CTAs' barriers exist before any cross-CTA signal
+  else
+    __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = tmem_base_slot;
+
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer
     if (lane == 0) {
       int it = 0;
       bool ok = true;
-      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      for (int t = walker; t < ntiles && ok; t += walkers) {
         const TileJob job = get_job(args, &tmA, &tmB, t);
-        const int ya = job.tm * BM, yb = job.tn * BN;
+        const int ya = job.tm * C_::TILE_M + static_cast<int>(rank) * BM;
+        const int yb = job.tn * BN + static_cast<int>(rank) * (BN / CG);
         for_each_step<MODE>(job.P->s, job.P->nkb, [&](const Step& st, int) {
           if (!ok) return;
           const int stage = it % C_::STAGES;
@@ -231,9 +257,17 @@ __global__ void __launch_bounds__(Cfg<BN, MODE>::NUM_THREADS, 1)
           if (!mbar_wait(&empty_bar[stage], (use & 1u) ^ 1u, wc)) { ok = false; return; }
           uint8_t* sa = smem_gen + stage * C_::STAGE_BYTES;
           uint8_t* sb = sa + C_::A_BYTES;
-          mbar_arrive_expect_tx(&full_bar[stage], C_::STAGE_BYTES);
-          tma_load_3d(sa, job.ta, st.kb * BK, ya, st.pa, &full_bar[stage]);
-          tma_load_3d(sb, job.tb, st.kb * BK, yb, st.pb, &full_bar[stage]);
+          if constexpr (CG == 2) {
+            // both CTAs' bytes complete on the leader's barrier; only the leader arrives
+            if (leader) mbar_arrive_expect_tx(&full_bar[stage], 2 * C_::STAGE_BYTES);
+            const uint32_t fb = mapa_shared(smem_u32(&full_bar[stage]), 0);
+            tma_load_3d_pair(sa, job.ta, st.kb * BK, ya, st.pa, fb);
+            tma_load_3d_pair(sb, job.tb, st.kb * BK, yb, st.pb, fb);
+          } else {
+            mbar_arrive_expect_tx(&full_bar[stage], C_::STAGE_BYTES);
+            tma_load_3d(sa, job.ta, st.kb * BK, ya, st.pa, &full_bar[stage]);
+            tma_load_3d(sb, job.tb, st.kb * BK, yb, st.pb, &full_bar[stage]);
+          }
           ++it;
         });
       }
@@ -247,13 +281,13 @@ __global__ void __launch_bounds__(Cfg<BN, MODE>::NUM_THREADS, 1)
     __syncwarp();
   } else if (warp == 1) {
     // ----------------------------------------------------------------- MMA
-    if (lane == 0) {
-      const uint32_t idesc = idesc_bf16_f32(BM, BN);
+    if (lane == 0 && leader) {
+      const uint32_t idesc = idesc_bf16_f32(C_::TILE_M, BN);
       int it = 0;
       int chunk_base = 0;
       bool ok = true;
       bool issued_any = false;
-      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      for (int t = walker; t < ntiles && ok; t += walkers) {
         const TileJob job = get_job(args, &tmA, &tmB, t);
         const int s = job.P->s, nkb = job.P->nkb;
         for_each_step<MODE>(s, nkb, [&](const Step& st, int cofs) {
@@ -262,7 +296,12 @@ __global__ void __launch_bounds__(Cfg<BN, MODE>::NUM_THREADS, 1)
           const int slot = chunk & 1;
           if (st.first) {
             const uint32_t use = static_cast<uint32_t>(chunk >> 1);
-            if (!mbar_wait(&acce_bar[slot], (use & 1u) ^ 1u, wc)) { ok = false; return; }
+            bool w;
+            if constexpr (CG == 2)
+              w = mbar_wait_cluster(&acce_bar[slot], (use & 1u) ^ 1u, wc);
+            else
+              w = mbar_wait(&acce_bar[slot], (use & 1u) ^ 1u, wc);
+            if (!w) { ok = false; return; }
             tc_fence_after();
           }
           const int stage = it % C_::STAGES;
@@ -276,36 +315,50 @@ __global__ void __launch_bounds__(Cfg<BN, MODE>::NUM_THREADS, 1)
 #pragma unroll
           for (int kk = 0; kk < BK / 16; ++kk) {
             // 16 bf16 (32 bytes) further along K inside the 128-byte swizzled rows
-            umma_bf16(dt, da + static_cast<uint64_t>(kk * 2), db + static_cast<uint64_t>(kk * 2), idesc,
-                      (st.first && kk == 0) ? 0u : 1u);
+            const uint32_t acc = (st.first && kk == 0) ? 0u : 1u;
+            if constexpr (CG == 2)
+              umma_bf16_pair(dt, da + static_cast<uint64_t>(kk * 2), db + static_cast<uint64_t>(kk * 2), idesc, acc);
+            else
+              umma_bf16(dt, da + static_cast<uint64_t>(kk * 2), db + static_cast<uint64_t>(kk * 2), idesc, acc);
           }
           issued_any = true;
-          umma_commit(&empty_bar[stage]);
-          if (st.last) umma_commit(&accf_bar[slot]);
+          if constexpr (CG == 2) {
+            umma_commit_pair(&empty_bar[stage]);
+            if (st.last) umma_commit_pair(&accf_bar[slot]);
+          } else {
+            umma_commit(&empty_bar[stage]);
+            if (st.last) umma_commit(&accf_bar[slot]);
+          }
           ++it;
         });
         chunk_base += chunks_per_tile<MODE>(s, nkb);
       }
       if (!ok && issued_any) {
-        umma_commit(&drain_bar);
+        if constexpr (CG == 2)
+          umma_commit_pair_local(&drain_bar);
+        else
+          umma_commit(&drain_bar);
         mbar_wait_quiet(&drain_bar, 0u, globaltimer_ns() + 100000000ull);
       }
     }
     __syncwarp();
-  } else {
+  } else if (static_cast<int>(warp) >= C_::EPI_WARP0) {
     // ------------------------------------------------------------ epilogue
-    const int ew = static_cast<int>(warp) - 2;          // 0..7
+    const int ew = static_cast<int>(warp) - C_::EPI_WARP0;   // 0 .. EPI_WARPS-1
     const int quad = static_cast<int>(warp & 3u);        // TMEM lane quadrant this warp may access
-    const int half = ew >> 2;                            // which half of the tile's columns
+    const int half = ew >> 2;                            // which share of the tile's columns
     const int row_in_tile = quad * 32 + static_cast<int>(lane);
     const int col_off = half * C_::COLS_PER_THREAD;
     const uint32_t t_lane = static_cast<uint32_t>(quad * 32) << 16;
     int chunk = 0;
     bool ok = true;
-    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+    // where this warp reports "slot drained": the leader's barrier
+    const uint32_t acce_remote0 = (CG == 2) ? mapa_shared(smem_u32(&acce_bar[0]), 0) : 0u;
+    const uint32_t acce_remote1 = (CG == 2) ? mapa_shared(smem_u32(&acce_bar[1]), 0) : 0u;
+    for (int t = walker; t < ntiles && ok; t += walkers) {
       const TileJob job = get_job(args, &tmA, &tmB, t);
       const SliceProblem& P = *job.P;
-      const int64_t row = static_cast<int64_t>(job.tm) * BM + row_in_tile;
+      const int64_t row = static_cast<int64_t>(job.tm) * C_::TILE_M + static_cast<int64_t>(rank) * BM + row_in_tile;
       const int64_t col0 = static_cast<int64_t>(job.tn) * BN + col_off;
       const int64_t n = P.n;
       const bool row_ok = row < P.m;
@@ -319,8 +372,7 @@ __global__ void __launch_bounds__(Cfg<BN, MODE>::NUM_THREADS, 1)
 #pragma unroll 1
         for (int cg = 0; cg < C_::COLS_PER_THREAD / 32; ++cg) {
           uint32_t r[32];
-          tmem_ld32(tmem_base + t_lane + static_cast<uint32_t>(slot * BN + col_off + cg * 32), r);
-          tmem_ld_wait();
+          tmem_ld32_sync(tmem_base + t_lane + static_cast<uint32_t>(slot * BN + col_off + cg * 32), r);
           if (row_ok) {
 #pragma unroll
             for (int v = 0; v < 32; ++v) {
@@ -339,8 +391,100 @@ __global__ void __launch_bounds__(Cfg<BN, MODE>::NUM_THREADS, 1)
         }
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(&acce_bar[slot]);
+        if (lane == 0) {
+          if constexpr (CG == 2)
+            mbar_arrive_remote(slot ? acce_remote1 : acce_remote0);
+          else
+            mbar_arrive(&acce_bar[slot]);
+        }
         ++chunk;
+      } else if constexpr (BN == 256) {
+        // 256-wide tiles: TMEM holds just the two accumulator slots. Each thread
+        // keeps int32 level sums of its 128 columns in registers (one TMEM load
+        // per element per chunk) and folds them into the exact int64 total,
+        // kept in C's storage, at the end of each level.
+        int64_t* const xrow = reinterpret_cast<int64_t*>(P.C) + row * P.ldc;
+        const int s = P.s;
+        const int nkb = P.nkb;
+        const int fix_shift = P.fix_shift;
+        constexpr int NG = C_::COLS_PER_THREAD / 8;
+        int32_t lsum[NG][8];
+#pragma unroll
+        for (int g = 0; g < NG; ++g)
+#pragma unroll
+          for (int v = 0; v < 8; ++v) lsum[g][v] = 0;
+        bool first_fold = true;
+        for (int d = 2; d <= s + 1 && ok; ++d) {
+          const int kc = chunk_blocks(d);
+          const int nch = (nkb + kc - 1) / kc;
+          const int lsh = (MODE == SLICE_LEVELS) ? 0 : 8 * (s + 1 - d) - fix_shift;
+          for (int c = 0; c < nch; ++c, ++chunk) {
+            const int slot = chunk & 1;
+            if (!mbar_wait(&accf_bar[slot], static_cast<uint32_t>(chunk >> 1) & 1u, wc)) { ok = false; break; }
+            tc_fence_after();
+            if (lsh >= 0) {
+#pragma unroll
+              for (int g = 0; g < NG; ++g)
+                tmem_ld8_add_i32(tmem_base + t_lane + static_cast<uint32_t>(slot * BN + col_off + g * 8), lsum[g]);
+            } else {
+              // below the fixed point: each chunk is rounded on its own, as in
+              // the 128-wide path, so both tilings give the same total
+#pragma unroll
+              for (int g = 0; g < NG; ++g)
+                tmem_ld8_add_rshift_i32(tmem_base + t_lane + static_cast<uint32_t>(slot * BN + col_off + g * 8),
+                                        lsum[g], -lsh);
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) {
+              if constexpr (CG == 2)
+                mbar_arrive_remote(slot ? acce_remote1 : acce_remote0);
+              else
+                mbar_arrive(&acce_bar[slot]);
+            }
+            const bool level_end = (c == nch - 1);
+            const bool seg_end = ((c + 1) % SEG_CHUNKS) == 0;
+            if (!(level_end || seg_end)) continue;
+            const bool last = level_end && (d == s + 1);
+            if (row_ok) {
+#pragma unroll
+              for (int q4 = 0; q4 < C_::COLS_PER_THREAD / 4; ++q4) {
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                  const int i = q4 * 4 + v;
+                  const int64_t col = col0 + i;
+                  if (col < n) {
+                    const int64_t lv = static_cast<int64_t>(lsum[i >> 3][i & 7]);
+                    if constexpr (MODE == SLICE_LEVELS) {
+                      P.levels[(static_cast<int64_t>(d - 2) * P.m + row) * n + col] += lv;
+                    } else {
+                      const int64_t add = (lsh >= 0) ? (lv << lsh) : lv;   // lsh < 0: rounded per chunk
+                      const int64_t X = first_fold ? add : (xrow[col] + add);
+                      if (last) {
+                        const int32_t Fj = __ldg(P.F + col);
+                        double o;
+                        if (Ei == EXP_NONFINITE || Fj == EXP_NONFINITE)
+                          o = __longlong_as_double(0x7FF8000000000000ll);
+                        else
+                          o = scale_pow2(__ll2double_rn(X), Ei + Fj - 8 * (s + 1) + fix_shift);
+                        reinterpret_cast<double*>(xrow)[col] = o;
+                      } else {
+                        xrow[col] = X;
+                      }
+                    }
+                  }
+                }
+                // keep the next group's loads from being hoisted (register pressure)
+                asm volatile("" ::: "memory");
+              }
+            }
+#pragma unroll
+            for (int g = 0; g < NG; ++g)
+#pragma unroll
+              for (int v = 0; v < 8; ++v) lsum[g][v] = 0;
+            first_fold = false;
+          }
+        }
       } else {
         double* const crow = P.C + row * P.ldc;
         const int s = P.s;
@@ -364,15 +508,14 @@ __global__ void __launch_bounds__(Cfg<BN, MODE>::NUM_THREADS, 1)
 #pragma unroll 1
             for (int cg = 0; cg < C_::COLS_PER_THREAD / 16; ++cg) {
               uint32_t r[16], lo[16], hi[16];
-              tmem_ld16(tmem_base + t_lane + static_cast<uint32_t>(slot * BN + col_off + cg * 16), r);
+              const uint32_t tacc = tmem_base + t_lane + static_cast<uint32_t>(slot * BN + col_off + cg * 16);
               if (!fresh) {
-                tmem_ld16(txlo + cg * 16, lo);
-                tmem_ld16(txhi + cg * 16, hi);
+                tmem_ld16x3_sync(tacc, txlo + cg * 16, txhi + cg * 16, r, lo, hi);
               } else {
+                tmem_ld16_sync(tacc, r);
 #pragma unroll
                 for (int v = 0; v < 16; ++v) lo[v] = hi[v] = 0u;
               }
-              tmem_ld_wait();
 #pragma unroll
               for (int v = 0; v < 16; ++v) {
                 const int64_t a = static_cast<int64_t>(__float2int_rz(__uint_as_float(r[v])));
@@ -408,7 +551,12 @@ __global__ void __launch_bounds__(Cfg<BN, MODE>::NUM_THREADS, 1)
             if (!out) tmem_st_wait();
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&acce_bar[slot]);
+            if (lane == 0) {
+          if constexpr (CG == 2)
+            mbar_arrive_remote(slot ? acce_remote1 : acce_remote0);
+          else
+            mbar_arrive(&acce_bar[slot]);
+        }
             fresh = false;
           }
         }
@@ -417,24 +565,68 @@ __global__ void __launch_bounds__(Cfg<BN, MODE>::NUM_THREADS, 1)
   }
 
   tc_fence_before();
-  __syncthreads();
+  if constexpr (CG == 2)
+    cluster_sync_all();   // the leader's MMAs into this CTA's TMEM and all remote arrivals are done
+  else
+    __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    tmem_dealloc(tmem_base, C_::TMEM_COLS);
+    if constexpr (CG == 2)
+      tmem_dealloc_pair(tmem_base, C_::TMEM_COLS);
+    else
+      tmem_dealloc(tmem_base, C_::TMEM_COLS);
   }
 }
 
-template <int BN, int MODE>
+template <int BN, int MODE, int CG>
 static cudaError_t set_smem_attr() {
-  return cudaFuncSetAttribute(slice_gemm_kernel<BN, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              Cfg<BN, MODE>::SMEM_BYTES);
+  return cudaFuncSetAttribute(slice_gemm_kernel<BN, MODE, CG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              Cfg<BN, MODE, CG>::SMEM_BYTES);
+}
+
+template <int BN, int MODE, int CG>
+static cudaError_t launch_t(const CUtensorMap* tmA, const CUtensorMap* tmB, const SliceGemmArgs& a, int grid,
+                            cudaStream_t st) {
+  using C_ = Cfg<BN, MODE, CG>;
+  if (CG == 1) {
+    slice_gemm_kernel<BN, MODE, 1><<<grid, C_::NUM_THREADS, C_::SMEM_BYTES, st>>>(*tmA, *tmB, a);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(static_cast<unsigned>(grid));
+  cfg.blockDim = dim3(C_::NUM_THREADS);
+  cfg.dynamicSmemBytes = C_::SMEM_BYTES;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, slice_gemm_kernel<BN, MODE, CG>, *tmA, *tmB, a);
 }
 
 template <int BN, int MODE>
-static cudaError_t launch_t(const CUtensorMap* tmA, const CUtensorMap* tmB, const SliceGemmArgs& a, int grid,
-                            cudaStream_t st) {
-  slice_gemm_kernel<BN, MODE><<<grid, Cfg<BN, MODE>::NUM_THREADS, Cfg<BN, MODE>::SMEM_BYTES, st>>>(*tmA, *tmB, a);
-  return cudaGetLastError();
+static int max_pairs_t() {
+  using C_ = Cfg<BN, MODE, 2>;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(2);
+  cfg.blockDim = dim3(C_::NUM_THREADS);
+  cfg.dynamicSmemBytes = C_::SMEM_BYTES;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, slice_gemm_kernel<BN, MODE, 2>, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
 }
 
 }  // namespace mmdev
@@ -443,25 +635,49 @@ using namespace mmdev;
 
 cudaError_t slice_gemm_prepare() {
   cudaError_t e;
-  if ((e = set_smem_attr<256, SLICE_FP32EMU>()) != cudaSuccess) return e;
-  if ((e = set_smem_attr<128, SLICE_FP32EMU>()) != cudaSuccess) return e;
-  if ((e = set_smem_attr<128, SLICE_FP64EMU>()) != cudaSuccess) return e;
-  if ((e = set_smem_attr<128, SLICE_LEVELS>()) != cudaSuccess) return e;
+  if ((e = set_smem_attr<256, SLICE_FP32EMU, 1>()) != cudaSuccess) return e;
+  if ((e = set_smem_attr<128, SLICE_FP32EMU, 1>()) != cudaSuccess) return e;
+  if ((e = set_smem_attr<128, SLICE_FP64EMU, 1>()) != cudaSuccess) return e;
+  if ((e = set_smem_attr<128, SLICE_LEVELS, 1>()) != cudaSuccess) return e;
+  if ((e = set_smem_attr<256, SLICE_FP32EMU, 2>()) != cudaSuccess) return e;
+  if ((e = set_smem_attr<128, SLICE_FP64EMU, 2>()) != cudaSuccess) return e;
+  if ((e = set_smem_attr<128, SLICE_LEVELS, 2>()) != cudaSuccess) return e;
+  if ((e = set_smem_attr<256, SLICE_FP64EMU, 1>()) != cudaSuccess) return e;
+  if ((e = set_smem_attr<256, SLICE_FP64EMU, 2>()) != cudaSuccess) return e;
+  if ((e = set_smem_attr<256, SLICE_LEVELS, 1>()) != cudaSuccess) return e;
+  if ((e = set_smem_attr<256, SLICE_LEVELS, 2>()) != cudaSuccess) return e;
   return cudaSuccess;
 }
 
-int slice_gemm_smem_bytes(int bn) {
-  return bn == 256 ? Cfg<256, SLICE_FP32EMU>::SMEM_BYTES : Cfg<128, SLICE_FP32EMU>::SMEM_BYTES;
+int slice_gemm_max_pairs(int mode) {
+  if (mode == SLICE_FP32EMU) return max_pairs_t<256, SLICE_FP32EMU>();
+  if (mode == SLICE_FP64EMU) return max_pairs_t<256, SLICE_FP64EMU>();
+  return max_pairs_t<256, SLICE_LEVELS>();
 }
 
-// FP32-accuracy: BN 256 or 128. FP64-accuracy and level output: BN 128 (the
-// per-thread int32 level sums of a 256-wide tile do not fit the register file).
-cudaError_t launch_slice_gemm(int mode, int bn, const CUtensorMap* tmA, const CUtensorMap* tmB,
+// bn 256: every mode; FP64-accuracy and level output keep int32 level sums in
+// registers and the int64 total in C. bn 128: FP64-accuracy and level output
+// keep the int64 total in TMEM (used by grouped launches of small products).
+// cg = 2: CTA pairs on 256-row tiles (grid = 2 x pairs).
+cudaError_t launch_slice_gemm(int mode, int bn, int cg, const CUtensorMap* tmA, const CUtensorMap* tmB,
                               const SliceGemmArgs& a, int grid, cudaStream_t st) {
   if (grid <= 0) return cudaSuccess;
-  if (mode == SLICE_FP32EMU)
-    return bn == 256 ? launch_t<256, SLICE_FP32EMU>(tmA, tmB, a, grid, st)
-                     : launch_t<128, SLICE_FP32EMU>(tmA, tmB, a, grid, st);
-  if (mode == SLICE_FP64EMU) return launch_t<128, SLICE_FP64EMU>(tmA, tmB, a, grid, st);
-  return launch_t<128, SLICE_LEVELS>(tmA, tmB, a, grid, st);
+  if (cg == 2) {
+    if (bn == 256) {
+      if (mode == SLICE_FP32EMU) return launch_t<256, SLICE_FP32EMU, 2>(tmA, tmB, a, grid, st);
+      if (mode == SLICE_FP64EMU) return launch_t<256, SLICE_FP64EMU, 2>(tmA, tmB, a, grid, st);
+      return launch_t<256, SLICE_LEVELS, 2>(tmA, tmB, a, grid, st);
+    }
+    if (mode == SLICE_FP64EMU) return launch_t<128, SLICE_FP64EMU, 2>(tmA, tmB, a, grid, st);
+    if (mode == SLICE_LEVELS) return launch_t<128, SLICE_LEVELS, 2>(tmA, tmB, a, grid, st);
+    return cudaErrorInvalidValue;
+  }
+  if (bn == 256) {
+    if (mode == SLICE_FP32EMU) return launch_t<256, SLICE_FP32EMU, 1>(tmA, tmB, a, grid, st);
+    if (mode == SLICE_FP64EMU) return launch_t<256, SLICE_FP64EMU, 1>(tmA, tmB, a, grid, st);
+    return launch_t<256, SLICE_LEVELS, 1>(tmA, tmB, a, grid, st);
+  }
+  if (mode == SLICE_FP32EMU) return launch_t<128, SLICE_FP32EMU, 1>(tmA, tmB, a, grid, st);
+  if (mode == SLICE_FP64EMU) return launch_t<128, SLICE_FP64EMU, 1>(tmA, tmB, a, grid, st);
+  return launch_t<128, SLICE_LEVELS, 1>(tmA, tmB, a, grid, st);
 }

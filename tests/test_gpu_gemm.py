@@ -346,3 +346,68 @@ def test_budget_exceeded(mm):
         with pytest.raises(mm.MMError) as ei:
             hs.gemm(A, B, precision=mm.FP64_EMU)
         assert ei.value.status == 3
+
+
+# ---------------------------------------------------------- single vs CTA-pair tiles
+@pytest.mark.parametrize("m,n,k", [(300, 260, 1100), (520, 136, 700), (129, 400, 64), (257, 255, 4100)])
+def test_cta_pair_and_single_tiles_agree(h, mm, m, n, k):
+    A = inputs.row_scaled(m, k, 900 + k)
+    B = inputs.col_scaled(k, n, 900 + k)
+    out = {}
+    for cg in (1, 2):
+        h.set_option(mm.OPT_CTA_PAIR, cg)
+        try:
+            out[(cg, 1)], rc1 = run(h, A, B, mm.FP64_EMU)
+            out[(cg, 2)], rc2 = run(h, A, B, mm.FP32_EMU)
+        finally:
+            h.set_option(mm.OPT_CTA_PAIR, 0)
+        assert rc1 == 0 and rc2 == 0
+    assert np.array_equal(out[(1, 1)], out[(2, 1)])          # exact integer path: identical bits
+    C_ref, D = oracle.gemm(A, B), oracle.absprod(A, B)
+    for cg in (1, 2):
+        assert bound_ok(out[(cg, 1)], C_ref, D, em.gamma(k, "fp64_emu"))
+        assert bound_ok(out[(cg, 2)], C_ref, D, em.gamma(k, "fp32_emu"))
+
+
+@pytest.mark.parametrize("cg", [1, 2])
+def test_level_products_bit_exact_both_tilings(h, mm, cg):
+    m, n, k, s = 300, 150, 1100, 5
+    A = inputs.row_scaled(m, k, 31)
+    B = inputs.col_scaled(k, n, 31)
+    _, sA = em.fp64_slices_A(A, s)
+    _, sB = em.fp64_slices_B(B, s)
+    L_ref = em.level_products(sA, sB, s)
+    h.set_option(mm.OPT_CTA_PAIR, cg)
+    try:
+        L = h.debug_levels(dev(A), dev(B), s).cpu().numpy()
+    finally:
+        h.set_option(mm.OPT_CTA_PAIR, 0)
+    assert np.array_equal(L, L_ref)
+
+
+@pytest.mark.parametrize("m,n,k", [(200, 300, 50), (150, 520, 300), (130, 257, 3000), (140, 300, 4500)])
+def test_tile_widths_agree_bitwise(h, mm, m, n, k):
+    # s = 7, 6, 6, 5: the first three have a fixed point below the lowest level
+    A = inputs.row_scaled(m, k, 700 + k)
+    B = inputs.col_scaled(k, n, 700 + k)
+    out = {}
+    for cg in (1, 2):
+        for bn in (128, 256):
+            h.set_option(mm.OPT_CTA_PAIR, cg)
+            h.set_option(mm.OPT_TILE_N, bn)
+            try:
+                out[(cg, bn)], rc = run(h, A, B, mm.FP64_EMU)
+            finally:
+                h.set_option(mm.OPT_CTA_PAIR, 0)
+                h.set_option(mm.OPT_TILE_N, 0)
+            assert rc == 0
+    first = out[(1, 128)]
+    for key, C in out.items():
+        assert np.array_equal(C, first), key
+    assert bound_ok(first, oracle.gemm(A, B), oracle.absprod(A, B), em.gamma(k, "fp64_emu"))
+
+
+def test_tile_width_option_checked(h, mm):
+    with pytest.raises(mm.MMError):
+        h.set_option(mm.OPT_TILE_N, 192)
+    assert h.get_option(mm.OPT_TILE_N) == 0
