@@ -184,8 +184,8 @@ enum {
     MM_OPT_PROFILE = 7,           /* 1 = time every kernel launch with CUDA events (see mm_profile_read) */
     MM_OPT_CTA_PAIR = 8,          /* emulated products: 0 = automatic, 1 = one CTA per 128-row tile,
                                      2 = CTA pairs (cta_group::2) on 256-row tiles */
-    MM_OPT_TILE_N = 9             /* FP64-accuracy tile width: 0 = automatic, 128 or 256 columns.
-                                     Every choice gives the same bits. */
+    MM_OPT_TILE_N = 9             /* FP64-accuracy tile width: 0 = automatic, 128, 192, 240 or 256
+                                     columns. Every choice gives the same bits. */
 };
 
 /* Kernel classes for mm_profile_read. */

@@ -93,6 +93,8 @@ cudaError_t launch_slice_gemm(int mode, int bn, int cg, const CUtensorMap* tmA, 
 cudaError_t slice_gemm_prepare();
 // Largest number of co-resident CTA pairs of the pair kernel for a mode.
 int slice_gemm_max_pairs(int mode);
+// whether launch_slice_gemm has a kernel for (mode, tile width, CTAs per tile)
+bool slice_gemm_tile_ok(int mode, int bn, int cg);
 
 // ------------------------------------------------------------- fp64_gemm.cu
 struct Fp64GemmArgs {

@@ -243,7 +243,7 @@ int run_emulated(mm_handle_s* h, int precision, int64_t m, int64_t n, int64_t k,
     // tensor cores need N = 256 per MMA for full rate); FP32-accuracy pairs always 256
     int bn;
     if (fp64)
-      bn = (h->opt_tile_n == 128 || h->opt_tile_n == 256) ? h->opt_tile_n : (n > 128 ? 256 : 128);
+      bn = h->opt_tile_n ? h->opt_tile_n : (n > 128 ? 256 : 128);
     else
       bn = (cg == 2) ? 256 : pick_bn(h, precision, m, n);
     CUtensorMap tmA, tmB;
@@ -476,7 +476,7 @@ int mm_set_option(mm_handle h, int option, int64_t value) {
       h->opt_cta_pair = static_cast<int>(value);
       return MM_OK;
     case MM_OPT_TILE_N:
-      if (value != 0 && value != 128 && value != 256) return MM_ERR_INVALID_ARG;
+      if (value != 0 && !slice_gemm_tile_ok(SLICE_FP64EMU, static_cast<int>(value), 1)) return MM_ERR_INVALID_ARG;
       h->opt_tile_n = static_cast<int>(value);
       return MM_OK;
     default: return MM_ERR_INVALID_ARG;

@@ -322,6 +322,11 @@ __device__ __forceinline__ void tmem_ld16x3_sync(uint32_t ta, uint32_t tb, uint3
 // acc[v] += (int) column v of 8 consecutive f32 columns holding exact integers
 // (truncation is exact for integer values): load, wait, convert and add in one
 // statement, so the sums are the only registers live around it.
+// Hint: bring the line holding p into L2 (no fault on a valid address).
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 __device__ __forceinline__ void tmem_ld8_add_i32(uint32_t taddr, int32_t (&acc)[8]) {
   asm volatile(
       "{\n"
@@ -337,15 +342,6 @@ __device__ __forceinline__ void tmem_ld8_add_i32(uint32_t taddr, int32_t (&acc)[
       : "+r"(acc[0]), "+r"(acc[1]), "+r"(acc[2]), "+r"(acc[3]), "+r"(acc[4]), "+r"(acc[5]), "+r"(acc[6]),
         "+r"(acc[7])
       : "r"(taddr));
-}
-// As tmem_ld8_add_i32, but each truncated value is first divided by 2^sh with
-// round-half-up ((q + 2^(sh-1)) >> sh, arithmetic shift), 1 <= sh <= 30.
-__device__ __forceinline__ void tmem_ld8_add_rshift_i32(uint32_t taddr, int32_t (&acc)[8], int sh) {
-  uint32_t t[8];
-  tmem_ld8_sync(taddr, t);
-  const int32_t half = 1 << (sh - 1);
-#pragma unroll
-  for (int v = 0; v < 8; ++v) acc[v] += (__float2int_rz(__uint_as_float(t[v])) + half) >> sh;
 }
 // 32 lanes x 8 consecutive 32-bit columns.
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {

@@ -19,15 +19,21 @@
 // products first; the epilogue scales by 2^(E_i + F_j) and stores doubles.
 //
 // FP64-accuracy (integer slices, levels d = p + q = 2..s+1, Ozaki-style): the
-// kernel walks the levels one after the other. Level d sums d-1 slice pairs;
-// with |slice| <= 2^7 each product is at most 2^14, so a K-chunk of Kc with
-// Kc * (d-1) <= 1024 sums to at most 2^24 and the f32 accumulator holds it
-// exactly. The epilogue converts each finished chunk to integers and adds it,
-// shifted by its level weight, to an exact int64 fixed-point total
-// X = sum_d 2^(8(s+1-d) - shift) L_d kept in TMEM (512 columns = two 128-wide
-// accumulator slots + the low and high 32-bit planes of X). After the last
-// chunk of the tile X is converted to double once, scaled by
-// 2^(E_i + F_j - 8(s+1) + shift) and stored: C is written exactly once.
+// kernel walks the levels one after the other, smallest first (d = s+1 down
+// to 2). Level d sums d-1 slice pairs; with |slice| <= 2^7 each product is at
+// most 2^14, so a K-chunk of Kc with Kc * (d-1) <= 1024 sums to at most 2^24
+// and the f32 accumulator holds it exactly. The epilogue converts each
+// finished chunk to integers and adds it, at its level weight w_d = 8(s+1-d),
+// to an int64 fixed-point total with unit 2^shift (shift >= 0 keeps the total
+// below 2^62):
+//   X = round(sum_{w_d < shift} 2^w_d L_d / 2^shift) + sum_{w_d >= shift} 2^(w_d - shift) L_d,
+// which is the exact total rounded once (half up) to the fixed point: the
+// levels below the fixed point are summed exactly first and rounded at the
+// end of the last of them. 128-wide tiles keep X in TMEM (512 columns = two
+// accumulator slots + the low and high 32-bit planes of X); 256-wide tiles keep
+// int32 level sums in registers and X in C's storage. After the last level X
+// is converted to double once, scaled by 2^(E_i + F_j - 8(s+1) + shift) and
+// stored. Every tiling gives the same bits.
 #include <cstdint>
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -46,10 +52,12 @@ static constexpr int SEG_CHUNKS = 120;        // chunks per int32 level sum (120
 // memory and its 128 rows of the accumulator in its own TMEM.
 template <int BN, int MODE, int CG>
 struct Cfg {
-  // epilogue warps: 8 (two per TMEM lane quadrant); 16 for 256-wide FP64-accuracy
-  // tiles, whose threads keep their columns' int32 level sums in registers
-  static constexpr bool REG_SUMS = (BN == 256) && (MODE != SLICE_FP32EMU);
-  static constexpr int EPI_WARPS = REG_SUMS ? 16 : 8;
+  // epilogue warps: 8 (two per TMEM lane quadrant). FP64-accuracy tiles wider
+  // than 128 keep their columns' int32 level sums in registers: 16 warps for
+  // 256 columns (64 sums a thread), 12 for 192 or 240 (64 or 80 sums a thread;
+  // 14 warps leave 128 registers a thread)
+  static constexpr bool REG_SUMS = (BN != 128) && (MODE != SLICE_FP32EMU);
+  static constexpr int EPI_WARPS = !REG_SUMS ? 8 : (BN == 256 ? 16 : 12);
   static constexpr int EPI_WARP0 = 2;
   static constexpr int NUM_THREADS = 32 * (EPI_WARP0 + EPI_WARPS);
   static constexpr int A_BYTES = BM * BK * 2;
@@ -120,7 +128,7 @@ __device__ __forceinline__ void for_each_step(int s, int nkb, Fn&& f) {
     }
   } else {
     int chunk = 0;
-    for (int d = 2; d <= s + 1; ++d) {
+    for (int d = s + 1; d >= 2; --d) {   // smallest level first
       const int kc = chunk_blocks(d);
       for (int kb0 = 0; kb0 < nkb; kb0 += kc, ++chunk) {
         const int kb1 = min(kb0 + kc, nkb);
@@ -398,11 +406,11 @@ __global__ void __launch_bounds__(Cfg<BN, MODE, CG>::NUM_THREADS, 1)
             mbar_arrive(&acce_bar[slot]);
         }
         ++chunk;
-      } else if constexpr (BN == 256) {
-        // 256-wide tiles: TMEM holds just the two accumulator slots. Each thread
-        // keeps int32 level sums of its 128 columns in registers (one TMEM load
-        // per element per chunk) and folds them into the exact int64 total,
-        // kept in C's storage, at the end of each level.
+      } else if constexpr (C_::REG_SUMS) {
+        // wide tiles: TMEM holds just the two accumulator slots. Each thread
+        // keeps int32 level sums of its columns in registers (one TMEM load
+        // per element per chunk) and folds them into the int64 total, kept in
+        // C's storage, at the end of each level.
         int64_t* const xrow = reinterpret_cast<int64_t*>(P.C) + row * P.ldc;
         const int s = P.s;
         const int nkb = P.nkb;
@@ -414,26 +422,28 @@ __global__ void __launch_bounds__(Cfg<BN, MODE, CG>::NUM_THREADS, 1)
 #pragma unroll
           for (int v = 0; v < 8; ++v) lsum[g][v] = 0;
         bool first_fold = true;
-        for (int d = 2; d <= s + 1 && ok; ++d) {
+        for (int d = s + 1; d >= 2 && ok; --d) {
           const int kc = chunk_blocks(d);
           const int nch = (nkb + kc - 1) / kc;
-          const int lsh = (MODE == SLICE_LEVELS) ? 0 : 8 * (s + 1 - d) - fix_shift;
+          const int w = 8 * (s + 1 - d);
+          const bool raw = w < fix_shift;   // summed exactly, rounded after the last such level
+          const int lsh = (MODE == SLICE_LEVELS) ? 0 : (raw ? w : w - fix_shift);
+          const bool round_at_end = (MODE != SLICE_LEVELS) && raw && (d == 2 || w + 8 >= fix_shift);
           for (int c = 0; c < nch; ++c, ++chunk) {
             const int slot = chunk & 1;
+            const bool level_end = (c == nch - 1);
+            const bool seg_end = ((c + 1) % SEG_CHUNKS) == 0;
+            if ((level_end || seg_end) && !first_fold && row_ok && MODE != SLICE_LEVELS) {
+              // the fold after this chunk reads X: start its lines towards L2 now
+              const int64_t cend = (col0 + C_::COLS_PER_THREAD < n) ? col0 + C_::COLS_PER_THREAD : n;
+              for (int64_t cc = col0; cc < cend; cc += 16) prefetch_l2(xrow + cc);
+              if (cend > col0) prefetch_l2(xrow + cend - 1);
+            }
             if (!mbar_wait(&accf_bar[slot], static_cast<uint32_t>(chunk >> 1) & 1u, wc)) { ok = false; break; }
             tc_fence_after();
-            if (lsh >= 0) {
 #pragma unroll
-              for (int g = 0; g < NG; ++g)
-                tmem_ld8_add_i32(tmem_base + t_lane + static_cast<uint32_t>(slot * BN + col_off + g * 8), lsum[g]);
-            } else {
-              // below the fixed point: each chunk is rounded on its own, as in
-              // the 128-wide path, so both tilings give the same total
-#pragma unroll
-              for (int g = 0; g < NG; ++g)
-                tmem_ld8_add_rshift_i32(tmem_base + t_lane + static_cast<uint32_t>(slot * BN + col_off + g * 8),
-                                        lsum[g], -lsh);
-            }
+            for (int g = 0; g < NG; ++g)
+              tmem_ld8_add_i32(tmem_base + t_lane + static_cast<uint32_t>(slot * BN + col_off + g * 8), lsum[g]);
             tc_fence_before();
             __syncwarp();
             if (lane == 0) {
@@ -442,40 +452,63 @@ __global__ void __launch_bounds__(Cfg<BN, MODE, CG>::NUM_THREADS, 1)
               else
                 mbar_arrive(&acce_bar[slot]);
             }
-            const bool level_end = (c == nch - 1);
-            const bool seg_end = ((c + 1) % SEG_CHUNKS) == 0;
             if (!(level_end || seg_end)) continue;
-            const bool last = level_end && (d == s + 1);
+            const bool last = level_end && (d == 2);
+            const bool rnd = level_end && round_at_end;
             if (row_ok) {
-#pragma unroll
-              for (int q4 = 0; q4 < C_::COLS_PER_THREAD / 4; ++q4) {
-#pragma unroll
-                for (int v = 0; v < 4; ++v) {
-                  const int i = q4 * 4 + v;
-                  const int64_t col = col0 + i;
-                  if (col < n) {
-                    const int64_t lv = static_cast<int64_t>(lsum[i >> 3][i & 7]);
-                    if constexpr (MODE == SLICE_LEVELS) {
-                      P.levels[(static_cast<int64_t>(d - 2) * P.m + row) * n + col] += lv;
-                    } else {
-                      const int64_t add = (lsh >= 0) ? (lv << lsh) : lv;   // lsh < 0: rounded per chunk
-                      const int64_t X = first_fold ? add : (xrow[col] + add);
-                      if (last) {
-                        const int32_t Fj = __ldg(P.F + col);
-                        double o;
-                        if (Ei == EXP_NONFINITE || Fj == EXP_NONFINITE)
-                          o = __longlong_as_double(0x7FF8000000000000ll);
-                        else
-                          o = scale_pow2(__ll2double_rn(X), Ei + Fj - 8 * (s + 1) + fix_shift);
-                        reinterpret_cast<double*>(xrow)[col] = o;
-                      } else {
-                        xrow[col] = X;
-                      }
-                    }
-                  }
+              const int ebase = Ei - 8 * (s + 1) + fix_shift;
+              const bool nan_row = (Ei == EXP_NONFINITE);
+              // new total of element i from its old value
+              auto fold1 = [&](int i, int64_t old, int32_t Fj) -> int64_t {
+                int64_t X = old + (static_cast<int64_t>(lsum[i >> 3][i & 7]) << lsh);
+                if (rnd) X = (X + (1ll << (fix_shift - 1))) >> fix_shift;
+                if (last) {
+                  const double o = (nan_row || Fj == EXP_NONFINITE) ? __longlong_as_double(0x7FF8000000000000ll)
+                                                                   : scale_pow2(__ll2double_rn(X), ebase + Fj);
+                  X = __double_as_longlong(o);
                 }
-                // keep the next group's loads from being hoisted (register pressure)
-                asm volatile("" ::: "memory");
+                return X;
+              };
+              int64_t* const xp = xrow + col0;
+              const bool full = (n - col0 >= C_::COLS_PER_THREAD) && ((reinterpret_cast<uintptr_t>(xp) & 15u) == 0);
+              if constexpr (MODE == SLICE_LEVELS) {
+                int64_t* const lp = P.levels + (static_cast<int64_t>(d - 2) * P.m + row) * n + col0;
+#pragma unroll
+                for (int i = 0; i < C_::COLS_PER_THREAD; ++i)
+                  if (col0 + i < n) lp[i] += static_cast<int64_t>(lsum[i >> 3][i & 7]);
+              } else if (full) {
+                // 16 columns at a time: eight 16-byte loads in flight, then the stores
+#pragma unroll
+                for (int q = 0; q < C_::COLS_PER_THREAD / 16; ++q) {
+                  longlong2 xv[8];
+#pragma unroll
+                  for (int j = 0; j < 8; ++j)
+                    xv[j] = first_fold ? make_longlong2(0, 0) : reinterpret_cast<const longlong2*>(xp)[q * 8 + j];
+                  int4 fv[4] = {};
+                  if (last) {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) fv[j] = __ldg(reinterpret_cast<const int4*>(P.F + col0) + q * 4 + j);
+                  }
+#pragma unroll
+                  for (int j = 0; j < 8; ++j) {
+                    const int i = q * 16 + 2 * j;
+                    const int4& f4 = fv[j >> 1];
+                    xv[j].x = fold1(i, xv[j].x, (j & 1) ? f4.z : f4.x);
+                    xv[j].y = fold1(i + 1, xv[j].y, (j & 1) ? f4.w : f4.y);
+                    reinterpret_cast<longlong2*>(xp)[q * 8 + j] = xv[j];
+                  }
+                  asm volatile("" ::: "memory");   // one group's values live at a time
+                }
+              } else {
+#pragma unroll
+                for (int q4 = 0; q4 < C_::COLS_PER_THREAD / 4; ++q4) {
+#pragma unroll
+                  for (int v = 0; v < 4; ++v) {
+                    const int i = q4 * 4 + v;
+                    if (col0 + i < n) xp[i] = fold1(i, first_fold ? 0ll : xp[i], last ? __ldg(P.F + col0 + i) : 0);
+                  }
+                  asm volatile("" ::: "memory");
+                }
               }
             }
 #pragma unroll
@@ -493,16 +526,20 @@ __global__ void __launch_bounds__(Cfg<BN, MODE, CG>::NUM_THREADS, 1)
         const uint32_t txlo = tmem_base + t_lane + static_cast<uint32_t>(C_::XLO_COL + col_off);
         const uint32_t txhi = tmem_base + t_lane + static_cast<uint32_t>(C_::XHI_COL + col_off);
         bool fresh = true;   // X holds nothing yet (reads as zero)
-        for (int d = 2; d <= s + 1 && ok; ++d) {
+        for (int d = s + 1; d >= 2 && ok; --d) {
           const int kc = chunk_blocks(d);
           const int nch = (nkb + kc - 1) / kc;
-          // weight of level d in the fixed-point total (level output: unweighted)
-          const int lsh = (MODE == SLICE_LEVELS) ? 0 : 8 * (s + 1 - d) - fix_shift;
+          // weight of level d in the total (level output: unweighted)
+          const int w = 8 * (s + 1 - d);
+          const bool raw = w < fix_shift;
+          const int lsh = (MODE == SLICE_LEVELS) ? 0 : (raw ? w : w - fix_shift);
+          const bool round_at_end = (MODE != SLICE_LEVELS) && raw && (d == 2 || w + 8 >= fix_shift);
           if (MODE == SLICE_LEVELS) fresh = true;
           for (int c = 0; c < nch; ++c, ++chunk) {
             const int slot = chunk & 1;
             const bool level_end = (c == nch - 1);
-            const bool out = (MODE == SLICE_LEVELS) ? level_end : (level_end && d == s + 1);
+            const bool out = (MODE == SLICE_LEVELS) ? level_end : (level_end && d == 2);
+            const bool rnd = level_end && round_at_end;
             if (!mbar_wait(&accf_bar[slot], static_cast<uint32_t>(chunk >> 1) & 1u, wc)) { ok = false; break; }
             tc_fence_after();
 #pragma unroll 1
@@ -519,8 +556,8 @@ __global__ void __launch_bounds__(Cfg<BN, MODE, CG>::NUM_THREADS, 1)
 #pragma unroll
               for (int v = 0; v < 16; ++v) {
                 const int64_t a = static_cast<int64_t>(__float2int_rz(__uint_as_float(r[v])));
-                const int64_t add = (lsh >= 0) ? (a << lsh) : ((a + (1ll << (-lsh - 1))) >> (-lsh));
-                const int64_t X = static_cast<int64_t>((static_cast<uint64_t>(hi[v]) << 32) | lo[v]) + add;
+                int64_t X = static_cast<int64_t>((static_cast<uint64_t>(hi[v]) << 32) | lo[v]) + (a << lsh);
+                if (rnd) X = (X + (1ll << (fix_shift - 1))) >> fix_shift;
                 lo[v] = static_cast<uint32_t>(static_cast<uint64_t>(X));
                 hi[v] = static_cast<uint32_t>(static_cast<uint64_t>(X) >> 32);
               }
@@ -633,20 +670,36 @@ static int max_pairs_t() {
 
 using namespace mmdev;
 
+namespace {
+
+template <int BN, int CG>
+cudaError_t launch_emu(int mode, const CUtensorMap* tmA, const CUtensorMap* tmB, const SliceGemmArgs& a, int grid,
+                       cudaStream_t st) {
+  if (mode == SLICE_FP64EMU) return launch_t<BN, SLICE_FP64EMU, CG>(tmA, tmB, a, grid, st);
+  if (mode == SLICE_LEVELS) return launch_t<BN, SLICE_LEVELS, CG>(tmA, tmB, a, grid, st);
+  return cudaErrorInvalidValue;
+}
+
+template <int BN>
+cudaError_t prepare_emu() {
+  cudaError_t e;
+  if ((e = set_smem_attr<BN, SLICE_FP64EMU, 1>()) != cudaSuccess) return e;
+  if ((e = set_smem_attr<BN, SLICE_FP64EMU, 2>()) != cudaSuccess) return e;
+  if ((e = set_smem_attr<BN, SLICE_LEVELS, 1>()) != cudaSuccess) return e;
+  return set_smem_attr<BN, SLICE_LEVELS, 2>();
+}
+
+}  // namespace
+
 cudaError_t slice_gemm_prepare() {
   cudaError_t e;
   if ((e = set_smem_attr<256, SLICE_FP32EMU, 1>()) != cudaSuccess) return e;
   if ((e = set_smem_attr<128, SLICE_FP32EMU, 1>()) != cudaSuccess) return e;
-  if ((e = set_smem_attr<128, SLICE_FP64EMU, 1>()) != cudaSuccess) return e;
-  if ((e = set_smem_attr<128, SLICE_LEVELS, 1>()) != cudaSuccess) return e;
   if ((e = set_smem_attr<256, SLICE_FP32EMU, 2>()) != cudaSuccess) return e;
-  if ((e = set_smem_attr<128, SLICE_FP64EMU, 2>()) != cudaSuccess) return e;
-  if ((e = set_smem_attr<128, SLICE_LEVELS, 2>()) != cudaSuccess) return e;
-  if ((e = set_smem_attr<256, SLICE_FP64EMU, 1>()) != cudaSuccess) return e;
-  if ((e = set_smem_attr<256, SLICE_FP64EMU, 2>()) != cudaSuccess) return e;
-  if ((e = set_smem_attr<256, SLICE_LEVELS, 1>()) != cudaSuccess) return e;
-  if ((e = set_smem_attr<256, SLICE_LEVELS, 2>()) != cudaSuccess) return e;
-  return cudaSuccess;
+  if ((e = prepare_emu<128>()) != cudaSuccess) return e;
+  if ((e = prepare_emu<192>()) != cudaSuccess) return e;
+  if ((e = prepare_emu<240>()) != cudaSuccess) return e;
+  return prepare_emu<256>();
 }
 
 int slice_gemm_max_pairs(int mode) {
@@ -655,29 +708,33 @@ int slice_gemm_max_pairs(int mode) {
   return max_pairs_t<256, SLICE_LEVELS>();
 }
 
-// bn 256: every mode; FP64-accuracy and level output keep int32 level sums in
-// registers and the int64 total in C. bn 128: FP64-accuracy and level output
-// keep the int64 total in TMEM (used by grouped launches of small products).
-// cg = 2: CTA pairs on 256-row tiles (grid = 2 x pairs).
+bool slice_gemm_tile_ok(int mode, int bn, int cg) {
+  if (cg != 1 && cg != 2) return false;
+  if (mode == SLICE_FP32EMU) return bn == 256 || (bn == 128 && cg == 1);
+  return bn == 128 || bn == 192 || bn == 240 || bn == 256;
+}
+
+// FP32-accuracy: bn 256 (cg 1 or 2) or 128 (cg 1). FP64-accuracy and level
+// output: bn 128 keeps the int64 total in TMEM (grouped launches of small
+// products); bn 192, 240, 256 keep int32 level sums in registers and the int64
+// total in C. cg = 2: CTA pairs on 256-row tiles (grid = 2 x pairs).
 cudaError_t launch_slice_gemm(int mode, int bn, int cg, const CUtensorMap* tmA, const CUtensorMap* tmB,
                               const SliceGemmArgs& a, int grid, cudaStream_t st) {
   if (grid <= 0) return cudaSuccess;
-  if (cg == 2) {
-    if (bn == 256) {
-      if (mode == SLICE_FP32EMU) return launch_t<256, SLICE_FP32EMU, 2>(tmA, tmB, a, grid, st);
-      if (mode == SLICE_FP64EMU) return launch_t<256, SLICE_FP64EMU, 2>(tmA, tmB, a, grid, st);
-      return launch_t<256, SLICE_LEVELS, 2>(tmA, tmB, a, grid, st);
-    }
-    if (mode == SLICE_FP64EMU) return launch_t<128, SLICE_FP64EMU, 2>(tmA, tmB, a, grid, st);
-    if (mode == SLICE_LEVELS) return launch_t<128, SLICE_LEVELS, 2>(tmA, tmB, a, grid, st);
-    return cudaErrorInvalidValue;
+  if (!slice_gemm_tile_ok(mode, bn, cg)) return cudaErrorInvalidValue;
+  if (mode == SLICE_FP32EMU) {
+    if (cg == 2) return launch_t<256, SLICE_FP32EMU, 2>(tmA, tmB, a, grid, st);
+    if (bn == 256) return launch_t<256, SLICE_FP32EMU, 1>(tmA, tmB, a, grid, st);
+    return launch_t<128, SLICE_FP32EMU, 1>(tmA, tmB, a, grid, st);
   }
-  if (bn == 256) {
-    if (mode == SLICE_FP32EMU) return launch_t<256, SLICE_FP32EMU, 1>(tmA, tmB, a, grid, st);
-    if (mode == SLICE_FP64EMU) return launch_t<256, SLICE_FP64EMU, 1>(tmA, tmB, a, grid, st);
-    return launch_t<256, SLICE_LEVELS, 1>(tmA, tmB, a, grid, st);
+  switch (bn * 4 + cg) {
+    case 128 * 4 + 1: return launch_emu<128, 1>(mode, tmA, tmB, a, grid, st);
+    case 128 * 4 + 2: return launch_emu<128, 2>(mode, tmA, tmB, a, grid, st);
+    case 192 * 4 + 1: return launch_emu<192, 1>(mode, tmA, tmB, a, grid, st);
+    case 192 * 4 + 2: return launch_emu<192, 2>(mode, tmA, tmB, a, grid, st);
+    case 240 * 4 + 1: return launch_emu<240, 1>(mode, tmA, tmB, a, grid, st);
+    case 240 * 4 + 2: return launch_emu<240, 2>(mode, tmA, tmB, a, grid, st);
+    case 256 * 4 + 1: return launch_emu<256, 1>(mode, tmA, tmB, a, grid, st);
+    default: return launch_emu<256, 2>(mode, tmA, tmB, a, grid, st);
   }
-  if (mode == SLICE_FP32EMU) return launch_t<128, SLICE_FP32EMU, 1>(tmA, tmB, a, grid, st);
-  if (mode == SLICE_FP64EMU) return launch_t<128, SLICE_FP64EMU, 1>(tmA, tmB, a, grid, st);
-  return launch_t<128, SLICE_LEVELS, 1>(tmA, tmB, a, grid, st);
 }
