@@ -456,11 +456,21 @@ __global__ void __launch_bounds__(Cfg<BN, MODE, CG>::NUM_THREADS, 1)
             const bool last = level_end && (d == 2);
             const bool rnd = level_end && round_at_end;
             if (row_ok) {
+              // park the sums in local memory for the fold (and reset them here,
+              // inside the branch: rows past m keep stale sums that are never
+              // stored). Either way round, the compiler spills the sums inside
+              // the chunk loop.
+              int32_t sums[C_::COLS_PER_THREAD];
+#pragma unroll
+              for (int g = 0; g < NG; ++g)
+#pragma unroll
+                for (int v = 0; v < 8; ++v) { sums[g * 8 + v] = lsum[g][v]; lsum[g][v] = 0; }
+              asm volatile("" ::"l"(sums) : "memory");
               const int ebase = Ei - 8 * (s + 1) + fix_shift;
               const bool nan_row = (Ei == EXP_NONFINITE);
               // new total of element i from its old value
               auto fold1 = [&](int i, int64_t old, int32_t Fj) -> int64_t {
-                int64_t X = old + (static_cast<int64_t>(lsum[i >> 3][i & 7]) << lsh);
+                int64_t X = old + (static_cast<int64_t>(sums[i]) << lsh);
                 if (rnd) X = (X + (1ll << (fix_shift - 1))) >> fix_shift;
                 if (last) {
                   const double o = (nan_row || Fj == EXP_NONFINITE) ? __longlong_as_double(0x7FF8000000000000ll)
@@ -475,7 +485,7 @@ __global__ void __launch_bounds__(Cfg<BN, MODE, CG>::NUM_THREADS, 1)
                 int64_t* const lp = P.levels + (static_cast<int64_t>(d - 2) * P.m + row) * n + col0;
 #pragma unroll
                 for (int i = 0; i < C_::COLS_PER_THREAD; ++i)
-                  if (col0 + i < n) lp[i] += static_cast<int64_t>(lsum[i >> 3][i & 7]);
+                  if (col0 + i < n) lp[i] += static_cast<int64_t>(sums[i]);
               } else if (full) {
                 // 16 columns at a time: eight 16-byte loads in flight, then the stores
 #pragma unroll
@@ -511,10 +521,6 @@ __global__ void __launch_bounds__(Cfg<BN, MODE, CG>::NUM_THREADS, 1)
                 }
               }
             }
-#pragma unroll
-            for (int g = 0; g < NG; ++g)
-#pragma unroll
-              for (int v = 0; v < 8; ++v) lsum[g][v] = 0;
             first_fold = false;
           }
         }
