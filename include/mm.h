@@ -64,7 +64,7 @@ enum {
     MM_ERR_NONFINITE = 4,    /* emulated mode met Inf or NaN in A or B */
     MM_ERR_CUDA = 5,         /* a CUDA runtime or driver call failed */
     MM_ERR_TIMEOUT = 6,      /* a bounded device-side wait ran out; the kernel returned early */
-    MM_ERR_NOT_FOUND = 7,    /* serve: unknown or already collected ticket */
+    MM_ERR_NOT_FOUND = 7,    /* serve: unknown or already collected ticket; tune: no entry, no file */
     MM_ERR_SHUTDOWN = 8,     /* serve: handle is being destroyed; request cancelled */
     MM_ERR_UNSUPPORTED = 9   /* no sm_100-family GPU (tcgen05) present */
 };
@@ -177,7 +177,9 @@ int mm_serve_drain(mm_handle h);
 enum {
     MM_OPT_SLICES = 1,        /* FP64-accuracy slice count s (0 = automatic rule, else 3..7) */
     MM_OPT_TIMEOUT_MS = 2,    /* bound on every device-side wait (default 2000) */
-    MM_OPT_AUTOTUNE = 3,      /* 1 = time candidate tile shapes on first use of a shape bucket */
+    MM_OPT_AUTOTUNE = 3,      /* 1 = on the first product (or group) of a shape bucket, time every
+                                 candidate launch configuration on the caller's stream (blocking
+                                 that call) and keep the fastest; see mm_tune_save */
     MM_OPT_SERVE_MAX_BATCH = 4,   /* requests per grouped launch (default 64) */
     MM_OPT_SERVE_STREAMS = 5,     /* serving streams (default 2) */
     MM_OPT_FP64_KERNEL = 6,       /* 0 = automatic, 1 = DFMA tiles, 2 = DMMA (mma.sync f64) tiles */
@@ -199,6 +201,33 @@ int mm_get_option(mm_handle h, int option, int64_t *value);
 
 /* The slice count the automatic rule picks for inner dimension k (FP64-EMU). */
 int mm_slices_for_k(int64_t k);
+
+/* ---------------------------------------------------------------- autotuner */
+
+/* The tuning table maps shape buckets to launch configurations. Buckets:
+ * single products by (precision, ceil(log2 m), ceil(log2 n), ceil(log2 k));
+ * grouped calls by (precision, ceil(log2 count), ceil(log2 d)) where d is the
+ * mean over the group of (m*n*k)^(1/3). Configurations: tile width (128, 192,
+ * 240, 256) and CTAs per tile (1, 2) for the emulated modes, the FP64 tile
+ * kernel (1 = DFMA, 2 = DMMA) for the plain mode. Entries are filled by
+ * MM_OPT_AUTOTUNE or loaded from a file; explicit tile options
+ * (MM_OPT_TILE_N, MM_OPT_CTA_PAIR, MM_OPT_FP64_KERNEL) take precedence. The
+ * FP64-accuracy result never depends on the configuration.
+ *
+ * mm_tune_save writes the table as text (a header line, then one entry per
+ * line: kind precision b0 b1 b2 bn cg kern ms); MM_ERR_INVALID_ARG if the
+ * file cannot be written. mm_tune_load merges a saved table into the handle's;
+ * MM_ERR_NOT_FOUND if the file does not exist, MM_ERR_INVALID_ARG (and nothing
+ * merged) if any line is malformed or names a configuration the library
+ * cannot launch. */
+int mm_tune_save(mm_handle h, const char *path);
+int mm_tune_load(mm_handle h, const char *path);
+
+/* The configuration tuned for a bucket: grouped = 0 looks up the single
+ * product (a, b, c) = (m, n, k); grouped = 1 the group bucket of a problems of
+ * mean dimension b (c unused). MM_ERR_NOT_FOUND if the bucket has no entry. */
+int mm_tune_lookup(mm_handle h, int grouped, int precision, int64_t a, int64_t b, int64_t c,
+                   int *bn, int *cg, int *kern);
 
 /* --------------------------------------------------- inputs and diagnostics */
 

@@ -10,6 +10,7 @@ stride) or, for the host entry point, numpy float64 arrays.
 from __future__ import annotations
 
 import ctypes
+import os
 
 from . import _lib
 
@@ -19,6 +20,7 @@ FP32_EMU = 2
 PRECISIONS = {"fp64": FP64, "fp64_emu": FP64_EMU, "fp32_emu": FP32_EMU}
 
 OK, PENDING = 0, 1
+INVALID_ARG, BUDGET, NONFINITE, CUDA_ERROR, TIMEOUT, NOT_FOUND = 2, 3, 4, 5, 6, 7
 OPT_SLICES, OPT_TIMEOUT_MS, OPT_AUTOTUNE, OPT_SERVE_MAX_BATCH, OPT_SERVE_STREAMS, OPT_FP64_KERNEL = 1, 2, 3, 4, 5, 6
 OPT_PROFILE = 7
 OPT_CTA_PAIR = 8
@@ -204,6 +206,23 @@ class Handle:
         _check(self.lib.mm_profile_read(self.h, kernel, ctypes.byref(ms), ctypes.byref(n), int(reset)),
                "mm_profile_read")
         return ms.value, n.value
+
+    # ----------------------------------------------------------- autotuner
+    def tune_save(self, path: str):
+        _check(self.lib.mm_tune_save(self.h, os.fsencode(path)), "mm_tune_save")
+
+    def tune_load(self, path: str):
+        _check(self.lib.mm_tune_load(self.h, os.fsencode(path)), "mm_tune_load")
+
+    def tune_lookup(self, precision: int, a: int, b: int, c: int = 0, grouped: bool = False):
+        """(bn, cg, kern) tuned for the bucket, or None."""
+        bn, cg, kern = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        rc = self.lib.mm_tune_lookup(self.h, int(grouped), precision, a, b, c, ctypes.byref(bn), ctypes.byref(cg),
+                                     ctypes.byref(kern))
+        if rc == NOT_FOUND:
+            return None
+        _check(rc, "mm_tune_lookup")
+        return bn.value, cg.value, kern.value
 
     def peak_fp64(self):
         a, b = ctypes.c_double(), ctypes.c_double()

@@ -64,6 +64,10 @@ SIGNATURES = {
     "mm_set_option": (c_int, [c_vp, c_int, c_i64]),
     "mm_get_option": (c_int, [c_vp, c_int, ctypes.POINTER(c_i64)]),
     "mm_slices_for_k": (c_int, [c_i64]),
+    "mm_tune_save": (c_int, [c_vp, ctypes.c_char_p]),
+    "mm_tune_load": (c_int, [c_vp, ctypes.c_char_p]),
+    "mm_tune_lookup": (c_int, [c_vp, c_int, c_int, c_i64, c_i64, c_i64, ctypes.POINTER(c_int), ctypes.POINTER(c_int),
+                               ctypes.POINTER(c_int)]),
     "mm_fill_uniform": (c_int, [c_vp, c_i64, c_i64, c_i64, c_u64, c_u64, c_int, c_u64, c_vp]),
     "mm_debug_slices": (c_int, [c_vp, c_int, c_int, c_int, c_i64, c_i64, c_vp, c_i64, c_vp, c_vp, c_vp]),
     "mm_debug_level_products": (c_int, [c_vp, c_i64, c_i64, c_i64, c_vp, c_i64, c_vp, c_i64, c_int, c_vp, c_vp]),

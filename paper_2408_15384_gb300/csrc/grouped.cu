@@ -86,7 +86,9 @@ struct EmuPlan {
   std::vector<Prob> p;
   std::vector<TileCost> tiles;
   size_t colmax_bytes = 0, ws_bytes = 0;
-  void build(mm_handle_s* h, const std::vector<int>& idx, const mm_problem* probs, bool fp64) {
+  int bn = 128;   // output tile width of the group's slice GEMM (one CTA per 128 x bn tile)
+  void build(mm_handle_s* h, const std::vector<int>& idx, const mm_problem* probs, bool fp64, int bn_) {
+    bn = bn_;
     const int count = static_cast<int>(idx.size());
     p.resize(count);
     tiles.clear();
@@ -102,7 +104,7 @@ struct EmuPlan {
       r.F = o; o = align_up(o + 4 * static_cast<size_t>(q.n), 256);
       r.sa = o; o = align_up(o + 2 * static_cast<size_t>(r.s) * q.m * r.kp, 1024);
       r.sb = o; o = align_up(o + 2 * static_cast<size_t>(r.s) * q.n * r.kp, 1024);
-      const int tm = static_cast<int>((q.m + 127) / 128), tn = static_cast<int>((q.n + 127) / 128);
+      const int tm = static_cast<int>((q.m + 127) / 128), tn = static_cast<int>((q.n + bn - 1) / bn);
       const int64_t nkb = (q.k + 63) / 64;
       const int64_t pairs = fp64 ? static_cast<int64_t>(r.s) * (r.s + 1) / 2 : 6;
       for (int a = 0; a < tm; ++a)
@@ -154,10 +156,10 @@ static int fill_emu_blob(mm_handle_s* h, const EmuPlan& plan, const EmuLayout& L
     P.s = r.s;
     P.fix_shift = fp64 ? fixed_shift(r.s, q.k) : 0;
     P.tiles_m = static_cast<int>((q.m + 127) / 128);
-    P.tiles_n = static_cast<int>((q.n + 127) / 128);
+    P.tiles_n = static_cast<int>((q.n + plan.bn - 1) / plan.bn);
     P.E = g.E; P.F = g.F; P.C = q.C; P.ldc = q.ldc; P.levels = nullptr;
     if (!encode_slices_tmap(h, &tm[2 * i], g.slA, q.k, q.m, r.s, r.kp, 128) ||
-        !encode_slices_tmap(h, &tm[2 * i + 1], g.slB, q.k, q.n, r.s, r.kp, 128))
+        !encode_slices_tmap(h, &tm[2 * i + 1], g.slB, q.k, q.n, r.s, r.kp, plan.bn))
       return MM_ERR_CUDA;
   }
   // the offsets of problems past `count` repeat the totals
@@ -168,7 +170,7 @@ static int fill_emu_blob(mm_handle_s* h, const EmuPlan& plan, const EmuLayout& L
 }
 
 // The launches of an emulated group whose blob is at db (device).
-static cudaError_t launch_emu_group(mm_handle_s* h, bool fp64, const EmuLayout& L, char* db, char* ws,
+static cudaError_t launch_emu_group(mm_handle_s* h, bool fp64, int bn, const EmuLayout& L, char* db, char* ws,
                                     size_t colmax_cap, cudaStream_t st) {
   GroupedSplitArgs ga;
   ga.probs = reinterpret_cast<const GroupedSplit*>(db + L.off_split);
@@ -188,7 +190,7 @@ static cudaError_t launch_emu_group(mm_handle_s* h, bool fp64, const EmuLayout& 
   cudaError_t e = cudaMemsetAsync(ws, 0, colmax_cap, st);
   if (e == cudaSuccess) e = launch_grouped_split(fp64 ? 0 : 1, ga, h->sm_count * 8, st);
   if (e == cudaSuccess)
-    e = launch_slice_gemm(fp64 ? SLICE_FP64EMU : SLICE_FP32EMU, 128, 1, &dummy, &dummy, sa, h->sm_count, st);
+    e = launch_slice_gemm(fp64 ? SLICE_FP64EMU : SLICE_FP32EMU, bn, 1, &dummy, &dummy, sa, h->sm_count, st);
   return e;
 }
 
@@ -223,8 +225,9 @@ static void fill_fp64_blob(const Fp64Plan& plan, const Fp64Layout& L, const std:
   for (size_t t = 0; t < plan.tiles.size(); ++t) tr[t] = plan.tiles[t].ref;
 }
 
-static cudaError_t launch_fp64_group(mm_handle_s* h, const Fp64Layout& L, char* db, cudaStream_t st) {
-  return launch_fp64_grouped(fp64_kind(h), reinterpret_cast<const Fp64GemmArgs*>(db + L.off_args),
+static cudaError_t launch_fp64_group(mm_handle_s* h, int kern, const Fp64Layout& L, char* db, cudaStream_t st) {
+  return launch_fp64_grouped((kern == 1 || kern == 2) ? kern : fp64_kind(h),
+                             reinterpret_cast<const Fp64GemmArgs*>(db + L.off_args),
                              reinterpret_cast<const TileRef*>(db + L.off_tiles),
                              reinterpret_cast<const int*>(db + L.off_hdr) + 1, h->sm_count * 2, st);
 }
@@ -257,7 +260,10 @@ struct GroupedSlot {
 struct GroupedKey {
   int precision;
   cudaStream_t stream;
-  bool operator<(const GroupedKey& o) const { return std::tie(precision, stream) < std::tie(o.precision, o.stream); }
+  int bn, kern;   // launch configuration captured in the graph
+  bool operator<(const GroupedKey& o) const {
+    return std::tie(precision, stream, bn, kern) < std::tie(o.precision, o.stream, o.bn, o.kern);
+  }
 };
 
 struct GroupedEntry {
@@ -346,11 +352,11 @@ static int alloc_slot(mm_handle_s* h, GroupedSlot& slot, size_t blob_bytes, size
 }
 
 static int graph_emulated(mm_handle_s* h, GroupedEntry& ent, const std::vector<int>& idx, const mm_problem* probs,
-                          int precision, cudaStream_t st) {
+                          int precision, int bn, cudaStream_t st) {
   const bool fp64 = precision == MM_FP64_EMU;
   const int count = static_cast<int>(idx.size());
   EmuPlan plan;
-  plan.build(h, idx, probs, fp64);
+  plan.build(h, idx, probs, fp64, bn);
   const int ntiles = static_cast<int>(plan.tiles.size());
   GroupedSlot& slot = ent.slot[ent.next];
   if (slot.launched) cudaEventSynchronize(slot.done);
@@ -370,7 +376,8 @@ static int graph_emulated(mm_handle_s* h, GroupedEntry& ent, const std::vector<i
     slot.colmax_cap = colmax_cap;
     char* db = static_cast<char*>(slot.dblob);
     char* ws = static_cast<char*>(slot.ws);
-    rc = capture_slot(slot, [&](cudaStream_t cs) { return launch_emu_group(h, fp64, L, db, ws, colmax_cap, cs); });
+    rc = capture_slot(slot,
+                      [&](cudaStream_t cs) { return launch_emu_group(h, fp64, bn, L, db, ws, colmax_cap, cs); });
     if (rc != MM_OK) {
       release_slot(h, slot);
       return rc;
@@ -393,7 +400,7 @@ static int graph_emulated(mm_handle_s* h, GroupedEntry& ent, const std::vector<i
 }
 
 static int graph_fp64(mm_handle_s* h, GroupedEntry& ent, const std::vector<int>& idx, const mm_problem* probs,
-                      cudaStream_t st) {
+                      int kern, cudaStream_t st) {
   const int count = static_cast<int>(idx.size());
   Fp64Plan plan;
   plan.build(idx, probs);
@@ -410,7 +417,7 @@ static int graph_fp64(mm_handle_s* h, GroupedEntry& ent, const std::vector<int>&
     slot.count_cap = cc;
     slot.tiles_cap = tc;
     char* db = static_cast<char*>(slot.dblob);
-    rc = capture_slot(slot, [&](cudaStream_t cs) { return launch_fp64_group(h, L, db, cs); });
+    rc = capture_slot(slot, [&](cudaStream_t cs) { return launch_fp64_group(h, kern, L, db, cs); });
     if (rc != MM_OK) {
       release_slot(h, slot);
       return rc;
@@ -440,20 +447,66 @@ static int run_side(mm_handle_s* h, const std::vector<int>& side_idx, const mm_p
   return MM_OK;
 }
 
+namespace {
+struct GroupedRun {
+  mm_handle_s* h;
+  int count;
+  const mm_problem* probs;
+  int precision;
+  cudaStream_t st;
+  std::vector<char> host;
+};
+int grouped_tune_run(void* ctx, const TileCfg& c) {
+  GroupedRun* r = static_cast<GroupedRun*>(ctx);
+  size_t hb = 0;
+  grouped_direct_bytes(r->h, r->count, r->probs, r->precision, c, &hb);
+  if (r->host.size() < hb) r->host.resize(hb);
+  // the staging buffer is reused by the next run: wait for this one's copy
+  int rc = grouped_direct(r->h, r->count, r->probs, r->precision, c, r->host.data(), r->host.size(), r->st);
+  if (rc == MM_OK && cudaStreamSynchronize(r->st) != cudaSuccess) rc = MM_ERR_CUDA;
+  return rc;
+}
+}  // namespace
+
+TileCfg grouped_cfg(mm_handle_s* h, int count, const mm_problem* probs, int precision) {
+  TileCfg c = grouped_default_cfg(h, precision);
+  if (tile_options_set(h)) return c;
+  int key[5];
+  tune_key_grouped(precision, count, probs, key);
+  TileCfg t;
+  if (tune_lookup(h, key, &t)) c = t;
+  return c;
+}
+
 int grouped_run(mm_handle_s* h, int count, const mm_problem* probs, int precision, cudaStream_t st) {
   std::vector<int> main_idx, side_idx;
   partition(count, probs, precision, main_idx, side_idx);
   int rc = run_side(h, side_idx, probs, precision, st);
   if (rc != MM_OK || main_idx.empty()) return rc;
+  TileCfg cfg = grouped_default_cfg(h, precision);
+  if (!tile_options_set(h)) {
+    int key[5];
+    tune_key_grouped(precision, count, probs, key);
+    if (!tune_lookup(h, key, &cfg) && h->opt_autotune && !stream_capturing(st)) {
+      // the tuning runs go through the direct path (same kernels); the chosen
+      // configuration then runs once more below, through the graph
+      GroupedRun r{h, count, probs, precision, st, {}};
+      rc = tune_pick(h, key, tune_candidates(h, TUNE_GROUPED, precision, 0, 0), st, grouped_tune_run, &r, &cfg);
+      if (rc == MM_ERR_BUDGET) cfg = grouped_default_cfg(h, precision);
+      else if (rc != MM_OK) return rc;
+    }
+  }
   std::lock_guard<std::mutex> lk(h->grouped_mu);
   if (!h->grouped) h->grouped = new GroupedCache();
-  GroupedEntry& ent = h->grouped->entries[GroupedKey{precision, st}];
-  if (precision == MM_FP64) return graph_fp64(h, ent, main_idx, probs, st);
-  return graph_emulated(h, ent, main_idx, probs, precision, st);
+  const bool plain = precision == MM_FP64;
+  GroupedEntry& ent = h->grouped->entries[GroupedKey{precision, st, plain ? 0 : cfg.bn, plain ? cfg.kern : 0}];
+  if (plain) return graph_fp64(h, ent, main_idx, probs, cfg.kern, st);
+  return graph_emulated(h, ent, main_idx, probs, precision, cfg.bn, st);
 }
 
 // -------------------------------------------------------------- direct path
-size_t grouped_direct_bytes(mm_handle_s* h, int count, const mm_problem* probs, int precision, size_t* host_bytes) {
+size_t grouped_direct_bytes(mm_handle_s* h, int count, const mm_problem* probs, int precision, const TileCfg& cfg,
+                            size_t* host_bytes) {
   std::vector<int> main_idx, side_idx;
   partition(count, probs, precision, main_idx, side_idx);
   *host_bytes = 0;
@@ -467,15 +520,15 @@ size_t grouped_direct_bytes(mm_handle_s* h, int count, const mm_problem* probs, 
     return L.bytes;
   }
   EmuPlan plan;
-  plan.build(h, main_idx, probs, precision == MM_FP64_EMU);
+  plan.build(h, main_idx, probs, precision == MM_FP64_EMU, cfg.bn ? cfg.bn : 128);
   EmuLayout L;
   L.plan(static_cast<int>(main_idx.size()), static_cast<int>(plan.tiles.size()));
   *host_bytes = L.bytes;
   return align_up(L.bytes, 1024) + plan.colmax_bytes + plan.ws_bytes;
 }
 
-int grouped_direct(mm_handle_s* h, int count, const mm_problem* probs, int precision, void* host_blob,
-                   size_t host_cap, cudaStream_t st) {
+int grouped_direct(mm_handle_s* h, int count, const mm_problem* probs, int precision, const TileCfg& cfg,
+                   void* host_blob, size_t host_cap, cudaStream_t st) {
   std::vector<int> main_idx, side_idx;
   partition(count, probs, precision, main_idx, side_idx);
   int rc = run_side(h, side_idx, probs, precision, st);
@@ -494,15 +547,16 @@ int grouped_direct(mm_handle_s* h, int count, const mm_problem* probs, int preci
     cudaError_t e = cudaMemcpyAsync(dev, hb, L.bytes, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) {
       ProfScope ps(h, MM_KERNEL_FP64_GEMM, st);
-      e = launch_fp64_group(h, L, static_cast<char*>(dev), st);
+      e = launch_fp64_group(h, cfg.kern, L, static_cast<char*>(dev), st);
     }
     ws_free(h, dev, L.bytes, st);
     count_launch(h, 1);
     return cuda_status(e, "grouped fp64");
   }
   const bool fp64 = precision == MM_FP64_EMU;
+  const int bn = cfg.bn ? cfg.bn : 128;
   EmuPlan plan;
-  plan.build(h, main_idx, probs, fp64);
+  plan.build(h, main_idx, probs, fp64, bn);
   EmuLayout L;
   L.plan(n, static_cast<int>(plan.tiles.size()));
   if (L.bytes > host_cap) return MM_ERR_INVALID_ARG;
@@ -518,7 +572,7 @@ int grouped_direct(mm_handle_s* h, int count, const mm_problem* probs, int preci
     e = cudaMemcpyAsync(db, hb, L.bytes, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) {
       ProfScope ps(h, MM_KERNEL_SLICE_GEMM, st);
-      e = launch_emu_group(h, fp64, L, db, ws, plan.colmax_bytes, st);
+      e = launch_emu_group(h, fp64, bn, L, db, ws, plan.colmax_bytes, st);
     }
     count_launch(h, 3);
   }

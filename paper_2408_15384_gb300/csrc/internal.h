@@ -30,6 +30,14 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
 namespace mmhost {
 struct GroupedCache;
 struct ServeEngine;
+struct TuneTable;
+
+// Launch configuration of a product: 0 in a field means "automatic".
+struct TileCfg {
+  int bn = 0;     // emulated modes: output tile width (128, 192, 240, 256)
+  int cg = 0;     // emulated modes: CTAs per tile (1, or 2 = CTA pair)
+  int kern = 0;   // plain FP64: 1 = DFMA tiles, 2 = DMMA tiles
+};
 }
 
 struct mm_handle_s {
@@ -53,7 +61,7 @@ struct mm_handle_s {
   int opt_fp32_bn = 0;
   bool opt_profile = false;
   int opt_cta_pair = 0;
-  int opt_tile_n = 0;        // FP64-accuracy tile width (0 = automatic, 128, 256)
+  int opt_tile_n = 0;        // FP64-accuracy tile width (0 = automatic, 128, 192, 240, 256)
   int max_pairs_fp32 = 0, max_pairs_fp64 = 0;   // co-resident CTA pairs of the pair kernels
 
   // profiling: (start, end) event pairs per kernel class, drained by mm_profile_read
@@ -66,6 +74,7 @@ struct mm_handle_s {
   mmhost::GroupedCache* grouped = nullptr;
   std::mutex serve_mu;
   mmhost::ServeEngine* serve = nullptr;
+  mmhost::TuneTable* tune = nullptr;         // autotuned launch configurations (tune.cu)
 };
 
 namespace mmhost {
@@ -83,10 +92,12 @@ int fixed_shift(int s, int64_t k);
 bool encode_slices_tmap(mm_handle_s* h, CUtensorMap* tm, const void* base, int64_t k, int64_t rows, int S, int64_t kp,
                         int box_rows);
 void count_launch(mm_handle_s* h, uint64_t n);
-int pick_bn(mm_handle_s* h, int precision, int64_t m, int64_t n);
 int fp64_kind(mm_handle_s* h);
 int gemm_device(mm_handle_s* h, int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
                 int64_t ldb, double* C, int64_t ldc, int precision, cudaStream_t st);
+// one product with an explicit launch configuration (no tuning)
+int gemm_with_cfg(mm_handle_s* h, int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
+                  int64_t ldb, double* C, int64_t ldc, int precision, const TileCfg& cfg, cudaStream_t st);
 int read_and_clear_err(mm_handle_s* h);
 
 // Brackets one launch with events when profiling is on.
@@ -116,9 +127,36 @@ struct SplitLayout {
 int run_split(mm_handle_s* h, int mode01, const SplitLayout& L, char* ws, const double* A, int64_t lda,
               const double* B, int64_t ldb, cudaStream_t st);
 
+// tune.cu: the autotuner. Keys are shape buckets (ceil(log2) of the single
+// product's m, n, k; of a group's problem count and mean dimension).
+enum { TUNE_SINGLE = 0, TUNE_GROUPED = 1 };
+bool tile_options_set(const mm_handle_s* h);
+TileCfg default_cfg(const mm_handle_s* h, int precision, int64_t m, int64_t n);
+TileCfg grouped_default_cfg(const mm_handle_s* h, int precision);
+void tune_key_single(int precision, int64_t m, int64_t n, int64_t k, int key[5]);
+void tune_key_grouped(int precision, int count, const mm_problem* probs, int key[5]);
+bool tune_lookup(mm_handle_s* h, const int key[5], TileCfg* out);
+std::vector<TileCfg> tune_candidates(const mm_handle_s* h, int kind, int precision, int64_t m, int64_t n);
+// Times every candidate (one warm-up and two timed runs of run(cfg) on st,
+// CUDA events), stores the fastest under key and returns it in *best. The
+// runs write the caller's outputs; the caller runs the chosen configuration
+// once more afterwards. Returns MM_OK, or the first CUDA error.
+int tune_pick(mm_handle_s* h, const int key[5], const std::vector<TileCfg>& cands, cudaStream_t st,
+              int (*run)(void* ctx, const TileCfg& cfg), void* ctx, TileCfg* best);
+bool stream_capturing(cudaStream_t st);
+void tune_init(mm_handle_s* h);
+void tune_release(mm_handle_s* h);
+
 // grouped.cu / serve.cu
 void grouped_release(mm_handle_s* h);
 int grouped_run(mm_handle_s* h, int count, const mm_problem* probs, int precision, cudaStream_t st);
+// direct (graph-free) grouped launch with the pool's workspace, as the
+// serving engine issues it; cfg as from grouped_cfg
+TileCfg grouped_cfg(mm_handle_s* h, int count, const mm_problem* probs, int precision);
+size_t grouped_direct_bytes(mm_handle_s* h, int count, const mm_problem* probs, int precision, const TileCfg& cfg,
+                            size_t* host_bytes);
+int grouped_direct(mm_handle_s* h, int count, const mm_problem* probs, int precision, const TileCfg& cfg,
+                   void* host_blob, size_t host_cap, cudaStream_t st);
 void serve_shutdown(mm_handle_s* h);
 
 }  // namespace mmhost

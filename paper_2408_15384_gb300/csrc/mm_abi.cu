@@ -209,19 +209,11 @@ int run_split(mm_handle_s* h, int mode01, const SplitLayout& L, char* ws, const 
   return MM_OK;
 }
 
-int pick_bn(mm_handle_s* h, int precision, int64_t m, int64_t n) {
-  if (precision != MM_FP32_EMU) return 128;
-  if (h->opt_fp32_bn == 128 || h->opt_fp32_bn == 256) return h->opt_fp32_bn;
-  // 256-wide tiles halve the operand traffic per flop; narrow products keep 128
-  const int64_t t256 = ((m + 127) / 128) * ((n + 255) / 256);
-  return (n > 128 && t256 >= h->sm_count / 2) ? 256 : 128;
-}
-
 // The emulated product of one problem (FP64-accuracy, FP32-accuracy, or the
 // level-product diagnostic when levels != nullptr).
 int run_emulated(mm_handle_s* h, int precision, int64_t m, int64_t n, int64_t k, const double* A, int64_t lda,
                  const double* B, int64_t ldb, double* C, int64_t ldc, cudaStream_t st, int64_t* levels,
-                 int s_override) {
+                 int s_override, const TileCfg& cfg_in) {
   const bool fp64 = (precision == MM_FP64_EMU);
   const int s = fp64 ? (s_override > 0 ? s_override : (h->opt_slices > 0 ? h->opt_slices : slices_for_k(k))) : 3;
   SplitLayout L;
@@ -235,17 +227,17 @@ int run_emulated(mm_handle_s* h, int precision, int64_t m, int64_t n, int64_t k,
     rc = run_split(h, fp64 ? 0 : 1, L, ws, A, lda, B, ldb, st);
   }
   if (rc == MM_OK) {
-    // CTA pairs (256-row tiles, half of B per CTA) unless the product is one tile high
+    // CTA pairs (256-row tiles, half of B per CTA) unless the product is one
+    // tile high; the tile width from the configuration (tuned or default)
     const int pairs_avail = fp64 ? h->max_pairs_fp64 : h->max_pairs_fp32;
-    int cg = (h->opt_cta_pair == 1) ? 1 : (h->opt_cta_pair == 2 ? 2 : (m > 128 ? 2 : 1));
+    const TileCfg dflt = default_cfg(h, precision, m, n);
+    int cg = cfg_in.cg ? cfg_in.cg : dflt.cg;
+    int bn = cfg_in.bn ? cfg_in.bn : dflt.bn;
     if (pairs_avail <= 0) cg = 1;
-    // 256-wide tiles whenever the product is wider than one 128-wide tile (the
-    // tensor cores need N = 256 per MMA for full rate); FP32-accuracy pairs always 256
-    int bn;
-    if (fp64)
-      bn = h->opt_tile_n ? h->opt_tile_n : (n > 128 ? 256 : 128);
-    else
-      bn = (cg == 2) ? 256 : pick_bn(h, precision, m, n);
+    if (!slice_gemm_tile_ok(fp64 ? SLICE_FP64EMU : SLICE_FP32EMU, bn, cg)) {
+      bn = dflt.bn;
+      cg = dflt.cg;
+    }
     CUtensorMap tmA, tmB;
     if (!encode_slices_tmap(h, &tmA, ws + L.off_sa, k, m, L.S, L.kp, 128) ||
         !encode_slices_tmap(h, &tmB, ws + L.off_sb, k, n, L.S, L.kp, bn / cg)) {
@@ -286,26 +278,62 @@ int run_emulated(mm_handle_s* h, int precision, int64_t m, int64_t n, int64_t k,
 int fp64_kind(mm_handle_s* h) { return h->opt_fp64_kernel == 1 ? 1 : 2; }
 
 int run_fp64(mm_handle_s* h, int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
-             int64_t ldb, double* C, int64_t ldc, cudaStream_t st) {
+             int64_t ldb, double* C, int64_t ldc, cudaStream_t st, int kern) {
   Fp64GemmArgs a{m, n, k, A, lda, B, ldb, C, ldc};
   ProfScope ps(h, MM_KERNEL_FP64_GEMM, st);
-  cudaError_t e = launch_fp64_gemm(fp64_kind(h), a, st);
+  cudaError_t e = launch_fp64_gemm((kern == 1 || kern == 2) ? kern : fp64_kind(h), a, st);
   count_launch(h, 1);
   return cuda_status(e, "fp64 gemm");
 }
 
-int gemm_device(mm_handle_s* h, int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
-                int64_t ldb, double* C, int64_t ldc, int precision, cudaStream_t st) {
-  int rc = validate_problem(m, n, k, A, lda, B, ldb, C, ldc, precision);
-  if (rc != MM_OK) return rc;
+int gemm_with_cfg(mm_handle_s* h, int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
+                  int64_t ldb, double* C, int64_t ldc, int precision, const TileCfg& cfg, cudaStream_t st) {
   if (m == 0 || n == 0) return MM_OK;
   if (k == 0) {
     count_launch(h, 1);
     return cuda_status(launch_zero_c(C, m, n, ldc, st), "zero C");
   }
   if (precision == MM_FP64 || (precision == MM_FP64_EMU && k <= 4))
-    return run_fp64(h, m, n, k, A, lda, B, ldb, C, ldc, st);
-  return run_emulated(h, precision, m, n, k, A, lda, B, ldb, C, ldc, st, nullptr, 0);
+    return run_fp64(h, m, n, k, A, lda, B, ldb, C, ldc, st, cfg.kern);
+  return run_emulated(h, precision, m, n, k, A, lda, B, ldb, C, ldc, st, nullptr, 0, cfg);
+}
+
+namespace {
+struct SingleRun {
+  mm_handle_s* h;
+  int64_t m, n, k, lda, ldb, ldc;
+  const double *A, *B;
+  double* C;
+  int precision;
+  cudaStream_t st;
+};
+int single_run(void* ctx, const TileCfg& c) {
+  SingleRun* r = static_cast<SingleRun*>(ctx);
+  return gemm_with_cfg(r->h, r->m, r->n, r->k, r->A, r->lda, r->B, r->ldb, r->C, r->ldc, r->precision, c, r->st);
+}
+}  // namespace
+
+int gemm_device(mm_handle_s* h, int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
+                int64_t ldb, double* C, int64_t ldc, int precision, cudaStream_t st) {
+  int rc = validate_problem(m, n, k, A, lda, B, ldb, C, ldc, precision);
+  if (rc != MM_OK) return rc;
+  if (m == 0 || n == 0 || k == 0) return gemm_with_cfg(h, m, n, k, A, lda, B, ldb, C, ldc, precision, TileCfg(), st);
+  // the launch configuration: explicit options, else the tuned entry of the
+  // shape bucket (tuned now if autotuning is on), else the defaults
+  const bool plain = precision == MM_FP64 || (precision == MM_FP64_EMU && k <= 4);
+  const int kprec = plain ? MM_FP64 : precision;
+  TileCfg cfg;
+  if (!tile_options_set(h)) {
+    int key[5];
+    tune_key_single(kprec, m, n, k, key);
+    if (!tune_lookup(h, key, &cfg) && h->opt_autotune && !stream_capturing(st)) {
+      SingleRun r{h, m, n, k, lda, ldb, ldc, A, B, C, precision, st};
+      rc = tune_pick(h, key, tune_candidates(h, TUNE_SINGLE, kprec, m, n), st, single_run, &r, &cfg);
+      if (rc != MM_OK && rc != MM_ERR_BUDGET) return rc;
+      if (rc == MM_ERR_BUDGET) cfg = TileCfg();
+    }
+  }
+  return gemm_with_cfg(h, m, n, k, A, lda, B, ldb, C, ldc, precision, cfg, st);
 }
 
 int read_and_clear_err(mm_handle_s* h) {
@@ -378,6 +406,7 @@ int mm_create(mm_handle* out, int device, size_t mem_budget_bytes) {
     delete h;
     return MM_ERR_CUDA;
   }
+  tune_init(h);
   *out = h;
   return MM_OK;
 }
@@ -387,6 +416,7 @@ int mm_destroy(mm_handle h) {
   DeviceGuard g(h->device);
   serve_shutdown(h);
   grouped_release(h);
+  tune_release(h);
   cudaDeviceSynchronize();
   cudaFree(h->d_err);
   cudaMemPoolDestroy(h->pool);
@@ -567,7 +597,8 @@ int mm_debug_level_products(mm_handle h, int64_t m, int64_t n, int64_t k, const 
   cudaError_t e = cudaMemsetAsync(levels, 0, sizeof(int64_t) * static_cast<size_t>(s) * m * n, st);
   if (e != cudaSuccess) return cuda_status(e, "memset");
   // C is not written in level mode; pass the level buffer as a placeholder
-  rc = run_emulated(h, MM_FP64_EMU, m, n, k, A, lda, B, ldb, reinterpret_cast<double*>(levels), n, st, levels, s);
+  rc = run_emulated(h, MM_FP64_EMU, m, n, k, A, lda, B, ldb, reinterpret_cast<double*>(levels), n, st, levels, s,
+                    TileCfg());
   if (rc != MM_OK) return rc;
   e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_status(e, "synchronize");

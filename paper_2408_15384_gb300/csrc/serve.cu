@@ -27,9 +27,6 @@
 
 namespace mmhost {
 
-size_t grouped_direct_bytes(mm_handle_s* h, int count, const mm_problem* probs, int precision, size_t* host_bytes);
-int grouped_direct(mm_handle_s* h, int count, const mm_problem* probs, int precision, void* host_blob,
-                   size_t host_cap, cudaStream_t st);
 
 struct ServeReq {
   mm_request r;
@@ -153,7 +150,8 @@ static void engine_loop(ServeEngine* ep) {
       b->stream = si;
       // pinned staging for the batch's descriptor blob
       size_t host_bytes = 0;
-      grouped_direct_bytes(h, static_cast<int>(probs.size()), probs.data(), prec, &host_bytes);
+      const TileCfg cfg = grouped_cfg(h, static_cast<int>(probs.size()), probs.data(), prec);
+      grouped_direct_bytes(h, static_cast<int>(probs.size()), probs.data(), prec, cfg, &host_bytes);
       for (size_t i = 0; i < e.pinned_pool.size(); ++i)
         if (e.pinned_pool[i].second >= host_bytes) {
           b->pinned = e.pinned_pool[i].first;
@@ -175,7 +173,7 @@ static void engine_loop(ServeEngine* ep) {
       const double tl = now_us(h);
       cudaStream_t st = e.streams[si];
       if (rc == MM_OK)
-        rc = grouped_direct(h, static_cast<int>(probs.size()), probs.data(), prec, b->pinned, b->pinned_cap, st);
+        rc = grouped_direct(h, static_cast<int>(probs.size()), probs.data(), prec, cfg, b->pinned, b->pinned_cap, st);
       b->status = rc;
       if (rc != MM_OK || cudaLaunchHostFunc(st, batch_done, b) != cudaSuccess) {
         cudaGetLastError();
