@@ -257,6 +257,13 @@ int mm_debug_level_products(mm_handle h, int64_t m, int64_t n, int64_t k,
                             const double *A, int64_t lda, const double *B, int64_t ldb,
                             int s, int64_t *levels, void *stream);
 
+/* Failure-detection check of the device-side waits: launches one thread
+ * that waits, with the same bounded wait every kernel of the library uses, on
+ * an mbarrier that nothing arrives at, for timeout_ms (1..10000). The wait
+ * gives up, the kernel returns and the call reports MM_ERR_TIMEOUT; the
+ * context stays usable. Synchronous. */
+int mm_debug_wait_timeout(mm_handle h, int64_t timeout_ms, void *stream);
+
 /* Device peak microbenchmarks: FP64 DFMA and DMMA (mma.sync f64) rates in
  * TFLOP/s, each from a fixed-length register-resident loop on every SM. */
 int mm_peak_fp64(mm_handle h, double *dfma_tflops, double *dmma_tflops);

@@ -224,6 +224,10 @@ class Handle:
         _check(rc, "mm_tune_lookup")
         return bn.value, cg.value, kern.value
 
+    def debug_wait_timeout(self, timeout_ms: int, stream=None) -> int:
+        """Status of a bounded device wait that is made to run out (MM_ERR_TIMEOUT expected)."""
+        return self.lib.mm_debug_wait_timeout(self.h, int(timeout_ms), _stream_handle(stream))
+
     def peak_fp64(self):
         a, b = ctypes.c_double(), ctypes.c_double()
         _check(self.lib.mm_peak_fp64(self.h, ctypes.byref(a), ctypes.byref(b)), "mm_peak_fp64")

@@ -71,6 +71,7 @@ SIGNATURES = {
     "mm_fill_uniform": (c_int, [c_vp, c_i64, c_i64, c_i64, c_u64, c_u64, c_int, c_u64, c_vp]),
     "mm_debug_slices": (c_int, [c_vp, c_int, c_int, c_int, c_i64, c_i64, c_vp, c_i64, c_vp, c_vp, c_vp]),
     "mm_debug_level_products": (c_int, [c_vp, c_i64, c_i64, c_i64, c_vp, c_i64, c_vp, c_i64, c_int, c_vp, c_vp]),
+    "mm_debug_wait_timeout": (c_int, [c_vp, c_i64, c_vp]),
     "mm_peak_fp64": (c_int, [c_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "mm_stats": (c_int, [c_vp, ctypes.POINTER(c_u64)]),
     "mm_profile_read": (c_int, [c_vp, c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(c_u64), c_int]),

@@ -116,3 +116,5 @@ int fp64_tile_size();
 cudaError_t fp64_gemm_prepare();
 cudaError_t launch_zero_c(double* C, int64_t m, int64_t n, int64_t ldc, cudaStream_t st);
 cudaError_t launch_peak_fp64(int kind, double* sink, int iters, int blocks, cudaStream_t st);
+// a bounded wait on an mbarrier nothing arrives at (failure-detection check)
+cudaError_t launch_wait_probe(uint32_t* err, uint64_t timeout_ns, int* gave_up, cudaStream_t st);

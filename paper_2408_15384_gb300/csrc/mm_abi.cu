@@ -605,6 +605,25 @@ int mm_debug_level_products(mm_handle h, int64_t m, int64_t n, int64_t k, const 
   return read_and_clear_err(h);
 }
 
+int mm_debug_wait_timeout(mm_handle h, int64_t timeout_ms, void* stream) {
+  if (!h || timeout_ms < 1 || timeout_ms > 10000) return MM_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int* gave_up = nullptr;
+  if (cudaMalloc(&gave_up, sizeof(int)) != cudaSuccess) return MM_ERR_CUDA;
+  int rc = cuda_status(launch_wait_probe(h->d_err, static_cast<uint64_t>(timeout_ms) * 1000000ull, gave_up, st),
+                       "wait probe");
+  count_launch(h, 1);
+  int host = 0;
+  if (rc == MM_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = MM_ERR_CUDA;
+  if (rc == MM_OK && cudaMemcpy(&host, gave_up, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) rc = MM_ERR_CUDA;
+  cudaFree(gave_up);
+  if (rc != MM_OK) return rc;
+  rc = read_and_clear_err(h);
+  if (rc == MM_OK && host) rc = MM_ERR_CUDA;   // gave up without raising the error bit: inconsistent
+  return rc;
+}
+
 int mm_peak_fp64(mm_handle h, double* dfma_tflops, double* dmma_tflops) {
   if (!h || !dfma_tflops || !dmma_tflops) return MM_ERR_INVALID_ARG;
   DeviceGuard g(h->device);

@@ -496,3 +496,35 @@ cudaError_t launch_fill_uniform(double* X, int64_t rows, int64_t cols, int64_t l
   fill_uniform_kernel<<<blocks, 256, 0, st>>>(X, rows, cols, ld, base, scale_mode, ebase);
   return cudaGetLastError();
 }
+
+// ------------------------------------------------------------ wait probe
+namespace mmdev {
+
+// One thread waits, with the kernels' bounded wait, on an mbarrier that no
+// thread ever arrives at: the wait gives up at the deadline, sets the timeout
+// bit of the error word and the kernel returns normally.
+__global__ void wait_probe_kernel(uint32_t* err, uint64_t timeout_ns, int* gave_up) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ volatile uint32_t abort_flag;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    abort_flag = 0u;
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    WaitCtl wc;
+    wc.abort = &abort_flag;
+    wc.err = err;
+    wc.deadline_ns = globaltimer_ns() + timeout_ns;
+    *gave_up = mbar_wait(&bar, 0u, wc) ? 0 : 1;
+  }
+}
+
+}  // namespace mmdev
+
+cudaError_t launch_wait_probe(uint32_t* err, uint64_t timeout_ns, int* gave_up, cudaStream_t st) {
+  mmdev::wait_probe_kernel<<<1, 32, 0, st>>>(err, timeout_ns, gave_up);
+  return cudaGetLastError();
+}
+

@@ -411,3 +411,17 @@ def test_tile_width_option_checked(h, mm):
     with pytest.raises(mm.MMError):
         h.set_option(mm.OPT_TILE_N, 200)
     assert h.get_option(mm.OPT_TILE_N) == 0
+
+
+# ------------------------------------------------------- failure detection
+def test_bounded_wait_times_out_and_context_survives(h, mm):
+    # a wait on a barrier nothing arrives at gives up after 50 ms with MM_ERR_TIMEOUT
+    assert h.debug_wait_timeout(50) == mm.TIMEOUT
+    assert h.sync() == 0                       # the error word was read and cleared
+    A = inputs.row_scaled(130, 70, 5)
+    B = inputs.col_scaled(70, 90, 5)
+    C, rc = run(h, A, B, mm.FP64_EMU)          # the context still computes
+    assert rc == 0
+    assert bound_ok(C, oracle.gemm(A, B), oracle.absprod(A, B), em.gamma(70, "fp64_emu"))
+    with pytest.raises(Exception):
+        mm._check(h.debug_wait_timeout(0), "wait probe")
