@@ -44,19 +44,20 @@ WORKLOAD = "split-precision FP64-accuracy GEMM M=N=K=8192, A uniform[-1,1)*2^e p
 class ClockSampler:
     """nvidia-smi sampling of SM clock and throttle reasons while running."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu_index: int):
         self.idx = gpu_index
         self.proc = None
-        self.lines = []
+        self.lines = []          # csv lines, each stamped by nvidia-smi (wall clock of this host)
+        self.window = None       # (t0, t1) of the timed region
 
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                                          "-lms", "200", "-i", str(self.idx)],
+                                          "-lms", "50", "-i", str(self.idx)],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.th = threading.Thread(target=self._read, daemon=True)
             self.th.start()
@@ -67,6 +68,9 @@ class ClockSampler:
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
+    def mark(self, t0: float, t1: float):
+        self.window = (t0, t1)
+
     def stop(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
@@ -75,22 +79,39 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        sm, smax, reasons = [], [], set()
+        sm, smax, power, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            parts = [p.strip() for p in ln.split(",")]
+        import datetime
+
+        def stamp(ln):
+            try:
+                ts = ln.split(",")[0].strip()
+                return datetime.datetime.strptime(ts, "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except ValueError:
+                return None
+
+        lines = self.lines
+        scope = "all samples"
+        if self.window is not None:
+            inside = [ln for ln in lines if (stamp(ln) or -1.0) >= self.window[0] and (stamp(ln) or -1.0) <= self.window[1]]
+            if inside:
+                lines, scope = inside, "timed region"
+        for ln in lines:
+            parts = [p.strip() for p in ln.split(",")][1:]
             if len(parts) < 9:
                 continue
             try:
                 sm.append(float(parts[1]))
                 smax.append(float(parts[2]))
+                power.append(float(parts[3]))
             except ValueError:
                 continue
             for nm, v in zip(names, parts[5:9]):
                 if v.lower().startswith("active"):
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "scope": scope,
+                "power_w_median": statistics.median(power) if power else None}
 
 
 # ---------------------------------------------------------------- helpers
@@ -236,12 +257,15 @@ def ours(args):
     torch.cuda.synchronize(dev)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    tw0 = time.time()
     e0.record(stream)
     for _ in range(args.steps):
         h.gemm(A, B, C, precision=mm.FP64_EMU, stream=stream)
     e1.record(stream)
     torch.cuda.synchronize(dev)
+    tw1 = time.time()
     barrier()
+    sampler.mark(tw0, tw1)
     clocks = sampler.stop()
     t_ms = e0.elapsed_time(e1)
     launches = h.stats() - launches0

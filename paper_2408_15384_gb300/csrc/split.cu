@@ -92,18 +92,6 @@ __device__ __forceinline__ uint16_t bf16_of_small_int(int32_t d) {
   return static_cast<uint16_t>(__float_as_uint(f) >> 16);
 }
 
-// FP64-accuracy digits of one entry: out[p] for p = 0..s-1, most significant
-// first, as bfloat16 bit patterns.
-__device__ __forceinline__ void fp64_digits(uint64_t bits, int sh, int s, uint16_t* out) {
-  int64_t R = scaled_rne(bits, sh);
-  for (int p = s - 1; p >= 1; --p) {
-    int64_t d = ((R + 128) & 255) - 128;
-    out[p] = bf16_of_small_int(static_cast<int32_t>(d));
-    R = (R - d) >> 8;
-  }
-  out[0] = bf16_of_small_int(static_cast<int32_t>(R));
-}
-
 // Round the value M * 2^e (M signed) to the nearest bfloat16 (ties to even,
 // bfloat16 subnormals below 2^-126 with step 2^-133); subtract the rounded
 // value from M (exact) and return its bit pattern.
@@ -124,10 +112,8 @@ __device__ __forceinline__ uint16_t bf16_rne_take(int64_t& M, int e) {
     if (sh >= 64) {
       q = 0;
     } else {
-      q = a >> sh;
-      uint64_t rem = a & ((1ull << sh) - 1ull);
-      uint64_t half = 1ull << (sh - 1);
-      if (rem > half || (rem == half && (q & 1ull))) ++q;
+      // round half to even: add half - 1, plus one more when the kept part is odd
+      q = (a + ((1ull << (sh - 1)) - 1ull) + ((a >> sh) & 1ull)) >> sh;
     }
     L = e + sh;
     uint64_t taken = (sh >= 64) ? 0ull : (q << sh);
@@ -139,19 +125,21 @@ __device__ __forceinline__ uint16_t bf16_rne_take(int64_t& M, int e) {
     ++L;
   }
   // normalise q into [128, 256) unless that would pass below 2^-133
-  while (q < 128 && L > -133) {
-    q <<= 1;
-    --L;
+  if (q < 128) {
+    int up = __clz(static_cast<uint32_t>(q)) - 24;   // shifts that bring the top bit to bit 7
+    if (L - up < -133) up = L + 133;
+    q <<= up;
+    L -= up;
   }
   if (q < 128) return static_cast<uint16_t>(sgn | q);  // subnormal bfloat16, L == -133
   int biased = L + 7 + 127;
   return static_cast<uint16_t>(sgn | (static_cast<uint32_t>(biased) << 7) | static_cast<uint32_t>(q - 128));
 }
 
-__device__ __forceinline__ void fp32_slices3(uint64_t bits, int E, uint16_t* out) {
+__device__ __forceinline__ void fp32_slices3(uint64_t bits, int E, uint32_t& s0, uint32_t& s1, uint32_t& s2) {
   uint64_t ab = bits & ABS_MASK;
   if (ab == 0) {
-    out[0] = out[1] = out[2] = 0;
+    s0 = s1 = s2 = 0u;
     return;
   }
   uint64_t mant;
@@ -159,25 +147,96 @@ __device__ __forceinline__ void fp32_slices3(uint64_t bits, int E, uint16_t* out
   decompose(ab, mant, e);
   int64_t M = (bits >> 63) ? -static_cast<int64_t>(mant) : static_cast<int64_t>(mant);
   e -= E;
-  out[0] = bf16_rne_take(M, e);
-  out[1] = bf16_rne_take(M, e);
-  out[2] = bf16_rne_take(M, e);
+  s0 = bf16_rne_take(M, e);
+  s1 = bf16_rne_take(M, e);
+  s2 = bf16_rne_take(M, e);
+}
+
+// The slices of 8 consecutive entries (bit patterns vb, scale exponent X of
+// their row or column), stored to dst + P * plane for P = 0 .. S-1 (plane 0
+// the most significant): one 16-byte vector per plane when the run is whole
+// and aligned, else element by element. Everything stays in registers.
+//
+// FP64-accuracy digits from the biased integer Rb = R + B,
+// B = sum_{j=0}^{s-2} 128 * 256^j: digit j (least significant first) is
+// ((Rb >> 8j) & 255) - 128 for j < s-1 and the top digit is Rb >> 8(s-1)
+// (arithmetic shift), the same digits the one-at-a-time expansion
+// d = ((R + 128) mod 256) - 128, R = (R - d) / 256 produces.
+template <int MODE>
+__device__ __forceinline__ void slice8_store(const uint64_t (&vb)[8], int32_t X, int s, uint16_t* __restrict__ dst,
+                                             size_t plane, int cnt) {
+  const bool vec = (cnt == 8) && ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0);
+  if constexpr (MODE == 0) {
+    int64_t bias = 0;
+    for (int j = 0; j < s - 1; ++j) bias = (bias << 8) | 128;
+    int64_t Rb[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) Rb[u] = scaled_rne(vb[u], 8 * s - X) + bias;
+#pragma unroll
+    for (int P = 0; P < 7; ++P) {
+      if (P >= s) break;
+      const int sh = 8 * (s - 1 - P);
+      uint32_t h[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int32_t d = (P == 0) ? static_cast<int32_t>(Rb[u] >> sh)
+                                   : static_cast<int32_t>((Rb[u] >> sh) & 255) - 128;
+        h[u] = bf16_of_small_int(d);
+      }
+      uint16_t* o = dst + P * plane;
+      if (vec) {
+        *reinterpret_cast<uint4*>(o) =
+            make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16), h[6] | (h[7] << 16));
+      } else {
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (u < cnt) o[u] = static_cast<uint16_t>(h[u]);
+      }
+    }
+  } else {
+    uint32_t h[3][8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) fp32_slices3(vb[u], X, h[0][u], h[1][u], h[2][u]);
+#pragma unroll
+    for (int P = 0; P < 3; ++P) {
+      uint16_t* o = dst + P * plane;
+      if (vec) {
+        *reinterpret_cast<uint4*>(o) = make_uint4(h[P][0] | (h[P][1] << 16), h[P][2] | (h[P][3] << 16),
+                                                  h[P][4] | (h[P][5] << 16), h[P][6] | (h[P][7] << 16));
+      } else {
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (u < cnt) o[u] = static_cast<uint16_t>(h[P][u]);
+      }
+    }
+  }
 }
 
 // ---------------------------------------------------------- kernel bodies
-// Row maximum of |a| bits for one row by one warp.
+// Row maximum of |a| bits for one row by one warp (16-byte loads when the row
+// start is 16-byte aligned).
 __device__ __forceinline__ void row_absmax_body(const double* __restrict__ A, int64_t k, int64_t lda, int64_t row,
                                                 uint64_t* __restrict__ rowmax) {
   const double* a = A + row * lda;
   uint64_t mx = 0;
   const uint32_t lane = threadIdx.x & 31u;
-  int64_t c = lane;
-  for (; c + 96 < k; c += 128) {
-    uint64_t v0 = dbits(__ldg(a + c)) & ABS_MASK, v1 = dbits(__ldg(a + c + 32)) & ABS_MASK;
-    uint64_t v2 = dbits(__ldg(a + c + 64)) & ABS_MASK, v3 = dbits(__ldg(a + c + 96)) & ABS_MASK;
-    mx = max(mx, max(max(v0, v1), max(v2, v3)));
+  int64_t c0 = 0;
+  if ((reinterpret_cast<uintptr_t>(a) & 15u) == 0) {
+    const double2* a2 = reinterpret_cast<const double2*>(a);
+    const int64_t k2 = k >> 1;   // whole pairs
+    int64_t c = lane;
+    for (; c + 96 < k2; c += 128) {
+      const double2 v0 = __ldg(a2 + c), v1 = __ldg(a2 + c + 32), v2 = __ldg(a2 + c + 64), v3 = __ldg(a2 + c + 96);
+      mx = max(mx, max(max(dbits(v0.x) & ABS_MASK, dbits(v0.y) & ABS_MASK), max(dbits(v1.x) & ABS_MASK, dbits(v1.y) & ABS_MASK)));
+      mx = max(mx, max(max(dbits(v2.x) & ABS_MASK, dbits(v2.y) & ABS_MASK), max(dbits(v3.x) & ABS_MASK, dbits(v3.y) & ABS_MASK)));
+    }
+    for (; c < k2; c += 32) {
+      const double2 v = __ldg(a2 + c);
+      mx = max(mx, max(dbits(v.x) & ABS_MASK, dbits(v.y) & ABS_MASK));
+    }
+    c0 = 2 * k2;   // an odd last entry is left for the scalar loop
   }
-  for (; c < k; c += 32) mx = max(mx, dbits(__ldg(a + c)) & ABS_MASK);
+  for (int64_t c = c0 + lane; c < k; c += 32) mx = max(mx, dbits(__ldg(a + c)) & ABS_MASK);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1)
     mx = max(mx, static_cast<uint64_t>(__shfl_xor_sync(0xffffffffu, static_cast<unsigned long long>(mx), o)));
@@ -188,7 +247,13 @@ __device__ __forceinline__ void row_absmax_body(const double* __restrict__ A, in
 __device__ __forceinline__ void col_absmax_body(const double* __restrict__ B, int64_t ldb, int64_t j, int64_t r0,
                                                 int64_t r1, unsigned long long* __restrict__ colmax) {
   uint64_t mx = 0;
-  for (int64_t r = r0; r < r1; ++r) mx = max(mx, dbits(__ldg(B + r * ldb + j)) & ABS_MASK);
+  int64_t r = r0;
+  for (; r + 3 < r1; r += 4) {
+    const uint64_t v0 = dbits(__ldg(B + r * ldb + j)), v1 = dbits(__ldg(B + (r + 1) * ldb + j));
+    const uint64_t v2 = dbits(__ldg(B + (r + 2) * ldb + j)), v3 = dbits(__ldg(B + (r + 3) * ldb + j));
+    mx = max(mx, max(max(v0 & ABS_MASK, v1 & ABS_MASK), max(v2 & ABS_MASK, v3 & ABS_MASK)));
+  }
+  for (; r < r1; ++r) mx = max(mx, dbits(__ldg(B + r * ldb + j)) & ABS_MASK);
   if (mx) atomicMax(colmax + j, static_cast<unsigned long long>(mx));
 }
 
@@ -209,31 +274,7 @@ __device__ __forceinline__ void slice_rows_body(const double* __restrict__ A, in
   const int cnt = static_cast<int>((k - c0) < 8 ? (k - c0) : 8);
 #pragma unroll
   for (int u = 0; u < 8; ++u) vb[u] = (u < cnt && Ei != EXP_NONFINITE) ? dbits(__ldg(a + u)) : 0ull;
-  const int S = (MODE == 0) ? s : 3;
-  const size_t plane = static_cast<size_t>(m) * kp;
-  uint16_t dig[8][8];
-#pragma unroll
-  for (int u = 0; u < 8; ++u) {
-    if (MODE == 0)
-      fp64_digits(vb[u], 8 * s - Ei, s, dig[u]);
-    else
-      fp32_slices3(vb[u], Ei, dig[u]);
-  }
-  uint16_t* dst = slices + row * kp + c0;
-  const bool vec = (cnt == 8) && ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0);
-  for (int p = 0; p < S; ++p) {
-    uint16_t* d = dst + p * plane;
-    if (vec) {
-      uint4 w;
-      w.x = dig[0][p] | (static_cast<uint32_t>(dig[1][p]) << 16);
-      w.y = dig[2][p] | (static_cast<uint32_t>(dig[3][p]) << 16);
-      w.z = dig[4][p] | (static_cast<uint32_t>(dig[5][p]) << 16);
-      w.w = dig[6][p] | (static_cast<uint32_t>(dig[7][p]) << 16);
-      *reinterpret_cast<uint4*>(d) = w;
-    } else {
-      for (int u = 0; u < cnt; ++u) d[u] = dig[u][p];
-    }
-  }
+  slice8_store<MODE>(vb, Ei, s, slices + row * kp + c0, static_cast<size_t>(m) * kp, cnt);
 }
 
 // Slices of the 64 (k) x 32 (n) block of B at (k0, n0), transposed through
@@ -275,32 +316,10 @@ __device__ __forceinline__ void slice_cols_body(const double* __restrict__ B, in
   if (j < n && c0 < k) {
     const int32_t Fj = fexp[jl];
     const int cnt = static_cast<int>((k - c0) < 8 ? (k - c0) : 8);
-    const int S = (MODE == 0) ? s : 3;
-    uint16_t dig[8][8];
+    uint64_t vb[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const uint64_t b = (Fj == EXP_NONFINITE) ? 0ull : tile[kb + u][jl];
-      if (MODE == 0)
-        fp64_digits(b, 8 * s - Fj, s, dig[u]);
-      else
-        fp32_slices3(b, Fj, dig[u]);
-    }
-    const size_t plane = static_cast<size_t>(n) * kp;
-    uint16_t* dst = slices + j * kp + c0;
-    const bool vec = (cnt == 8) && ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0);
-    for (int p = 0; p < S; ++p) {
-      uint16_t* d = dst + p * plane;
-      if (vec) {
-        uint4 w;
-        w.x = dig[0][p] | (static_cast<uint32_t>(dig[1][p]) << 16);
-        w.y = dig[2][p] | (static_cast<uint32_t>(dig[3][p]) << 16);
-        w.z = dig[4][p] | (static_cast<uint32_t>(dig[5][p]) << 16);
-        w.w = dig[6][p] | (static_cast<uint32_t>(dig[7][p]) << 16);
-        *reinterpret_cast<uint4*>(d) = w;
-      } else {
-        for (int u = 0; u < cnt; ++u) d[u] = dig[u][p];
-      }
-    }
+    for (int u = 0; u < 8; ++u) vb[u] = (Fj == EXP_NONFINITE || u >= cnt) ? 0ull : tile[kb + u][jl];
+    slice8_store<MODE>(vb, Fj, s, slices + j * kp + c0, static_cast<size_t>(n) * kp, cnt);
   }
   __syncthreads();  // the tile is reused by the next block of a persistent loop
 }
