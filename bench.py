@@ -336,6 +336,12 @@ def ours(args):
         e2e_s = (time.perf_counter() - t0) / reps
         extra["e2e"] = {"value": flop / e2e_s / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": 16 * N * N,
                         "d2h_bytes_per_step": 8 * N * N}
+        # ---------------- the paper's own sizes and inputs (Sec. IV), every mode
+        if not args.no_paper_sweep:
+            extra["paper_sweep"] = paper_sweep_leg(h, args, mm, inputs, torch, dev, stream)
+        # ---------------- grouped: 512 products, dims log-uniform on [32, 1024], one graph replay each
+        if not args.no_grouped:
+            extra["grouped"] = grouped_leg(h, args, mm, inputs, torch, dev, stream)
         # ---------------- serving: capacity (closed loop), then Poisson arrivals at 80 % of it
         if not args.no_serve:
             extra["serve"] = serve_leg(h, args, mm, inputs)
@@ -375,6 +381,121 @@ def ours(args):
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+# The paper's best serial times (GCC -O3, Sec. VI table, Cirrus Xeon E5-2695
+# at 2.1 GHz, mean of 15 runs): context for the sweep below, not a target.
+PAPER_SERIAL_GCC_O3_S = {32: 0.00003, 64: 0.00026, 128: 0.00228, 256: 0.02028, 512: 0.17037, 1024: 1.69891}
+
+
+def paper_sweep_leg(h, args, mm, inputs, torch, dev, stream):
+    """The paper's sizes (32 .. 1024, Sec. IV) with its Box-Muller normal
+    entries, through every mode: median device time of 15 products (the paper
+    averages 15 runs) and, with the CPU leg on, the error of every output
+    against the oracle."""
+    import numpy as np
+    out = {"inputs": "Box-Muller normal deviates from two seeded unit draws (Sec. IV)", "sizes": {},
+           "slice_rule": "1 (calibrated on normal rows)"}
+    names = {mm.FP64: "fp64", mm.FP64_EMU: "fp64_emu", mm.FP32_EMU: "fp32_emu"}
+    h.set_option(mm.OPT_SLICE_RULE, 1)
+    for N in sorted(PAPER_SERIAL_GCC_O3_S):
+        A = inputs.box_muller(N, N, 7 + N, inputs.STREAM_A)
+        B = inputs.box_muller(N, N, 7 + N, inputs.STREAM_B)
+        Ad, Bd = torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev)
+        Cd = torch.empty((N, N), dtype=torch.float64, device=dev)
+        row = {"paper_serial_gcc_O3_s": PAPER_SERIAL_GCC_O3_S[N]}
+        ref = D = None
+        if not args.no_cpu_baseline:
+            import oracle
+            ref, D = oracle.gemm(A, B), oracle.absprod(A, B)
+        for prec, name in names.items():
+            h.gemm(Ad, Bd, Cd, precision=prec, stream=stream)
+            torch.cuda.synchronize(dev)
+            ts = []
+            for _ in range(15):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                h.gemm(Ad, Bd, Cd, precision=prec, stream=stream)
+                e1.record(stream)
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            ms = statistics.median(ts)
+            row[name + "_s"] = ms * 1e-3
+            row[name + "_gflops"] = 2.0 * N ** 3 / (ms * 1e-3) / 1e9
+            if ref is not None:
+                from oracle import emulation as em
+                row[name + "_max_err_over_bound"] = float(np.max(np.abs(Cd.cpu().numpy() - ref) / (em.gamma(N, name) * D)))
+        out["sizes"][str(N)] = row
+    h.set_option(mm.OPT_SLICE_RULE, 0)
+    return out
+
+
+def grouped_leg(h, args, mm, inputs, torch, dev, stream):
+    """The grouped workload: 512 independent products with M, N, K each
+    log-uniform on [32, 1024], entries uniform[-1,1), in one grouped call
+    (persistent kernels replayed from a CUDA graph). TFLOP/s = sum 2mnk over
+    the group / device time of a call, per mode, with the default tiles and
+    with autotuned tiles; sampled rows of a few problems are checked against
+    the oracle."""
+    import numpy as np
+    dims = inputs.problem_set(512, 32, 1024, 4)
+    probs, flop = [], 0.0
+    for i, (m, n, k) in enumerate(dims):
+        m, n, k = int(m), int(n), int(k)
+        A = torch.empty((m, k), dtype=torch.float64, device=dev)
+        B = torch.empty((k, n), dtype=torch.float64, device=dev)
+        C = torch.empty((m, n), dtype=torch.float64, device=dev)
+        mm.fill_uniform(A, 4000 + i, inputs.STREAM_A)
+        mm.fill_uniform(B, 4000 + i, inputs.STREAM_B)
+        probs.append((A, B, C))
+        flop += 2.0 * m * n * k
+    arr = mm.Handle.problem_array(probs)
+    torch.cuda.synchronize(dev)
+
+    def timed(prec, reps=10):
+        for _ in range(3):
+            h.grouped(arr, precision=prec, stream=stream)
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            h.grouped(arr, precision=prec, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    out = {"problems": 512, "dims": "log-uniform [32, 1024]", "flop_per_call": flop}
+    names = {mm.FP64: "fp64", mm.FP64_EMU: "fp64_emu", mm.FP32_EMU: "fp32_emu"}
+    for prec, name in names.items():
+        ms = timed(prec)
+        out[name + "_tflops"] = flop / (ms * 1e-3) / 1e12
+        out[name + "_ms"] = ms
+    h.set_option(mm.OPT_AUTOTUNE, 1)
+    for prec, name in names.items():
+        ms = timed(prec)
+        out[name + "_tuned_tflops"] = flop / (ms * 1e-3) / 1e12
+        d = np.mean([np.cbrt(a * b * c) for a, b, c in dims])
+        out[name + "_tuned_cfg"] = h.tune_lookup(prec, 512, int(round(d)), grouped=True)
+    h.set_option(mm.OPT_AUTOTUNE, 0)
+    if not args.no_cpu_baseline:
+        import oracle
+        from oracle import emulation as em
+        worst = 0.0
+        for prec, name in names.items():
+            h.grouped(arr, precision=prec, stream=stream)
+            torch.cuda.synchronize(dev)
+            for i in range(0, 512, 128):
+                A, B, C = probs[i]
+                Ah, Bh = A.cpu().numpy(), B.cpu().numpy()
+                rows = [0, Ah.shape[0] - 1]
+                D = oracle.absprod_rows(Ah, Bh, rows)
+                ref = oracle.gemm_rows(Ah, Bh, rows)
+                worst = max(worst, float(np.max(np.abs(C[rows].cpu().numpy() - ref) /
+                                                (em.gamma(Ah.shape[1], name) * D))))
+        out["sampled_max_err_over_bound"] = worst
+    return out
 
 
 def serve_leg(h, args, mm, inputs):
@@ -423,6 +544,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="headline line only")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
+    ap.add_argument("--no-grouped", action="store_true", help="skip the grouped leg")
+    ap.add_argument("--no-paper-sweep", action="store_true", help="skip the paper-size sweep")
     ap.add_argument("--serve-requests", type=int, default=100000)
     args = ap.parse_args()
     if args.impl == "reference":

@@ -186,8 +186,11 @@ enum {
     MM_OPT_PROFILE = 7,           /* 1 = time every kernel launch with CUDA events (see mm_profile_read) */
     MM_OPT_CTA_PAIR = 8,          /* emulated products: 0 = automatic, 1 = one CTA per 128-row tile,
                                      2 = CTA pairs (cta_group::2) on 256-row tiles */
-    MM_OPT_TILE_N = 9             /* FP64-accuracy tile width: 0 = automatic, 128, 192, 240 or 256
+    MM_OPT_TILE_N = 9,            /* FP64-accuracy tile width: 0 = automatic, 128, 192, 240 or 256
                                      columns. Every choice gives the same bits. */
+    MM_OPT_SLICE_RULE = 10        /* automatic FP64-accuracy slice count (see mm_slices_for_k_rule):
+                                     0 = calibrated on uniform-like rows (default), 1 = on rows of
+                                     normal deviates (heavier tails, more slices) */
 };
 
 /* Kernel classes for mm_profile_read. */
@@ -199,8 +202,16 @@ enum {
 int mm_set_option(mm_handle h, int option, int64_t value);
 int mm_get_option(mm_handle h, int option, int64_t *value);
 
-/* The slice count the automatic rule picks for inner dimension k (FP64-EMU). */
+/* The slice count the automatic rule picks for inner dimension k (FP64-EMU),
+ * default rule. The slice count sets the accuracy: the error of the emulated
+ * product grows with each row's (column's) largest entry against its typical
+ * ones, and the componentwise bound 4k*2^-53*|A||B| is what the rules are
+ * calibrated to, at most half of it at each threshold:
+ *   rule 0 (rows like uniform samples):   s = 7 for k < 96, 6 for k < 4096, else 5
+ *   rule 1 (rows like normal deviates):   s = 7 for k < 160, 6 for k < 12288, else 5
+ * mm_slices_for_k_rule returns -1 for an unknown rule. */
 int mm_slices_for_k(int64_t k);
+int mm_slices_for_k_rule(int64_t k, int rule);
 
 /* ---------------------------------------------------------------- autotuner */
 

@@ -25,6 +25,7 @@ OPT_SLICES, OPT_TIMEOUT_MS, OPT_AUTOTUNE, OPT_SERVE_MAX_BATCH, OPT_SERVE_STREAMS
 OPT_PROFILE = 7
 OPT_CTA_PAIR = 8
 OPT_TILE_N = 9
+OPT_SLICE_RULE = 10
 KERNEL_SLICE_GEMM, KERNEL_SPLIT, KERNEL_FP64_GEMM = 0, 1, 2
 
 
@@ -135,15 +136,23 @@ class Handle:
         """Wait for the stream; return the sticky device status (0 = ok)."""
         return self.lib.mm_sync(self.h, _stream_handle(stream))
 
-    def grouped(self, problems, precision=FP64_EMU, stream=None):
-        """problems: list of (A, B, C) CUDA tensors; one grouped launch."""
+    @staticmethod
+    def problem_array(problems):
+        """The mm_problem array of a list of (A, B, C) CUDA tensors, reusable
+        across grouped calls on the same tensors."""
         arr = (_lib.Problem * len(problems))()
         for i, (A, B, C) in enumerate(problems):
             pa, m, k, lda = _mat(A, "A")
             pb, _, n, ldb = _mat(B, "B")
             pc, _, _, ldc = _mat(C, "C")
             arr[i] = _lib.Problem(m, n, k, pa, lda, pb, ldb, pc, ldc)
-        _check(self.lib.mm_gemm_grouped(self.h, len(problems), arr, _prec(precision), _stream_handle(stream)),
+        return arr
+
+    def grouped(self, problems, precision=FP64_EMU, stream=None):
+        """problems: list of (A, B, C) CUDA tensors, or an array from
+        problem_array; one grouped launch."""
+        arr = problems if isinstance(problems, ctypes.Array) else self.problem_array(problems)
+        _check(self.lib.mm_gemm_grouped(self.h, len(arr), arr, _prec(precision), _stream_handle(stream)),
                "mm_gemm_grouped")
 
     # ------------------------------------------------------------- serving
@@ -259,8 +268,8 @@ class Handle:
         return L
 
 
-def slices_for_k(k: int) -> int:
-    return _lib.load().mm_slices_for_k(int(k))
+def slices_for_k(k: int, rule: int = 0) -> int:
+    return _lib.load().mm_slices_for_k_rule(int(k), int(rule))
 
 
 def fill_uniform(X, seed: int, stream_id: int, scale_mode: int = 0, exp_stream_id: int = 0, stream=None):

@@ -64,6 +64,7 @@ SIGNATURES = {
     "mm_set_option": (c_int, [c_vp, c_int, c_i64]),
     "mm_get_option": (c_int, [c_vp, c_int, ctypes.POINTER(c_i64)]),
     "mm_slices_for_k": (c_int, [c_i64]),
+    "mm_slices_for_k_rule": (c_int, [c_i64, c_int]),
     "mm_tune_save": (c_int, [c_vp, ctypes.c_char_p]),
     "mm_tune_load": (c_int, [c_vp, ctypes.c_char_p]),
     "mm_tune_lookup": (c_int, [c_vp, c_int, c_int, c_i64, c_i64, c_i64, ctypes.POINTER(c_int), ctypes.POINTER(c_int),

@@ -96,7 +96,7 @@ struct EmuPlan {
     for (int i = 0; i < count; ++i) {
       const mm_problem& q = probs[idx[i]];
       Prob& r = p[i];
-      r.s = fp64 ? (h->opt_slices > 0 ? h->opt_slices : slices_for_k(q.k)) : 3;
+      r.s = fp64 ? (h->opt_slices > 0 ? h->opt_slices : slices_for_k(q.k, h->opt_slice_rule)) : 3;
       r.kp = static_cast<int64_t>(align_up(static_cast<size_t>(q.k), 8));
       r.colmax = cm; cm += align_up(8 * static_cast<size_t>(q.n), 256);
       r.rowmax = o; o = align_up(o + 8 * static_cast<size_t>(q.m), 256);

@@ -53,6 +53,7 @@ struct mm_handle_s {
 
   // options
   int opt_slices = 0;
+  int opt_slice_rule = 0;    // automatic slice count: 0 uniform-calibrated, 1 normal-calibrated
   int64_t opt_timeout_ms = 2000;
   bool opt_autotune = false;
   int opt_serve_max_batch = 64;
@@ -87,7 +88,7 @@ int ws_alloc(mm_handle_s* h, size_t bytes, cudaStream_t st, void** out);
 void ws_free(mm_handle_s* h, void* p, size_t bytes, cudaStream_t st);
 int validate_problem(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B, int64_t ldb,
                      const double* C, int64_t ldc, int precision);
-int slices_for_k(int64_t k);
+int slices_for_k(int64_t k, int rule);
 int fixed_shift(int s, int64_t k);
 bool encode_slices_tmap(mm_handle_s* h, CUtensorMap* tm, const void* base, int64_t k, int64_t rows, int S, int64_t kp,
                         int box_rows);

@@ -131,7 +131,17 @@ int validate_problem(int64_t m, int64_t n, int64_t k, const double* A, int64_t l
 // Slice count of the FP64-accuracy mode for inner dimension k: the smallest s
 // whose measured error stays near a quarter of the bound 4k*2^-53 |A||B| on the
 // workload distributions (uniform rows/columns times a power of two).
-int slices_for_k(int64_t k) {
+// Slice count for inner dimension k. Rule 0 is calibrated on rows whose
+// entries are spread like uniform samples (maximum about twice the mean
+// magnitude); rule 1 on rows of normal deviates (maximum about five times the
+// mean), whose dropped level s+2 weighs more against the componentwise bound.
+// Both keep the oracle's error at most half the bound at their thresholds.
+int slices_for_k(int64_t k, int rule) {
+  if (rule == 1) {
+    if (k >= 12288) return 5;
+    if (k >= 160) return 6;
+    return 7;
+  }
   if (k >= 4096) return 5;
   if (k >= 96) return 6;
   return 7;
@@ -215,7 +225,8 @@ int run_emulated(mm_handle_s* h, int precision, int64_t m, int64_t n, int64_t k,
                  const double* B, int64_t ldb, double* C, int64_t ldc, cudaStream_t st, int64_t* levels,
                  int s_override, const TileCfg& cfg_in) {
   const bool fp64 = (precision == MM_FP64_EMU);
-  const int s = fp64 ? (s_override > 0 ? s_override : (h->opt_slices > 0 ? h->opt_slices : slices_for_k(k))) : 3;
+  const int s = fp64 ? (s_override > 0 ? s_override : (h->opt_slices > 0 ? h->opt_slices : slices_for_k(k, h->opt_slice_rule)))
+                     : 3;
   SplitLayout L;
   L.plan(m, n, k, s);
   void* wsv = nullptr;
@@ -505,6 +516,10 @@ int mm_set_option(mm_handle h, int option, int64_t value) {
       if (value < 0 || value > 2) return MM_ERR_INVALID_ARG;
       h->opt_cta_pair = static_cast<int>(value);
       return MM_OK;
+    case MM_OPT_SLICE_RULE:
+      if (value != 0 && value != 1) return MM_ERR_INVALID_ARG;
+      h->opt_slice_rule = static_cast<int>(value);
+      return MM_OK;
     case MM_OPT_TILE_N:
       if (value != 0 && !slice_gemm_tile_ok(SLICE_FP64EMU, static_cast<int>(value), 1)) return MM_ERR_INVALID_ARG;
       h->opt_tile_n = static_cast<int>(value);
@@ -525,11 +540,13 @@ int mm_get_option(mm_handle h, int option, int64_t* value) {
     case MM_OPT_PROFILE: *value = h->opt_profile; return MM_OK;
     case MM_OPT_CTA_PAIR: *value = h->opt_cta_pair; return MM_OK;
     case MM_OPT_TILE_N: *value = h->opt_tile_n; return MM_OK;
+    case MM_OPT_SLICE_RULE: *value = h->opt_slice_rule; return MM_OK;
     default: return MM_ERR_INVALID_ARG;
   }
 }
 
-int mm_slices_for_k(int64_t k) { return slices_for_k(k); }
+int mm_slices_for_k(int64_t k) { return slices_for_k(k, 0); }
+int mm_slices_for_k_rule(int64_t k, int rule) { return (rule == 0 || rule == 1) ? slices_for_k(k, rule) : -1; }
 
 // ------------------------------------------------------------- diagnostics
 int mm_fill_uniform(double* X, int64_t rows, int64_t cols, int64_t ld, uint64_t seed, uint64_t stream_id,

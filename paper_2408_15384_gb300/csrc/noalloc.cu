@@ -108,7 +108,7 @@ int mm_gemm_emu_static(int64_t m, int64_t n, int64_t k, const double* A, int64_t
     return cuda_status(launch_fp64_gemm(2, a, st), "fp64 gemm");
   }
   const bool fp64 = precision == MM_FP64_EMU;
-  const int s = fp64 ? slices_for_k(k) : 3;
+  const int s = fp64 ? slices_for_k(k, 0) : 3;
   SplitLayout L;
   L.plan(m, n, k, s);
   const size_t status_bytes = 256;

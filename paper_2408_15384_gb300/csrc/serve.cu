@@ -70,7 +70,7 @@ static size_t request_charge(mm_handle_s* h, const mm_request& r) {
   const mm_problem& p = r.prob;
   size_t bytes = 8 * static_cast<size_t>(p.m * p.k + p.k * p.n + p.m * p.n);
   if (r.precision != MM_FP64 && p.k > 0) {
-    const int s = (r.precision == MM_FP64_EMU) ? (h->opt_slices > 0 ? h->opt_slices : slices_for_k(p.k)) : 3;
+    const int s = (r.precision == MM_FP64_EMU) ? (h->opt_slices > 0 ? h->opt_slices : slices_for_k(p.k, h->opt_slice_rule)) : 3;
     const size_t kp = align_up(static_cast<size_t>(p.k), 8);
     bytes += 2 * static_cast<size_t>(s) * (p.m + p.n) * kp + 16 * static_cast<size_t>(p.m + p.n) + 8192;
   }

@@ -153,3 +153,24 @@ def test_config_serve_stream(h, mm):
             continue
         Ah, Bh = A.cpu().numpy(), B.cpu().numpy()
         check_rows(C, Ah, Bh, [0, A.shape[0] - 1], MODE[p])
+
+
+@pytest.mark.parametrize("N", [32, 64, 128, 256, 512, 1024])
+def test_paper_sizes_box_muller_every_output(h, mm, N):
+    # the paper's sizes (Sec. IV) with its Box-Muller normal entries
+    A = inputs.box_muller(N, N, 7 + N, inputs.STREAM_A)
+    B = inputs.box_muller(N, N, 7 + N, inputs.STREAM_B)
+    ref, D = oracle.gemm(A, B), oracle.absprod(A, B)
+    Ad, Bd = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    for prec in (mm.FP64, mm.FP64_EMU, mm.FP32_EMU):
+        C = h.gemm(Ad, Bd, precision=prec)
+        assert h.sync() == 0
+        assert bound_ok(C.cpu().numpy(), ref, D, em.gamma(N, MODE[prec])), (N, prec)
+    # the slice rule calibrated on normal rows keeps half the bound
+    h.set_option(mm.OPT_SLICE_RULE, 1)
+    try:
+        C = h.gemm(Ad, Bd, precision=mm.FP64_EMU)
+        assert h.sync() == 0
+    finally:
+        h.set_option(mm.OPT_SLICE_RULE, 0)
+    assert bound_ok(C.cpu().numpy(), ref, D, 0.5 * em.gamma(N, "fp64_emu")), N
