@@ -146,8 +146,8 @@ static int fill_emu_blob(mm_handle_s* h, const EmuPlan& plan, const EmuLayout& L
     g.slA = reinterpret_cast<uint16_t*>(wsp + r.sa);
     g.slB = reinterpret_cast<uint16_t*>(wsp + r.sb);
     off[0 * (cap + 1) + i] = acc[0]; acc[0] += (q.m + 7) / 8;
-    off[1 * (cap + 1) + i] = acc[1]; acc[1] += ((q.n + 255) / 256) * ((q.k + 255) / 256);
-    off[2 * (cap + 1) + i] = acc[2]; acc[2] += q.m * ((q.k + 2047) / 2048);
+    off[1 * (cap + 1) + i] = acc[1]; acc[1] += ((q.n + 31) / 32) * ((q.k + 255) / 256);
+    off[2 * (cap + 1) + i] = acc[2]; acc[2] += (q.m * ((q.k + 7) / 8) + 255) / 256;
     off[3 * (cap + 1) + i] = acc[3]; acc[3] += ((q.n + 31) / 32) * ((q.k + 63) / 64);
     SliceProblem& P = sp[i];
     memset(&P, 0, sizeof(P));

@@ -385,15 +385,21 @@ __global__ void __launch_bounds__(256) grouped_absmax_kernel(const GroupedSplitA
       const int p = find_problem(a.off[1], count, v);
       const GroupedSplit& g = a.probs[p];
       const int64_t lb = v - a.off[1][p];
-      const int64_t ncb = (g.n + 255) / 256;
-      const int64_t j = (lb % ncb) * 256 + threadIdx.x, r0 = (lb / ncb) * 256;
-      if (j < g.n) col_absmax_body(g.B, g.ldb, j, r0, min(g.k, r0 + 256), reinterpret_cast<unsigned long long*>(g.colmax));
+      // 32 columns x 256 rows per block: warp w takes rows r0 + w, r0 + w + 8, ...
+      const int64_t ncb = (g.n + 31) / 32;
+      const int64_t j = (lb % ncb) * 32 + (threadIdx.x & 31), r0 = (lb / ncb) * 256 + (threadIdx.x >> 5);
+      if (j < g.n) {
+        uint64_t mx = 0;
+        const int64_t r1 = min(g.k, (lb / ncb) * 256 + 256);
+        for (int64_t r = r0; r < r1; r += 8) mx = max(mx, dbits(__ldg(g.B + r * g.ldb + j)) & ABS_MASK);
+        if (mx) atomicMax(reinterpret_cast<unsigned long long*>(g.colmax) + j, static_cast<unsigned long long>(mx));
+      }
     }
   }
 }
 
-// Phase 2: slices of every row of A (2048 entries per block) then of every
-// 64 x 32 block of B.
+// Phase 2: slices of A, 256 runs of 8 entries per block taken row after row
+// (so short rows share a block), then of every 64 x 32 block of B.
 template <int MODE>
 __global__ void __launch_bounds__(256) grouped_slice_kernel(const GroupedSplitArgs a) {
   const int count = *a.count_dev;
@@ -403,9 +409,10 @@ __global__ void __launch_bounds__(256) grouped_slice_kernel(const GroupedSplitAr
       const int p = find_problem(a.off[2], count, vb);
       const GroupedSplit& g = a.probs[p];
       const int64_t lb = vb - a.off[2][p];
-      const int64_t nkc = (g.k + 2047) / 2048;
-      const int64_t row = lb / nkc, c0 = (lb % nkc) * 2048 + threadIdx.x * 8;
-      if (row < g.m && c0 < g.k) slice_rows_body<MODE>(g.A, g.m, g.k, g.lda, g.rowmax, g.s, g.kp, g.slA, g.E, a.err, row, c0);
+      const int64_t runs = (g.k + 7) / 8;   // runs of 8 entries per row
+      const int64_t u = lb * 256 + threadIdx.x;
+      const int64_t row = u / runs, c0 = (u - row * runs) * 8;
+      if (row < g.m) slice_rows_body<MODE>(g.A, g.m, g.k, g.lda, g.rowmax, g.s, g.kp, g.slA, g.E, a.err, row, c0);
     } else {
       const int64_t v = vb - t2;
       const int p = find_problem(a.off[3], count, v);
