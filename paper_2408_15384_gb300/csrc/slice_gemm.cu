@@ -421,6 +421,63 @@ __global__ void __launch_bounds__(Cfg<BN, MODE, CG>::NUM_THREADS, 1)
         for (int g = 0; g < NG; ++g)
 #pragma unroll
           for (int v = 0; v < 8; ++v) lsum[g][v] = 0;
+        // Folds run from a copy of the sums parked in local memory, 16 columns
+        // (one 128-byte line of the total) per group. The fold of a level is
+        // spread over the following chunks, one group per chunk, so its loads
+        // of the total overlap the tensor cores' next chunks; it completes
+        // before the next fold and before the tile's last one, which converts
+        // the total to doubles at once.
+        constexpr int NQ = C_::COLS_PER_THREAD / 16;
+        int32_t sums[C_::COLS_PER_THREAD];
+        asm volatile("" ::"l"(sums) : "memory");
+        int64_t* const xp = xrow + col0;
+        const bool full = (n - col0 >= C_::COLS_PER_THREAD) && ((reinterpret_cast<uintptr_t>(xp) & 15u) == 0);
+        const int ebase = Ei - 8 * (s + 1) + fix_shift;
+        const bool nan_row = (Ei == EXP_NONFINITE);
+        // fold groups [q0, q1) of the parked sums with the given level parameters
+        auto fold_groups = [&](int q0, int q1, int lsh, bool first, bool rnd, bool last) {
+          auto fold1 = [&](int i, int64_t old, int32_t Fj) -> int64_t {
+            int64_t X = old + (static_cast<int64_t>(sums[i]) << lsh);
+            if (rnd) X = (X + (1ll << (fix_shift - 1))) >> fix_shift;
+            if (last) {
+              const double o = (nan_row || Fj == EXP_NONFINITE) ? __longlong_as_double(0x7FF8000000000000ll)
+                                                               : scale_pow2(__ll2double_rn(X), ebase + Fj);
+              X = __double_as_longlong(o);
+            }
+            return X;
+          };
+#pragma unroll 1
+          for (int q = q0; q < q1; ++q) {
+            if (full) {
+              // eight 16-byte loads in flight, then the stores
+              longlong2 xv[8];
+#pragma unroll
+              for (int j = 0; j < 8; ++j)
+                xv[j] = first ? make_longlong2(0, 0) : reinterpret_cast<const longlong2*>(xp)[q * 8 + j];
+              int4 fv[4] = {};
+              if (last) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) fv[j] = __ldg(reinterpret_cast<const int4*>(P.F + col0) + q * 4 + j);
+              }
+#pragma unroll
+              for (int j = 0; j < 8; ++j) {
+                const int i = q * 16 + 2 * j;
+                const int4& f4 = fv[j >> 1];
+                xv[j].x = fold1(i, xv[j].x, (j & 1) ? f4.z : f4.x);
+                xv[j].y = fold1(i + 1, xv[j].y, (j & 1) ? f4.w : f4.y);
+                reinterpret_cast<longlong2*>(xp)[q * 8 + j] = xv[j];
+              }
+            } else {
+#pragma unroll 4
+              for (int v = 0; v < 16; ++v) {
+                const int i = q * 16 + v;
+                if (col0 + i < n) xp[i] = fold1(i, first ? 0ll : xp[i], last ? __ldg(P.F + col0 + i) : 0);
+              }
+            }
+          }
+        };
+        int pend_q = NQ, pend_lsh = 0;   // the deferred fold: next group, level parameters
+        bool pend_first = false, pend_rnd = false;
         bool first_fold = true;
         for (int d = s + 1; d >= 2 && ok; --d) {
           const int kc = chunk_blocks(d);
@@ -433,12 +490,6 @@ __global__ void __launch_bounds__(Cfg<BN, MODE, CG>::NUM_THREADS, 1)
             const int slot = chunk & 1;
             const bool level_end = (c == nch - 1);
             const bool seg_end = ((c + 1) % SEG_CHUNKS) == 0;
-            if ((level_end || seg_end) && !first_fold && row_ok && MODE != SLICE_LEVELS) {
-              // the fold after this chunk reads X: start its lines towards L2 now
-              const int64_t cend = (col0 + C_::COLS_PER_THREAD < n) ? col0 + C_::COLS_PER_THREAD : n;
-              for (int64_t cc = col0; cc < cend; cc += 16) prefetch_l2(xrow + cc);
-              if (cend > col0) prefetch_l2(xrow + cend - 1);
-            }
             if (!mbar_wait(&accf_bar[slot], static_cast<uint32_t>(chunk >> 1) & 1u, wc)) { ok = false; break; }
             tc_fence_after();
 #pragma unroll
@@ -452,72 +503,48 @@ __global__ void __launch_bounds__(Cfg<BN, MODE, CG>::NUM_THREADS, 1)
               else
                 mbar_arrive(&acce_bar[slot]);
             }
+            if constexpr (MODE != SLICE_LEVELS) {
+              if (pend_q < NQ && row_ok) {
+                // one group of the deferred fold; the next group's line towards L2
+                if (!pend_first && pend_q + 1 < NQ && col0 + (pend_q + 1) * 16 < n) prefetch_l2(xp + (pend_q + 1) * 16);
+                fold_groups(pend_q, pend_q + 1, pend_lsh, pend_first, pend_rnd, false);
+                ++pend_q;
+              }
+            }
             if (!(level_end || seg_end)) continue;
             const bool last = level_end && (d == 2);
             const bool rnd = level_end && round_at_end;
             if (row_ok) {
-              // park the sums in local memory for the fold (and reset them here,
-              // inside the branch: rows past m keep stale sums that are never
-              // stored). Either way round, the compiler spills the sums inside
-              // the chunk loop.
-              int32_t sums[C_::COLS_PER_THREAD];
-#pragma unroll
-              for (int g = 0; g < NG; ++g)
-#pragma unroll
-                for (int v = 0; v < 8; ++v) { sums[g * 8 + v] = lsum[g][v]; lsum[g][v] = 0; }
-              asm volatile("" ::"l"(sums) : "memory");
-              const int ebase = Ei - 8 * (s + 1) + fix_shift;
-              const bool nan_row = (Ei == EXP_NONFINITE);
-              // new total of element i from its old value
-              auto fold1 = [&](int i, int64_t old, int32_t Fj) -> int64_t {
-                int64_t X = old + (static_cast<int64_t>(sums[i]) << lsh);
-                if (rnd) X = (X + (1ll << (fix_shift - 1))) >> fix_shift;
-                if (last) {
-                  const double o = (nan_row || Fj == EXP_NONFINITE) ? __longlong_as_double(0x7FF8000000000000ll)
-                                                                   : scale_pow2(__ll2double_rn(X), ebase + Fj);
-                  X = __double_as_longlong(o);
-                }
-                return X;
-              };
-              int64_t* const xp = xrow + col0;
-              const bool full = (n - col0 >= C_::COLS_PER_THREAD) && ((reinterpret_cast<uintptr_t>(xp) & 15u) == 0);
               if constexpr (MODE == SLICE_LEVELS) {
                 int64_t* const lp = P.levels + (static_cast<int64_t>(d - 2) * P.m + row) * n + col0;
 #pragma unroll
-                for (int i = 0; i < C_::COLS_PER_THREAD; ++i)
-                  if (col0 + i < n) lp[i] += static_cast<int64_t>(sums[i]);
-              } else if (full) {
-                // 16 columns at a time: eight 16-byte loads in flight, then the stores
+                for (int g = 0; g < NG; ++g)
 #pragma unroll
-                for (int q = 0; q < C_::COLS_PER_THREAD / 16; ++q) {
-                  longlong2 xv[8];
-#pragma unroll
-                  for (int j = 0; j < 8; ++j)
-                    xv[j] = first_fold ? make_longlong2(0, 0) : reinterpret_cast<const longlong2*>(xp)[q * 8 + j];
-                  int4 fv[4] = {};
-                  if (last) {
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) fv[j] = __ldg(reinterpret_cast<const int4*>(P.F + col0) + q * 4 + j);
+                  for (int v = 0; v < 8; ++v) {
+                    const int i = g * 8 + v;
+                    if (col0 + i < n) lp[i] += static_cast<int64_t>(lsum[g][v]);
+                    lsum[g][v] = 0;
                   }
-#pragma unroll
-                  for (int j = 0; j < 8; ++j) {
-                    const int i = q * 16 + 2 * j;
-                    const int4& f4 = fv[j >> 1];
-                    xv[j].x = fold1(i, xv[j].x, (j & 1) ? f4.z : f4.x);
-                    xv[j].y = fold1(i + 1, xv[j].y, (j & 1) ? f4.w : f4.y);
-                    reinterpret_cast<longlong2*>(xp)[q * 8 + j] = xv[j];
-                  }
-                  asm volatile("" ::: "memory");   // one group's values live at a time
-                }
               } else {
+                // finish the previous fold, then park these sums (and reset them
+                // here, inside the branch: rows past m keep stale sums that are
+                // never stored; resetting outside makes the compiler spill the
+                // sums in the chunk loop)
+                if (pend_q < NQ) fold_groups(pend_q, NQ, pend_lsh, pend_first, pend_rnd, false);
 #pragma unroll
-                for (int q4 = 0; q4 < C_::COLS_PER_THREAD / 4; ++q4) {
+                for (int g = 0; g < NG; ++g)
 #pragma unroll
-                  for (int v = 0; v < 4; ++v) {
-                    const int i = q4 * 4 + v;
-                    if (col0 + i < n) xp[i] = fold1(i, first_fold ? 0ll : xp[i], last ? __ldg(P.F + col0 + i) : 0);
-                  }
-                  asm volatile("" ::: "memory");
+                  for (int v = 0; v < 8; ++v) { sums[g * 8 + v] = lsum[g][v]; lsum[g][v] = 0; }
+                asm volatile("" ::"l"(sums) : "memory");
+                if (last) {
+                  fold_groups(0, NQ, lsh, first_fold, rnd, true);
+                  pend_q = NQ;
+                } else {
+                  if (!first_fold) prefetch_l2(xp);
+                  pend_q = 0;
+                  pend_lsh = lsh;
+                  pend_first = first_fold;
+                  pend_rnd = rnd;
                 }
               }
             }

@@ -59,7 +59,9 @@ TileCfg default_cfg(const mm_handle_s* h, int precision, int64_t m, int64_t n) {
   }
   const bool fp64 = precision == MM_FP64_EMU;
   const int pairs = fp64 ? h->max_pairs_fp64 : h->max_pairs_fp32;
-  c.cg = (h->opt_cta_pair == 1) ? 1 : (h->opt_cta_pair == 2 ? 2 : (m > 128 ? 2 : 1));
+  // CTA pairs for FP32-accuracy products taller than one tile; FP64-accuracy
+  // runs faster on single CTAs (its epilogue, not operand traffic, limits it)
+  c.cg = (h->opt_cta_pair == 1) ? 1 : (h->opt_cta_pair == 2 ? 2 : ((!fp64 && m > 128) ? 2 : 1));
   if (pairs <= 0) c.cg = 1;
   if (fp64) {
     // 256-wide tiles whenever the product is wider than one 128-wide tile

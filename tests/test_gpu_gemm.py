@@ -425,3 +425,24 @@ def test_bounded_wait_times_out_and_context_survives(h, mm):
     assert bound_ok(C, oracle.gemm(A, B), oracle.absprod(A, B), em.gamma(70, "fp64_emu"))
     with pytest.raises(Exception):
         mm._check(h.debug_wait_timeout(0), "wait probe")
+
+
+def test_long_k_segment_folds_agree_across_tilings(h, mm):
+    # k = 24000 (s = 5): level 6 has more than 120 chunks, so its sums are folded
+    # mid-level too; the 128-wide (TMEM total) and 256-wide (register sums,
+    # folds spread over the following chunks) kernels must agree bit for bit
+    m, n, k = 130, 260, 24000
+    A = inputs.row_scaled(m, k, 901)
+    B = inputs.col_scaled(k, n, 901)
+    out = {}
+    for bn in (128, 256):
+        h.set_option(mm.OPT_TILE_N, bn)
+        try:
+            out[bn], rc = run(h, A, B, mm.FP64_EMU)
+        finally:
+            h.set_option(mm.OPT_TILE_N, 0)
+        assert rc == 0
+    assert np.array_equal(out[128], out[256])
+    rows = [0, 64, 129]
+    assert bound_ok(out[256][rows], oracle.gemm_rows(A, B, rows), oracle.absprod_rows(A, B, rows),
+                    em.gamma(k, "fp64_emu"))
