@@ -144,12 +144,19 @@ int mm_gemm_host(mm_handle h, int64_t m, int64_t n, int64_t k,
  * MM_OK, MM_ERR_NONFINITE or MM_ERR_TIMEOUT. */
 int mm_sync(mm_handle h, void *stream);
 
-/* `count` independent products in one persistent launch (per stage), replayed
- * from a CUDA graph that is captured once per (count, precision, stream) and
- * updated with the new descriptors on every call. Each problem's result equals
- * mm_gemm on that problem (same kernels and tile choices, so bit-identical for
- * MM_FP64 and MM_FP64_EMU). Problems may have any shapes; their C must not
- * overlap any A or B. Errors as for mm_gemm, checked for every problem. */
+/* `count` independent products in one persistent launch per stage (the split
+ * kernels, then the slice GEMM, for the emulated modes; one FP64 kernel for
+ * MM_FP64), replayed from a CUDA graph. The graph is captured once per
+ * (precision, stream, launch configuration) and again only when a call needs
+ * more problems, tiles or workspace than the captured capacities; every call
+ * copies its descriptors into it first. The launch configuration comes from
+ * the autotuner's table (MM_OPT_AUTOTUNE) or the defaults. Each problem's
+ * result equals mm_gemm on that problem: bit-identical for MM_FP64_EMU (the
+ * same slice counts and exact recombination whatever the tiles) and for
+ * MM_FP64 when both use the same FP64 tile kernel; within its bound for
+ * MM_FP32_EMU. Problems may have any shapes; their C must not overlap any A
+ * or B. Errors as for mm_gemm, checked for every problem. The call blocks only
+ * while it tunes, or when both graph slots are still running earlier calls. */
 int mm_gemm_grouped(mm_handle h, int count, const mm_problem *probs,
                     int precision, void *stream);
 
