@@ -90,12 +90,18 @@ int validate_problem(int64_t m, int64_t n, int64_t k, const double* A, int64_t l
                      const double* C, int64_t ldc, int precision);
 int slices_for_k(int64_t k, int rule);
 int fixed_shift(int s, int64_t k);
+// 3-D map (k, rows, slice) over bfloat16 slices; planes of plane_rows rows
+// (0: rows), so a panel of a larger matrix's slices can be mapped.
 bool encode_slices_tmap(mm_handle_s* h, CUtensorMap* tm, const void* base, int64_t k, int64_t rows, int S, int64_t kp,
-                        int box_rows);
+                        int box_rows, int64_t plane_rows = 0);
 void count_launch(mm_handle_s* h, uint64_t n);
 int fp64_kind(mm_handle_s* h);
 int gemm_device(mm_handle_s* h, int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
                 int64_t ldb, double* C, int64_t ldc, int precision, cudaStream_t st);
+struct SplitLayout;
+int emu_slices(mm_handle_s* h, int precision, int64_t k, int s_override);
+int emu_gemm_rows(mm_handle_s* h, int precision, const SplitLayout& L, char* ws, int s, int64_t r0, int64_t mr,
+                  double* C, int64_t ldc, int64_t* levels, const TileCfg& cfg, cudaStream_t st);
 // one product with an explicit launch configuration (no tuning)
 int gemm_with_cfg(mm_handle_s* h, int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
                   int64_t ldb, double* C, int64_t ldc, int precision, const TileCfg& cfg, cudaStream_t st);

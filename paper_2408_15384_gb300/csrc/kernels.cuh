@@ -16,8 +16,11 @@ static inline uint64_t splitmix_mix_host(uint64_t z) {
 // ---------------------------------------------------------------- split.cu
 cudaError_t launch_absmax(const double* A, int64_t m, int64_t k, int64_t lda, const double* B, int64_t n,
                           int64_t ldb, uint64_t* rowmax, uint64_t* colmax, cudaStream_t st);
+// Slices of rows [0, m) of A into planes of plane_rows rows (0: m), so a
+// panel of a larger matrix can be sliced into its place.
 cudaError_t launch_slice_rows(int mode, const double* A, int64_t m, int64_t k, int64_t lda, const uint64_t* rowmax,
-                              int s, int64_t kp, uint16_t* slices, int32_t* E, uint32_t* err, cudaStream_t st);
+                              int s, int64_t kp, uint16_t* slices, int32_t* E, uint32_t* err, cudaStream_t st,
+                              int64_t plane_rows = 0);
 cudaError_t launch_slice_cols(int mode, const double* B, int64_t k, int64_t n, int64_t ldb, const uint64_t* colmax,
                               int s, int64_t kp, uint16_t* slices, int32_t* F, uint32_t* err, cudaStream_t st);
 cudaError_t launch_fill_uniform(double* X, int64_t rows, int64_t cols, int64_t ld, uint64_t seed, uint64_t stream_id,

@@ -158,9 +158,10 @@ int fixed_shift(int s, int64_t k) {
 }
 
 bool encode_slices_tmap(mm_handle_s* h, CUtensorMap* tm, const void* base, int64_t k, int64_t rows, int S, int64_t kp,
-                        int box_rows) {
+                        int box_rows, int64_t plane_rows) {
   cuuint64_t dims[3] = {static_cast<cuuint64_t>(k), static_cast<cuuint64_t>(rows), static_cast<cuuint64_t>(S)};
-  cuuint64_t strides[2] = {static_cast<cuuint64_t>(kp * 2), static_cast<cuuint64_t>(rows * kp * 2)};
+  cuuint64_t strides[2] = {static_cast<cuuint64_t>(kp * 2),
+                           static_cast<cuuint64_t>((plane_rows > rows ? plane_rows : rows) * kp * 2)};
   cuuint32_t box[3] = {64u, static_cast<cuuint32_t>(box_rows), 1u};
   cuuint32_t estr[3] = {1u, 1u, 1u};
   CUresult r = h->encode(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
@@ -221,12 +222,69 @@ int run_split(mm_handle_s* h, int mode01, const SplitLayout& L, char* ws, const 
 
 // The emulated product of one problem (FP64-accuracy, FP32-accuracy, or the
 // level-product diagnostic when levels != nullptr).
+int emu_slices(mm_handle_s* h, int precision, int64_t k, int s_override) {
+  if (precision != MM_FP64_EMU) return 3;
+  if (s_override > 0) return s_override;
+  return h->opt_slices > 0 ? h->opt_slices : slices_for_k(k, h->opt_slice_rule);
+}
+
+// The slice GEMM of rows [r0, r0 + mr) of an emulated product whose exponents
+// and slices are in the workspace ws (layout L: A planes of L.m rows, B planes
+// of L.n rows). C points at row 0 of the product's output.
+int emu_gemm_rows(mm_handle_s* h, int precision, const SplitLayout& L, char* ws, int s, int64_t r0, int64_t mr,
+                  double* C, int64_t ldc, int64_t* levels, const TileCfg& cfg_in, cudaStream_t st) {
+  const bool fp64 = (precision == MM_FP64_EMU);
+  const int64_t n = L.n, k = L.k;
+  // CTA pairs (256-row tiles, half of B per CTA) unless the product is one
+  // tile high; the tile width from the configuration (tuned or default)
+  const int pairs_avail = fp64 ? h->max_pairs_fp64 : h->max_pairs_fp32;
+  const TileCfg dflt = default_cfg(h, precision, mr, n);
+  int cg = cfg_in.cg ? cfg_in.cg : dflt.cg;
+  int bn = cfg_in.bn ? cfg_in.bn : dflt.bn;
+  if (pairs_avail <= 0) cg = 1;
+  if (!slice_gemm_tile_ok(fp64 ? SLICE_FP64EMU : SLICE_FP32EMU, bn, cg)) {
+    bn = dflt.bn;
+    cg = dflt.cg;
+  }
+  CUtensorMap tmA, tmB;
+  if (!encode_slices_tmap(h, &tmA, ws + L.off_sa + 2 * static_cast<size_t>(r0) * L.kp, k, mr, L.S, L.kp, 128, L.m) ||
+      !encode_slices_tmap(h, &tmB, ws + L.off_sb, k, n, L.S, L.kp, bn / cg))
+    return MM_ERR_CUDA;
+  SliceGemmArgs a;
+  memset(&a, 0, sizeof(a));
+  SliceProblem& P = a.single;
+  P.m = mr; P.n = n; P.k = k;
+  P.nkb = static_cast<int>((k + 63) / 64);
+  P.s = s;
+  P.fix_shift = fp64 ? fixed_shift(s, k) : 0;
+  P.tiles_m = static_cast<int>((mr + 128 * cg - 1) / (128 * cg));
+  P.tiles_n = static_cast<int>((n + bn - 1) / bn);
+  P.E = reinterpret_cast<const int32_t*>(ws + L.off_E) + r0;
+  P.F = reinterpret_cast<const int32_t*>(ws + L.off_F);
+  P.C = C + r0 * ldc;
+  P.ldc = ldc;
+  P.levels = levels;
+  a.err = h->d_err;
+  a.timeout_ns = static_cast<uint64_t>(h->opt_timeout_ms) * 1000000ull;
+  const int ntiles = P.tiles_m * P.tiles_n;
+  const int grid = (cg == 2) ? 2 * std::min(ntiles, pairs_avail) : std::min(ntiles, h->sm_count);
+  const int mode = levels ? SLICE_LEVELS : (fp64 ? SLICE_FP64EMU : SLICE_FP32EMU);
+  cudaError_t e;
+  {
+    ProfScope ps(h, MM_KERNEL_SLICE_GEMM, st);
+    e = launch_slice_gemm(mode, bn, cg, &tmA, &tmB, a, grid, st);
+  }
+  count_launch(h, 1);
+  return cuda_status(e, "slice gemm");
+}
+
+// The emulated product of one problem (FP64-accuracy, FP32-accuracy, or the
+// level-product diagnostic when levels != nullptr).
 int run_emulated(mm_handle_s* h, int precision, int64_t m, int64_t n, int64_t k, const double* A, int64_t lda,
                  const double* B, int64_t ldb, double* C, int64_t ldc, cudaStream_t st, int64_t* levels,
                  int s_override, const TileCfg& cfg_in) {
   const bool fp64 = (precision == MM_FP64_EMU);
-  const int s = fp64 ? (s_override > 0 ? s_override : (h->opt_slices > 0 ? h->opt_slices : slices_for_k(k, h->opt_slice_rule)))
-                     : 3;
+  const int s = emu_slices(h, precision, k, s_override);
   SplitLayout L;
   L.plan(m, n, k, s);
   void* wsv = nullptr;
@@ -237,51 +295,7 @@ int run_emulated(mm_handle_s* h, int precision, int64_t m, int64_t n, int64_t k,
     ProfScope ps(h, MM_KERNEL_SPLIT, st);
     rc = run_split(h, fp64 ? 0 : 1, L, ws, A, lda, B, ldb, st);
   }
-  if (rc == MM_OK) {
-    // CTA pairs (256-row tiles, half of B per CTA) unless the product is one
-    // tile high; the tile width from the configuration (tuned or default)
-    const int pairs_avail = fp64 ? h->max_pairs_fp64 : h->max_pairs_fp32;
-    const TileCfg dflt = default_cfg(h, precision, m, n);
-    int cg = cfg_in.cg ? cfg_in.cg : dflt.cg;
-    int bn = cfg_in.bn ? cfg_in.bn : dflt.bn;
-    if (pairs_avail <= 0) cg = 1;
-    if (!slice_gemm_tile_ok(fp64 ? SLICE_FP64EMU : SLICE_FP32EMU, bn, cg)) {
-      bn = dflt.bn;
-      cg = dflt.cg;
-    }
-    CUtensorMap tmA, tmB;
-    if (!encode_slices_tmap(h, &tmA, ws + L.off_sa, k, m, L.S, L.kp, 128) ||
-        !encode_slices_tmap(h, &tmB, ws + L.off_sb, k, n, L.S, L.kp, bn / cg)) {
-      rc = MM_ERR_CUDA;
-    } else {
-      SliceGemmArgs a;
-      memset(&a, 0, sizeof(a));
-      SliceProblem& P = a.single;
-      P.m = m; P.n = n; P.k = k;
-      P.nkb = static_cast<int>((k + 63) / 64);
-      P.s = s;
-      P.fix_shift = fp64 ? fixed_shift(s, k) : 0;
-      P.tiles_m = static_cast<int>((m + 128 * cg - 1) / (128 * cg));
-      P.tiles_n = static_cast<int>((n + bn - 1) / bn);
-      P.E = reinterpret_cast<const int32_t*>(ws + L.off_E);
-      P.F = reinterpret_cast<const int32_t*>(ws + L.off_F);
-      P.C = C;
-      P.ldc = ldc;
-      P.levels = levels;
-      a.err = h->d_err;
-      a.timeout_ns = static_cast<uint64_t>(h->opt_timeout_ms) * 1000000ull;
-      const int ntiles = P.tiles_m * P.tiles_n;
-      const int grid = (cg == 2) ? 2 * std::min(ntiles, pairs_avail) : std::min(ntiles, h->sm_count);
-      const int mode = levels ? SLICE_LEVELS : (fp64 ? SLICE_FP64EMU : SLICE_FP32EMU);
-      cudaError_t e;
-      {
-        ProfScope ps(h, MM_KERNEL_SLICE_GEMM, st);
-        e = launch_slice_gemm(mode, bn, cg, &tmA, &tmB, a, grid, st);
-      }
-      rc = cuda_status(e, "slice gemm");
-      count_launch(h, 1);
-    }
-  }
+  if (rc == MM_OK) rc = emu_gemm_rows(h, precision, L, ws, s, 0, m, C, ldc, levels, cfg_in, st);
   ws_free(h, wsv, L.bytes, st);
   return rc;
 }
@@ -443,6 +457,91 @@ int mm_gemm(mm_handle h, int64_t m, int64_t n, int64_t k, const double* A, int64
   return gemm_device(h, m, n, k, A, lda, B, ldb, C, ldc, precision, static_cast<cudaStream_t>(stream));
 }
 
+namespace {
+
+// Emulated product from host buffers in two row panels, copies overlapping
+// the kernels: a copy stream brings B and then A's panels over while the
+// caller's stream slices B and runs each panel as soon as its rows arrive;
+// each panel's C goes back while the next one computes. Same kernels and
+// slices as the one-panel path, so the same bits.
+int gemm_host_pipelined(mm_handle_s* h, int64_t m, int64_t n, int64_t k, const double* A, int64_t lda,
+                        const double* B, int64_t ldb, double* C, int64_t ldc, int precision, cudaStream_t st,
+                        double* dA, double* dB, double* dC) {
+  const bool fp64 = precision == MM_FP64_EMU;
+  const int s = emu_slices(h, precision, k, 0);
+  SplitLayout L;
+  L.plan(m, n, k, s);
+  void* wsv = nullptr;
+  int rc = ws_alloc(h, L.bytes, st, &wsv);
+  if (rc != MM_OK) return rc;
+  char* ws = static_cast<char*>(wsv);
+  const int64_t r1 = std::min<int64_t>(m, ((m / 2 + 255) / 256) * 256);   // panel boundary, whole 256-row tiles
+  const int64_t rows[3] = {0, r1, m};
+  cudaStream_t cs = nullptr;
+  cudaEvent_t ev[7] = {};   // ready, B, A0, A1, C0, C1, done
+  cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  for (int i = 0; i < 7 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+  uint64_t* rowmax = reinterpret_cast<uint64_t*>(ws + L.off_rowmax);
+  uint64_t* colmax = reinterpret_cast<uint64_t*>(ws + L.off_colmax);
+  uint16_t* sa = reinterpret_cast<uint16_t*>(ws + L.off_sa);
+  int32_t* E = reinterpret_cast<int32_t*>(ws + L.off_E);
+  // copies: B, then A's two panels (after the caller's stream has the buffers)
+  if (e == cudaSuccess) e = cudaEventRecord(ev[0], st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev[0], 0);
+  if (e == cudaSuccess) e = cudaMemcpy2DAsync(dB, 8 * n, B, 8 * ldb, 8 * n, k, cudaMemcpyHostToDevice, cs);
+  if (e == cudaSuccess) e = cudaEventRecord(ev[1], cs);
+  for (int p = 0; p < 2 && e == cudaSuccess; ++p) {
+    const int64_t r0 = rows[p], mr = rows[p + 1] - rows[p];
+    if (mr > 0) e = cudaMemcpy2DAsync(dA + r0 * k, 8 * k, A + r0 * lda, 8 * lda, 8 * k, mr, cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[2 + p], cs);
+  }
+  // B's exponents and slices as soon as B is in
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev[1], 0);
+  if (e == cudaSuccess) {
+    ProfScope ps(h, MM_KERNEL_SPLIT, st);
+    e = launch_absmax(nullptr, 0, k, 0, dB, n, n, nullptr, colmax, st);
+    if (e == cudaSuccess)
+      e = launch_slice_cols(fp64 ? 0 : 1, dB, k, n, n, colmax, L.S, L.kp, reinterpret_cast<uint16_t*>(ws + L.off_sb),
+                            reinterpret_cast<int32_t*>(ws + L.off_F), h->d_err, st);
+    count_launch(h, 2);
+  }
+  // each panel: its rows' slices, its slice GEMM, then its C back
+  for (int p = 0; p < 2 && e == cudaSuccess && rc == MM_OK; ++p) {
+    const int64_t r0 = rows[p], mr = rows[p + 1] - rows[p];
+    e = cudaStreamWaitEvent(st, ev[2 + p], 0);
+    if (e == cudaSuccess && mr > 0) {
+      {
+        ProfScope ps(h, MM_KERNEL_SPLIT, st);
+        e = launch_absmax(dA + r0 * k, mr, k, k, nullptr, 0, 0, rowmax + r0, nullptr, st);
+        if (e == cudaSuccess)
+          e = launch_slice_rows(fp64 ? 0 : 1, dA + r0 * k, mr, k, k, rowmax + r0, L.S, L.kp, sa + r0 * L.kp, E + r0,
+                                h->d_err, st, m);
+        count_launch(h, 2);
+      }
+      if (e == cudaSuccess) rc = emu_gemm_rows(h, precision, L, ws, s, r0, mr, dC, n, nullptr, TileCfg(), st);
+    }
+    if (e == cudaSuccess && rc == MM_OK) e = cudaEventRecord(ev[4 + p], st);
+    if (e == cudaSuccess && rc == MM_OK) e = cudaStreamWaitEvent(cs, ev[4 + p], 0);
+    if (e == cudaSuccess && rc == MM_OK && mr > 0)
+      e = cudaMemcpy2DAsync(C + r0 * ldc, 8 * ldc, dC + r0 * n, 8 * n, 8 * n, mr, cudaMemcpyDeviceToHost, cs);
+  }
+  // the buffers go back to the pool only after the copy stream is done with them
+  if (cs) {
+    if (cudaEventRecord(ev[6], cs) == cudaSuccess) cudaStreamWaitEvent(st, ev[6], 0);
+  }
+  ws_free(h, wsv, L.bytes, st);
+  if (cs) {
+    cudaStreamSynchronize(cs);
+    cudaStreamDestroy(cs);
+  }
+  for (cudaEvent_t x : ev)
+    if (x) cudaEventDestroy(x);
+  if (e != cudaSuccess) return cuda_status(e, "pipelined host product");
+  return rc;
+}
+
+}  // namespace
+
 int mm_gemm_host(mm_handle h, int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
                  int64_t ldb, double* C, int64_t ldc, int precision, void* stream) {
   if (!h) return MM_ERR_INVALID_ARG;
@@ -459,20 +558,30 @@ int mm_gemm_host(mm_handle h, int64_t m, int64_t n, int64_t k, const double* A, 
   if ((rc = ws_alloc(h, bb, st, &dB)) != MM_OK) { ws_free(h, dA, ab, st); return rc; }
   if ((rc = ws_alloc(h, cb, st, &dC)) != MM_OK) { ws_free(h, dA, ab, st); ws_free(h, dB, bb, st); return rc; }
   cudaError_t e = cudaSuccess;
-  if (k > 0) {
-    e = cudaMemcpy2DAsync(dA, 8 * k, A, 8 * lda, 8 * k, m, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpy2DAsync(dB, 8 * n, B, 8 * ldb, 8 * n, k, cudaMemcpyHostToDevice, st);
-  }
-  if (e == cudaSuccess) {
-    rc = gemm_device(h, m, n, k, static_cast<double*>(dA), std::max<int64_t>(k, 1), static_cast<double*>(dB), n,
-                     static_cast<double*>(dC), n, precision, st);
-    if (rc == MM_OK) e = cudaMemcpy2DAsync(C, 8 * ldc, dC, 8 * n, 8 * n, m, cudaMemcpyDeviceToHost, st);
+  // large emulated products: two row panels with the copies overlapping the kernels
+  const bool emulated = precision == MM_FP32_EMU || (precision == MM_FP64_EMU && k > 4);
+  if (emulated && m >= 2048 && k > 0 && !tile_options_set(h)) {
+    rc = gemm_host_pipelined(h, m, n, k, A, lda, B, ldb, C, ldc, precision, st, static_cast<double*>(dA),
+                             static_cast<double*>(dB), static_cast<double*>(dC));
+  } else {
+    if (k > 0) {
+      e = cudaMemcpy2DAsync(dA, 8 * k, A, 8 * lda, 8 * k, m, cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess) e = cudaMemcpy2DAsync(dB, 8 * n, B, 8 * ldb, 8 * n, k, cudaMemcpyHostToDevice, st);
+    }
+    if (e == cudaSuccess) {
+      rc = gemm_device(h, m, n, k, static_cast<double*>(dA), std::max<int64_t>(k, 1), static_cast<double*>(dB), n,
+                       static_cast<double*>(dC), n, precision, st);
+      if (rc == MM_OK) e = cudaMemcpy2DAsync(C, 8 * ldc, dC, 8 * n, 8 * n, m, cudaMemcpyDeviceToHost, st);
+    }
   }
   ws_free(h, dA, ab, st);
   ws_free(h, dB, bb, st);
   ws_free(h, dC, cb, st);
   if (e != cudaSuccess) return cuda_status(e, "host copies");
-  if (rc != MM_OK) return rc;
+  if (rc != MM_OK) {
+    cudaStreamSynchronize(st);
+    return rc;
+  }
   e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_status(e, "synchronize");
   return read_and_clear_err(h);

@@ -259,8 +259,8 @@ __device__ __forceinline__ void col_absmax_body(const double* __restrict__ B, in
 
 // Slices of 8 consecutive entries A[row][c0 .. c0+8) (rows scaled by E).
 template <int MODE>  // 0: FP64-accuracy digits, 1: FP32-accuracy bf16 slices
-__device__ __forceinline__ void slice_rows_body(const double* __restrict__ A, int64_t m, int64_t k, int64_t lda,
-                                                const uint64_t* __restrict__ rowmax, int s, int64_t kp,
+__device__ __forceinline__ void slice_rows_body(const double* __restrict__ A, int64_t plane_rows, int64_t k,
+                                                int64_t lda, const uint64_t* __restrict__ rowmax, int s, int64_t kp,
                                                 uint16_t* __restrict__ slices, int32_t* __restrict__ E,
                                                 uint32_t* __restrict__ err, int64_t row, int64_t c0) {
   const uint64_t mx = rowmax[row];
@@ -274,7 +274,7 @@ __device__ __forceinline__ void slice_rows_body(const double* __restrict__ A, in
   const int cnt = static_cast<int>((k - c0) < 8 ? (k - c0) : 8);
 #pragma unroll
   for (int u = 0; u < 8; ++u) vb[u] = (u < cnt && Ei != EXP_NONFINITE) ? dbits(__ldg(a + u)) : 0ull;
-  slice8_store<MODE>(vb, Ei, s, slices + row * kp + c0, static_cast<size_t>(m) * kp, cnt);
+  slice8_store<MODE>(vb, Ei, s, slices + row * kp + c0, static_cast<size_t>(plane_rows) * kp, cnt);
 }
 
 // Slices of the 64 (k) x 32 (n) block of B at (k0, n0), transposed through
@@ -343,10 +343,10 @@ template <int MODE>
 __global__ void slice_rows_kernel(const double* __restrict__ A, int64_t m, int64_t k, int64_t lda,
                                   const uint64_t* __restrict__ rowmax, int s, int64_t kp,
                                   uint16_t* __restrict__ slices, int32_t* __restrict__ E,
-                                  uint32_t* __restrict__ err) {
+                                  uint32_t* __restrict__ err, int64_t plane_rows) {
   const int64_t row = blockIdx.x;
   const int64_t c0 = (static_cast<int64_t>(blockIdx.y) * blockDim.x + threadIdx.x) * 8;
-  if (row < m && c0 < k) slice_rows_body<MODE>(A, m, k, lda, rowmax, s, kp, slices, E, err, row, c0);
+  if (row < m && c0 < k) slice_rows_body<MODE>(A, plane_rows, k, lda, rowmax, s, kp, slices, E, err, row, c0);
 }
 
 template <int MODE>
@@ -480,13 +480,15 @@ cudaError_t launch_absmax(const double* A, int64_t m, int64_t k, int64_t lda, co
 }
 
 cudaError_t launch_slice_rows(int mode, const double* A, int64_t m, int64_t k, int64_t lda, const uint64_t* rowmax,
-                              int s, int64_t kp, uint16_t* slices, int32_t* E, uint32_t* err, cudaStream_t st) {
+                              int s, int64_t kp, uint16_t* slices, int32_t* E, uint32_t* err, cudaStream_t st,
+                              int64_t plane_rows) {
   if (m <= 0 || k <= 0) return cudaSuccess;
+  if (plane_rows < m) plane_rows = m;
   dim3 blk(128), grd(static_cast<unsigned>(m), static_cast<unsigned>((k + 1023) / 1024));
   if (mode == 0)
-    slice_rows_kernel<0><<<grd, blk, 0, st>>>(A, m, k, lda, rowmax, s, kp, slices, E, err);
+    slice_rows_kernel<0><<<grd, blk, 0, st>>>(A, m, k, lda, rowmax, s, kp, slices, E, err, plane_rows);
   else
-    slice_rows_kernel<1><<<grd, blk, 0, st>>>(A, m, k, lda, rowmax, s, kp, slices, E, err);
+    slice_rows_kernel<1><<<grd, blk, 0, st>>>(A, m, k, lda, rowmax, s, kp, slices, E, err, plane_rows);
   return cudaGetLastError();
 }
 

@@ -446,3 +446,23 @@ def test_long_k_segment_folds_agree_across_tilings(h, mm):
     rows = [0, 64, 129]
     assert bound_ok(out[256][rows], oracle.gemm_rows(A, B, rows), oracle.absprod_rows(A, B, rows),
                     em.gamma(k, "fp64_emu"))
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_host_entry_two_panels_same_bits(h, mm, prec):
+    # m >= 2048: the host entry runs two row panels with the copies overlapping
+    # the kernels; the result is the device entry's, bit for bit
+    m, n, k = 2600, 530, 700
+    A = inputs.row_scaled(m, k, 1300 + prec)
+    B = inputs.col_scaled(k, n, 1300 + prec)
+    Ch = h.gemm_host(A, B, precision=prec)
+    Cd, rc = run(h, A, B, prec)
+    assert rc == 0
+    assert np.array_equal(Ch, Cd)
+    rows = [0, 1299, 1300, 2599]
+    mode = "fp64_emu" if prec == 1 else "fp32_emu"
+    assert bound_ok(Ch[rows], oracle.gemm_rows(A, B, rows), oracle.absprod_rows(A, B, rows), em.gamma(k, mode))
+    # a strided host output (ldc > n) lands in place
+    big = np.full((m, n + 9), -7.0)
+    h.gemm_host(A, B, big[:, :n], precision=prec)
+    assert np.array_equal(big[:, :n], Cd) and np.all(big[:, n:] == -7.0)
