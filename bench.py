@@ -358,6 +358,17 @@ def ours(args):
                                      "kind": "oracle",
                                      "sample": f"{rows} rows of the {N}^3 product by the OpenMP triple loop "
                                                f"({dt:.1f} s, {os.cpu_count()} host cores)"}
+            # the paper's two CPU optimisations of the loop (Sec. III), on a smaller row sample
+            variants = {}
+            rv = max(used, rows // 4)
+            for name, fn in (("column_prefetch", oracle.gemm_colprefetch_rows), ("cache_tiled", oracle.gemm_tiled_rows)):
+                t0 = time.perf_counter()
+                Cv, uv = fn(An, Bn, 0, rv)
+                dv = time.perf_counter() - t0
+                variants[name] = {"value": 2.0 * rv * N * N / dv / 1e12, "unit": "TFLOP/s", "cores": uv,
+                                  "rows": rv, "same_bits_as_oracle": bool(np.array_equal(Cv[:min(rv, rows)],
+                                                                                         Cr[:min(rv, rows)]))}
+            extra["cpu_variants"] = variants
             extra["max_abs_err"] = float(np.max(np.abs(got - ref)))
             extra["max_err_over_bound"] = ratio
             extra["err_sample"] = f"{min(rows, 8)} rows x {N} columns vs the FP64 triple-loop oracle"

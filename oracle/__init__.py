@@ -6,7 +6,9 @@ may import this package. It shares no code with the GPU library:
 * ``mm_oracle.c``  the paper's FP64 triple loop (Sec. III definition, Sec. V
   serial program, Sec. III-A-1 OpenMP scheme) and |A||B| for the error bound;
 * ``emulation.py`` the split-precision modes written from the published
-  splitting methods (numpy, integer-exact).
+  splitting methods (numpy, integer-exact);
+* ``cpu_variants.c`` the paper's column-prefetching and cache-tiling forms of
+  the loop (Sec. III), for extra CPU-baseline rows; same values as the oracle.
 
 ``build()`` compiles ``mm_oracle.c`` into ``oracle/_build/libmm_oracle.so`` with
 gcc (-O2 -ffp-contract=off, OpenMP). Parity status: every function here is
@@ -25,16 +27,17 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "libmm_oracle.so")
 _SRC = os.path.join(_HERE, "mm_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "cpu_variants.c")]
 _lib = None
 
 
 def build(force: bool = False) -> str:
     """Compile the C oracle (plain gcc; portable C, no intrinsics)."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+    if force or not os.path.exists(_SO) or any(os.path.getmtime(_SO) < os.path.getmtime(f) for f in _SRCS):
         tmp = _SO + f".{os.getpid()}.tmp"
         cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
-               "-fPIC", "-shared", "-o", tmp, _SRC]
+               "-fPIC", "-shared", "-o", tmp] + _SRCS
         subprocess.run(cmd, check=True)
         os.replace(tmp, _SO)
     return _SO
@@ -52,8 +55,9 @@ def _load():
         for name in ("oracle_gemm_rows", "oracle_absprod_rows"):
             getattr(lib, name).argtypes = [i64, i64, i64, i64, P, i64, P, i64, P, i64]
             getattr(lib, name).restype = None
-        lib.oracle_gemm_omp.argtypes = [i64, i64, i64, i64, P, i64, P, i64, P, i64, ctypes.c_int]
-        lib.oracle_gemm_omp.restype = ctypes.c_int
+        for name in ("oracle_gemm_omp", "cpu_gemm_colprefetch", "cpu_gemm_tiled"):
+            getattr(lib, name).argtypes = [i64, i64, i64, i64, P, i64, P, i64, P, i64, ctypes.c_int]
+            getattr(lib, name).restype = ctypes.c_int
         lib.oracle_dot.argtypes = [i64, i64, i64, P, i64, P, i64]
         lib.oracle_dot.restype = ctypes.c_double
         _lib = lib
@@ -134,3 +138,24 @@ def gemm_omp_rows(A, B, r0: int, r1: int, nthreads: int = 0):
     used = _load().oracle_gemm_omp(r0, r1, n, k, _p(A), max(k, 1), _p(B), max(n, 1),
                                    _p(out), max(n, 1), nthreads)
     return out, used
+
+
+def _rows_variant(fn, A, B, r0, r1, nthreads):
+    A, B = _prep(A, B)
+    k, n = B.shape
+    out = np.zeros((r1 - r0, n))
+    used = fn(r0, r1, n, k, _p(A), max(k, 1), _p(B), max(n, 1), _p(out), max(n, 1), nthreads)
+    if used <= 0:
+        raise MemoryError("cpu variant could not allocate its buffer")
+    return out, used
+
+
+def gemm_colprefetch_rows(A, B, r0: int, r1: int, nthreads: int = 0):
+    """Rows [r0, r1) with column prefetching (Sec. III), OpenMP; (C_rows, threads)."""
+    return _rows_variant(_load().cpu_gemm_colprefetch, A, B, r0, r1, nthreads)
+
+
+def gemm_tiled_rows(A, B, r0: int, r1: int, nthreads: int = 0):
+    """Rows [r0, r1) with cache tiling (Sec. III), OpenMP; (C_rows, threads)."""
+    return _rows_variant(_load().cpu_gemm_tiled, A, B, r0, r1, nthreads)
+

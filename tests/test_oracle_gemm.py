@@ -135,3 +135,18 @@ def test_ieee_special_values_propagate():
 def test_empty_shapes():
     assert oracle.gemm(np.zeros((0, 3)), np.zeros((3, 4))).shape == (0, 4)
     assert np.array_equal(oracle.gemm(np.zeros((2, 0)), np.zeros((0, 3))), np.zeros((2, 3)))
+
+
+@pytest.mark.parametrize("m,n,k", [(37, 300, 261), (64, 17, 1000), (5, 513, 3)])
+def test_cpu_variants_equal_the_oracle(m, n, k):
+    # the paper's column-prefetching and cache-tiling loops take each element's
+    # products in the oracle's order, so they return the oracle's bits
+    from paper_2408_15384_gb300 import inputs
+    A = inputs.row_scaled(m, k, 51)
+    B = inputs.col_scaled(k, n, 51)
+    ref = oracle.gemm(A, B)
+    for fn in (oracle.gemm_colprefetch_rows, oracle.gemm_tiled_rows):
+        C, used = fn(A, B, 0, m, 3)
+        assert used >= 1 and np.array_equal(C, ref), fn.__name__
+        part, _ = fn(A, B, 2, m - 1, 2)
+        assert np.array_equal(part, ref[2:m - 1])
