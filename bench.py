@@ -143,6 +143,22 @@ def workload_config(N: int, ws: int) -> dict:
             "l2": "inputs 2 x 512 MiB > 129 MB L2 (no flush)", "parallelism": f"replicas x{ws}"}
 
 
+def slowest_rank_ms(t_ms: float, dist, dev) -> float:
+    """The timed region's length on the slowest rank (every rank gets it)."""
+    if dist is None:
+        return t_ms
+    import torch
+    tt = torch.tensor([t_ms], dtype=torch.float64, device=dev)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def whole_job_tflops(world_size: int, flop_per_product: float, steps: int, t_ms: float) -> float:
+    """Every rank runs its own replica of the product (replicas only): the job's
+    throughput is all ranks' flops over the slowest rank's time."""
+    return world_size * flop_per_product * steps / (t_ms * 1e-3) / 1e12
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -273,12 +289,9 @@ def ours(args):
     gemm_ms, gemm_n = h.profile_read(mm.KERNEL_SLICE_GEMM, reset=True)
     split_ms, split_n = h.profile_read(mm.KERNEL_SPLIT, reset=True)
     h.set_option(mm.OPT_PROFILE, 0)
-    if dist is not None:
-        tt = torch.tensor([t_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt.item())
+    t_ms = slowest_rank_ms(t_ms, dist, dev)
     ms_step = t_ms / args.steps
-    value = ws * flop * args.steps / (t_ms * 1e-3) / 1e12
+    value = whole_job_tflops(ws, flop, args.steps, t_ms)
 
     # ---------------- dominant kernel roofline (tensor pipe, bf16)
     peaks = measured_peaks()
