@@ -469,7 +469,7 @@ int grouped_tune_run(void* ctx, const TileCfg& c) {
 }  // namespace
 
 TileCfg grouped_cfg(mm_handle_s* h, int count, const mm_problem* probs, int precision) {
-  TileCfg c = grouped_default_cfg(h, precision);
+  TileCfg c = grouped_default_cfg(h, precision, count, probs);
   if (tile_options_set(h)) return c;
   int key[5];
   tune_key_grouped(precision, count, probs, key);
@@ -483,7 +483,7 @@ int grouped_run(mm_handle_s* h, int count, const mm_problem* probs, int precisio
   partition(count, probs, precision, main_idx, side_idx);
   int rc = run_side(h, side_idx, probs, precision, st);
   if (rc != MM_OK || main_idx.empty()) return rc;
-  TileCfg cfg = grouped_default_cfg(h, precision);
+  TileCfg cfg = grouped_default_cfg(h, precision, count, probs);
   if (!tile_options_set(h)) {
     int key[5];
     tune_key_grouped(precision, count, probs, key);
@@ -492,7 +492,7 @@ int grouped_run(mm_handle_s* h, int count, const mm_problem* probs, int precisio
       // configuration then runs once more below, through the graph
       GroupedRun r{h, count, probs, precision, st, {}};
       rc = tune_pick(h, key, tune_candidates(h, TUNE_GROUPED, precision, 0, 0), st, grouped_tune_run, &r, &cfg);
-      if (rc == MM_ERR_BUDGET) cfg = grouped_default_cfg(h, precision);
+      if (rc == MM_ERR_BUDGET) cfg = grouped_default_cfg(h, precision, count, probs);
       else if (rc != MM_OK) return rc;
     }
   }

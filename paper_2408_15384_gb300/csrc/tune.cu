@@ -79,12 +79,28 @@ TileCfg default_cfg(const mm_handle_s* h, int precision, int64_t m, int64_t n) {
   return c;
 }
 
-TileCfg grouped_default_cfg(const mm_handle_s* h, int precision) {
+// mean over the group's non-empty problems of (m n k)^(1/3)
+static double group_mean_dim(int count, const mm_problem* probs) {
+  double sum = 0;
+  int used = 0;
+  for (int i = 0; i < count; ++i) {
+    const mm_problem& p = probs[i];
+    if (p.m == 0 || p.n == 0) continue;
+    sum += std::cbrt(static_cast<double>(p.m) * static_cast<double>(p.n) * static_cast<double>(std::max<int64_t>(p.k, 1)));
+    ++used;
+  }
+  return used ? sum / used : 0.0;
+}
+
+TileCfg grouped_default_cfg(const mm_handle_s* h, int precision, int count, const mm_problem* probs) {
   TileCfg c;
   if (precision == MM_FP64) {
     c.kern = h->opt_fp64_kernel == 1 ? 1 : 2;
   } else {
-    c.bn = 128;
+    // 256-wide tiles once the products are large enough to fill them (the
+    // tensor cores need N = 256 per MMA for full rate); 128 for small ones
+    const double d = group_mean_dim(count, probs);
+    c.bn = (d >= (precision == MM_FP64_EMU ? 384.0 : 256.0)) ? 256 : 128;
     c.cg = 1;
   }
   return c;
@@ -99,18 +115,10 @@ void tune_key_single(int precision, int64_t m, int64_t n, int64_t k, int key[5])
 }
 
 void tune_key_grouped(int precision, int count, const mm_problem* probs, int key[5]) {
-  double sum = 0;
-  int used = 0;
-  for (int i = 0; i < count; ++i) {
-    const mm_problem& p = probs[i];
-    if (p.m == 0 || p.n == 0) continue;
-    sum += std::cbrt(static_cast<double>(p.m) * static_cast<double>(p.n) * static_cast<double>(std::max<int64_t>(p.k, 1)));
-    ++used;
-  }
   key[0] = TUNE_GROUPED;
   key[1] = precision;
   key[2] = ceil_log2(count);
-  key[3] = ceil_log2(used ? static_cast<int64_t>(std::llround(sum / used)) : 1);
+  key[3] = ceil_log2(static_cast<int64_t>(std::llround(std::max(group_mean_dim(count, probs), 1.0))));
   key[4] = 0;
 }
 
