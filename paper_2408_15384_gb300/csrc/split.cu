@@ -145,9 +145,22 @@ __device__ __forceinline__ void fp32_slices3(uint64_t bits, int E, uint32_t& s0,
   uint64_t mant;
   int e;
   decompose(ab, mant, e);
-  int64_t M = (bits >> 63) ? -static_cast<int64_t>(mant) : static_cast<int64_t>(mant);
   e -= E;
-  s0 = bf16_rne_take(M, e);
+  const bool neg = (bits >> 63) != 0;
+  int64_t M;
+  // the first slice of a normal entry rounds at a fixed bit (45 of the 53-bit
+  // significand): round half to even, the residual kept exact
+  if ((mant >> 52) != 0 && e + 45 >= -126) {
+    const uint64_t q = (mant + ((1ull << 44) - 1ull) + ((mant >> 45) & 1ull)) >> 45;   // 128 .. 256
+    const int64_t rest = static_cast<int64_t>(mant) - static_cast<int64_t>(q << 45);
+    M = neg ? -rest : rest;
+    const int L = e + 45 + (q == 256 ? 1 : 0);
+    const uint32_t q8 = (q == 256) ? 128u : static_cast<uint32_t>(q);
+    s0 = (neg ? 0x8000u : 0u) | (static_cast<uint32_t>(L + 7 + 127) << 7) | (q8 - 128u);
+  } else {
+    M = neg ? -static_cast<int64_t>(mant) : static_cast<int64_t>(mant);
+    s0 = bf16_rne_take(M, e);
+  }
   s1 = bf16_rne_take(M, e);
   s2 = bf16_rne_take(M, e);
 }
