@@ -187,8 +187,8 @@ enum {
     MM_OPT_AUTOTUNE = 3,      /* 1 = on the first product (or group) of a shape bucket, time every
                                  candidate launch configuration on the caller's stream (blocking
                                  that call) and keep the fastest; see mm_tune_save */
-    MM_OPT_SERVE_MAX_BATCH = 4,   /* requests per grouped launch (default 64) */
-    MM_OPT_SERVE_STREAMS = 5,     /* serving streams (default 2) */
+    MM_OPT_SERVE_MAX_BATCH = 4,   /* requests per grouped launch (default 32) */
+    MM_OPT_SERVE_STREAMS = 5,     /* serving streams (default 4) */
     MM_OPT_FP64_KERNEL = 6,       /* 0 = automatic, 1 = DFMA tiles, 2 = DMMA (mma.sync f64) tiles */
     MM_OPT_PROFILE = 7,           /* 1 = time every kernel launch with CUDA events (see mm_profile_read) */
     MM_OPT_CTA_PAIR = 8,          /* emulated products: 0 = automatic, 1 = one CTA per 128-row tile,

@@ -56,8 +56,8 @@ struct mm_handle_s {
   int opt_slice_rule = 0;    // automatic slice count: 0 uniform-calibrated, 1 normal-calibrated
   int64_t opt_timeout_ms = 2000;
   bool opt_autotune = false;
-  int opt_serve_max_batch = 64;
-  int opt_serve_streams = 2;
+  int opt_serve_max_batch = 32;
+  int opt_serve_streams = 4;
   int opt_fp64_kernel = 0;
   int opt_fp32_bn = 0;
   bool opt_profile = false;

@@ -66,7 +66,9 @@ double now_us(const mm_handle_s* h) {
 
 DeviceGuard::DeviceGuard(int dev) {
   cudaGetDevice(&prev);
-  if (prev != dev) cudaSetDevice(dev);
+  // always set: on a thread that has made no runtime call yet this also binds
+  // the primary context, which the driver-level tensor-map encoder needs
+  cudaSetDevice(dev);
   target = dev;
 }
 DeviceGuard::~DeviceGuard() {

@@ -107,7 +107,9 @@ static void retire(ServeEngine& e, Batch* b) {
 static void engine_loop(ServeEngine* ep) {
   ServeEngine& e = *ep;
   mm_handle_s* h = e.h;
-  DeviceGuard g(h->device);
+  // a new thread has no current context until a runtime call binds one; the
+  // driver-level tensor-map encoder needs it bound before the first batch
+  cudaSetDevice(h->device);
   std::unique_lock<std::mutex> lk(e.mu);
   for (;;) {
     for (Batch* b : e.finished) retire(e, b);
@@ -218,6 +220,24 @@ static ServeEngine* engine(mm_handle_s* h) {
     }
     e->streams.push_back(s);
     e->load.push_back(0);
+  }
+  // Reserve pool memory up front (the pool keeps freed memory up to the
+  // budget), so the first bursts do not wait on the driver for new memory,
+  // and a few pinned staging buffers for batch descriptors.
+  {
+    const size_t warm = std::min<size_t>(h->budget / 2, size_t(16) << 30);
+    void* p = nullptr;
+    if (cudaMallocFromPoolAsync(&p, warm, h->pool, e->streams[0]) == cudaSuccess) {
+      cudaFreeAsync(p, e->streams[0]);
+      cudaStreamSynchronize(e->streams[0]);
+    } else {
+      cudaGetLastError();
+    }
+    for (int i = 0; i < 2 * ns; ++i) {
+      void* hp = nullptr;
+      if (cudaMallocHost(&hp, size_t(1) << 20) == cudaSuccess) e->pinned_pool.emplace_back(hp, size_t(1) << 20);
+      else cudaGetLastError();
+    }
   }
   e->th = std::thread(engine_loop, e);
   h->serve = e;
