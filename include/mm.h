@@ -335,8 +335,10 @@ typedef struct {
  * Latency is measured from each request's scheduled arrival to the completion
  * time the serving engine records. Every sample_every-th request's C is copied
  * to sample_host (capacity sample_cap doubles) and described in samples
- * (capacity max_samples); *n_samples receives the count. Slots are allocated
- * for the run and freed after it. */
+ * (capacity max_samples); *n_samples receives the count. Sampled outputs are
+ * gathered in a device buffer of sample_cap doubles during the run and copied
+ * to sample_host after it (MM_ERR_BUDGET if that buffer cannot be had). Slots
+ * are allocated for the run and freed after it. */
 int mm_serve_bench(mm_handle h, const mm_serve_load *load, mm_serve_load_result *res,
                    mm_serve_sample *samples, int64_t max_samples, int64_t *n_samples,
                    double *sample_host, int64_t sample_cap);

@@ -83,6 +83,22 @@ int mm_serve_bench(mm_handle h, const mm_serve_load* L, mm_serve_load_result* re
         launch_fill_uniform(B[s], D, D, D, sd, 2, 0, 0, fs) != cudaSuccess)
       rc = MM_ERR_CUDA;
   }
+  // Sampled outputs are copied device to device on the side stream while the
+  // load runs (the slot stays held until its copy is done) and brought to the
+  // host after the run, so sampling never stalls the arrival loop.
+  const bool sampling = L->sample_every > 0 && samples && sample_host && max_samples > 0 && sample_cap > 0;
+  double* samp_dev = nullptr;
+  std::vector<cudaEvent_t> slot_ev(S, nullptr);
+  std::vector<char> slot_copy(S, 0);
+  if (rc == MM_OK && sampling) {
+    if (cudaMalloc(&samp_dev, static_cast<size_t>(sample_cap) * 8) != cudaSuccess) {
+      cudaGetLastError();
+      samp_dev = nullptr;
+      rc = MM_ERR_BUDGET;
+    }
+    for (int s = 0; s < S && rc == MM_OK; ++s)
+      if (cudaEventCreateWithFlags(&slot_ev[s], cudaEventDisableTiming) != cudaSuccess) rc = MM_ERR_CUDA;
+  }
   if (rc == MM_OK && cudaStreamSynchronize(fs) != cudaSuccess) rc = MM_ERR_CUDA;
   std::vector<double> lat(L->count, 0.0);
   std::vector<double> done_at(L->count, 0.0);
@@ -112,9 +128,12 @@ int mm_serve_bench(mm_handle h, const mm_serve_load* L, mm_serve_load_result* re
           done_at[i] = st.t_done_us;
           t_last = std::max(t_last, st.t_done_us);
           flop += 2.0 * static_cast<double>(q.m) * q.n * q.k;
-          if (L->sample_every > 0 && i % L->sample_every == 0 && samples && sample_host && ns < max_samples &&
-              host_used + q.m * q.n <= sample_cap) {
-            cudaMemcpy2D(sample_host + host_used, 8 * q.n, C[s], 8 * D, 8 * q.n, q.m, cudaMemcpyDeviceToHost);
+          if (sampling && i % L->sample_every == 0 && ns < max_samples && host_used + q.m * q.n <= sample_cap) {
+            if (cudaMemcpy2DAsync(samp_dev + host_used, 8 * q.n, C[s], 8 * D, 8 * q.n, q.m, cudaMemcpyDeviceToDevice,
+                                  fs) != cudaSuccess ||
+                cudaEventRecord(slot_ev[s], fs) != cudaSuccess)
+              rc = MM_ERR_CUDA;
+            slot_copy[s] = 1;
             samples[ns] = mm_serve_sample{i, q.m, q.n, q.k, q.prec, s, host_used};
             host_used += q.m * q.n;
             ++ns;
@@ -131,6 +150,12 @@ int mm_serve_bench(mm_handle h, const mm_serve_load* L, mm_serve_load_result* re
       while (next < L->count && start_us + spec[next].arrival_s * 1e6 <= now) {
         const int s = static_cast<int>(next % S);
         if (slot_req[s] >= 0) break;
+        if (slot_copy[s]) {
+          const cudaError_t qe = cudaEventQuery(slot_ev[s]);
+          if (qe == cudaErrorNotReady) break;
+          if (qe != cudaSuccess) rc = MM_ERR_CUDA;
+          slot_copy[s] = 0;
+        }
         const Spec& q = spec[next];
         mm_request r;
         r.prob = mm_problem{q.m, q.n, q.k, A[s], D, B[s], D, C[s], D};
@@ -173,8 +198,15 @@ int mm_serve_bench(mm_handle h, const mm_serve_load* L, mm_serve_load_result* re
   res->mean_ms = all.empty() ? 0.0 : sum / all.size();
   res->fp64_p99_ms = pct(l64, 0.99);
   res->fp32_p99_ms = pct(l32, 0.99);
+  if (cudaStreamSynchronize(fs) != cudaSuccess && rc == MM_OK) rc = MM_ERR_CUDA;
+  if (samp_dev && host_used > 0 &&
+      cudaMemcpy(sample_host, samp_dev, static_cast<size_t>(host_used) * 8, cudaMemcpyDeviceToHost) != cudaSuccess &&
+      rc == MM_OK)
+    rc = MM_ERR_CUDA;
   if (n_samples) *n_samples = ns;
-  cudaStreamSynchronize(fs);
+  for (cudaEvent_t ev : slot_ev)
+    if (ev) cudaEventDestroy(ev);
+  if (samp_dev) cudaFree(samp_dev);
   cudaStreamDestroy(fs);
   for (int s = 0; s < S; ++s) {
     if (A[s]) cudaFree(A[s]);
