@@ -494,6 +494,116 @@ __global__ void __launch_bounds__(Cfg<BN, MODE, CG>::NUM_THREADS, 1)
             }
           }
         };
+        // Carry path, taken for s <= 5 by warps whose rows are all full
+        // 16-byte aligned segments while every level fits one int32 segment
+        // and the fixed point lies at or below the last level's weight (the
+        // choice is warp-uniform, as the TMEM loads are warp-collective). After level d
+        // the low byte of each column's running sum is final (every later
+        // level adds multiples of 2^8 at this weight): it is written once to
+        // the thread's own part of C and the rest, an arithmetic shift by 8,
+        // carries into the next level's sum. The last sum S and the bytes b_l
+        // (l = 0 .. s-2, weight 2^(8l)) give the exact total
+        //   X = S 2^(8(s-1)) + sum_l b_l 2^(8l),
+        // rounded once to the fixed point as the fold path rounds it; |S| stays
+        // below SEG_CHUNKS 2^24 + 2^23 < 2^31. Full rows keep the bytes of each
+        // 16-column group (one 16-byte word per level) in the first 16(s-1) <=
+        // 64 bytes of that group's own 128-byte output, which its 4-column
+        // blocks 0 and 1 cover: blocks 3 and 2 are converted first, then the
+        // bytes of blocks 1 and 0 are read before either is written.
+        const int kc_top = chunk_blocks(s + 1);
+        const bool carry = (MODE == SLICE_FP64EMU) && s <= 5 && ((nkb + kc_top - 1) / kc_top <= SEG_CHUNKS) &&
+                           (fix_shift <= 8 * (s - 1)) && __all_sync(0xffffffffu, full);
+        if (carry) {
+          uint8_t* const xb = reinterpret_cast<uint8_t*>(xp);
+          const int W = 8 * (s - 1);
+          auto total = [&](int32_t S, uint64_t R, int32_t Fj) -> double {
+            int64_t X;
+            if (fix_shift == 0)
+              X = (static_cast<int64_t>(S) << W) + static_cast<int64_t>(R);
+            else
+              X = (static_cast<int64_t>(S) << (W - fix_shift)) +
+                  static_cast<int64_t>((R + (1ull << (fix_shift - 1))) >> fix_shift);
+            if (nan_row || Fj == EXP_NONFINITE) return __longlong_as_double(0x7FF8000000000000ll);
+            return scale_pow2(__ll2double_rn(X), ebase + Fj);
+          };
+          for (int d = s + 1; d >= 2 && ok; --d) {
+            const int kc = chunk_blocks(d);
+            const int nch = (nkb + kc - 1) / kc;
+            for (int c = 0; c < nch; ++c, ++chunk) {
+              const int slot = chunk & 1;
+              if (!mbar_wait(&accf_bar[slot], static_cast<uint32_t>(chunk >> 1) & 1u, wc)) { ok = false; break; }
+              tc_fence_after();
+#pragma unroll
+              for (int g = 0; g < NG; ++g)
+                tmem_ld8_add_i32(tmem_base + t_lane + static_cast<uint32_t>(slot * BN + col_off + g * 8), lsum[g]);
+              tc_fence_before();
+              __syncwarp();
+              if (lane == 0) {
+                if constexpr (CG == 2)
+                  mbar_arrive_remote(slot ? acce_remote1 : acce_remote0);
+                else
+                  mbar_arrive(&acce_bar[slot]);
+              }
+            }
+            if (!ok || !row_ok) continue;
+            const int l = s + 1 - d;
+            if (d > 2) {
+              // emit this level's low bytes, carry the rest
+              {
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) {
+                  uint32_t w[4];
+#pragma unroll
+                  for (int j = 0; j < 4; ++j) {
+                    uint32_t x = 0u;
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                      int32_t& v = lsum[(q * 16 + j * 4 + b) >> 3][(q * 16 + j * 4 + b) & 7];
+                      x |= (static_cast<uint32_t>(v) & 255u) << (8 * b);
+                      v >>= 8;
+                    }
+                    w[j] = x;
+                  }
+                  *reinterpret_cast<uint4*>(xb + q * 128 + 16 * l) = make_uint4(w[0], w[1], w[2], w[3]);
+                }
+              }
+            } else {
+              // the last level: assemble, round, convert
+              auto load_block = [&](int q, int j, uint32_t (&bw)[4]) {
+#pragma unroll
+                for (int ll = 0; ll < 4; ++ll)
+                  bw[ll] = (ll < s - 1) ? *reinterpret_cast<const uint32_t*>(xb + q * 128 + 16 * ll + 4 * j) : 0u;
+              };
+              auto convert_block = [&](int q, int j, const uint32_t (&bw)[4]) {
+                const int4 f4 = __ldg(reinterpret_cast<const int4*>(P.F + col0) + q * 4 + j);
+                double o[4];
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                  uint64_t R = 0;
+#pragma unroll
+                  for (int ll = 0; ll < 4; ++ll) R |= static_cast<uint64_t>((bw[ll] >> (8 * b)) & 255u) << (8 * ll);
+                  const int32_t Fj = b == 0 ? f4.x : b == 1 ? f4.y : b == 2 ? f4.z : f4.w;
+                  o[b] = total(lsum[(q * 16 + j * 4 + b) >> 3][(q * 16 + j * 4 + b) & 7], R, Fj);
+                }
+                double2* const op = reinterpret_cast<double2*>(xp) + q * 8 + j * 2;
+                op[0] = make_double2(o[0], o[1]);
+                op[1] = make_double2(o[2], o[3]);
+              };
+#pragma unroll
+              for (int q = 0; q < NQ; ++q) {
+                uint32_t b3[4], b2[4], b1[4], b0[4];
+                load_block(q, 3, b3);
+                convert_block(q, 3, b3);
+                load_block(q, 2, b2);
+                convert_block(q, 2, b2);
+                load_block(q, 1, b1);
+                load_block(q, 0, b0);
+                convert_block(q, 1, b1);
+                convert_block(q, 0, b0);
+              }
+            }
+          }
+        } else {
         int pend_q = NQ, pend_lsh = 0;   // the deferred fold: next group, level parameters
         bool pend_first = false, pend_rnd = false;
         bool first_fold = true;
@@ -568,6 +678,7 @@ __global__ void __launch_bounds__(Cfg<BN, MODE, CG>::NUM_THREADS, 1)
             }
             first_fold = false;
           }
+        }
         }
       } else {
         double* const crow = P.C + row * P.ldc;
