@@ -138,7 +138,7 @@ int run_split(mm_handle_s* h, int mode01, const SplitLayout& L, char* ws, const 
 // product's m, n, k; of a group's problem count and mean dimension).
 enum { TUNE_SINGLE = 0, TUNE_GROUPED = 1 };
 bool tile_options_set(const mm_handle_s* h);
-TileCfg default_cfg(const mm_handle_s* h, int precision, int64_t m, int64_t n);
+TileCfg default_cfg(const mm_handle_s* h, int precision, int64_t m, int64_t n, int s);
 TileCfg grouped_default_cfg(const mm_handle_s* h, int precision, int count, const mm_problem* probs);
 void tune_key_single(int precision, int64_t m, int64_t n, int64_t k, int key[5]);
 void tune_key_grouped(int precision, int count, const mm_problem* probs, int key[5]);

@@ -237,10 +237,10 @@ int emu_gemm_rows(mm_handle_s* h, int precision, const SplitLayout& L, char* ws,
                   double* C, int64_t ldc, int64_t* levels, const TileCfg& cfg_in, cudaStream_t st) {
   const bool fp64 = (precision == MM_FP64_EMU);
   const int64_t n = L.n, k = L.k;
-  // CTA pairs (256-row tiles, half of B per CTA) unless the product is one
-  // tile high; the tile width from the configuration (tuned or default)
+  // tile width and CTA pairing (256-row tiles, half of B per CTA) from the
+  // configuration: tuned, else the default for this shape and slice count
   const int pairs_avail = fp64 ? h->max_pairs_fp64 : h->max_pairs_fp32;
-  const TileCfg dflt = default_cfg(h, precision, mr, n);
+  const TileCfg dflt = default_cfg(h, precision, mr, n, s);
   int cg = cfg_in.cg ? cfg_in.cg : dflt.cg;
   int bn = cfg_in.bn ? cfg_in.bn : dflt.bn;
   if (pairs_avail <= 0) cg = 1;

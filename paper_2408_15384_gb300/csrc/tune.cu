@@ -51,7 +51,7 @@ bool tile_options_set(const mm_handle_s* h) {
   return h->opt_tile_n != 0 || h->opt_cta_pair != 0 || h->opt_fp64_kernel != 0 || h->opt_fp32_bn != 0;
 }
 
-TileCfg default_cfg(const mm_handle_s* h, int precision, int64_t m, int64_t n) {
+TileCfg default_cfg(const mm_handle_s* h, int precision, int64_t m, int64_t n, int s) {
   TileCfg c;
   if (precision == MM_FP64) {
     c.kern = h->opt_fp64_kernel == 1 ? 1 : 2;
@@ -59,9 +59,13 @@ TileCfg default_cfg(const mm_handle_s* h, int precision, int64_t m, int64_t n) {
   }
   const bool fp64 = precision == MM_FP64_EMU;
   const int pairs = fp64 ? h->max_pairs_fp64 : h->max_pairs_fp32;
-  // CTA pairs for FP32-accuracy products taller than one tile; FP64-accuracy
-  // runs faster on single CTAs (its epilogue, not operand traffic, limits it)
-  c.cg = (h->opt_cta_pair == 1) ? 1 : (h->opt_cta_pair == 2 ? 2 : ((!fp64 && m > 128) ? 2 : 1));
+  // CTA pairs for FP32-accuracy products taller than one tile. FP64-accuracy
+  // products take pairs on 256-wide tiles when the carry epilogue applies
+  // (s <= 5) and there are at least as many 256 x 256 pair tiles as SMs;
+  // otherwise single CTAs (measured at M = N = K = 2048, 4096 and 8192)
+  const int64_t pair_tiles = ((m + 255) / 256) * ((n + 255) / 256);
+  const int fp64_cg = (n > 128 && s <= 5 && pair_tiles >= h->sm_count) ? 2 : 1;
+  c.cg = (h->opt_cta_pair == 1) ? 1 : (h->opt_cta_pair == 2 ? 2 : (fp64 ? fp64_cg : (m > 128 ? 2 : 1)));
   if (pairs <= 0) c.cg = 1;
   if (fp64) {
     // 256-wide tiles whenever the product is wider than one 128-wide tile
