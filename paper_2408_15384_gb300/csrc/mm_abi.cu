@@ -270,7 +270,9 @@ int emu_gemm_rows(mm_handle_s* h, int precision, const SplitLayout& L, char* ws,
   a.timeout_ns = static_cast<uint64_t>(h->opt_timeout_ms) * 1000000ull;
   const int ntiles = P.tiles_m * P.tiles_n;
   const int grid = (cg == 2) ? 2 * std::min(ntiles, pairs_avail) : std::min(ntiles, h->sm_count);
-  const int mode = levels ? SLICE_LEVELS : (fp64 ? SLICE_FP64EMU : SLICE_FP32EMU);
+  const int mode = levels ? SLICE_LEVELS
+                          : (!fp64 ? SLICE_FP32EMU
+                                   : (slice_fp64_carry_ok(s, k, P.fix_shift) ? SLICE_FP64EMU_CARRY : SLICE_FP64EMU));
   cudaError_t e;
   {
     ProfScope ps(h, MM_KERNEL_SLICE_GEMM, st);

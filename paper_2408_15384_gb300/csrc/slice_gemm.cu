@@ -45,7 +45,7 @@ namespace mmdev {
 
 static constexpr int BM = 128;
 static constexpr int BK = 64;                 // bf16 elements per K block (128 bytes)
-static constexpr int SEG_CHUNKS = 120;        // chunks per int32 level sum (120 * 2^24 < 2^31)
+static constexpr int SEG_CHUNKS = SLICE_SEG_CHUNKS;   // chunks per int32 level sum
 
 // CG = CTAs per output tile: 1, or 2 for a CTA pair (cta_group::2) computing a
 // 256-row tile, each CTA holding 128 rows of A and BN/2 rows of B in shared
@@ -510,10 +510,14 @@ __global__ void __launch_bounds__(Cfg<BN, MODE, CG>::NUM_THREADS, 1)
         // 64 bytes of that group's own 128-byte output, which its 4-column
         // blocks 0 and 1 cover: blocks 3 and 2 are converted first, then the
         // bytes of blocks 1 and 0 are read before either is written.
-        const int kc_top = chunk_blocks(s + 1);
-        const bool carry = (MODE == SLICE_FP64EMU) && s <= 5 && ((nkb + kc_top - 1) / kc_top <= SEG_CHUNKS) &&
-                           (fix_shift <= 8 * (s - 1)) && __all_sync(0xffffffffu, full);
+        bool carry = false;
+        if constexpr (MODE == SLICE_FP64EMU_CARRY) {
+          const int kc_top = chunk_blocks(s + 1);
+          carry = s <= 5 && ((nkb + kc_top - 1) / kc_top <= SEG_CHUNKS) && (fix_shift <= 8 * (s - 1)) &&
+                  __all_sync(0xffffffffu, full);
+        }
         if (carry) {
+          if constexpr (MODE == SLICE_FP64EMU_CARRY) {
           uint8_t* const xb = reinterpret_cast<uint8_t*>(xp);
           const int W = 8 * (s - 1);
           auto total = [&](int32_t S, uint64_t R, int32_t Fj) -> double {
@@ -602,6 +606,7 @@ __global__ void __launch_bounds__(Cfg<BN, MODE, CG>::NUM_THREADS, 1)
                 convert_block(q, 0, b0);
               }
             }
+          }
           }
         } else {
         int pend_q = NQ, pend_lsh = 0;   // the deferred fold: next group, level parameters
@@ -837,6 +842,11 @@ namespace {
 template <int BN, int CG>
 cudaError_t launch_emu(int mode, const CUtensorMap* tmA, const CUtensorMap* tmB, const SliceGemmArgs& a, int grid,
                        cudaStream_t st) {
+  if (mode == SLICE_FP64EMU_CARRY) {
+    // the carry epilogue needs register level sums (tiles wider than 128)
+    if constexpr (BN != 128) return launch_t<BN, SLICE_FP64EMU_CARRY, CG>(tmA, tmB, a, grid, st);
+    mode = SLICE_FP64EMU;
+  }
   if (mode == SLICE_FP64EMU) return launch_t<BN, SLICE_FP64EMU, CG>(tmA, tmB, a, grid, st);
   if (mode == SLICE_LEVELS) return launch_t<BN, SLICE_LEVELS, CG>(tmA, tmB, a, grid, st);
   return cudaErrorInvalidValue;
@@ -847,6 +857,10 @@ cudaError_t prepare_emu() {
   cudaError_t e;
   if ((e = set_smem_attr<BN, SLICE_FP64EMU, 1>()) != cudaSuccess) return e;
   if ((e = set_smem_attr<BN, SLICE_FP64EMU, 2>()) != cudaSuccess) return e;
+  if constexpr (BN != 128) {
+    if ((e = set_smem_attr<BN, SLICE_FP64EMU_CARRY, 1>()) != cudaSuccess) return e;
+    if ((e = set_smem_attr<BN, SLICE_FP64EMU_CARRY, 2>()) != cudaSuccess) return e;
+  }
   if ((e = set_smem_attr<BN, SLICE_LEVELS, 1>()) != cudaSuccess) return e;
   return set_smem_attr<BN, SLICE_LEVELS, 2>();
 }
@@ -866,7 +880,7 @@ cudaError_t slice_gemm_prepare() {
 
 int slice_gemm_max_pairs(int mode) {
   if (mode == SLICE_FP32EMU) return max_pairs_t<256, SLICE_FP32EMU>();
-  if (mode == SLICE_FP64EMU) return max_pairs_t<256, SLICE_FP64EMU>();
+  if (mode == SLICE_FP64EMU || mode == SLICE_FP64EMU_CARRY) return max_pairs_t<256, SLICE_FP64EMU>();
   return max_pairs_t<256, SLICE_LEVELS>();
 }
 
