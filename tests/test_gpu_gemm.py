@@ -466,3 +466,60 @@ def test_host_entry_two_panels_same_bits(h, mm, prec):
     big = np.full((m, n + 9), -7.0)
     h.gemm_host(A, B, big[:, :n], precision=prec)
     assert np.array_equal(big[:, :n], Cd) and np.all(big[:, n:] == -7.0)
+
+
+def _tilings(h, mm, A, B, bns=(128, 256), cgs=(1, 2)):
+    out = {}
+    for cg in cgs:
+        for bn in bns:
+            h.set_option(mm.OPT_CTA_PAIR, cg)
+            h.set_option(mm.OPT_TILE_N, bn)
+            try:
+                out[(cg, bn)], rc = run(h, A, B, mm.FP64_EMU)
+            finally:
+                h.set_option(mm.OPT_CTA_PAIR, 0)
+                h.set_option(mm.OPT_TILE_N, 0)
+            assert rc == 0
+    return out
+
+
+@pytest.mark.parametrize("s", [3, 4, 5])
+def test_byte_carry_forced_slices_exact(h, mm, s):
+    # s <= 5 on 256-wide tiles takes the byte-carry recombination (full rows)
+    # next to the int64 fold (the partial last tile); the 128-wide kernel keeps
+    # the total in TMEM. All agree bit for bit and equal the exact total
+    # rounded once (fixed point at 2^0 here).
+    m, n, k = 300, 600, 1000
+    A = inputs.row_scaled(m, k, 1500 + s)
+    B = inputs.col_scaled(k, n, 1500 + s)
+    h.set_option(mm.OPT_SLICES, s)
+    try:
+        out = _tilings(h, mm, A, B)
+    finally:
+        h.set_option(mm.OPT_SLICES, 0)
+    first = out[(1, 128)]
+    for key, C in out.items():
+        assert np.array_equal(C, first), key
+    assert fixed_shift(s, k) == 0
+    E, sA = em.fp64_slices_A(A, s)
+    F, sB = em.fp64_slices_B(B, s)
+    rows = [0, 1, 127, 128, 255, 256, 299]
+    Ce = em.recombine_exact(em.level_products(sA[:, rows], sB, s), E[rows], F, s)
+    assert np.array_equal(first[rows], Ce)
+
+
+@pytest.mark.parametrize("k", [23040, 23104])
+def test_byte_carry_segment_limit(h, mm, k):
+    # s = 5: k = 23040 puts exactly 120 chunks in the top level (byte carry);
+    # one more K block (k = 23104) needs a mid-level fold (int64 fold path)
+    m, n = 260, 512
+    A = inputs.row_scaled(m, k, 1600)
+    B = inputs.col_scaled(k, n, 1600)
+    assert mm.slices_for_k(k) == 5
+    out = _tilings(h, mm, A, B, cgs=(1, 2))
+    first = out[(1, 128)]
+    for key, C in out.items():
+        assert np.array_equal(C, first), (k, key)
+    rows = [0, 131, 259]
+    assert bound_ok(first[rows], oracle.gemm_rows(A, B, rows), oracle.absprod_rows(A, B, rows),
+                    em.gamma(k, "fp64_emu"))
