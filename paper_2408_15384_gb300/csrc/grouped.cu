@@ -169,9 +169,26 @@ static int fill_emu_blob(mm_handle_s* h, const EmuPlan& plan, const EmuLayout& L
   return MM_OK;
 }
 
+// The slice GEMM mode of an emulated group: FP32-accuracy, or FP64-accuracy
+// with the byte-carry recombination when every problem allows it on tiles
+// wider than 128 (the s = 6, 7 kernel whenever one of them has s >= 6).
+static int group_mode(const mm_handle_s* h, const std::vector<int>& idx, const mm_problem* probs, int precision,
+                      int bn) {
+  if (precision != MM_FP64_EMU) return SLICE_FP32EMU;
+  if (bn == 128) return SLICE_FP64EMU;
+  int max_s = 0;
+  for (int i : idx) {
+    const mm_problem& q = probs[i];
+    const int s = h->opt_slices > 0 ? h->opt_slices : slices_for_k(q.k, h->opt_slice_rule);
+    if (!slice_fp64_carry_ok(s, q.k, fixed_shift(s, q.k))) return SLICE_FP64EMU;
+    max_s = std::max(max_s, s);
+  }
+  return max_s >= 6 ? SLICE_FP64EMU_CARRY7 : SLICE_FP64EMU_CARRY;
+}
+
 // The launches of an emulated group whose blob is at db (device).
-static cudaError_t launch_emu_group(mm_handle_s* h, bool fp64, int bn, const EmuLayout& L, char* db, char* ws,
-                                    size_t colmax_cap, cudaStream_t st) {
+static cudaError_t launch_emu_group(mm_handle_s* h, bool fp64, int mode, int bn, const EmuLayout& L, char* db,
+                                    char* ws, size_t colmax_cap, cudaStream_t st) {
   GroupedSplitArgs ga;
   ga.probs = reinterpret_cast<const GroupedSplit*>(db + L.off_split);
   for (int q = 0; q < 4; ++q) ga.off[q] = reinterpret_cast<const int64_t*>(db + L.off_off) + q * (L.count_cap + 1);
@@ -190,7 +207,7 @@ static cudaError_t launch_emu_group(mm_handle_s* h, bool fp64, int bn, const Emu
   cudaError_t e = cudaMemsetAsync(ws, 0, colmax_cap, st);
   if (e == cudaSuccess) e = launch_grouped_split(fp64 ? 0 : 1, ga, h->sm_count * 8, st);
   if (e == cudaSuccess)
-    e = launch_slice_gemm(fp64 ? SLICE_FP64EMU : SLICE_FP32EMU, bn, 1, &dummy, &dummy, sa, h->sm_count, st);
+    e = launch_slice_gemm(mode, bn, 1, &dummy, &dummy, sa, h->sm_count, st);
   return e;
 }
 
@@ -260,9 +277,9 @@ struct GroupedSlot {
 struct GroupedKey {
   int precision;
   cudaStream_t stream;
-  int bn, kern;   // launch configuration captured in the graph
+  int bn, kern, mode;   // launch configuration captured in the graph
   bool operator<(const GroupedKey& o) const {
-    return std::tie(precision, stream, bn, kern) < std::tie(o.precision, o.stream, o.bn, o.kern);
+    return std::tie(precision, stream, bn, kern, mode) < std::tie(o.precision, o.stream, o.bn, o.kern, o.mode);
   }
 };
 
@@ -352,7 +369,7 @@ static int alloc_slot(mm_handle_s* h, GroupedSlot& slot, size_t blob_bytes, size
 }
 
 static int graph_emulated(mm_handle_s* h, GroupedEntry& ent, const std::vector<int>& idx, const mm_problem* probs,
-                          int precision, int bn, cudaStream_t st) {
+                          int precision, int bn, int mode, cudaStream_t st) {
   const bool fp64 = precision == MM_FP64_EMU;
   const int count = static_cast<int>(idx.size());
   EmuPlan plan;
@@ -377,7 +394,7 @@ static int graph_emulated(mm_handle_s* h, GroupedEntry& ent, const std::vector<i
     char* db = static_cast<char*>(slot.dblob);
     char* ws = static_cast<char*>(slot.ws);
     rc = capture_slot(slot,
-                      [&](cudaStream_t cs) { return launch_emu_group(h, fp64, bn, L, db, ws, colmax_cap, cs); });
+                      [&](cudaStream_t cs) { return launch_emu_group(h, fp64, mode, bn, L, db, ws, colmax_cap, cs); });
     if (rc != MM_OK) {
       release_slot(h, slot);
       return rc;
@@ -499,9 +516,10 @@ int grouped_run(mm_handle_s* h, int count, const mm_problem* probs, int precisio
   std::lock_guard<std::mutex> lk(h->grouped_mu);
   if (!h->grouped) h->grouped = new GroupedCache();
   const bool plain = precision == MM_FP64;
-  GroupedEntry& ent = h->grouped->entries[GroupedKey{precision, st, plain ? 0 : cfg.bn, plain ? cfg.kern : 0}];
+  const int mode = plain ? 0 : group_mode(h, main_idx, probs, precision, cfg.bn);
+  GroupedEntry& ent = h->grouped->entries[GroupedKey{precision, st, plain ? 0 : cfg.bn, plain ? cfg.kern : 0, mode}];
   if (plain) return graph_fp64(h, ent, main_idx, probs, cfg.kern, st);
-  return graph_emulated(h, ent, main_idx, probs, precision, cfg.bn, st);
+  return graph_emulated(h, ent, main_idx, probs, precision, cfg.bn, mode, st);
 }
 
 // -------------------------------------------------------------- direct path
@@ -572,7 +590,7 @@ int grouped_direct(mm_handle_s* h, int count, const mm_problem* probs, int preci
     e = cudaMemcpyAsync(db, hb, L.bytes, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) {
       ProfScope ps(h, MM_KERNEL_SLICE_GEMM, st);
-      e = launch_emu_group(h, fp64, bn, L, db, ws, plan.colmax_bytes, st);
+      e = launch_emu_group(h, fp64, group_mode(h, main_idx, probs, precision, bn), bn, L, db, ws, plan.colmax_bytes, st);
     }
     count_launch(h, 3);
   }

@@ -55,23 +55,36 @@ cudaError_t launch_grouped_split(int mode01, const GroupedSplitArgs& a, int grid
 
 // ----------------------------------------------------------- slice_gemm.cu
 // Epilogue kinds of the slice GEMM.
-// SLICE_FP64EMU_CARRY: FP64-accuracy with the byte-carry recombination, for
-// products slice_fp64_carry_ok accepts (same results as SLICE_FP64EMU).
-enum SliceMode { SLICE_FP32EMU = 0, SLICE_FP64EMU = 1, SLICE_LEVELS = 2, SLICE_FP64EMU_CARRY = 3 };
+// SLICE_FP64EMU_CARRY (s <= 5) and SLICE_FP64EMU_CARRY7 (s = 6, 7):
+// FP64-accuracy with the byte-carry recombination, for products
+// slice_fp64_carry_ok accepts (same results as SLICE_FP64EMU).
+enum SliceMode {
+  SLICE_FP32EMU = 0,
+  SLICE_FP64EMU = 1,
+  SLICE_LEVELS = 2,
+  SLICE_FP64EMU_CARRY = 3,
+  SLICE_FP64EMU_CARRY7 = 4
+};
 
 // Chunks per int32 level-sum segment (SLICE_SEG_CHUNKS * 2^24 < 2^31).
 constexpr int SLICE_SEG_CHUNKS = 120;
 
 // Whether an FP64-accuracy product of inner dimension k with s slices and
-// fixed-point shift fix_shift can take the byte-carry epilogue: s <= 5, every
+// fixed-point shift fix_shift can take the byte-carry epilogue: s <= 7, every
 // level within one int32 segment (the top level d = s + 1 has the shortest
 // chunks, 16 / s K blocks), and the fixed point at or below the last level's
 // weight 8(s-1).
 inline bool slice_fp64_carry_ok(int s, int64_t k, int fix_shift) {
-  if (s < 1 || s > 5) return false;
+  if (s < 1 || s > 7) return false;
   const int64_t nkb = (k + 63) / 64;
   const int kc = (16 / s) < 1 ? 1 : 16 / s;
   return (nkb + kc - 1) / kc <= SLICE_SEG_CHUNKS && fix_shift <= 8 * (s - 1);
+}
+
+// The slice GEMM mode of an FP64-accuracy product.
+inline int slice_fp64_mode(int s, int64_t k, int fix_shift) {
+  if (!slice_fp64_carry_ok(s, k, fix_shift)) return SLICE_FP64EMU;
+  return s <= 5 ? SLICE_FP64EMU_CARRY : SLICE_FP64EMU_CARRY7;
 }
 
 // One product as the slice GEMM sees it (also the grouped problem record).

@@ -272,7 +272,7 @@ int emu_gemm_rows(mm_handle_s* h, int precision, const SplitLayout& L, char* ws,
   const int grid = (cg == 2) ? 2 * std::min(ntiles, pairs_avail) : std::min(ntiles, h->sm_count);
   const int mode = levels ? SLICE_LEVELS
                           : (!fp64 ? SLICE_FP32EMU
-                                   : (slice_fp64_carry_ok(s, k, P.fix_shift) ? SLICE_FP64EMU_CARRY : SLICE_FP64EMU));
+                                   : slice_fp64_mode(s, k, P.fix_shift));
   cudaError_t e;
   {
     ProfScope ps(h, MM_KERNEL_SLICE_GEMM, st);

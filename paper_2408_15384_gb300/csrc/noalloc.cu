@@ -149,7 +149,7 @@ int mm_gemm_emu_static(int64_t m, int64_t n, int64_t k, const double* A, int64_t
   a.err = err;
   a.timeout_ns = 2000ull * 1000000ull;
   const int grid = std::min(P.tiles_m * P.tiles_n, d.sm_count);
-  const int mode = !fp64 ? SLICE_FP32EMU : (slice_fp64_carry_ok(s, k, P.fix_shift) ? SLICE_FP64EMU_CARRY : SLICE_FP64EMU);
+  const int mode = !fp64 ? SLICE_FP32EMU : slice_fp64_mode(s, k, P.fix_shift);
   e = launch_slice_gemm(mode, bn, 1, &tmA, &tmB, a, grid, st);
   return cuda_status(e, "slice gemm");
 }

@@ -494,7 +494,7 @@ __global__ void __launch_bounds__(Cfg<BN, MODE, CG>::NUM_THREADS, 1)
             }
           }
         };
-        // Carry path, taken for s <= 5 by warps whose rows are all full
+        // Carry path, taken for s <= 7 by warps whose rows are all full
         // 16-byte aligned segments while every level fits one int32 segment
         // and the fixed point lies at or below the last level's weight (the
         // choice is warp-uniform, as the TMEM loads are warp-collective). After level d
@@ -507,17 +507,21 @@ __global__ void __launch_bounds__(Cfg<BN, MODE, CG>::NUM_THREADS, 1)
         // rounded once to the fixed point as the fold path rounds it; |S| stays
         // below SEG_CHUNKS 2^24 + 2^23 < 2^31. Full rows keep the bytes of each
         // 16-column group (one 16-byte word per level) in the first 16(s-1) <=
-        // 64 bytes of that group's own 128-byte output, which its 4-column
-        // blocks 0 and 1 cover: blocks 3 and 2 are converted first, then the
-        // bytes of blocks 1 and 0 are read before either is written.
+        // 96 bytes of that group's own 128-byte output. The group's 4-column
+        // blocks are converted from block 3 down to block 0; block j's doubles
+        // cover level words 2j and 2j+1, so before block 2 is written the
+        // lower blocks' parts of words 4 and 5 are kept in registers, and
+        // before block 1 is written block 0's parts of words 2 and 3.
         bool carry = false;
-        if constexpr (MODE == SLICE_FP64EMU_CARRY) {
+        // level words a group keeps: s - 1 <= 4 (s <= 5) or <= 6 (s = 6, 7)
+        constexpr int LV = (MODE == SLICE_FP64EMU_CARRY7) ? 6 : 4;
+        if constexpr (MODE == SLICE_FP64EMU_CARRY || MODE == SLICE_FP64EMU_CARRY7) {
           const int kc_top = chunk_blocks(s + 1);
-          carry = s <= 5 && ((nkb + kc_top - 1) / kc_top <= SEG_CHUNKS) && (fix_shift <= 8 * (s - 1)) &&
+          carry = s <= LV + 1 && ((nkb + kc_top - 1) / kc_top <= SEG_CHUNKS) && (fix_shift <= 8 * (s - 1)) &&
                   __all_sync(0xffffffffu, full);
         }
         if (carry) {
-          if constexpr (MODE == SLICE_FP64EMU_CARRY) {
+          if constexpr (MODE == SLICE_FP64EMU_CARRY || MODE == SLICE_FP64EMU_CARRY7) {
           uint8_t* const xb = reinterpret_cast<uint8_t*>(xp);
           const int W = 8 * (s - 1);
           auto total = [&](int32_t S, uint64_t R, int32_t Fj) -> double {
@@ -573,19 +577,18 @@ __global__ void __launch_bounds__(Cfg<BN, MODE, CG>::NUM_THREADS, 1)
               }
             } else {
               // the last level: assemble, round, convert
-              auto load_block = [&](int q, int j, uint32_t (&bw)[4]) {
-#pragma unroll
-                for (int ll = 0; ll < 4; ++ll)
-                  bw[ll] = (ll < s - 1) ? *reinterpret_cast<const uint32_t*>(xb + q * 128 + 16 * ll + 4 * j) : 0u;
+              // word ll's bytes of 4-column block j of group q (0 past the levels)
+              auto ldw = [&](int q, int j, int ll) -> uint32_t {
+                return (ll < LV && ll < s - 1) ? *reinterpret_cast<const uint32_t*>(xb + q * 128 + 16 * ll + 4 * j) : 0u;
               };
-              auto convert_block = [&](int q, int j, const uint32_t (&bw)[4]) {
+              auto convert_block = [&](int q, int j, const uint32_t (&bw)[6]) {
                 const int4 f4 = __ldg(reinterpret_cast<const int4*>(P.F + col0) + q * 4 + j);
                 double o[4];
 #pragma unroll
                 for (int b = 0; b < 4; ++b) {
                   uint64_t R = 0;
 #pragma unroll
-                  for (int ll = 0; ll < 4; ++ll) R |= static_cast<uint64_t>((bw[ll] >> (8 * b)) & 255u) << (8 * ll);
+                  for (int ll = 0; ll < LV; ++ll) R |= static_cast<uint64_t>((bw[ll] >> (8 * b)) & 255u) << (8 * ll);
                   const int32_t Fj = b == 0 ? f4.x : b == 1 ? f4.y : b == 2 ? f4.z : f4.w;
                   o[b] = total(lsum[(q * 16 + j * 4 + b) >> 3][(q * 16 + j * 4 + b) & 7], R, Fj);
                 }
@@ -595,14 +598,21 @@ __global__ void __launch_bounds__(Cfg<BN, MODE, CG>::NUM_THREADS, 1)
               };
 #pragma unroll
               for (int q = 0; q < NQ; ++q) {
-                uint32_t b3[4], b2[4], b1[4], b0[4];
-                load_block(q, 3, b3);
-                convert_block(q, 3, b3);
-                load_block(q, 2, b2);
-                convert_block(q, 2, b2);
-                load_block(q, 1, b1);
-                load_block(q, 0, b0);
-                convert_block(q, 1, b1);
+                {
+                  const uint32_t b3[6] = {ldw(q, 3, 0), ldw(q, 3, 1), ldw(q, 3, 2), ldw(q, 3, 3), ldw(q, 3, 4), ldw(q, 3, 5)};
+                  convert_block(q, 3, b3);
+                }
+                const uint32_t w14 = ldw(q, 1, 4), w15 = ldw(q, 1, 5), w04 = ldw(q, 0, 4), w05 = ldw(q, 0, 5);
+                {
+                  const uint32_t b2[6] = {ldw(q, 2, 0), ldw(q, 2, 1), ldw(q, 2, 2), ldw(q, 2, 3), ldw(q, 2, 4), ldw(q, 2, 5)};
+                  convert_block(q, 2, b2);
+                }
+                const uint32_t w02 = ldw(q, 0, 2), w03 = ldw(q, 0, 3);
+                {
+                  const uint32_t b1[6] = {ldw(q, 1, 0), ldw(q, 1, 1), ldw(q, 1, 2), ldw(q, 1, 3), w14, w15};
+                  convert_block(q, 1, b1);
+                }
+                const uint32_t b0[6] = {ldw(q, 0, 0), ldw(q, 0, 1), w02, w03, w04, w05};
                 convert_block(q, 0, b0);
               }
             }
@@ -842,9 +852,12 @@ namespace {
 template <int BN, int CG>
 cudaError_t launch_emu(int mode, const CUtensorMap* tmA, const CUtensorMap* tmB, const SliceGemmArgs& a, int grid,
                        cudaStream_t st) {
-  if (mode == SLICE_FP64EMU_CARRY) {
+  if (mode == SLICE_FP64EMU_CARRY || mode == SLICE_FP64EMU_CARRY7) {
     // the carry epilogue needs register level sums (tiles wider than 128)
-    if constexpr (BN != 128) return launch_t<BN, SLICE_FP64EMU_CARRY, CG>(tmA, tmB, a, grid, st);
+    if constexpr (BN != 128) {
+      if (mode == SLICE_FP64EMU_CARRY) return launch_t<BN, SLICE_FP64EMU_CARRY, CG>(tmA, tmB, a, grid, st);
+      return launch_t<BN, SLICE_FP64EMU_CARRY7, CG>(tmA, tmB, a, grid, st);
+    }
     mode = SLICE_FP64EMU;
   }
   if (mode == SLICE_FP64EMU) return launch_t<BN, SLICE_FP64EMU, CG>(tmA, tmB, a, grid, st);
@@ -860,6 +873,8 @@ cudaError_t prepare_emu() {
   if constexpr (BN != 128) {
     if ((e = set_smem_attr<BN, SLICE_FP64EMU_CARRY, 1>()) != cudaSuccess) return e;
     if ((e = set_smem_attr<BN, SLICE_FP64EMU_CARRY, 2>()) != cudaSuccess) return e;
+    if ((e = set_smem_attr<BN, SLICE_FP64EMU_CARRY7, 1>()) != cudaSuccess) return e;
+    if ((e = set_smem_attr<BN, SLICE_FP64EMU_CARRY7, 2>()) != cudaSuccess) return e;
   }
   if ((e = set_smem_attr<BN, SLICE_LEVELS, 1>()) != cudaSuccess) return e;
   return set_smem_attr<BN, SLICE_LEVELS, 2>();
@@ -880,7 +895,8 @@ cudaError_t slice_gemm_prepare() {
 
 int slice_gemm_max_pairs(int mode) {
   if (mode == SLICE_FP32EMU) return max_pairs_t<256, SLICE_FP32EMU>();
-  if (mode == SLICE_FP64EMU || mode == SLICE_FP64EMU_CARRY) return max_pairs_t<256, SLICE_FP64EMU>();
+  if (mode == SLICE_FP64EMU || mode == SLICE_FP64EMU_CARRY || mode == SLICE_FP64EMU_CARRY7)
+    return max_pairs_t<256, SLICE_FP64EMU>();
   return max_pairs_t<256, SLICE_LEVELS>();
 }
 
