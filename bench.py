@@ -122,14 +122,26 @@ def measured_peaks():
         return {}
 
 
-def profiled_traffic(kernel_src: str):
+SLICE_GEMM_SOURCES = ("slice_gemm_kernel.cuh", "slice_gemm.cu", "slice_gemm_fold.cu", "slice_gemm_carry.cu")
+
+
+def slice_gemm_source_hash() -> str:
+    """sha256[:16] over the slice GEMM's kernel header and sources, in order."""
+    h = hashlib.sha256()
+    for name in SLICE_GEMM_SOURCES:
+        with open(os.path.join(ROOT, "paper_2408_15384_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
     """DRAM bytes per launch of the slice GEMM from the committed ncu summary,
     if it was taken on the current kernel source (else None)."""
     path = os.path.join(ROOT, "profiles", "slice_gemm_fp64emu_traffic.md")
     if not os.path.exists(path):
         return None, None
     txt = open(path).read()
-    src_hash = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+    src_hash = slice_gemm_source_hash()
     m_hash = re.search(r"source sha256\[:16\]:\s*`?([0-9a-f]{16})", txt)
     m_bytes = re.search(r"bytes per launch at N=8192:\s*`?([0-9.eE+]+)", txt)
     if not m_hash or not m_bytes or m_hash.group(1) != src_hash:
@@ -302,7 +314,7 @@ def ours(args):
         peak, peak_note = peaks["bf16_tflops_sustained"], "of measured (bf16 sustained)"
     else:
         peak, peak_note = 1700.0, "of fallback (bf16 sustained)"
-    traffic, src_hash = profiled_traffic(os.path.join(ROOT, "paper_2408_15384_gb300", "csrc", "slice_gemm.cu"))
+    traffic, src_hash = profiled_traffic()
 
     extra = {}
     if rank == 0 and not args.quick:

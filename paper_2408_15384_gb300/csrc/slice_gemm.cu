@@ -1,903 +1,23 @@
-// slice_gemm.cu -- tcgen05 tensor-core product of bfloat16 operand slices, with
-// the FP32-accuracy or FP64-accuracy epilogue. Persistent: each CTA (one per
-// SM) walks a list of 128 x BN output tiles, of one product or of a group of
-// products.
-//
-// Warp roles:
-//   warp 0      TMA producer: one A-slice tile (128 x 64) and one B-slice tile
-//               (BN x 64) per pipeline step into a STAGES-deep shared ring.
-//   warp 1      allocates TMEM; one thread issues tcgen05.mma (M=128, N=BN,
-//               K=16, bf16 x bf16 -> f32) and tcgen05.commit.
-//   warps 2..9  epilogue: tcgen05.ld of the accumulator, row = TMEM lane,
-//               two warps per TMEM lane quadrant, each on half the columns.
-// Accumulation chunks alternate between two TMEM slots of BN columns, so the
-// tensor cores run the next chunk (or the next tile) while the epilogue drains
-// the previous one.
-//
-// FP32-accuracy (three bfloat16 slices per operand): the six slice pairs
-// (p, q) with p + q <= 2 accumulate into one f32 accumulator, smallest
-// products first; the epilogue scales by 2^(E_i + F_j) and stores doubles.
-//
-// FP64-accuracy (integer slices, levels d = p + q = 2..s+1, Ozaki-style): the
-// kernel walks the levels one after the other, smallest first (d = s+1 down
-// to 2). Level d sums d-1 slice pairs; with |slice| <= 2^7 each product is at
-// most 2^14, so a K-chunk of Kc with Kc * (d-1) <= 1024 sums to at most 2^24
-// and the f32 accumulator holds it exactly. The epilogue converts each
-// finished chunk to integers and adds it, at its level weight w_d = 8(s+1-d),
-// to an int64 fixed-point total with unit 2^shift (shift >= 0 keeps the total
-// below 2^62):
-//   X = round(sum_{w_d < shift} 2^w_d L_d / 2^shift) + sum_{w_d >= shift} 2^(w_d - shift) L_d,
-// which is the exact total rounded once (half up) to the fixed point: the
-// levels below the fixed point are summed exactly first and rounded at the
-// end of the last of them. 128-wide tiles keep X in TMEM (512 columns = two
-// accumulator slots + the low and high 32-bit planes of X); 256-wide tiles keep
-// int32 level sums in registers and X in C's storage. After the last level X
-// is converted to double once, scaled by 2^(E_i + F_j - 8(s+1) + shift) and
-// stored. Every tiling gives the same bits.
-#include <cstdint>
-#include <cuda.h>
-#include <cuda_runtime.h>
-
-#include "kernels.cuh"
-#include "ptx.cuh"
-
-namespace mmdev {
-
-static constexpr int BM = 128;
-static constexpr int BK = 64;                 // bf16 elements per K block (128 bytes)
-static constexpr int SEG_CHUNKS = SLICE_SEG_CHUNKS;   // chunks per int32 level sum
-
-// CG = CTAs per output tile: 1, or 2 for a CTA pair (cta_group::2) computing a
-// 256-row tile, each CTA holding 128 rows of A and BN/2 rows of B in shared
-// memory and its 128 rows of the accumulator in its own TMEM.
-template <int BN, int MODE, int CG>
-struct Cfg {
-  // epilogue warps: 8 (two per TMEM lane quadrant). FP64-accuracy tiles wider
-  // than 128 keep their columns' int32 level sums in registers: 16 warps for
-  // 256 columns (64 sums a thread), 12 for 192 or 240 (64 or 80 sums a thread;
-  // 14 warps leave 128 registers a thread)
-  static constexpr bool REG_SUMS = (BN != 128) && (MODE != SLICE_FP32EMU);
-  static constexpr int EPI_WARPS = !REG_SUMS ? 8 : (BN == 256 ? 16 : 12);
-  static constexpr int EPI_WARP0 = 2;
-  static constexpr int NUM_THREADS = 32 * (EPI_WARP0 + EPI_WARPS);
-  static constexpr int A_BYTES = BM * BK * 2;
-  static constexpr int B_BYTES = (BN / CG) * BK * 2;
-  static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-  static constexpr int SMEM_LIMIT = 232448 - 1024 - 256;   // max dynamic smem - alignment - static
-  static constexpr int STAGES_FIT = SMEM_LIMIT / STAGE_BYTES;
-  static constexpr int STAGES = STAGES_FIT > 10 ? 10 : STAGES_FIT;
-  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
-  // two accumulator slots; FP64-accuracy adds the int64 total's planes (BN = 128)
-  static constexpr int TMEM_COLS = (MODE == SLICE_FP32EMU) ? 2 * BN : 512;
-  static constexpr int XLO_COL = 2 * BN;
-  static constexpr int XHI_COL = 3 * BN;
-  static constexpr int COLS_PER_THREAD = BN / (EPI_WARPS / 4);
-  static constexpr int TILE_M = BM * CG;
-};
-
-// K blocks per chunk at level d (d - 1 pairs): Kc * (d-1) <= 1024.
-__device__ __forceinline__ int chunk_blocks(int d) {
-  int kb = 16 / (d - 1);
-  return kb < 1 ? 1 : kb;
-}
-
-__device__ __forceinline__ uint64_t dbits(double x) { return static_cast<uint64_t>(__double_as_longlong(x)); }
-__device__ __forceinline__ double bitsd(uint64_t b) { return __longlong_as_double(static_cast<long long>(b)); }
-
-// x * 2^e for finite x, exact unless the result leaves the normal range.
-__device__ __forceinline__ double scale_pow2(double x, int e) {
-  uint64_t b = dbits(x);
-  uint64_t ab = b & 0x7FFFFFFFFFFFFFFFull;
-  if (ab == 0) return x;
-  int ex = static_cast<int>(ab >> 52);
-  if (ex > 0 && ex + e >= 1 && ex + e <= 2046) return bitsd(b + (static_cast<uint64_t>(static_cast<int64_t>(e)) << 52));
-  // rare: step through exact powers of two (a subnormal result rounds here)
-  while (e > 1000) { x *= bitsd(static_cast<uint64_t>(1000 + 1023) << 52); e -= 1000; }
-  while (e < -1000) { x *= bitsd(static_cast<uint64_t>(-1000 + 1023) << 52); e += 1000; }
-  return x * bitsd(static_cast<uint64_t>(e + 1023) << 52);
-}
-
-// exact float -> double with a power-of-two scale
-__device__ __forceinline__ double f32_to_f64_scaled(uint32_t fb, int e) {
-  uint32_t e8 = (fb >> 23) & 255u;
-  if (e8 == 0u || e8 == 255u) return scale_pow2(static_cast<double>(__uint_as_float(fb)), e);
-  int ex = static_cast<int>(e8) - 127 + 1023;
-  uint64_t sgn = static_cast<uint64_t>(fb >> 31) << 63;
-  uint64_t man = static_cast<uint64_t>(fb & 0x7FFFFFu) << 29;
-  if (ex + e >= 1 && ex + e <= 2046) return bitsd(sgn | (static_cast<uint64_t>(ex + e) << 52) | man);
-  return scale_pow2(bitsd(sgn | (static_cast<uint64_t>(ex) << 52) | man), e);
-}
-
-struct Step {
-  int kb, pa, pb;      // K block, A slice index, B slice index
-  bool first, last;    // first / last step of its chunk
-};
-
-// The steps of one FP64-accuracy level D: K chunks of KC blocks, in each K
-// block the D-1 pairs (p, D-p). D is a compile-time constant so the pair loop
-// unrolls into straight-line issue with constant slice indices; a runtime pair
-// loop costs the single issuing threads about a quarter of the tensor rate.
-template <int D, typename Fn>
-__device__ __forceinline__ void walk_level(int nkb, int& chunk, Fn& f) {
-  constexpr int KC = (16 / (D - 1)) < 1 ? 1 : 16 / (D - 1);
-  for (int kb0 = 0; kb0 < nkb; kb0 += KC, ++chunk) {
-    const int kb1 = min(kb0 + KC, nkb);
-    for (int kb = kb0; kb < kb1; ++kb) {
-#pragma unroll
-      for (int p = 1; p < D; ++p) f(Step{kb, p - 1, D - p - 1, kb == kb0 && p == 1, kb == kb1 - 1 && p == D - 1}, chunk);
-    }
-  }
-}
-
-// Walk the pipeline steps of one tile in order; f(Step, chunk offset in tile).
-template <int MODE, typename Fn>
-__device__ __forceinline__ void for_each_step(int s, int nkb, Fn&& f) {
-  if (MODE == SLICE_FP32EMU) {
-    // pairs (p, q), p + q <= 2, smallest products first
-    for (int kb = 0; kb < nkb; ++kb) {
-      f(Step{kb, 2, 0, kb == 0, false}, 0);
-      f(Step{kb, 1, 1, false, false}, 0);
-      f(Step{kb, 0, 2, false, false}, 0);
-      f(Step{kb, 1, 0, false, false}, 0);
-      f(Step{kb, 0, 1, false, false}, 0);
-      f(Step{kb, 0, 0, false, kb == nkb - 1}, 0);
-    }
-  } else {
-    int chunk = 0;
-    for (int d = s + 1; d >= 2; --d) {   // smallest level first; s is 3 .. 7
-      switch (d) {
-        case 8: walk_level<8>(nkb, chunk, f); break;
-        case 7: walk_level<7>(nkb, chunk, f); break;
-        case 6: walk_level<6>(nkb, chunk, f); break;
-        case 5: walk_level<5>(nkb, chunk, f); break;
-        case 4: walk_level<4>(nkb, chunk, f); break;
-        case 3: walk_level<3>(nkb, chunk, f); break;
-        default: walk_level<2>(nkb, chunk, f); break;
-      }
-    }
-  }
-}
-
-template <int MODE>
-__device__ __forceinline__ int chunks_per_tile(int s, int nkb) {
-  if (MODE == SLICE_FP32EMU) return 1;
-  int c = 0;
-  for (int d = 2; d <= s + 1; ++d) {
-    const int kc = chunk_blocks(d);
-    c += (nkb + kc - 1) / kc;
-  }
-  return c;
-}
-
-struct TileJob {
-  const SliceProblem* P;
-  const CUtensorMap* ta;
-  const CUtensorMap* tb;
-  int tm, tn;
-};
-
-__device__ __forceinline__ TileJob get_job(const SliceGemmArgs& a, const CUtensorMap* pa, const CUtensorMap* pb,
-                                           int t) {
-  TileJob j;
-  if (a.probs == nullptr) {
-    // raster in groups of 8 tile rows so consecutive tiles share B panels
-    const SliceProblem& P = a.single;
-    const int GROUP = 8;
-    const int in_group = GROUP * P.tiles_n;
-    const int gid = t / in_group;
-    const int first_m = gid * GROUP;
-    const int gsize = min(P.tiles_m - first_m, GROUP);
-    j.tm = first_m + (t % in_group) % gsize;
-    j.tn = (t % in_group) / gsize;
-    j.P = &a.single;
-    j.ta = pa;
-    j.tb = pb;
-  } else {
-    const TileRef r = a.tiles[t];
-    j.P = a.probs + r.prob;
-    j.ta = a.tmaps + 2 * r.prob;
-    j.tb = a.tmaps + 2 * r.prob + 1;
-    j.tm = r.tm;
-    j.tn = r.tn;
-  }
-  return j;
-}
-
-template <int BN, int MODE, int CG>
-__global__ void __launch_bounds__(Cfg<BN, MODE, CG>::NUM_THREADS, 1)
-    slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                      const __grid_constant__ SliceGemmArgs args) {
-  using C_ = Cfg<BN, MODE, CG>;
-  extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t full_bar[C_::STAGES];
-  __shared__ __align__(8) uint64_t empty_bar[C_::STAGES];
-  __shared__ __align__(8) uint64_t accf_bar[2];
-  __shared__ __align__(8) uint64_t acce_bar[2];
-  __shared__ __align__(8) uint64_t drain_bar;
-  __shared__ uint32_t tmem_base_slot;
-  __shared__ volatile uint32_t abort_flag;
-
-  const uint32_t warp = warp_id(), lane = lane_id();
-  const uint32_t smem_base = (smem_u32(smem_raw) + 1023u) & ~1023u;
-  uint8_t* smem_gen = smem_raw + (smem_base - smem_u32(smem_raw));
-  const int ntiles = (args.probs == nullptr) ? args.single.tiles_m * args.single.tiles_n : *args.ntiles_dev;
-  // tile walk: CTAs (CG = 1) or CTA pairs (CG = 2) stride over the tile list
-  const uint32_t rank = (CG == 2) ? cluster_ctarank() : 0u;
-  const int walker = (CG == 2) ? static_cast<int>(cluster_id_x()) : static_cast<int>(blockIdx.x);
-  const int walkers = (CG == 2) ? static_cast<int>(cluster_count_x()) : static_cast<int>(gridDim.x);
-  const bool leader = (rank == 0);
-
-  WaitCtl wc;
-  wc.abort = &abort_flag;
-  wc.err = args.err;
-  wc.deadline_ns = globaltimer_ns() + args.timeout_ns;
-
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < C_::STAGES; ++i) {
-      mbar_init(&full_bar[i], 1);
-      mbar_init(&empty_bar[i], 1);
-    }
-    for (int i = 0; i < 2; ++i) {
-      mbar_init(&accf_bar[i], 1);
-      mbar_init(&acce_bar[i], C_::EPI_WARPS * CG);   // the pair's epilogue warps all report to the leader
-    }
-    mbar_init(&drain_bar, 1);
-    abort_flag = 0u;
-    fence_mbar_init();
-  }
-  if (warp == 0 && lane == 0 && args.probs == nullptr) {
-    tma_prefetch_desc(&tmA);
-    tma_prefetch_desc(&tmB);
-  }
-  if (warp == 1) {
-    if constexpr (CG == 2) {
-      tmem_alloc_pair(&tmem_base_slot, C_::TMEM_COLS);   // collective: the same columns in both CTAs
-      tmem_relinquish_pair();
-    } else {
-      tmem_alloc(&tmem_base_slot, C_::TMEM_COLS);
-      tmem_relinquish();
-    }
-  }
-  tc_fence_before();
-  if constexpr (CG == 2)
-    cluster_sync_all();   // both CTAs' barriers exist before any cross-CTA signal
-  else
-    __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem_base = tmem_base_slot;
-
-
-  if (warp == 0) {
-    // ------------------------------------------------------------ producer
-    if (lane == 0) {
-      int it = 0;
-      bool ok = true;
-      for (int t = walker; t < ntiles && ok; t += walkers) {
-        const TileJob job = get_job(args, &tmA, &tmB, t);
-        const int ya = job.tm * C_::TILE_M + static_cast<int>(rank) * BM;
-        const int yb = job.tn * BN + static_cast<int>(rank) * (BN / CG);
-        for_each_step<MODE>(job.P->s, job.P->nkb, [&](const Step& st, int) {
-          if (!ok) return;
-          const int stage = it % C_::STAGES;
-          const uint32_t use = static_cast<uint32_t>(it / C_::STAGES);
-          if (!mbar_wait(&empty_bar[stage], (use & 1u) ^ 1u, wc)) { ok = false; return; }
-          uint8_t* sa = smem_gen + stage * C_::STAGE_BYTES;
-          uint8_t* sb = sa + C_::A_BYTES;
-          if constexpr (CG == 2) {
-            // both CTAs' bytes complete on the leader's barrier; only the leader arrives
-            if (leader) mbar_arrive_expect_tx(&full_bar[stage], 2 * C_::STAGE_BYTES);
-            const uint32_t fb = mapa_shared(smem_u32(&full_bar[stage]), 0);
-            tma_load_3d_pair(sa, job.ta, st.kb * BK, ya, st.pa, fb);
-            tma_load_3d_pair(sb, job.tb, st.kb * BK, yb, st.pb, fb);
-          } else {
-            mbar_arrive_expect_tx(&full_bar[stage], C_::STAGE_BYTES);
-            tma_load_3d(sa, job.ta, st.kb * BK, ya, st.pa, &full_bar[stage]);
-            tma_load_3d(sb, job.tb, st.kb * BK, yb, st.pb, &full_bar[stage]);
-          }
-          ++it;
-        });
-      }
-      if (!ok) {
-        // copies already issued must land before the CTA exits
-        const uint64_t dl = globaltimer_ns() + 100000000ull;
-        for (int j = (it > C_::STAGES ? it - C_::STAGES : 0); j < it; ++j)
-          mbar_wait_quiet(&full_bar[j % C_::STAGES], static_cast<uint32_t>(j / C_::STAGES) & 1u, dl);
-      }
-    }
-    __syncwarp();
-  } else if (warp == 1) {
-    // ----------------------------------------------------------------- MMA
-    if (lane == 0 && leader) {
-      const uint32_t idesc = idesc_bf16_f32(C_::TILE_M, BN);
-      int it = 0;
-      int chunk_base = 0;
-      bool ok = true;
-      bool issued_any = false;
-      for (int t = walker; t < ntiles && ok; t += walkers) {
-        const TileJob job = get_job(args, &tmA, &tmB, t);
-        const int s = job.P->s, nkb = job.P->nkb;
-        for_each_step<MODE>(s, nkb, [&](const Step& st, int cofs) {
-          if (!ok) return;
-          const int chunk = chunk_base + cofs;
-          const int slot = chunk & 1;
-          if (st.first) {
-            const uint32_t use = static_cast<uint32_t>(chunk >> 1);
-            bool w;
-            if constexpr (CG == 2)
-              w = mbar_wait_cluster(&acce_bar[slot], (use & 1u) ^ 1u, wc);
-            else
-              w = mbar_wait(&acce_bar[slot], (use & 1u) ^ 1u, wc);
-            if (!w) { ok = false; return; }
-            tc_fence_after();
-          }
-          const int stage = it % C_::STAGES;
-          const uint32_t use = static_cast<uint32_t>(it / C_::STAGES);
-          if (!mbar_wait(&full_bar[stage], use & 1u, wc)) { ok = false; return; }
-          tc_fence_after();
-          const uint32_t sa = smem_base + stage * C_::STAGE_BYTES;
-          const uint32_t sb = sa + C_::A_BYTES;
-          const uint64_t da = smem_desc_sw128(sa), db = smem_desc_sw128(sb);
-          const uint32_t dt = tmem_base + static_cast<uint32_t>(slot * BN);
-#pragma unroll
-          for (int kk = 0; kk < BK / 16; ++kk) {
-            // 16 bf16 (32 bytes) further along K inside the 128-byte swizzled rows
-            const uint32_t acc = (st.first && kk == 0) ? 0u : 1u;
-            if constexpr (CG == 2)
-              umma_bf16_pair(dt, da + static_cast<uint64_t>(kk * 2), db + static_cast<uint64_t>(kk * 2), idesc, acc);
-            else
-              umma_bf16(dt, da + static_cast<uint64_t>(kk * 2), db + static_cast<uint64_t>(kk * 2), idesc, acc);
-          }
-          issued_any = true;
-          if constexpr (CG == 2) {
-            umma_commit_pair(&empty_bar[stage]);
-            if (st.last) umma_commit_pair(&accf_bar[slot]);
-          } else {
-            umma_commit(&empty_bar[stage]);
-            if (st.last) umma_commit(&accf_bar[slot]);
-          }
-          ++it;
-        });
-        chunk_base += chunks_per_tile<MODE>(s, nkb);
-      }
-      if (!ok && issued_any) {
-        if constexpr (CG == 2)
-          umma_commit_pair_local(&drain_bar);
-        else
-          umma_commit(&drain_bar);
-        mbar_wait_quiet(&drain_bar, 0u, globaltimer_ns() + 100000000ull);
-      }
-    }
-    __syncwarp();
-  } else if (static_cast<int>(warp) >= C_::EPI_WARP0) {
-    // ------------------------------------------------------------ epilogue
-    const int ew = static_cast<int>(warp) - C_::EPI_WARP0;   // 0 .. EPI_WARPS-1
-    const int quad = static_cast<int>(warp & 3u);        // TMEM lane quadrant this warp may access
-    const int half = ew >> 2;                            // which share of the tile's columns
-    const int row_in_tile = quad * 32 + static_cast<int>(lane);
-    const int col_off = half * C_::COLS_PER_THREAD;
-    const uint32_t t_lane = static_cast<uint32_t>(quad * 32) << 16;
-    int chunk = 0;
-    bool ok = true;
-    // where this warp reports "slot drained": the leader's barrier
-    const uint32_t acce_remote0 = (CG == 2) ? mapa_shared(smem_u32(&acce_bar[0]), 0) : 0u;
-    const uint32_t acce_remote1 = (CG == 2) ? mapa_shared(smem_u32(&acce_bar[1]), 0) : 0u;
-    for (int t = walker; t < ntiles && ok; t += walkers) {
-      const TileJob job = get_job(args, &tmA, &tmB, t);
-      const SliceProblem& P = *job.P;
-      const int64_t row = static_cast<int64_t>(job.tm) * C_::TILE_M + static_cast<int64_t>(rank) * BM + row_in_tile;
-      const int64_t col0 = static_cast<int64_t>(job.tn) * BN + col_off;
-      const int64_t n = P.n;
-      const bool row_ok = row < P.m;
-      const int32_t Ei = row_ok ? P.E[row] : 0;
-
-      if (MODE == SLICE_FP32EMU) {
-        const int slot = chunk & 1;
-        if (!mbar_wait(&accf_bar[slot], static_cast<uint32_t>(chunk >> 1) & 1u, wc)) { ok = false; break; }
-        tc_fence_after();
-        double* crow = P.C + row * P.ldc;
-#pragma unroll 1
-        for (int cg = 0; cg < C_::COLS_PER_THREAD / 32; ++cg) {
-          uint32_t r[32];
-          tmem_ld32_sync(tmem_base + t_lane + static_cast<uint32_t>(slot * BN + col_off + cg * 32), r);
-          if (row_ok) {
-#pragma unroll
-            for (int v = 0; v < 32; ++v) {
-              const int64_t col = col0 + cg * 32 + v;
-              if (col < n) {
-                const int32_t Fj = __ldg(P.F + col);
-                double out;
-                if (Ei == EXP_NONFINITE || Fj == EXP_NONFINITE)
-                  out = __longlong_as_double(0x7FF8000000000000ll);
-                else
-                  out = f32_to_f64_scaled(r[v], Ei + Fj);
-                crow[col] = out;
-              }
-            }
-          }
-        }
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) {
-          if constexpr (CG == 2)
-            mbar_arrive_remote(slot ? acce_remote1 : acce_remote0);
-          else
-            mbar_arrive(&acce_bar[slot]);
-        }
-        ++chunk;
-      } else if constexpr (C_::REG_SUMS) {
-        // wide tiles: TMEM holds just the two accumulator slots. Each thread
-        // keeps int32 level sums of its columns in registers (one TMEM load
-        // per element per chunk) and folds them into the int64 total, kept in
-        // C's storage, at the end of each level.
-        int64_t* const xrow = reinterpret_cast<int64_t*>(P.C) + row * P.ldc;
-        const int s = P.s;
-        const int nkb = P.nkb;
-        const int fix_shift = P.fix_shift;
-        constexpr int NG = C_::COLS_PER_THREAD / 8;
-        int32_t lsum[NG][8];
-#pragma unroll
-        for (int g = 0; g < NG; ++g)
-#pragma unroll
-          for (int v = 0; v < 8; ++v) lsum[g][v] = 0;
-        // Folds run from a copy of the sums parked in local memory, 16 columns
-        // (one 128-byte line of the total) per group. The fold of a level is
-        // spread over the following chunks, one group per chunk, so its loads
-        // of the total overlap the tensor cores' next chunks; it completes
-        // before the next fold and before the tile's last one, which converts
-        // the total to doubles at once.
-        constexpr int NQ = C_::COLS_PER_THREAD / 16;
-        int32_t sums[C_::COLS_PER_THREAD];
-        asm volatile("" ::"l"(sums) : "memory");
-        int64_t* const xp = xrow + col0;
-        const bool full = (n - col0 >= C_::COLS_PER_THREAD) && ((reinterpret_cast<uintptr_t>(xp) & 15u) == 0);
-        const int ebase = Ei - 8 * (s + 1) + fix_shift;
-        const bool nan_row = (Ei == EXP_NONFINITE);
-        // fold groups [q0, q1) of the parked sums with the given level parameters
-        auto fold_groups = [&](int q0, int q1, int lsh, bool first, bool rnd, bool last) {
-          auto fold1 = [&](int i, int64_t old, int32_t Fj) -> int64_t {
-            int64_t X = old + (static_cast<int64_t>(sums[i]) << lsh);
-            if (rnd) X = (X + (1ll << (fix_shift - 1))) >> fix_shift;
-            if (last) {
-              const double o = (nan_row || Fj == EXP_NONFINITE) ? __longlong_as_double(0x7FF8000000000000ll)
-                                                               : scale_pow2(__ll2double_rn(X), ebase + Fj);
-              X = __double_as_longlong(o);
-            }
-            return X;
-          };
-#pragma unroll 1
-          for (int q = q0; q < q1; ++q) {
-            if (full) {
-              // eight 16-byte loads in flight, then the stores
-              longlong2 xv[8];
-#pragma unroll
-              for (int j = 0; j < 8; ++j)
-                xv[j] = first ? make_longlong2(0, 0) : reinterpret_cast<const longlong2*>(xp)[q * 8 + j];
-              int4 fv[4] = {};
-              if (last) {
-#pragma unroll
-                for (int j = 0; j < 4; ++j) fv[j] = __ldg(reinterpret_cast<const int4*>(P.F + col0) + q * 4 + j);
-              }
-#pragma unroll
-              for (int j = 0; j < 8; ++j) {
-                const int i = q * 16 + 2 * j;
-                const int4& f4 = fv[j >> 1];
-                xv[j].x = fold1(i, xv[j].x, (j & 1) ? f4.z : f4.x);
-                xv[j].y = fold1(i + 1, xv[j].y, (j & 1) ? f4.w : f4.y);
-                reinterpret_cast<longlong2*>(xp)[q * 8 + j] = xv[j];
-              }
-            } else {
-#pragma unroll 4
-              for (int v = 0; v < 16; ++v) {
-                const int i = q * 16 + v;
-                if (col0 + i < n) xp[i] = fold1(i, first ? 0ll : xp[i], last ? __ldg(P.F + col0 + i) : 0);
-              }
-            }
-          }
-        };
-        // Carry path, taken for s <= 7 by warps whose rows are all full
-        // 16-byte aligned segments while every level fits one int32 segment
-        // and the fixed point lies at or below the last level's weight (the
-        // choice is warp-uniform, as the TMEM loads are warp-collective). After level d
-        // the low byte of each column's running sum is final (every later
-        // level adds multiples of 2^8 at this weight): it is written once to
-        // the thread's own part of C and the rest, an arithmetic shift by 8,
-        // carries into the next level's sum. The last sum S and the bytes b_l
-        // (l = 0 .. s-2, weight 2^(8l)) give the exact total
-        //   X = S 2^(8(s-1)) + sum_l b_l 2^(8l),
-        // rounded once to the fixed point as the fold path rounds it; |S| stays
-        // below SEG_CHUNKS 2^24 + 2^23 < 2^31. Full rows keep the bytes of each
-        // 16-column group (one 16-byte word per level) in the first 16(s-1) <=
-        // 96 bytes of that group's own 128-byte output. The group's 4-column
-        // blocks are converted from block 3 down to block 0; block j's doubles
-        // cover level words 2j and 2j+1, so before block 2 is written the
-        // lower blocks' parts of words 4 and 5 are kept in registers, and
-        // before block 1 is written block 0's parts of words 2 and 3.
-        bool carry = false;
-        // level words a group keeps: s - 1 <= 4 (s <= 5) or <= 6 (s = 6, 7)
-        constexpr int LV = (MODE == SLICE_FP64EMU_CARRY7) ? 6 : 4;
-        if constexpr (MODE == SLICE_FP64EMU_CARRY || MODE == SLICE_FP64EMU_CARRY7) {
-          const int kc_top = chunk_blocks(s + 1);
-          carry = s <= LV + 1 && ((nkb + kc_top - 1) / kc_top <= SEG_CHUNKS) && (fix_shift <= 8 * (s - 1)) &&
-                  __all_sync(0xffffffffu, full);
-        }
-        if (carry) {
-          if constexpr (MODE == SLICE_FP64EMU_CARRY || MODE == SLICE_FP64EMU_CARRY7) {
-          uint8_t* const xb = reinterpret_cast<uint8_t*>(xp);
-          const int W = 8 * (s - 1);
-          auto total = [&](int32_t S, uint64_t R, int32_t Fj) -> double {
-            int64_t X;
-            if (fix_shift == 0)
-              X = (static_cast<int64_t>(S) << W) + static_cast<int64_t>(R);
-            else
-              X = (static_cast<int64_t>(S) << (W - fix_shift)) +
-                  static_cast<int64_t>((R + (1ull << (fix_shift - 1))) >> fix_shift);
-            if (nan_row || Fj == EXP_NONFINITE) return __longlong_as_double(0x7FF8000000000000ll);
-            return scale_pow2(__ll2double_rn(X), ebase + Fj);
-          };
-          for (int d = s + 1; d >= 2 && ok; --d) {
-            const int kc = chunk_blocks(d);
-            const int nch = (nkb + kc - 1) / kc;
-            for (int c = 0; c < nch; ++c, ++chunk) {
-              const int slot = chunk & 1;
-              if (!mbar_wait(&accf_bar[slot], static_cast<uint32_t>(chunk >> 1) & 1u, wc)) { ok = false; break; }
-              tc_fence_after();
-#pragma unroll
-              for (int g = 0; g < NG; ++g)
-                tmem_ld8_add_i32(tmem_base + t_lane + static_cast<uint32_t>(slot * BN + col_off + g * 8), lsum[g]);
-              tc_fence_before();
-              __syncwarp();
-              if (lane == 0) {
-                if constexpr (CG == 2)
-                  mbar_arrive_remote(slot ? acce_remote1 : acce_remote0);
-                else
-                  mbar_arrive(&acce_bar[slot]);
-              }
-            }
-            if (!ok || !row_ok) continue;
-            const int l = s + 1 - d;
-            if (d > 2) {
-              // emit this level's low bytes, carry the rest
-              {
-#pragma unroll
-                for (int q = 0; q < NQ; ++q) {
-                  uint32_t w[4];
-#pragma unroll
-                  for (int j = 0; j < 4; ++j) {
-                    uint32_t x = 0u;
-#pragma unroll
-                    for (int b = 0; b < 4; ++b) {
-                      int32_t& v = lsum[(q * 16 + j * 4 + b) >> 3][(q * 16 + j * 4 + b) & 7];
-                      x |= (static_cast<uint32_t>(v) & 255u) << (8 * b);
-                      v >>= 8;
-                    }
-                    w[j] = x;
-                  }
-                  *reinterpret_cast<uint4*>(xb + q * 128 + 16 * l) = make_uint4(w[0], w[1], w[2], w[3]);
-                }
-              }
-            } else {
-              // the last level: assemble, round, convert
-              // word ll's bytes of 4-column block j of group q (0 past the levels)
-              auto ldw = [&](int q, int j, int ll) -> uint32_t {
-                return (ll < LV && ll < s - 1) ? *reinterpret_cast<const uint32_t*>(xb + q * 128 + 16 * ll + 4 * j) : 0u;
-              };
-              auto convert_block = [&](int q, int j, const uint32_t (&bw)[6]) {
-                const int4 f4 = __ldg(reinterpret_cast<const int4*>(P.F + col0) + q * 4 + j);
-                double o[4];
-#pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                  uint64_t R = 0;
-#pragma unroll
-                  for (int ll = 0; ll < LV; ++ll) R |= static_cast<uint64_t>((bw[ll] >> (8 * b)) & 255u) << (8 * ll);
-                  const int32_t Fj = b == 0 ? f4.x : b == 1 ? f4.y : b == 2 ? f4.z : f4.w;
-                  o[b] = total(lsum[(q * 16 + j * 4 + b) >> 3][(q * 16 + j * 4 + b) & 7], R, Fj);
-                }
-                double2* const op = reinterpret_cast<double2*>(xp) + q * 8 + j * 2;
-                op[0] = make_double2(o[0], o[1]);
-                op[1] = make_double2(o[2], o[3]);
-              };
-#pragma unroll
-              for (int q = 0; q < NQ; ++q) {
-                {
-                  const uint32_t b3[6] = {ldw(q, 3, 0), ldw(q, 3, 1), ldw(q, 3, 2), ldw(q, 3, 3), ldw(q, 3, 4), ldw(q, 3, 5)};
-                  convert_block(q, 3, b3);
-                }
-                const uint32_t w14 = ldw(q, 1, 4), w15 = ldw(q, 1, 5), w04 = ldw(q, 0, 4), w05 = ldw(q, 0, 5);
-                {
-                  const uint32_t b2[6] = {ldw(q, 2, 0), ldw(q, 2, 1), ldw(q, 2, 2), ldw(q, 2, 3), ldw(q, 2, 4), ldw(q, 2, 5)};
-                  convert_block(q, 2, b2);
-                }
-                const uint32_t w02 = ldw(q, 0, 2), w03 = ldw(q, 0, 3);
-                {
-                  const uint32_t b1[6] = {ldw(q, 1, 0), ldw(q, 1, 1), ldw(q, 1, 2), ldw(q, 1, 3), w14, w15};
-                  convert_block(q, 1, b1);
-                }
-                const uint32_t b0[6] = {ldw(q, 0, 0), ldw(q, 0, 1), w02, w03, w04, w05};
-                convert_block(q, 0, b0);
-              }
-            }
-          }
-          }
-        } else {
-        int pend_q = NQ, pend_lsh = 0;   // the deferred fold: next group, level parameters
-        bool pend_first = false, pend_rnd = false;
-        bool first_fold = true;
-        for (int d = s + 1; d >= 2 && ok; --d) {
-          const int kc = chunk_blocks(d);
-          const int nch = (nkb + kc - 1) / kc;
-          const int w = 8 * (s + 1 - d);
-          const bool raw = w < fix_shift;   // summed exactly, rounded after the last such level
-          const int lsh = (MODE == SLICE_LEVELS) ? 0 : (raw ? w : w - fix_shift);
-          const bool round_at_end = (MODE != SLICE_LEVELS) && raw && (d == 2 || w + 8 >= fix_shift);
-          for (int c = 0; c < nch; ++c, ++chunk) {
-            const int slot = chunk & 1;
-            const bool level_end = (c == nch - 1);
-            const bool seg_end = ((c + 1) % SEG_CHUNKS) == 0;
-            if (!mbar_wait(&accf_bar[slot], static_cast<uint32_t>(chunk >> 1) & 1u, wc)) { ok = false; break; }
-            tc_fence_after();
-#pragma unroll
-            for (int g = 0; g < NG; ++g)
-              tmem_ld8_add_i32(tmem_base + t_lane + static_cast<uint32_t>(slot * BN + col_off + g * 8), lsum[g]);
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) {
-              if constexpr (CG == 2)
-                mbar_arrive_remote(slot ? acce_remote1 : acce_remote0);
-              else
-                mbar_arrive(&acce_bar[slot]);
-            }
-            if constexpr (MODE != SLICE_LEVELS) {
-              if (pend_q < NQ && row_ok) {
-                // one group of the deferred fold; the next group's line towards L2
-                if (!pend_first && pend_q + 1 < NQ && col0 + (pend_q + 1) * 16 < n) prefetch_l2(xp + (pend_q + 1) * 16);
-                fold_groups(pend_q, pend_q + 1, pend_lsh, pend_first, pend_rnd, false);
-                ++pend_q;
-              }
-            }
-            if (!(level_end || seg_end)) continue;
-            const bool last = level_end && (d == 2);
-            const bool rnd = level_end && round_at_end;
-            if (row_ok) {
-              if constexpr (MODE == SLICE_LEVELS) {
-                int64_t* const lp = P.levels + (static_cast<int64_t>(d - 2) * P.m + row) * n + col0;
-#pragma unroll
-                for (int g = 0; g < NG; ++g)
-#pragma unroll
-                  for (int v = 0; v < 8; ++v) {
-                    const int i = g * 8 + v;
-                    if (col0 + i < n) lp[i] += static_cast<int64_t>(lsum[g][v]);
-                    lsum[g][v] = 0;
-                  }
-              } else {
-                // finish the previous fold, then park these sums (and reset them
-                // here, inside the branch: rows past m keep stale sums that are
-                // never stored; resetting outside makes the compiler spill the
-                // sums in the chunk loop)
-                if (pend_q < NQ) fold_groups(pend_q, NQ, pend_lsh, pend_first, pend_rnd, false);
-#pragma unroll
-                for (int g = 0; g < NG; ++g)
-#pragma unroll
-                  for (int v = 0; v < 8; ++v) { sums[g * 8 + v] = lsum[g][v]; lsum[g][v] = 0; }
-                asm volatile("" ::"l"(sums) : "memory");
-                if (last) {
-                  fold_groups(0, NQ, lsh, first_fold, rnd, true);
-                  pend_q = NQ;
-                } else {
-                  if (!first_fold) prefetch_l2(xp);
-                  pend_q = 0;
-                  pend_lsh = lsh;
-                  pend_first = first_fold;
-                  pend_rnd = rnd;
-                }
-              }
-            }
-            first_fold = false;
-          }
-        }
-        }
-      } else {
-        double* const crow = P.C + row * P.ldc;
-        const int s = P.s;
-        const int nkb = P.nkb;
-        const int fix_shift = P.fix_shift;
-        const uint32_t txlo = tmem_base + t_lane + static_cast<uint32_t>(C_::XLO_COL + col_off);
-        const uint32_t txhi = tmem_base + t_lane + static_cast<uint32_t>(C_::XHI_COL + col_off);
-        bool fresh = true;   // X holds nothing yet (reads as zero)
-        for (int d = s + 1; d >= 2 && ok; --d) {
-          const int kc = chunk_blocks(d);
-          const int nch = (nkb + kc - 1) / kc;
-          // weight of level d in the total (level output: unweighted)
-          const int w = 8 * (s + 1 - d);
-          const bool raw = w < fix_shift;
-          const int lsh = (MODE == SLICE_LEVELS) ? 0 : (raw ? w : w - fix_shift);
-          const bool round_at_end = (MODE != SLICE_LEVELS) && raw && (d == 2 || w + 8 >= fix_shift);
-          if (MODE == SLICE_LEVELS) fresh = true;
-          for (int c = 0; c < nch; ++c, ++chunk) {
-            const int slot = chunk & 1;
-            const bool level_end = (c == nch - 1);
-            const bool out = (MODE == SLICE_LEVELS) ? level_end : (level_end && d == 2);
-            const bool rnd = level_end && round_at_end;
-            if (!mbar_wait(&accf_bar[slot], static_cast<uint32_t>(chunk >> 1) & 1u, wc)) { ok = false; break; }
-            tc_fence_after();
-#pragma unroll 1
-            for (int cg = 0; cg < C_::COLS_PER_THREAD / 16; ++cg) {
-              uint32_t r[16], lo[16], hi[16];
-              const uint32_t tacc = tmem_base + t_lane + static_cast<uint32_t>(slot * BN + col_off + cg * 16);
-              if (!fresh) {
-                tmem_ld16x3_sync(tacc, txlo + cg * 16, txhi + cg * 16, r, lo, hi);
-              } else {
-                tmem_ld16_sync(tacc, r);
-#pragma unroll
-                for (int v = 0; v < 16; ++v) lo[v] = hi[v] = 0u;
-              }
-#pragma unroll
-              for (int v = 0; v < 16; ++v) {
-                const int64_t a = static_cast<int64_t>(__float2int_rz(__uint_as_float(r[v])));
-                int64_t X = static_cast<int64_t>((static_cast<uint64_t>(hi[v]) << 32) | lo[v]) + (a << lsh);
-                if (rnd) X = (X + (1ll << (fix_shift - 1))) >> fix_shift;
-                lo[v] = static_cast<uint32_t>(static_cast<uint64_t>(X));
-                hi[v] = static_cast<uint32_t>(static_cast<uint64_t>(X) >> 32);
-              }
-              if (!out) {
-                tmem_st16(txlo + cg * 16, lo);
-                tmem_st16(txhi + cg * 16, hi);
-              } else if (row_ok) {
-#pragma unroll 4
-                for (int v = 0; v < 16; ++v) {
-                  const int64_t col = col0 + cg * 16 + v;
-                  if (col < n) {
-                    const int64_t X = static_cast<int64_t>((static_cast<uint64_t>(hi[v]) << 32) | lo[v]);
-                    if (MODE == SLICE_LEVELS) {
-                      P.levels[(static_cast<int64_t>(d - 2) * P.m + row) * n + col] = X;
-                    } else {
-                      const int32_t Fj = __ldg(P.F + col);
-                      double o;
-                      if (Ei == EXP_NONFINITE || Fj == EXP_NONFINITE)
-                        o = __longlong_as_double(0x7FF8000000000000ll);
-                      else
-                        o = scale_pow2(__ll2double_rn(X), Ei + Fj - 8 * (s + 1) + fix_shift);
-                      crow[col] = o;
-                    }
-                  }
-                }
-              }
-            }
-            if (!out) tmem_st_wait();
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) {
-          if constexpr (CG == 2)
-            mbar_arrive_remote(slot ? acce_remote1 : acce_remote0);
-          else
-            mbar_arrive(&acce_bar[slot]);
-        }
-            fresh = false;
-          }
-        }
-      }
-    }
-  }
-
-  tc_fence_before();
-  if constexpr (CG == 2)
-    cluster_sync_all();   // the leader's MMAs into this CTA's TMEM and all remote arrivals are done
-  else
-    __syncthreads();
-  if (warp == 1) {
-    tc_fence_after();
-    if constexpr (CG == 2)
-      tmem_dealloc_pair(tmem_base, C_::TMEM_COLS);
-    else
-      tmem_dealloc(tmem_base, C_::TMEM_COLS);
-  }
-}
-
-template <int BN, int MODE, int CG>
-static cudaError_t set_smem_attr() {
-  return cudaFuncSetAttribute(slice_gemm_kernel<BN, MODE, CG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              Cfg<BN, MODE, CG>::SMEM_BYTES);
-}
-
-template <int BN, int MODE, int CG>
-static cudaError_t launch_t(const CUtensorMap* tmA, const CUtensorMap* tmB, const SliceGemmArgs& a, int grid,
-                            cudaStream_t st) {
-  using C_ = Cfg<BN, MODE, CG>;
-  if (CG == 1) {
-    slice_gemm_kernel<BN, MODE, 1><<<grid, C_::NUM_THREADS, C_::SMEM_BYTES, st>>>(*tmA, *tmB, a);
-    return cudaGetLastError();
-  }
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(static_cast<unsigned>(grid));
-  cfg.blockDim = dim3(C_::NUM_THREADS);
-  cfg.dynamicSmemBytes = C_::SMEM_BYTES;
-  cfg.stream = st;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = 2;
-  at[0].val.clusterDim.y = 1;
-  at[0].val.clusterDim.z = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, slice_gemm_kernel<BN, MODE, CG>, *tmA, *tmB, a);
-}
-
-template <int BN, int MODE>
-static int max_pairs_t() {
-  using C_ = Cfg<BN, MODE, 2>;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(2);
-  cfg.blockDim = dim3(C_::NUM_THREADS);
-  cfg.dynamicSmemBytes = C_::SMEM_BYTES;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = 2;
-  at[0].val.clusterDim.y = 1;
-  at[0].val.clusterDim.z = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  int n = 0;
-  if (cudaOccupancyMaxActiveClusters(&n, slice_gemm_kernel<BN, MODE, 2>, &cfg) != cudaSuccess) {
-    cudaGetLastError();
-    return 0;
-  }
-  return n;
-}
-
-}  // namespace mmdev
+// slice_gemm.cu -- FP32-accuracy instances of the slice GEMM and the dispatch
+// over modes, tile widths and CTA groupings (the kernel itself is in
+// slice_gemm_kernel.cuh; the FP64-accuracy instances are in
+// slice_gemm_fold.cu and slice_gemm_carry.cu).
+#include "slice_gemm_kernel.cuh"
 
 using namespace mmdev;
-
-namespace {
-
-template <int BN, int CG>
-cudaError_t launch_emu(int mode, const CUtensorMap* tmA, const CUtensorMap* tmB, const SliceGemmArgs& a, int grid,
-                       cudaStream_t st) {
-  if (mode == SLICE_FP64EMU_CARRY || mode == SLICE_FP64EMU_CARRY7) {
-    // the carry epilogue needs register level sums (tiles wider than 128)
-    if constexpr (BN != 128) {
-      if (mode == SLICE_FP64EMU_CARRY) return launch_t<BN, SLICE_FP64EMU_CARRY, CG>(tmA, tmB, a, grid, st);
-      return launch_t<BN, SLICE_FP64EMU_CARRY7, CG>(tmA, tmB, a, grid, st);
-    }
-    mode = SLICE_FP64EMU;
-  }
-  if (mode == SLICE_FP64EMU) return launch_t<BN, SLICE_FP64EMU, CG>(tmA, tmB, a, grid, st);
-  if (mode == SLICE_LEVELS) return launch_t<BN, SLICE_LEVELS, CG>(tmA, tmB, a, grid, st);
-  return cudaErrorInvalidValue;
-}
-
-template <int BN>
-cudaError_t prepare_emu() {
-  cudaError_t e;
-  if ((e = set_smem_attr<BN, SLICE_FP64EMU, 1>()) != cudaSuccess) return e;
-  if ((e = set_smem_attr<BN, SLICE_FP64EMU, 2>()) != cudaSuccess) return e;
-  if constexpr (BN != 128) {
-    if ((e = set_smem_attr<BN, SLICE_FP64EMU_CARRY, 1>()) != cudaSuccess) return e;
-    if ((e = set_smem_attr<BN, SLICE_FP64EMU_CARRY, 2>()) != cudaSuccess) return e;
-    if ((e = set_smem_attr<BN, SLICE_FP64EMU_CARRY7, 1>()) != cudaSuccess) return e;
-    if ((e = set_smem_attr<BN, SLICE_FP64EMU_CARRY7, 2>()) != cudaSuccess) return e;
-  }
-  if ((e = set_smem_attr<BN, SLICE_LEVELS, 1>()) != cudaSuccess) return e;
-  return set_smem_attr<BN, SLICE_LEVELS, 2>();
-}
-
-}  // namespace
 
 cudaError_t slice_gemm_prepare() {
   cudaError_t e;
   if ((e = set_smem_attr<256, SLICE_FP32EMU, 1>()) != cudaSuccess) return e;
   if ((e = set_smem_attr<128, SLICE_FP32EMU, 1>()) != cudaSuccess) return e;
   if ((e = set_smem_attr<256, SLICE_FP32EMU, 2>()) != cudaSuccess) return e;
-  if ((e = prepare_emu<128>()) != cudaSuccess) return e;
-  if ((e = prepare_emu<192>()) != cudaSuccess) return e;
-  if ((e = prepare_emu<240>()) != cudaSuccess) return e;
-  return prepare_emu<256>();
+  if ((e = slice_prepare_fold()) != cudaSuccess) return e;
+  return slice_prepare_carry();
 }
 
 int slice_gemm_max_pairs(int mode) {
   if (mode == SLICE_FP32EMU) return max_pairs_t<256, SLICE_FP32EMU>();
-  if (mode == SLICE_FP64EMU || mode == SLICE_FP64EMU_CARRY || mode == SLICE_FP64EMU_CARRY7)
-    return max_pairs_t<256, SLICE_FP64EMU>();
-  return max_pairs_t<256, SLICE_LEVELS>();
+  return slice_max_pairs_fold(mode == SLICE_LEVELS ? SLICE_LEVELS : SLICE_FP64EMU);
 }
 
 bool slice_gemm_tile_ok(int mode, int bn, int cg) {
@@ -908,8 +28,10 @@ bool slice_gemm_tile_ok(int mode, int bn, int cg) {
 
 // FP32-accuracy: bn 256 (cg 1 or 2) or 128 (cg 1). FP64-accuracy and level
 // output: bn 128 keeps the int64 total in TMEM (grouped launches of small
-// products); bn 192, 240, 256 keep int32 level sums in registers and the int64
-// total in C. cg = 2: CTA pairs on 256-row tiles (grid = 2 x pairs).
+// products); bn 192, 240, 256 keep int32 level sums in registers, with the
+// int64 total in C (fold) or the byte-carry recombination (carry modes; on
+// bn 128 a carry mode runs the fold kernel, same results). cg = 2: CTA pairs
+// on 256-row tiles (grid = 2 x pairs).
 cudaError_t launch_slice_gemm(int mode, int bn, int cg, const CUtensorMap* tmA, const CUtensorMap* tmB,
                               const SliceGemmArgs& a, int grid, cudaStream_t st) {
   if (grid <= 0) return cudaSuccess;
@@ -919,14 +41,9 @@ cudaError_t launch_slice_gemm(int mode, int bn, int cg, const CUtensorMap* tmA, 
     if (bn == 256) return launch_t<256, SLICE_FP32EMU, 1>(tmA, tmB, a, grid, st);
     return launch_t<128, SLICE_FP32EMU, 1>(tmA, tmB, a, grid, st);
   }
-  switch (bn * 4 + cg) {
-    case 128 * 4 + 1: return launch_emu<128, 1>(mode, tmA, tmB, a, grid, st);
-    case 128 * 4 + 2: return launch_emu<128, 2>(mode, tmA, tmB, a, grid, st);
-    case 192 * 4 + 1: return launch_emu<192, 1>(mode, tmA, tmB, a, grid, st);
-    case 192 * 4 + 2: return launch_emu<192, 2>(mode, tmA, tmB, a, grid, st);
-    case 240 * 4 + 1: return launch_emu<240, 1>(mode, tmA, tmB, a, grid, st);
-    case 240 * 4 + 2: return launch_emu<240, 2>(mode, tmA, tmB, a, grid, st);
-    case 256 * 4 + 1: return launch_emu<256, 1>(mode, tmA, tmB, a, grid, st);
-    default: return launch_emu<256, 2>(mode, tmA, tmB, a, grid, st);
+  if (mode == SLICE_FP64EMU_CARRY || mode == SLICE_FP64EMU_CARRY7) {
+    if (bn != 128) return slice_launch_carry(mode, bn, cg, tmA, tmB, a, grid, st);
+    mode = SLICE_FP64EMU;
   }
+  return slice_launch_fold(mode, bn, cg, tmA, tmB, a, grid, st);
 }
