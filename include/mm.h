@@ -182,7 +182,8 @@ int mm_serve_drain(mm_handle h);
 
 /* Options (mm_set_option / mm_get_option). */
 enum {
-    MM_OPT_SLICES = 1,        /* FP64-accuracy slice count s (0 = automatic rule, else 3..7) */
+    MM_OPT_SLICES = 1,        /* FP64-accuracy slice count s (0 = automatic rule, else 3..7; the
+                                 environment variable MM_SLICES sets it at mm_create) */
     MM_OPT_TIMEOUT_MS = 2,    /* bound on every device-side wait (default 2000) */
     MM_OPT_AUTOTUNE = 3,      /* 1 = on the first product (or group) of a shape bucket, time every
                                  candidate launch configuration on the caller's stream (blocking

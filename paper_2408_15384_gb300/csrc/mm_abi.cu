@@ -398,8 +398,12 @@ int mm_create(mm_handle* out, int device, size_t mem_budget_bytes) {
   h->budget = mem_budget_bytes ? mem_budget_bytes : (size_t(40) << 30);
   h->sm_count = prop.multiProcessorCount;
   h->t0 = std::chrono::steady_clock::now();
-  const char* es = getenv("MM_SLICES");
-  if (es) h->opt_slices = atoi(es);
+  // MM_SLICES: the same range as MM_OPT_SLICES (3 .. 7); anything else is ignored
+  if (const char* es = getenv("MM_SLICES")) {
+    const int v = atoi(es);
+    if (v >= 3 && v <= 7) h->opt_slices = v;
+    else logf(1, "MM_SLICES=%s ignored (3 .. 7)", es);
+  }
   cudaDriverEntryPointQueryResult q;
   void* fn = nullptr;
   if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
