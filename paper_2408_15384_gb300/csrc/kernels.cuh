@@ -14,8 +14,11 @@ static inline uint64_t splitmix_mix_host(uint64_t z) {
 }
 
 // ---------------------------------------------------------------- split.cu
+// Row maxima of |A| and column maxima of |B| (bit patterns); one fused launch
+// when both operands are non-empty, else one per operand. *nlaunch, if given,
+// receives the kernel launches made.
 cudaError_t launch_absmax(const double* A, int64_t m, int64_t k, int64_t lda, const double* B, int64_t n,
-                          int64_t ldb, uint64_t* rowmax, uint64_t* colmax, cudaStream_t st);
+                          int64_t ldb, uint64_t* rowmax, uint64_t* colmax, cudaStream_t st, int* nlaunch = nullptr);
 // Slices of rows [0, m) of A into planes of plane_rows rows (0: m), so a
 // panel of a larger matrix can be sliced into its place.
 cudaError_t launch_slice_rows(int mode, const double* A, int64_t m, int64_t k, int64_t lda, const uint64_t* rowmax,

@@ -205,12 +205,13 @@ void SplitLayout::plan(int64_t m_, int64_t n_, int64_t k_, int S_) {
   bytes = off;
 }
 
-// Scan + split of both operands into the workspace (3 launches + 1 memset).
+// Scan + split of both operands into the workspace (3 or 4 launches + 1 memset).
 int run_split(mm_handle_s* h, int mode01, const SplitLayout& L, char* ws, const double* A, int64_t lda,
               const double* B, int64_t ldb, cudaStream_t st) {
   uint64_t* rowmax = reinterpret_cast<uint64_t*>(ws + L.off_rowmax);
   uint64_t* colmax = reinterpret_cast<uint64_t*>(ws + L.off_colmax);
-  cudaError_t e = launch_absmax(A, L.m, L.k, lda, B, L.n, ldb, rowmax, colmax, st);
+  int nscan = 0;
+  cudaError_t e = launch_absmax(A, L.m, L.k, lda, B, L.n, ldb, rowmax, colmax, st, &nscan);
   if (e != cudaSuccess) return cuda_status(e, "absmax");
   e = launch_slice_rows(mode01, A, L.m, L.k, lda, rowmax, L.S, L.kp, reinterpret_cast<uint16_t*>(ws + L.off_sa),
                         reinterpret_cast<int32_t*>(ws + L.off_E), h->d_err, st);
@@ -218,7 +219,7 @@ int run_split(mm_handle_s* h, int mode01, const SplitLayout& L, char* ws, const 
   e = launch_slice_cols(mode01, B, L.k, L.n, ldb, colmax, L.S, L.kp, reinterpret_cast<uint16_t*>(ws + L.off_sb),
                         reinterpret_cast<int32_t*>(ws + L.off_F), h->d_err, st);
   if (e != cudaSuccess) return cuda_status(e, "slice cols");
-  count_launch(h, 4);
+  count_launch(h, 2 + static_cast<uint64_t>(nscan));
   return MM_OK;
 }
 

@@ -352,6 +352,27 @@ __global__ void col_absmax_kernel(const double* __restrict__ B, int64_t k, int64
   col_absmax_body(B, ldb, j, r0, min(k, r0 + rows_per_block), colmax);
 }
 
+// Both maxima in one launch: blocks [0, row_blocks) take 8 rows of A each (a
+// warp per row), the rest 256 columns x rows_per_block rows of B each, so the
+// two read streams overlap and the launch's ramp and tail are paid once.
+__global__ void __launch_bounds__(256) absmax_both_kernel(const double* __restrict__ A, int64_t m, int64_t k,
+                                                          int64_t lda, uint64_t* __restrict__ rowmax,
+                                                          const double* __restrict__ B, int64_t n, int64_t ldb,
+                                                          int64_t rows_per_block, unsigned long long* __restrict__ colmax,
+                                                          int row_blocks, int col_bx) {
+  const int b = static_cast<int>(blockIdx.x);
+  if (b < row_blocks) {
+    const int64_t row = static_cast<int64_t>(b) * 8 + (threadIdx.x >> 5);
+    if (row < m) row_absmax_body(A, k, lda, row, rowmax);
+    return;
+  }
+  const int cb = b - row_blocks;
+  const int64_t j = static_cast<int64_t>(cb % col_bx) * 256 + threadIdx.x;
+  if (j >= n) return;
+  const int64_t r0 = static_cast<int64_t>(cb / col_bx) * rows_per_block;
+  col_absmax_body(B, ldb, j, r0, min(k, r0 + rows_per_block), colmax);
+}
+
 template <int MODE>
 __global__ void slice_rows_kernel(const double* __restrict__ A, int64_t m, int64_t k, int64_t lda,
                                   const uint64_t* __restrict__ rowmax, int s, int64_t kp,
@@ -477,17 +498,36 @@ __global__ void fill_uniform_kernel(double* __restrict__ X, int64_t rows, int64_
 using namespace mmdev;
 
 cudaError_t launch_absmax(const double* A, int64_t m, int64_t k, int64_t lda, const double* B, int64_t n,
-                          int64_t ldb, uint64_t* rowmax, uint64_t* colmax, cudaStream_t st) {
+                          int64_t ldb, uint64_t* rowmax, uint64_t* colmax, cudaStream_t st, int* nlaunch) {
+  if (nlaunch) *nlaunch = 0;
+  if (m > 0 && n > 0 && k > 0) {
+    cudaError_t e = cudaMemsetAsync(colmax, 0, sizeof(uint64_t) * n, st);
+    if (e != cudaSuccess) return e;
+    const int64_t rpb = 256;
+    const int64_t row_blocks = (m + 7) / 8, col_bx = (n + 255) / 256, col_by = (k + rpb - 1) / rpb;
+    const int64_t blocks = row_blocks + col_bx * col_by;
+    if (blocks <= 0x7fffffff) {
+      absmax_both_kernel<<<static_cast<unsigned>(blocks), 256, 0, st>>>(
+          A, m, k, lda, rowmax, B, n, ldb, rpb, reinterpret_cast<unsigned long long*>(colmax),
+          static_cast<int>(row_blocks), static_cast<int>(col_bx));
+      if (nlaunch) *nlaunch = 1;
+      return cudaGetLastError();
+    }
+  }
   if (m > 0) {
     dim3 blk(256), grd(static_cast<unsigned>((m + 7) / 8));
     row_absmax_kernel<<<grd, blk, 0, st>>>(A, m, k, lda, rowmax);
+    if (nlaunch) ++*nlaunch;
   }
   if (n > 0) {
     cudaError_t e = cudaMemsetAsync(colmax, 0, sizeof(uint64_t) * n, st);
     if (e != cudaSuccess) return e;
     int64_t rpb = 256;
     dim3 blk(128), grd(static_cast<unsigned>((n + 127) / 128), static_cast<unsigned>((k + rpb - 1) / rpb));
-    if (k > 0) col_absmax_kernel<<<grd, blk, 0, st>>>(B, k, n, ldb, rpb, reinterpret_cast<unsigned long long*>(colmax));
+    if (k > 0) {
+      col_absmax_kernel<<<grd, blk, 0, st>>>(B, k, n, ldb, rpb, reinterpret_cast<unsigned long long*>(colmax));
+      if (nlaunch) ++*nlaunch;
+    }
   }
   return cudaGetLastError();
 }

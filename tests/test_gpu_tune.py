@@ -51,10 +51,11 @@ def test_autotune_single_fp64_emu_same_bits(mm):
         assert entry is not None
         bn, cg, _ = entry
         assert bn in (128, 192, 240, 256) and cg in (1, 2)
-        # a later product of the same bucket uses the entry: one split pass + one slice GEMM
+        # a later product of the same bucket uses the entry: one split pass (the
+        # fused scan of both operands, row and column slicing) + one slice GEMM
         n0 = h.stats()
         C2 = run(h, A, B, mm.FP64_EMU)
-        assert h.stats() - n0 == 5
+        assert h.stats() - n0 == 4
         assert h.tune_lookup(mm.FP64_EMU, 720, 620, 1000) == entry   # same bucket
     assert np.array_equal(C1, ref) and np.array_equal(C2, ref)
 
