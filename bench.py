@@ -125,12 +125,21 @@ def measured_peaks():
 SLICE_GEMM_SOURCES = ("slice_gemm_kernel.cuh", "slice_gemm.cu", "slice_gemm_fold.cu", "slice_gemm_carry.cu")
 
 
+def code_of(text: str) -> str:
+    """C++ source without comments, trailing spaces and blank lines (what the
+    compiler sees), so a comment edit leaves the code hash unchanged."""
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    lines = [re.sub(r"//.*$", "", ln).rstrip() for ln in text.splitlines()]
+    return "\n".join(ln for ln in lines if ln)
+
+
 def slice_gemm_source_hash() -> str:
-    """sha256[:16] over the slice GEMM's kernel header and sources, in order."""
+    """sha256[:16] over the code of the slice GEMM's kernel header and sources,
+    in order, comments removed."""
     h = hashlib.sha256()
     for name in SLICE_GEMM_SOURCES:
-        with open(os.path.join(ROOT, "paper_2408_15384_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, "paper_2408_15384_gb300", "csrc", name)) as f:
+            h.update(code_of(f.read()).encode())
     return h.hexdigest()[:16]
 
 

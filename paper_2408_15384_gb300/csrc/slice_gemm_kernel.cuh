@@ -1,15 +1,17 @@
 // slice_gemm_kernel.cuh -- tcgen05 tensor-core product of bfloat16 operand slices, with
 // the FP32-accuracy or FP64-accuracy epilogue. Persistent: each CTA (one per
-// SM) walks a list of 128 x BN output tiles, of one product or of a group of
-// products.
+// SM), or CTA pair (cta_group::2, 256-row tiles), walks a list of 128 x BN
+// (256 x BN) output tiles, of one product or of a group of products.
 //
 // Warp roles:
 //   warp 0      TMA producer: one A-slice tile (128 x 64) and one B-slice tile
-//               (BN x 64) per pipeline step into a STAGES-deep shared ring.
-//   warp 1      allocates TMEM; one thread issues tcgen05.mma (M=128, N=BN,
-//               K=16, bf16 x bf16 -> f32) and tcgen05.commit.
-//   warps 2..9  epilogue: tcgen05.ld of the accumulator, row = TMEM lane,
-//               two warps per TMEM lane quadrant, each on half the columns.
+//               (BN x 64, or BN/2 x 64 per CTA of a pair) per pipeline step
+//               into a STAGES-deep shared ring.
+//   warp 1      allocates TMEM; one thread issues tcgen05.mma (M = 128 or 256,
+//               N = BN, K = 16, bf16 x bf16 -> f32) and tcgen05.commit.
+//   warps 2..   epilogue: 8 warps, or 12 / 16 when the FP64-accuracy level sums
+//               live in registers; warp w reads TMEM lane quadrant w % 4 (row
+//               = TMEM lane), the warps of a quadrant split the columns.
 // Accumulation chunks alternate between two TMEM slots of BN columns, so the
 // tensor cores run the next chunk (or the next tile) while the epilogue drains
 // the previous one.
@@ -23,17 +25,18 @@
 // to 2). Level d sums d-1 slice pairs; with |slice| <= 2^7 each product is at
 // most 2^14, so a K-chunk of Kc with Kc * (d-1) <= 1024 sums to at most 2^24
 // and the f32 accumulator holds it exactly. The epilogue converts each
-// finished chunk to integers and adds it, at its level weight w_d = 8(s+1-d),
-// to an int64 fixed-point total with unit 2^shift (shift >= 0 keeps the total
-// below 2^62):
+// finished chunk to integers and adds it at its level weight w_d = 8(s+1-d).
+// The exact total is rounded once (half up) to a fixed point 2^shift
+// (shift >= 0 keeps it below 2^62):
 //   X = round(sum_{w_d < shift} 2^w_d L_d / 2^shift) + sum_{w_d >= shift} 2^(w_d - shift) L_d,
-// which is the exact total rounded once (half up) to the fixed point: the
-// levels below the fixed point are summed exactly first and rounded at the
-// end of the last of them. 128-wide tiles keep X in TMEM (512 columns = two
-// accumulator slots + the low and high 32-bit planes of X); 256-wide tiles keep
-// int32 level sums in registers and X in C's storage. After the last level X
-// is converted to double once, scaled by 2^(E_i + F_j - 8(s+1) + shift) and
-// stored. Every tiling gives the same bits.
+// the levels below the fixed point summed exactly first. 128-wide tiles keep
+// X in TMEM (512 columns = two accumulator slots + the low and high 32-bit
+// planes of X). Wider tiles keep int32 level sums in registers and either fold
+// them into X held in C's storage (SLICE_FP64EMU) or recombine them by byte
+// carry (SLICE_FP64EMU_CARRY, _CARRY7: each level's final low byte stored once,
+// the rest carried into the next level's sum). After the last level X is
+// converted to double once, scaled by 2^(E_i + F_j - 8(s+1) + shift) and
+// stored. Every tiling and every recombination gives the same bits.
 //
 // The kernel templates and their launchers; slice_gemm.cu (FP32-accuracy and
 // the dispatch), slice_gemm_fold.cu (FP64-accuracy int64 fold and level
