@@ -85,6 +85,78 @@ def has_nonfinite(X: np.ndarray) -> bool:
 
 
 # ---------------------------------------------------------------------------
+# Step 1b (FP64-accuracy): slice count from the operands' spread
+# ---------------------------------------------------------------------------
+# Error estimate behind the automatic slice count. With digit width 8 and
+# s slices, every kept product is formed exactly; the error of output (i, j)
+# comes from (a) rounding each entry to the grid 2^(E-8s) (row i of A) or
+# 2^(F-8s) (column j of B) and (b) the dropped levels d >= s+2, led by level
+# s+2 with its s-1 digit pairs. Taking the digits below the leading ones as
+# independent and uniform on [-128, 128), one term a_ik*b_kj carries an error
+# of standard deviation at most KAPPA * 2^(E_i+F_j-8s): (a) gives at most
+# sqrt(2/12 * 1/4) = 0.204 (|a| < 2^(E-1)), (b) gives sqrt(s-1) * 128^2/3 *
+# 2^-16 = 0.083 sqrt(s-1), and for s <= 7 the two together stay below 0.3.
+# Over k terms with independent signs the error grows like sqrt(k); the
+# largest of up to 2^30 outputs stays within Z = 6.5 standard deviations.
+# The componentwise bound is 4k 2^-53 sum_k |a_ik||b_kj|, which for rows and
+# columns spread independently of each other is about
+# 4k 2^-53 * k * alpha_i * beta_j * 2^(E_i+F_j), where
+#     alpha_i = mean_k |a_ik| / 2^E_i,   beta_j = mean_k |b_kj| / 2^F_j.
+# So the error stays within THETA of the bound for every output when
+#     KAPPA * Z * 2^(53-8s) <= THETA * 4 * k * sqrt(k) * alpha_min * beta_min.
+# The slice count is the smallest s in 3..7 that passes; when none does the
+# product runs through the plain FP64 kernel (returned as s = 8).
+KAPPA = 0.3
+Z_MAX = 6.5
+THETA = 0.5
+S_MIN, S_MAX, S_PLAIN = 3, 7, 8
+
+
+def row_spread(A: np.ndarray, E: np.ndarray) -> np.ndarray:
+    """alpha_i = (sum_k |a_ik|) / (k * 2^E_i) in fp64; +inf for a row that is all
+    zero or holds Inf/NaN (such rows put no constraint on the slice count)."""
+    A = np.asarray(A, dtype=np.float64)
+    m, k = A.shape
+    out = np.full(m, np.inf)
+    for i in range(m):
+        row = A[i]
+        if not np.all(np.isfinite(row)):
+            continue
+        total = math.fsum(abs(float(x)) for x in row)
+        if total > 0.0:
+            out[i] = total / (k * math.ldexp(1.0, int(E[i])))
+    return out
+
+
+def col_spread(B: np.ndarray, F: np.ndarray) -> np.ndarray:
+    """beta_j = (sum_k |b_kj|) / (k * 2^F_j), as row_spread on the columns."""
+    return row_spread(np.asarray(B, dtype=np.float64).T, F)
+
+
+def slice_count_from_spread(k: int, alpha_min: float, beta_min: float) -> int:
+    """Smallest s in S_MIN..S_MAX with KAPPA*Z_MAX*2^(53-8s) <= THETA*4*k*sqrt(k)*alpha_min*beta_min,
+    else S_PLAIN. Evaluated in double (k*sqrt(k) with a correctly rounded sqrt)."""
+    rhs = THETA * 4.0 * float(k) * math.sqrt(float(k)) * float(alpha_min) * float(beta_min)
+    for s in range(S_MIN, S_MAX + 1):
+        if KAPPA * Z_MAX * math.ldexp(1.0, 53 - 8 * s) <= rhs:
+            return s
+    return S_PLAIN
+
+
+def slice_count(A: np.ndarray, B: np.ndarray) -> int:
+    """The automatic FP64-accuracy slice count of the product A*B (S_PLAIN:
+    the plain FP64 product)."""
+    A = np.asarray(A, dtype=np.float64)
+    B = np.asarray(B, dtype=np.float64)
+    k = A.shape[1]
+    alpha = row_spread(A, row_exponents(A, 2))
+    beta = col_spread(B, col_exponents(B, 2))
+    amin = float(alpha.min()) if alpha.size else math.inf
+    bmin = float(beta.min()) if beta.size else math.inf
+    return slice_count_from_spread(k, amin, bmin)
+
+
+# ---------------------------------------------------------------------------
 # Step 2 (FP64-accuracy): integer representation and balanced digits
 # ---------------------------------------------------------------------------
 def integer_repr(A: np.ndarray, E: np.ndarray, s: int, t: int = T_BITS) -> np.ndarray:

@@ -131,6 +131,29 @@ def box_muller(rows: int, cols: int, seed: int, stream: int) -> np.ndarray:
     return z[:count].reshape(rows, cols)
 
 
+def wide_spread(rows: int, cols: int, seed: int, stream: int, octaves: int = 16) -> np.ndarray:
+    """Heavy spread within every row and column: sym(i) * 2^-g(i), with g(i) an
+    integer uniform on [0, octaves] drawn from the stream after the values
+    (counters rows*cols + i)."""
+    v = uniform(rows, cols, seed, stream)
+    g = np.floor(unit(seed, stream, rows * cols, rows * cols) * (octaves + 1)).astype(np.int64)
+    return np.ldexp(v, -g.reshape(rows, cols))
+
+
+def student_t3(rows: int, cols: int, seed: int, stream: int) -> np.ndarray:
+    """Heavy-tailed deviates, Student's t with 3 degrees of freedom: z0 / sqrt((z1^2 + z2^2 + z3^2) / 3)
+    from four Box-Muller normals of the stream (entry i takes normals 4i .. 4i+3)."""
+    z = box_muller(4 * rows * cols, 1, seed, stream).reshape(rows * cols, 4)
+    t = z[:, 0] / np.sqrt((z[:, 1] ** 2 + z[:, 2] ** 2 + z[:, 3] ** 2) / 3.0)
+    return t.reshape(rows, cols)
+
+
+def cauchy(rows: int, cols: int, seed: int, stream: int) -> np.ndarray:
+    """Cauchy deviates (no finite mean): the ratio of two Box-Muller normals of the stream."""
+    z = box_muller(2 * rows * cols, 1, seed, stream).reshape(rows * cols, 2)
+    return (z[:, 0] / z[:, 1]).reshape(rows, cols)
+
+
 def problem_set(count: int, lo: int, hi: int, seed: int):
     """(m, n, k) triples, each dimension log-uniform on [lo, hi] independently."""
     d = loguniform_dims(3 * count, lo, hi, seed)
