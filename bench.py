@@ -267,7 +267,7 @@ def ours(args):
     C = torch.empty_like(A)
     mm.fill_uniform(A, seed, inputs.STREAM_A, 1, inputs.STREAM_EXP_A)
     mm.fill_uniform(B, seed, inputs.STREAM_B, 2, inputs.STREAM_EXP_B)
-    s = mm.slices_for_k(N)
+    s = h.debug_slice_count(A, B)[0]   # the automatic count the device decides for these inputs
     pairs = s * (s + 1) // 2
     flop = 2.0 * N ** 3
 
@@ -316,13 +316,16 @@ def ours(args):
 
     # ---------------- dominant kernel roofline (tensor pipe, bf16)
     peaks = measured_peaks()
-    kernel_ms = gemm_ms / max(gemm_n, 1)
+    # slice-GEMM device time per product: the launch that ran plus the launches
+    # for the other candidate counts, which return at once
+    kernel_ms = gemm_ms / max(args.steps, 1)
     slice_flop = flop * pairs
     achieved = slice_flop / (kernel_ms * 1e-3) / 1e12
-    if "bf16_tflops_sustained" in peaks:
-        peak, peak_note = peaks["bf16_tflops_sustained"], "of measured (bf16 sustained)"
+    # the kernel runs at full clock in a sub-second region: the burst peak
+    if "bf16_tflops" in peaks:
+        peak, peak_note = peaks["bf16_tflops"], "of measured (bf16 burst)"
     else:
-        peak, peak_note = 1700.0, "of fallback (bf16 sustained)"
+        peak, peak_note = 1900.0, "of fallback (bf16 burst)"
     traffic, src_hash = profiled_traffic()
 
     extra = {}
@@ -440,9 +443,8 @@ def paper_sweep_leg(h, args, mm, inputs, torch, dev, stream):
     against the oracle."""
     import numpy as np
     out = {"inputs": "Box-Muller normal deviates from two seeded unit draws (Sec. IV)", "sizes": {},
-           "slice_rule": "1 (calibrated on normal rows)"}
+           "slice_count": "automatic (decided on the device from the rows' and columns' spread)"}
     names = {mm.FP64: "fp64", mm.FP64_EMU: "fp64_emu", mm.FP32_EMU: "fp32_emu"}
-    h.set_option(mm.OPT_SLICE_RULE, 1)
     for N in sorted(PAPER_SERIAL_GCC_O3_S):
         A = inputs.box_muller(N, N, 7 + N, inputs.STREAM_A)
         B = inputs.box_muller(N, N, 7 + N, inputs.STREAM_B)
@@ -471,8 +473,8 @@ def paper_sweep_leg(h, args, mm, inputs, torch, dev, stream):
             if ref is not None:
                 from oracle import emulation as em
                 row[name + "_max_err_over_bound"] = float(np.max(np.abs(Cd.cpu().numpy() - ref) / (em.gamma(N, name) * D)))
+        row["fp64_emu_slices"] = h.debug_slice_count(Ad, Bd)[0]
         out["sizes"][str(N)] = row
-    h.set_option(mm.OPT_SLICE_RULE, 0)
     return out
 
 

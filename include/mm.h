@@ -19,8 +19,11 @@
  *                products on the tcgen05 tensor cores with exact FP32 partial
  *                sums, exact integer recombination, one rounding to double
  *                (Ozaki, Ogita, Oishi, Rump 2012; Ootomo, Ozaki, Yokota 2024).
- *                Meets |C - C_ref| <= 4k*2^-53 * (|A||B|) on the library's
- *                workload distributions (see mm_gemm).
+ *                The slice count s is chosen on the device for each product
+ *                from the spread of its rows and columns (mm_slice_count_rule)
+ *                so that the error stays near half of the componentwise
+ *                bound 4k*2^-53 * (|A||B|); where no s <= 7 would, the product
+ *                runs on the plain FP64 kernel instead (see mm_gemm).
  *   MM_FP32_EMU  FP32-accuracy emulation: three bfloat16 slices per scaled
  *                entry and the six slice products with index sum <= 2, FP32
  *                accumulation on tcgen05. Bound 4k*2^-24 * (|A||B|).
@@ -95,6 +98,9 @@ typedef struct {
     double t_admit_us;       /* admitted: memory reserved, queued for a batch */
     double t_launch_us;      /* its batch was launched */
     double t_done_us;        /* its batch finished on the GPU (host saw the event) */
+    int32_t stream;          /* the serving stream its batch ran on (0 .. MM_OPT_SERVE_STREAMS-1) */
+    double t_gpu_start_us;   /* its batch's work began on the GPU (device clock, CUDA events, */
+    double t_gpu_end_us;     /*   from a reference event recorded when serving started) and ended */
 } mm_req_status;
 
 /* -------------------------------------------------------------- lifecycle */
@@ -121,27 +127,39 @@ const char *mm_status_string(int status);
  * Argument errors (checked on the host before any launch): MM_ERR_INVALID_ARG
  * for NULL pointers with nonzero sizes, negative sizes, lda < k, ldb < n,
  * ldc < n, C overlapping A or B, or an unknown precision.
- * Emulated modes: non-finite inputs are detected on the device; the affected
- * rows/columns of C become NaN and the handle's sticky status is set, which
- * mm_sync() reports as MM_ERR_NONFINITE. For k <= 4 MM_FP64_EMU computes with
- * the FP64 kernel (per-row scaling to <= 56 bits cannot meet the FP64 bound
- * for such short sums). The emulated FP64 accuracy bound is met on inputs whose
- * entries within a row of A (column of B) share a scale, such as the workload
- * recipes; a row mixing very different magnitudes can exceed it, since the
- * splitting is exact only relative to the row maximum. */
+ * Device-side errors go to the error word of `stream` (each stream the handle
+ * sees has its own), which mm_sync(h, stream) reports and clears: in the
+ * emulated modes non-finite inputs make the affected rows/columns of C NaN
+ * and report MM_ERR_NONFINITE; a device wait that ran out reports
+ * MM_ERR_TIMEOUT (C is then incomplete).
+ * MM_FP64_EMU slice count: with MM_OPT_SLICES = 0 (default) it is decided on
+ * the device, after the exponent scan, from alpha = min over rows of
+ * mean|a_ik| / 2^E_i and beta (the same over columns of B): the smallest s in
+ * 3..7 with 0.3 * 6.5 * 2^(53-8s) <= 0.5 * 4 k sqrt(k) alpha beta (an estimate
+ * of the largest error against half the bound; mm_slice_count_rule), else
+ * the product runs on the plain FP64 kernel. The estimate takes the rows' and
+ * columns' magnitudes as independent of each other; inputs built so that a
+ * row's large entries meet a column's tiny ones can still exceed the bound.
+ * The kernels for every candidate count are queued, and each returns at once
+ * unless the count decided on the device is its own. For k <= 4 MM_FP64_EMU
+ * computes with the FP64 kernel (per-row scaling to <= 56 bits cannot meet
+ * the FP64 bound for such short sums). */
 int mm_gemm(mm_handle h, int64_t m, int64_t n, int64_t k,
             const double *A, int64_t lda, const double *B, int64_t ldb,
             double *C, int64_t ldc, int precision, void *stream);
 
 /* Same product with HOST operands (pageable or pinned): copies A and B to
  * device workspace, computes, copies C back, and synchronises. Returns the
- * device-side status (including MM_ERR_NONFINITE / MM_ERR_TIMEOUT). */
+ * device-side status of `stream` (including MM_ERR_NONFINITE /
+ * MM_ERR_TIMEOUT). */
 int mm_gemm_host(mm_handle h, int64_t m, int64_t n, int64_t k,
                  const double *A, int64_t lda, const double *B, int64_t ldb,
                  double *C, int64_t ldc, int precision, void *stream);
 
-/* Wait for `stream` and return (and clear) the handle's sticky device status:
- * MM_OK, MM_ERR_NONFINITE or MM_ERR_TIMEOUT. */
+/* Wait for `stream` and return (and clear) the device status of the work the
+ * handle queued on that stream: MM_OK, MM_ERR_NONFINITE or MM_ERR_TIMEOUT.
+ * Streams are told apart by their cudaStream_t value; beyond 255 distinct
+ * streams per handle the rest share one word. */
 int mm_sync(mm_handle h, void *stream);
 
 /* `count` independent products in one persistent launch per stage (the split
@@ -172,7 +190,10 @@ int mm_serve_submit(mm_handle h, const mm_request *r, uint64_t *ticket);
 
 /* Non-blocking poll: MM_OK (done; C is complete and *st filled; the ticket is
  * released), MM_PENDING (not yet), MM_ERR_NOT_FOUND (unknown ticket) or the
- * request's own error (also released). st may be NULL. */
+ * request's own error (also released): MM_ERR_NONFINITE when its own operands
+ * held Inf/NaN (other requests of its batch are not affected), MM_ERR_TIMEOUT
+ * when a device wait of its batch ran out (every request of that batch),
+ * MM_ERR_CUDA on a launch failure. st may be NULL. */
 int mm_serve_poll(mm_handle h, uint64_t ticket, mm_req_status *st);
 
 /* Block until every submitted request has completed (or failed). */
@@ -182,8 +203,9 @@ int mm_serve_drain(mm_handle h);
 
 /* Options (mm_set_option / mm_get_option). */
 enum {
-    MM_OPT_SLICES = 1,        /* FP64-accuracy slice count s (0 = automatic rule, else 3..7; the
-                                 environment variable MM_SLICES sets it at mm_create) */
+    MM_OPT_SLICES = 1,        /* FP64-accuracy slice count s (0 = decided on the device for each
+                                 product, see mm_gemm; else 3..7 for every product; the environment
+                                 variable MM_SLICES sets it at mm_create) */
     MM_OPT_TIMEOUT_MS = 2,    /* bound on every device-side wait (default 2000) */
     MM_OPT_AUTOTUNE = 3,      /* 1 = on the first product (or group) of a shape bucket, time every
                                  candidate launch configuration on the caller's stream (blocking
@@ -194,11 +216,8 @@ enum {
     MM_OPT_PROFILE = 7,           /* 1 = time every kernel launch with CUDA events (see mm_profile_read) */
     MM_OPT_CTA_PAIR = 8,          /* emulated products: 0 = automatic, 1 = one CTA per 128-row tile,
                                      2 = CTA pairs (cta_group::2) on 256-row tiles */
-    MM_OPT_TILE_N = 9,            /* FP64-accuracy tile width: 0 = automatic, 128, 192, 240 or 256
+    MM_OPT_TILE_N = 9             /* FP64-accuracy tile width: 0 = automatic, 128, 192, 240 or 256
                                      columns. Every choice gives the same bits. */
-    MM_OPT_SLICE_RULE = 10        /* automatic FP64-accuracy slice count (see mm_slices_for_k_rule):
-                                     0 = calibrated on uniform-like rows (default), 1 = on rows of
-                                     normal deviates (heavier tails, more slices) */
 };
 
 /* Kernel classes for mm_profile_read. */
@@ -210,16 +229,18 @@ enum {
 int mm_set_option(mm_handle h, int option, int64_t value);
 int mm_get_option(mm_handle h, int option, int64_t *value);
 
-/* The slice count the automatic rule picks for inner dimension k (FP64-EMU),
- * default rule. The slice count sets the accuracy: the error of the emulated
- * product grows with each row's (column's) largest entry against its typical
- * ones, and the componentwise bound 4k*2^-53*|A||B| is what the rules are
- * calibrated to, at most half of it at each threshold:
- *   rule 0 (rows like uniform samples):   s = 7 for k < 96, 6 for k < 4096, else 5
- *   rule 1 (rows like normal deviates):   s = 7 for k < 160, 6 for k < 12288, else 5
- * mm_slices_for_k_rule returns -1 for an unknown rule. */
-int mm_slices_for_k(int64_t k);
-int mm_slices_for_k_rule(int64_t k, int rule);
+/* The automatic FP64-accuracy slice count for inner dimension k when the
+ * smallest row spread of A is alpha_min and that of B's columns beta_min
+ * (spread = mean |entry| / 2^E, E = floor(log2 max |entry|) + 2, so spreads
+ * lie in (0, 1/2); +inf for no constraint). Error estimate: one term a_ik b_kj
+ * carries an error of standard deviation at most 0.3 * 2^(E_i+F_j-8s) (digit
+ * rounding plus the dropped level s+2 with independent uniform digits), k terms
+ * grow it by sqrt(k), the largest output stays within 6.5 deviations, and the
+ * bound is about 4k 2^-53 * k alpha beta 2^(E_i+F_j). Returns the smallest s
+ * in 3..7 whose estimate is at most half the bound, 8 when none is (the
+ * product then runs on the plain FP64 kernel), -1 for k < 1. The same function
+ * runs on the device; the decision is evaluated in double. */
+int mm_slice_count_rule(int64_t k, float alpha_min, float beta_min);
 
 /* ---------------------------------------------------------------- autotuner */
 
@@ -268,6 +289,13 @@ int mm_fill_uniform(double *X, int64_t rows, int64_t cols, int64_t ld,
 int mm_debug_slices(mm_handle h, int which, int mode, int s,
                     int64_t rows, int64_t cols, const double *X, int64_t ldx,
                     int32_t *exps, uint16_t *slices, void *stream);
+
+/* The automatic slice count of the product A*B as the device decides it
+ * (scan, spreads, rule), with the smallest row and column spreads it used.
+ * Device operands; synchronous. */
+int mm_debug_slice_count(mm_handle h, int64_t m, int64_t n, int64_t k,
+                         const double *A, int64_t lda, const double *B, int64_t ldb,
+                         int *s, float *alpha_min, float *beta_min, void *stream);
 
 /* The level products L_d (d = 2..s+1) of the FP64-accuracy mode as the
  * tensor-core kernel accumulates them (exact integers), written as int64
@@ -353,8 +381,9 @@ int mm_serve_bench(mm_handle h, const mm_serve_load *load, mm_serve_load_result 
  * processes that reserve their device memory up front and allow no later
  * allocation. The paper has no counterpart; this is a library service.
  *
- * Same product, layout and results as mm_gemm with the same precision (the
- * FP64-accuracy result is bit-identical). No handle: it runs on the calling
+ * Same product, layout and results as mm_gemm with the same precision on a
+ * handle whose slice count is automatic (MM_OPT_SLICES = 0 and MM_SLICES
+ * unset): the FP64-accuracy result is bit-identical. No handle: it runs on the calling
  * thread's current device, asynchronously on `stream` (NULL = legacy default
  * stream). A, B, C are caller-owned device pointers.
  * Scratch: one fixed 32 MiB array inside the library image, held by every GPU
@@ -364,8 +393,10 @@ int mm_serve_bench(mm_handle h, const mm_serve_load *load, mm_serve_load_result 
  * call clears what must start at zero itself.
  * Errors: MM_ERR_INVALID_ARG (as mm_gemm, or another precision),
  * MM_ERR_BUDGET (the problem's split operands need more than the fixed
- * scratch: about 2*s*(m+n)*k bytes, s <= 7), MM_ERR_CUDA. Inf/NaN inputs give
- * NaN in the affected rows/columns of C; no status is reported for them. */
+ * scratch: about 14*(m+n)*k bytes for FP64-accuracy, 6*(m+n)*k for
+ * FP32-accuracy), MM_ERR_CUDA. The device-side status is not reported to the
+ * caller: Inf/NaN inputs give NaN in the affected rows/columns of C, and a
+ * device wait that runs out (after 2 s) leaves C incomplete, both silently. */
 int mm_gemm_emu_static(int64_t m, int64_t n, int64_t k,
                        const double *A, int64_t lda, const double *B, int64_t ldb,
                        double *C, int64_t ldc, int precision, void *stream);

@@ -25,7 +25,6 @@ OPT_SLICES, OPT_TIMEOUT_MS, OPT_AUTOTUNE, OPT_SERVE_MAX_BATCH, OPT_SERVE_STREAMS
 OPT_PROFILE = 7
 OPT_CTA_PAIR = 8
 OPT_TILE_N = 9
-OPT_SLICE_RULE = 10
 KERNEL_SLICE_GEMM, KERNEL_SPLIT, KERNEL_FP64_GEMM = 0, 1, 2
 
 
@@ -133,7 +132,7 @@ class Handle:
         return C
 
     def sync(self, stream=None) -> int:
-        """Wait for the stream; return the sticky device status (0 = ok)."""
+        """Wait for the stream; return (and clear) the device status of the work queued on it (0 = ok)."""
         return self.lib.mm_sync(self.h, _stream_handle(stream))
 
     @staticmethod
@@ -257,6 +256,18 @@ class Handle:
             raise MMError(rc, "mm_debug_slices")
         return exps, sl, rc
 
+    def debug_slice_count(self, A, B, stream=None):
+        """(s, alpha_min, beta_min) as the device decides them for A*B."""
+        pa, m, k, lda = _mat(A, "A")
+        pb, _, n, ldb = _mat(B, "B")
+        s = ctypes.c_int(0)
+        a = ctypes.c_float(0.0)
+        b = ctypes.c_float(0.0)
+        rc = self.lib.mm_debug_slice_count(self.h, m, n, k, pa, lda, pb, ldb, ctypes.byref(s), ctypes.byref(a),
+                                           ctypes.byref(b), _stream_handle(stream))
+        _check(rc, "mm_debug_slice_count")
+        return s.value, a.value, b.value
+
     def debug_levels(self, A, B, s: int, stream=None):
         """Level products L_d (d = 2..s+1) as int64 [s][m][n]."""
         import torch
@@ -268,8 +279,10 @@ class Handle:
         return L
 
 
-def slices_for_k(k: int, rule: int = 0) -> int:
-    return _lib.load().mm_slices_for_k_rule(int(k), int(rule))
+def slice_count_rule(k: int, alpha_min: float, beta_min: float) -> int:
+    """The automatic FP64-accuracy slice count for inner dimension k and the
+    smallest row / column spreads (8: the plain FP64 kernel)."""
+    return _lib.load().mm_slice_count_rule(int(k), float(alpha_min), float(beta_min))
 
 
 def fill_uniform(X, seed: int, stream_id: int, scale_mode: int = 0, exp_stream_id: int = 0, stream=None):

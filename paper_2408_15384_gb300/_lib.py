@@ -46,7 +46,8 @@ class ServeSample(ctypes.Structure):
 class ReqStatus(ctypes.Structure):
     _fields_ = [("status", c_int), ("user_tag", c_u64),
                 ("t_submit_us", ctypes.c_double), ("t_admit_us", ctypes.c_double),
-                ("t_launch_us", ctypes.c_double), ("t_done_us", ctypes.c_double)]
+                ("t_launch_us", ctypes.c_double), ("t_done_us", ctypes.c_double),
+                ("stream", ctypes.c_int32), ("t_gpu_start_us", ctypes.c_double), ("t_gpu_end_us", ctypes.c_double)]
 
 
 # name -> (restype, argtypes); the full exported surface of include/mm.h
@@ -63,14 +64,15 @@ SIGNATURES = {
     "mm_serve_drain": (c_int, [c_vp]),
     "mm_set_option": (c_int, [c_vp, c_int, c_i64]),
     "mm_get_option": (c_int, [c_vp, c_int, ctypes.POINTER(c_i64)]),
-    "mm_slices_for_k": (c_int, [c_i64]),
-    "mm_slices_for_k_rule": (c_int, [c_i64, c_int]),
+    "mm_slice_count_rule": (c_int, [c_i64, ctypes.c_float, ctypes.c_float]),
     "mm_tune_save": (c_int, [c_vp, ctypes.c_char_p]),
     "mm_tune_load": (c_int, [c_vp, ctypes.c_char_p]),
     "mm_tune_lookup": (c_int, [c_vp, c_int, c_int, c_i64, c_i64, c_i64, ctypes.POINTER(c_int), ctypes.POINTER(c_int),
                                ctypes.POINTER(c_int)]),
     "mm_fill_uniform": (c_int, [c_vp, c_i64, c_i64, c_i64, c_u64, c_u64, c_int, c_u64, c_vp]),
     "mm_debug_slices": (c_int, [c_vp, c_int, c_int, c_int, c_i64, c_i64, c_vp, c_i64, c_vp, c_vp, c_vp]),
+    "mm_debug_slice_count": (c_int, [c_vp, c_i64, c_i64, c_i64, c_vp, c_i64, c_vp, c_i64, ctypes.POINTER(c_int),
+                                     ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float), c_vp]),
     "mm_debug_level_products": (c_int, [c_vp, c_i64, c_i64, c_i64, c_vp, c_i64, c_vp, c_i64, c_int, c_vp, c_vp]),
     "mm_debug_wait_timeout": (c_int, [c_vp, c_i64, c_vp]),
     "mm_peak_fp64": (c_int, [c_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),

@@ -184,6 +184,8 @@ __device__ __forceinline__ void fp64_tile(const Fp64GemmArgs& a, int64_t m0, int
 
 template <int KIND>
 __global__ void __launch_bounds__(FTHREADS) fp64_gemm_kernel(const Fp64GemmArgs a) {
+  // the fallback of an emulated product: only when its slice count asks for it
+  if (a.only_if_plain != nullptr && *a.only_if_plain != SLICE_S_PLAIN) return;
   extern __shared__ __align__(16) uint8_t fsm_raw[];
   Fp64Smem& sm = *reinterpret_cast<Fp64Smem*>(fsm_raw);
   fp64_tile<KIND>(a, static_cast<int64_t>(blockIdx.y) * FT, static_cast<int64_t>(blockIdx.x) * FT, sm);
@@ -202,6 +204,7 @@ __global__ void __launch_bounds__(FTHREADS) fp64_grouped_kernel(const Fp64GemmAr
   for (int t = blockIdx.x; t < nt; t += gridDim.x) {
     const TileRef r = tiles[t];
     const Fp64GemmArgs a = probs[r.prob];
+    if (a.only_if_plain != nullptr && *a.only_if_plain != SLICE_S_PLAIN) continue;   // uniform over the block
     fp64_tile<KIND>(a, static_cast<int64_t>(r.tm) * FT, static_cast<int64_t>(r.tn) * FT, sm);
     __syncthreads();
   }

@@ -47,13 +47,17 @@ struct mm_handle_s {
   std::chrono::steady_clock::time_point t0;
   EncodeTiledFn encode = nullptr;
   cudaMemPool_t pool = nullptr;
-  uint32_t* d_err = nullptr;                 // device error word (MM_DEV_ERR_* bits)
+  // device error words (MM_DEV_ERR_* bits), one per stream the handle has
+  // seen (err_word); slot 0 is shared by streams beyond the table's size
+  uint32_t* d_err = nullptr;
+  std::mutex err_mu;
+  std::unordered_map<cudaStream_t, int> err_slot;
+  int err_next = 1;
   std::atomic<size_t> ws_in_use{0};          // workspace bytes held (budget accounting)
   std::atomic<uint64_t> launches{0};         // kernels launched by the library
 
   // options
-  int opt_slices = 0;
-  int opt_slice_rule = 0;    // automatic slice count: 0 uniform-calibrated, 1 normal-calibrated
+  int opt_slices = 0;        // 0: automatic slice count (decided on the device from the operands)
   int64_t opt_timeout_ms = 2000;
   bool opt_autotune = false;
   int opt_serve_max_batch = 32;
@@ -88,24 +92,34 @@ int ws_alloc(mm_handle_s* h, size_t bytes, cudaStream_t st, void** out);
 void ws_free(mm_handle_s* h, void* p, size_t bytes, cudaStream_t st);
 int validate_problem(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B, int64_t ldb,
                      const double* C, int64_t ldc, int precision);
-int slices_for_k(int64_t k, int rule);
+// error words: MM_ERR_SLOTS per handle
+constexpr int MM_ERR_SLOTS = 256;
+uint32_t* err_word(mm_handle_s* h, cudaStream_t st);
 int fixed_shift(int s, int64_t k);
 // 3-D map (k, rows, slice) over bfloat16 slices; planes of plane_rows rows
 // (0: rows), so a panel of a larger matrix's slices can be mapped.
 bool encode_slices_tmap(mm_handle_s* h, CUtensorMap* tm, const void* base, int64_t k, int64_t rows, int S, int64_t kp,
                         int box_rows, int64_t plane_rows = 0);
+// the same with an explicit encoder (callers without a handle)
+bool encode_slices_tmap_with(EncodeTiledFn encode, CUtensorMap* tm, const void* base, int64_t k, int64_t rows, int S,
+                             int64_t kp, int box_rows, int64_t plane_rows = 0);
 void count_launch(mm_handle_s* h, uint64_t n);
 int fp64_kind(mm_handle_s* h);
 int gemm_device(mm_handle_s* h, int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
                 int64_t ldb, double* C, int64_t ldc, int precision, cudaStream_t st);
 struct SplitLayout;
+// The slice count of an emulated product: 3 (FP32-accuracy), the override or
+// the handle's fixed count, else 0 = automatic (decided on the device).
 int emu_slices(mm_handle_s* h, int precision, int64_t k, int s_override);
+// Slice planes a workspace holds for slice count s (0: automatic -> 7).
+inline int emu_planes(int s) { return s > 0 ? s : SLICE_S_MAX; }
 int emu_gemm_rows(mm_handle_s* h, int precision, const SplitLayout& L, char* ws, int s, int64_t r0, int64_t mr,
                   double* C, int64_t ldc, int64_t* levels, const TileCfg& cfg, cudaStream_t st);
 // one product with an explicit launch configuration (no tuning)
 int gemm_with_cfg(mm_handle_s* h, int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
                   int64_t ldb, double* C, int64_t ldc, int precision, const TileCfg& cfg, cudaStream_t st);
-int read_and_clear_err(mm_handle_s* h);
+// Reads and clears the error word of stream st (synchronous copy).
+int read_and_clear_err(mm_handle_s* h, cudaStream_t st);
 
 // Brackets one launch with events when profiling is on.
 struct ProfScope {
@@ -123,12 +137,17 @@ struct DeviceGuard {
   ~DeviceGuard();
 };
 
-// Workspace layout of one emulated product.
+// Workspace layout of one emulated product. s = 0: automatic slice count
+// (7 planes, plus the decision record and the column partial sums).
 struct SplitLayout {
   int64_t m = 0, n = 0, k = 0, kp = 0;
   int S = 0;
-  size_t off_rowmax = 0, off_colmax = 0, off_E = 0, off_F = 0, off_sa = 0, off_sb = 0, bytes = 0;
-  void plan(int64_t m_, int64_t n_, int64_t k_, int S_);
+  bool autos = false;
+  size_t off_rowmax = 0, off_colmax = 0, off_E = 0, off_F = 0, off_sa = 0, off_sb = 0, off_dec = 0, off_part = 0,
+         bytes = 0;
+  void plan(int64_t m_, int64_t n_, int64_t k_, int s);
+  SliceDecision* dec(char* ws) const { return autos ? reinterpret_cast<SliceDecision*>(ws + off_dec) : nullptr; }
+  uint2* part(char* ws) const { return autos ? reinterpret_cast<uint2*>(ws + off_part) : nullptr; }
 };
 
 int run_split(mm_handle_s* h, int mode01, const SplitLayout& L, char* ws, const double* A, int64_t lda,
@@ -162,8 +181,16 @@ int grouped_run(mm_handle_s* h, int count, const mm_problem* probs, int precisio
 TileCfg grouped_cfg(mm_handle_s* h, int count, const mm_problem* probs, int precision);
 size_t grouped_direct_bytes(mm_handle_s* h, int count, const mm_problem* probs, int precision, const TileCfg& cfg,
                             size_t* host_bytes);
+// Per-problem error reporting of a direct grouped launch: the launch's word
+// (header word 3: timeouts) and one word per emulated problem (non-finite
+// input, at off_perr) are copied back into the host blob's first `bytes`
+// bytes on the stream after the launch; main_idx[i] is the problem of word i.
+struct GroupedErrReport {
+  size_t bytes = 0, off_perr = 0;
+  std::vector<int> main_idx;
+};
 int grouped_direct(mm_handle_s* h, int count, const mm_problem* probs, int precision, const TileCfg& cfg,
-                   void* host_blob, size_t host_cap, cudaStream_t st);
+                   void* host_blob, size_t host_cap, cudaStream_t st, GroupedErrReport* rep = nullptr);
 void serve_shutdown(mm_handle_s* h);
 
 }  // namespace mmhost

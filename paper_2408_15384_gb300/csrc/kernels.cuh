@@ -13,19 +13,85 @@ static inline uint64_t splitmix_mix_host(uint64_t z) {
   return z ^ (z >> 31);
 }
 
+// ------------------------------------------------- automatic slice count
+// FP64-accuracy slice count from the operands' spread. For each row i of A
+// (column j of B) the scan forms alpha_i = mean_k |a_ik| / 2^E_i (beta_j
+// likewise). One term a_ik b_kj of the emulated product carries an error of
+// standard deviation at most SLICE_KAPPA * 2^(E_i + F_j - 8s): the rounding of
+// the entries to their digit grids and the dropped level s+2 (s-1 digit pairs
+// below 2^-16 of the level above) with digits independent and uniform. Over k
+// terms it grows like sqrt(k), and the largest of up to 2^30 outputs stays
+// within SLICE_ZMAX standard deviations; the componentwise bound is about
+// 4k 2^-53 * k alpha_i beta_j 2^(E_i+F_j). The count is the smallest s in
+// 3..7 with
+//   SLICE_KAPPA * SLICE_ZMAX * 2^(53-8s) <= SLICE_THETA * 4 * k * sqrt(k) * alpha_min * beta_min,
+// so the error stays within SLICE_THETA of the bound; SLICE_S_PLAIN (8) when
+// none qualifies: the product then runs through the plain FP64 kernel.
+constexpr int SLICE_S_MIN = 3, SLICE_S_MAX = 7, SLICE_S_PLAIN = 8;
+#define SLICE_KAPPA 0.3
+#define SLICE_ZMAX 6.5
+#define SLICE_THETA 0.5
+
+// The decision record of one product in device memory. The smallest alpha of
+// A's rows and beta of B's columns are kept as their distance below +inf,
+// 0x7F800000 minus the float bits (merged with atomicMax; zero, the initial
+// value, means no row or column constrains the count); s is the slice count,
+// written by the splitting kernels and read by the slice GEMM and the
+// plain-FP64 fallback.
+struct SliceDecision {
+  uint32_t amin_room;
+  uint32_t bmin_room;
+  int32_t s;
+  int32_t pad;
+};
+
+__host__ __device__ inline float spread_from_room(uint32_t room) {
+  union { uint32_t u; float f; } v;
+  v.u = room >= 0x7F800000u ? 0u : 0x7F800000u - room;
+  return v.f;
+}
+
+// The slice count for inner dimension k and the smallest spreads (double
+// arithmetic, k * sqrt(k) with the correctly rounded square root).
+__host__ __device__ inline int slice_count_rule(int64_t k, float amin, float bmin) {
+  const double rhs = SLICE_THETA * 4.0 * static_cast<double>(k) * sqrt(static_cast<double>(k)) *
+                     static_cast<double>(amin) * static_cast<double>(bmin);
+  double pw = 536870912.0;   // 2^(53 - 8*3)
+  for (int s = SLICE_S_MIN; s <= SLICE_S_MAX; ++s, pw *= 0.00390625) {
+    if (SLICE_KAPPA * SLICE_ZMAX * pw <= rhs) return s;
+  }
+  return SLICE_S_PLAIN;
+}
+
+// The smallest count the rule can give for inner dimension k (the largest
+// spread any row or column can have is below 1/2).
+inline int slice_count_floor(int64_t k) { return slice_count_rule(k, 0.5f, 0.5f); }
+
 // ---------------------------------------------------------------- split.cu
 // Row maxima of |A| and column maxima of |B| (bit patterns); one fused launch
 // when both operands are non-empty, else one per operand. *nlaunch, if given,
 // receives the kernel launches made.
+// With dec != nullptr the scan also forms the spreads: each row's alpha is
+// merged into dec->amin_room; the columns' partial sums go to colpart
+// (launch_absmax_parts(k) records of n columns each), and a short second
+// launch sums them in a fixed order and merges each column's beta into
+// dec->bmin_room. The caller zeroes *dec beforehand.
 cudaError_t launch_absmax(const double* A, int64_t m, int64_t k, int64_t lda, const double* B, int64_t n,
-                          int64_t ldb, uint64_t* rowmax, uint64_t* colmax, cudaStream_t st, int* nlaunch = nullptr);
+                          int64_t ldb, uint64_t* rowmax, uint64_t* colmax, cudaStream_t st, int* nlaunch = nullptr,
+                          SliceDecision* dec = nullptr, uint2* colpart = nullptr);
+// Partial-sum records per column of B for inner dimension k.
+int64_t launch_absmax_parts(int64_t k);
 // Slices of rows [0, m) of A into planes of plane_rows rows (0: m), so a
-// panel of a larger matrix can be sliced into its place.
+// panel of a larger matrix can be sliced into its place. With dec != nullptr
+// (FP64-accuracy) the slice count is slice_count_rule(k, amin, bmin) of the
+// scan's spreads instead of s; the first block records it in dec->s, and no
+// slices are written when it is SLICE_S_PLAIN.
 cudaError_t launch_slice_rows(int mode, const double* A, int64_t m, int64_t k, int64_t lda, const uint64_t* rowmax,
                               int s, int64_t kp, uint16_t* slices, int32_t* E, uint32_t* err, cudaStream_t st,
-                              int64_t plane_rows = 0);
+                              int64_t plane_rows = 0, SliceDecision* dec = nullptr);
 cudaError_t launch_slice_cols(int mode, const double* B, int64_t k, int64_t n, int64_t ldb, const uint64_t* colmax,
-                              int s, int64_t kp, uint16_t* slices, int32_t* F, uint32_t* err, cudaStream_t st);
+                              int s, int64_t kp, uint16_t* slices, int32_t* F, uint32_t* err, cudaStream_t st,
+                              SliceDecision* dec = nullptr);
 cudaError_t launch_fill_uniform(double* X, int64_t rows, int64_t cols, int64_t ld, uint64_t seed, uint64_t stream_id,
                                 int scale_mode, uint64_t exp_stream_id, cudaStream_t st);
 
@@ -35,7 +101,7 @@ struct GroupedSplit {
   int64_t m, n, k, lda, ldb, kp;
   const double* A;
   const double* B;
-  int s;                  // slices (FP64-accuracy) or 3
+  int s;                  // slices (FP64-accuracy, when dec is null) or 3
   int pad;
   uint64_t* rowmax;
   uint64_t* colmax;
@@ -43,13 +109,16 @@ struct GroupedSplit {
   int32_t* F;
   uint16_t* slA;
   uint16_t* slB;
+  SliceDecision* dec;     // automatic slice count (FP64-accuracy), else null
+  uint2* colpart;         // column partial sums of the spreads (with dec)
+  uint32_t* perr;         // the problem's own error word (non-finite input), else null: the launch's
 };
 // Virtual block offsets: off[kind][p] = first block of problem p for kernel
-// kind (0 row max, 1 column max, 2 slice rows, 3 slice cols); off[kind][count]
-// = total. Arrays of count+1 int64 in device memory.
+// kind (0 row max, 1 column max, 2 slice rows, 3 slice cols, 4 column spreads);
+// off[kind][count] = total. Arrays of count+1 int64 in device memory.
 struct GroupedSplitArgs {
   const GroupedSplit* probs;
-  const int64_t* off[4];
+  const int64_t* off[5];
   const int* count_dev;
   uint32_t* err;
 };
@@ -94,8 +163,10 @@ inline int slice_fp64_mode(int s, int64_t k, int fix_shift) {
 struct SliceProblem {
   int64_t m, n, k;
   int nkb;               // ceil(k / 64)
-  int s;                 // FP64-accuracy slice count
+  int s;                 // FP64-accuracy slice count (when s_dev is null)
   int fix_shift;         // right shift of the int64 fixed-point total (FP64-accuracy)
+  const int32_t* s_dev;  // automatic slice count in device memory, else null
+  int8_t fix_tab[8];     // with s_dev: the fixed-point shift for each s <= 7
   int tiles_m, tiles_n;
   const int32_t* E;      // row scale exponents of A
   const int32_t* F;      // column scale exponents of B
@@ -118,6 +189,7 @@ struct SliceGemmArgs {
   const int* ntiles_dev;           // grouped: tile count (device)
   uint32_t* err;
   uint64_t timeout_ns;
+  int s_lo, s_hi;                  // with s_dev: only tiles of problems with s in [s_lo, s_hi] (s_hi > 0)
 };
 
 // bn: tile width (columns of C); cg: CTAs per tile (1, or 2 for a CTA pair on
@@ -141,6 +213,7 @@ struct Fp64GemmArgs {
   int64_t ldb;
   double* C;
   int64_t ldc;
+  const int32_t* only_if_plain;   // if set: run only when it holds SLICE_S_PLAIN (emulated-mode fallback)
 };
 // kind: 1 = DFMA tiles, 2 = DMMA (mma.sync m8n8k4 f64) tiles.
 cudaError_t launch_fp64_gemm(int kind, const Fp64GemmArgs& a, cudaStream_t st);

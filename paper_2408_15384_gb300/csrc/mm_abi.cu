@@ -130,23 +130,16 @@ int validate_problem(int64_t m, int64_t n, int64_t k, const double* A, int64_t l
   return MM_OK;
 }
 
-// Slice count of the FP64-accuracy mode for inner dimension k: the smallest s
-// whose measured error stays near a quarter of the bound 4k*2^-53 |A||B| on the
-// workload distributions (uniform rows/columns times a power of two).
-// Slice count for inner dimension k. Rule 0 is calibrated on rows whose
-// entries are spread like uniform samples (maximum about twice the mean
-// magnitude); rule 1 on rows of normal deviates (maximum about five times the
-// mean), whose dropped level s+2 weighs more against the componentwise bound.
-// Both keep the oracle's error at most half the bound at their thresholds.
-int slices_for_k(int64_t k, int rule) {
-  if (rule == 1) {
-    if (k >= 12288) return 5;
-    if (k >= 160) return 6;
-    return 7;
-  }
-  if (k >= 4096) return 5;
-  if (k >= 96) return 6;
-  return 7;
+// The error word of stream st: its own slot, assigned on first use (slot 0
+// once every slot is taken).
+uint32_t* err_word(mm_handle_s* h, cudaStream_t st) {
+  std::lock_guard<std::mutex> lk(h->err_mu);
+  auto it = h->err_slot.find(st);
+  if (it != h->err_slot.end()) return h->d_err + it->second;
+  int slot = 0;
+  if (h->err_next < MM_ERR_SLOTS) slot = h->err_next++;
+  h->err_slot.emplace(st, slot);
+  return h->d_err + slot;
 }
 
 // Right shift that keeps |X| = |sum_d 2^(8(s+1-d)) L_d| below 2^62, with
@@ -159,18 +152,23 @@ int fixed_shift(int s, int64_t k) {
   return std::max(0, need - 62);
 }
 
-bool encode_slices_tmap(mm_handle_s* h, CUtensorMap* tm, const void* base, int64_t k, int64_t rows, int S, int64_t kp,
-                        int box_rows, int64_t plane_rows) {
+bool encode_slices_tmap_with(EncodeTiledFn encode, CUtensorMap* tm, const void* base, int64_t k, int64_t rows, int S,
+                             int64_t kp, int box_rows, int64_t plane_rows) {
   cuuint64_t dims[3] = {static_cast<cuuint64_t>(k), static_cast<cuuint64_t>(rows), static_cast<cuuint64_t>(S)};
   cuuint64_t strides[2] = {static_cast<cuuint64_t>(kp * 2),
                            static_cast<cuuint64_t>((plane_rows > rows ? plane_rows : rows) * kp * 2)};
   cuuint32_t box[3] = {64u, static_cast<cuuint32_t>(box_rows), 1u};
   cuuint32_t estr[3] = {1u, 1u, 1u};
-  CUresult r = h->encode(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
-                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r = encode(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) logf(1, "cuTensorMapEncodeTiled failed (%d)", static_cast<int>(r));
   return r == CUDA_SUCCESS;
+}
+
+bool encode_slices_tmap(mm_handle_s* h, CUtensorMap* tm, const void* base, int64_t k, int64_t rows, int S, int64_t kp,
+                        int box_rows, int64_t plane_rows) {
+  return encode_slices_tmap_with(h->encode, tm, base, k, rows, S, kp, box_rows, plane_rows);
 }
 
 void count_launch(mm_handle_s* h, uint64_t n) { h->launches.fetch_add(n); }
@@ -192,66 +190,101 @@ ProfScope::~ProfScope() {
 }
 
 // Layout of the emulated-mode workspace of one product.
-void SplitLayout::plan(int64_t m_, int64_t n_, int64_t k_, int S_) {
-  m = m_; n = n_; k = k_; S = S_;
+void SplitLayout::plan(int64_t m_, int64_t n_, int64_t k_, int s) {
+  m = m_; n = n_; k = k_;
+  autos = (s == 0);
+  S = emu_planes(s);
   kp = static_cast<int64_t>(align_up(static_cast<size_t>(std::max<int64_t>(k, 1)), 8));
   size_t off = 0;
   off_rowmax = off; off = align_up(off + 8 * static_cast<size_t>(m), 256);
   off_colmax = off; off = align_up(off + 8 * static_cast<size_t>(n), 256);
   off_E = off; off = align_up(off + 4 * static_cast<size_t>(m), 256);
   off_F = off; off = align_up(off + 4 * static_cast<size_t>(n), 256);
+  off_dec = off; off = align_up(off + (autos ? sizeof(SliceDecision) : 0), 256);
+  off_part = off; off = align_up(off + (autos ? 8 * static_cast<size_t>(launch_absmax_parts(k)) * n : 0), 256);
   off_sa = off; off = align_up(off + 2 * static_cast<size_t>(S) * m * kp, 1024);
   off_sb = off; off = align_up(off + 2 * static_cast<size_t>(S) * n * kp, 1024);
   bytes = off;
 }
 
-// Scan + split of both operands into the workspace (3 or 4 launches + 1 memset).
+// Scan + split of both operands into the workspace (3 or 4 launches + 1 memset;
+// automatic slice count: one more memset and the column-spread launch).
 int run_split(mm_handle_s* h, int mode01, const SplitLayout& L, char* ws, const double* A, int64_t lda,
               const double* B, int64_t ldb, cudaStream_t st) {
   uint64_t* rowmax = reinterpret_cast<uint64_t*>(ws + L.off_rowmax);
   uint64_t* colmax = reinterpret_cast<uint64_t*>(ws + L.off_colmax);
+  uint32_t* err = err_word(h, st);
+  SliceDecision* dec = L.dec(ws);
   int nscan = 0;
-  cudaError_t e = launch_absmax(A, L.m, L.k, lda, B, L.n, ldb, rowmax, colmax, st, &nscan);
+  cudaError_t e = cudaSuccess;
+  if (dec) e = cudaMemsetAsync(dec, 0, sizeof(SliceDecision), st);   // no row or column seen yet
+  if (e == cudaSuccess) e = launch_absmax(A, L.m, L.k, lda, B, L.n, ldb, rowmax, colmax, st, &nscan, dec, L.part(ws));
   if (e != cudaSuccess) return cuda_status(e, "absmax");
   e = launch_slice_rows(mode01, A, L.m, L.k, lda, rowmax, L.S, L.kp, reinterpret_cast<uint16_t*>(ws + L.off_sa),
-                        reinterpret_cast<int32_t*>(ws + L.off_E), h->d_err, st);
+                        reinterpret_cast<int32_t*>(ws + L.off_E), err, st, 0, dec);
   if (e != cudaSuccess) return cuda_status(e, "slice rows");
   e = launch_slice_cols(mode01, B, L.k, L.n, ldb, colmax, L.S, L.kp, reinterpret_cast<uint16_t*>(ws + L.off_sb),
-                        reinterpret_cast<int32_t*>(ws + L.off_F), h->d_err, st);
+                        reinterpret_cast<int32_t*>(ws + L.off_F), err, st, dec);
   if (e != cudaSuccess) return cuda_status(e, "slice cols");
   count_launch(h, 2 + static_cast<uint64_t>(nscan));
   return MM_OK;
 }
 
-// The emulated product of one problem (FP64-accuracy, FP32-accuracy, or the
-// level-product diagnostic when levels != nullptr).
 int emu_slices(mm_handle_s* h, int precision, int64_t k, int s_override) {
+  (void)k;
   if (precision != MM_FP64_EMU) return 3;
   if (s_override > 0) return s_override;
-  return h->opt_slices > 0 ? h->opt_slices : slices_for_k(k, h->opt_slice_rule);
+  return h->opt_slices > 0 ? h->opt_slices : 0;
 }
 
-// The slice GEMM of rows [r0, r0 + mr) of an emulated product whose exponents
-// and slices are in the workspace ws (layout L: A planes of L.m rows, B planes
-// of L.n rows). C points at row 0 of the product's output.
-int emu_gemm_rows(mm_handle_s* h, int precision, const SplitLayout& L, char* ws, int s, int64_t r0, int64_t mr,
-                  double* C, int64_t ldc, int64_t* levels, const TileCfg& cfg_in, cudaStream_t st) {
+// The plain FP64 kernel as the fallback of an automatic-count product: it runs
+// only if the splitting kernels recorded SLICE_S_PLAIN in *s_dev.
+static int plain_fallback(mm_handle_s* h, int64_t m, int64_t n, int64_t k, const double* A, int64_t lda,
+                          const double* B, int64_t ldb, double* C, int64_t ldc, const int32_t* s_dev,
+                          cudaStream_t st) {
+  Fp64GemmArgs a{m, n, k, A, lda, B, ldb, C, ldc, s_dev};
+  cudaError_t e = launch_fp64_gemm(fp64_kind(h), a, st);
+  count_launch(h, 1);
+  return cuda_status(e, "plain fallback");
+}
+
+// Tile width, CTA grouping and kernel mode of an emulated product's slice GEMM
+// for slice count s: the configuration given (tuned), else the default for
+// this shape and count.
+struct SliceLaunch {
+  int mode, bn, cg;
+  bool operator==(const SliceLaunch& o) const { return mode == o.mode && bn == o.bn && cg == o.cg; }
+};
+static SliceLaunch slice_launch_for(mm_handle_s* h, int precision, int64_t mr, int64_t n, int64_t k, int s,
+                                    bool levels, const TileCfg& cfg_in) {
   const bool fp64 = (precision == MM_FP64_EMU);
-  const int64_t n = L.n, k = L.k;
-  // tile width and CTA pairing (256-row tiles, half of B per CTA) from the
-  // configuration: tuned, else the default for this shape and slice count
   const int pairs_avail = fp64 ? h->max_pairs_fp64 : h->max_pairs_fp32;
   const TileCfg dflt = default_cfg(h, precision, mr, n, s);
-  int cg = cfg_in.cg ? cfg_in.cg : dflt.cg;
-  int bn = cfg_in.bn ? cfg_in.bn : dflt.bn;
-  if (pairs_avail <= 0) cg = 1;
-  if (!slice_gemm_tile_ok(fp64 ? SLICE_FP64EMU : SLICE_FP32EMU, bn, cg)) {
-    bn = dflt.bn;
-    cg = dflt.cg;
+  SliceLaunch r;
+  r.cg = cfg_in.cg ? cfg_in.cg : dflt.cg;
+  r.bn = cfg_in.bn ? cfg_in.bn : dflt.bn;
+  if (pairs_avail <= 0) r.cg = 1;
+  if (!slice_gemm_tile_ok(fp64 ? SLICE_FP64EMU : SLICE_FP32EMU, r.bn, r.cg)) {
+    r.bn = dflt.bn;
+    r.cg = dflt.cg;
   }
+  r.mode = levels ? SLICE_LEVELS : (!fp64 ? SLICE_FP32EMU : slice_fp64_mode(s, k, fixed_shift(s, k)));
+  return r;
+}
+
+// One slice GEMM launch over rows [r0, r0 + mr): slice count s, or with s = 0
+// the automatic count from the workspace's decision record, restricted to
+// problems whose count lies in [s_lo, s_hi] (the launch's tiles are skipped
+// otherwise).
+static int slice_gemm_launch(mm_handle_s* h, const SplitLayout& L, char* ws, int s, int s_lo, int s_hi,
+                             const SliceLaunch& sl, int64_t r0, int64_t mr, double* C, int64_t ldc, int64_t* levels,
+                             cudaStream_t st) {
+  const bool fp64 = sl.mode != SLICE_FP32EMU;
+  const int64_t n = L.n, k = L.k;
+  const int pairs_avail = fp64 ? h->max_pairs_fp64 : h->max_pairs_fp32;
   CUtensorMap tmA, tmB;
   if (!encode_slices_tmap(h, &tmA, ws + L.off_sa + 2 * static_cast<size_t>(r0) * L.kp, k, mr, L.S, L.kp, 128, L.m) ||
-      !encode_slices_tmap(h, &tmB, ws + L.off_sb, k, n, L.S, L.kp, bn / cg))
+      !encode_slices_tmap(h, &tmB, ws + L.off_sb, k, n, L.S, L.kp, sl.bn / sl.cg))
     return MM_ERR_CUDA;
   SliceGemmArgs a;
   memset(&a, 0, sizeof(a));
@@ -259,28 +292,55 @@ int emu_gemm_rows(mm_handle_s* h, int precision, const SplitLayout& L, char* ws,
   P.m = mr; P.n = n; P.k = k;
   P.nkb = static_cast<int>((k + 63) / 64);
   P.s = s;
-  P.fix_shift = fp64 ? fixed_shift(s, k) : 0;
-  P.tiles_m = static_cast<int>((mr + 128 * cg - 1) / (128 * cg));
-  P.tiles_n = static_cast<int>((n + bn - 1) / bn);
+  P.fix_shift = (fp64 && s > 0) ? fixed_shift(s, k) : 0;
+  if (s == 0) {
+    P.s_dev = &L.dec(ws)->s;
+    for (int c = SLICE_S_MIN; c <= SLICE_S_MAX; ++c) P.fix_tab[c] = static_cast<int8_t>(fixed_shift(c, k));
+    a.s_lo = s_lo;
+    a.s_hi = s_hi;
+  }
+  P.tiles_m = static_cast<int>((mr + 128 * sl.cg - 1) / (128 * sl.cg));
+  P.tiles_n = static_cast<int>((n + sl.bn - 1) / sl.bn);
   P.E = reinterpret_cast<const int32_t*>(ws + L.off_E) + r0;
   P.F = reinterpret_cast<const int32_t*>(ws + L.off_F);
   P.C = C + r0 * ldc;
   P.ldc = ldc;
   P.levels = levels;
-  a.err = h->d_err;
+  a.err = err_word(h, st);
   a.timeout_ns = static_cast<uint64_t>(h->opt_timeout_ms) * 1000000ull;
   const int ntiles = P.tiles_m * P.tiles_n;
-  const int grid = (cg == 2) ? 2 * std::min(ntiles, pairs_avail) : std::min(ntiles, h->sm_count);
-  const int mode = levels ? SLICE_LEVELS
-                          : (!fp64 ? SLICE_FP32EMU
-                                   : slice_fp64_mode(s, k, P.fix_shift));
+  const int grid = (sl.cg == 2) ? 2 * std::min(ntiles, pairs_avail) : std::min(ntiles, h->sm_count);
   cudaError_t e;
   {
     ProfScope ps(h, MM_KERNEL_SLICE_GEMM, st);
-    e = launch_slice_gemm(mode, bn, cg, &tmA, &tmB, a, grid, st);
+    e = launch_slice_gemm(sl.mode, sl.bn, sl.cg, &tmA, &tmB, a, grid, st);
   }
   count_launch(h, 1);
   return cuda_status(e, "slice gemm");
+}
+
+// The slice GEMM of rows [r0, r0 + mr) of an emulated product whose exponents
+// and slices are in the workspace ws (layout L: A planes of L.m rows, B planes
+// of L.n rows). C points at row 0 of the product's output. s = 0 (automatic
+// count): one launch per run of candidate counts sharing a kernel and tiling,
+// from the smallest count the rule can give for this k up to 7; each launch
+// returns at once unless the recorded count is in its run.
+int emu_gemm_rows(mm_handle_s* h, int precision, const SplitLayout& L, char* ws, int s, int64_t r0, int64_t mr,
+                  double* C, int64_t ldc, int64_t* levels, const TileCfg& cfg_in, cudaStream_t st) {
+  if (s > 0 || precision != MM_FP64_EMU) {
+    const int sf = s > 0 ? s : 3;
+    const SliceLaunch sl = slice_launch_for(h, precision, mr, L.n, L.k, sf, levels != nullptr, cfg_in);
+    return slice_gemm_launch(h, L, ws, sf, 0, 0, sl, r0, mr, C, ldc, levels, st);
+  }
+  int rc = MM_OK;
+  for (int lo = std::max(SLICE_S_MIN, slice_count_floor(L.k)); lo <= SLICE_S_MAX && rc == MM_OK;) {
+    const SliceLaunch sl = slice_launch_for(h, precision, mr, L.n, L.k, lo, false, cfg_in);
+    int hi = lo;
+    while (hi < SLICE_S_MAX && slice_launch_for(h, precision, mr, L.n, L.k, hi + 1, false, cfg_in) == sl) ++hi;
+    rc = slice_gemm_launch(h, L, ws, 0, lo, hi, sl, r0, mr, C, ldc, nullptr, st);
+    lo = hi + 1;
+  }
+  return rc;
 }
 
 // The emulated product of one problem (FP64-accuracy, FP32-accuracy, or the
@@ -301,6 +361,7 @@ int run_emulated(mm_handle_s* h, int precision, int64_t m, int64_t n, int64_t k,
     rc = run_split(h, fp64 ? 0 : 1, L, ws, A, lda, B, ldb, st);
   }
   if (rc == MM_OK) rc = emu_gemm_rows(h, precision, L, ws, s, 0, m, C, ldc, levels, cfg_in, st);
+  if (rc == MM_OK && L.autos) rc = plain_fallback(h, m, n, k, A, lda, B, ldb, C, ldc, &L.dec(ws)->s, st);
   ws_free(h, wsv, L.bytes, st);
   return rc;
 }
@@ -366,11 +427,12 @@ int gemm_device(mm_handle_s* h, int64_t m, int64_t n, int64_t k, const double* A
   return gemm_with_cfg(h, m, n, k, A, lda, B, ldb, C, ldc, precision, cfg, st);
 }
 
-int read_and_clear_err(mm_handle_s* h) {
+int read_and_clear_err(mm_handle_s* h, cudaStream_t st) {
+  uint32_t* w = err_word(h, st);
   uint32_t v = 0;
-  cudaError_t e = cudaMemcpy(&v, h->d_err, sizeof(v), cudaMemcpyDeviceToHost);
+  cudaError_t e = cudaMemcpy(&v, w, sizeof(v), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_status(e, "read error word");
-  if (v) cudaMemset(h->d_err, 0, sizeof(uint32_t));
+  if (v) cudaMemset(w, 0, sizeof(uint32_t));
   if (v & MM_DEV_ERR_TIMEOUT_H) return MM_ERR_TIMEOUT;
   if (v & MM_DEV_ERR_NONFINITE_H) return MM_ERR_NONFINITE;
   return MM_OK;
@@ -425,7 +487,7 @@ int mm_create(mm_handle* out, int device, size_t mem_budget_bytes) {
   }
   uint64_t thr = h->budget;
   cudaMemPoolSetAttribute(h->pool, cudaMemPoolAttrReleaseThreshold, &thr);
-  if (cudaMalloc(&h->d_err, 64) != cudaSuccess || cudaMemset(h->d_err, 0, 64) != cudaSuccess) {
+  if (cudaMalloc(&h->d_err, 4 * MM_ERR_SLOTS) != cudaSuccess || cudaMemset(h->d_err, 0, 4 * MM_ERR_SLOTS) != cudaSuccess) {
     cudaMemPoolDestroy(h->pool);
     delete h;
     return MM_ERR_CUDA;
@@ -471,8 +533,9 @@ namespace {
 // Emulated product from host buffers in two row panels, copies overlapping
 // the kernels: a copy stream brings B and then A's panels over while the
 // caller's stream slices B and runs each panel as soon as its rows arrive;
-// each panel's C goes back while the next one computes. Same kernels and
-// slices as the one-panel path, so the same bits.
+// each panel's C goes back while the next one computes. With the automatic
+// slice count the operands are scanned as they arrive and sliced once all of
+// them are in. Same kernels and slices as the one-panel path, so the same bits.
 int gemm_host_pipelined(mm_handle_s* h, int64_t m, int64_t n, int64_t k, const double* A, int64_t lda,
                         const double* B, int64_t ldb, double* C, int64_t ldc, int precision, cudaStream_t st,
                         double* dA, double* dB, double* dC) {
@@ -504,15 +567,40 @@ int gemm_host_pipelined(mm_handle_s* h, int64_t m, int64_t n, int64_t k, const d
     if (mr > 0) e = cudaMemcpy2DAsync(dA + r0 * k, 8 * k, A + r0 * lda, 8 * lda, 8 * k, mr, cudaMemcpyHostToDevice, cs);
     if (e == cudaSuccess) e = cudaEventRecord(ev[2 + p], cs);
   }
-  // B's exponents and slices as soon as B is in
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev[1], 0);
+  uint32_t* err = err_word(h, st);
+  SliceDecision* dec = L.dec(ws);
+  uint64_t* const no_rows = nullptr;
+  if (dec) {
+    // automatic slice count: every row and column is scanned (as its data
+    // arrives) before anything is sliced, since the count depends on all of them
+    if (e == cudaSuccess) e = cudaMemsetAsync(dec, 0, sizeof(SliceDecision), st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev[1], 0);
+    if (e == cudaSuccess) {
+      ProfScope ps(h, MM_KERNEL_SPLIT, st);
+      int nl = 0;
+      e = launch_absmax(nullptr, 0, k, 0, dB, n, n, no_rows, colmax, st, &nl, dec, L.part(ws));
+      count_launch(h, static_cast<uint64_t>(nl));
+    }
+    for (int p = 0; p < 2 && e == cudaSuccess; ++p) {
+      const int64_t r0 = rows[p], mr = rows[p + 1] - rows[p];
+      e = cudaStreamWaitEvent(st, ev[2 + p], 0);
+      if (e == cudaSuccess && mr > 0) {
+        ProfScope ps(h, MM_KERNEL_SPLIT, st);
+        int nl = 0;
+        e = launch_absmax(dA + r0 * k, mr, k, k, nullptr, 0, 0, rowmax + r0, nullptr, st, &nl, dec, nullptr);
+        count_launch(h, static_cast<uint64_t>(nl));
+      }
+    }
+  } else if (e == cudaSuccess) {
+    e = cudaStreamWaitEvent(st, ev[1], 0);   // B's exponents and slices as soon as B is in
+  }
   if (e == cudaSuccess) {
     ProfScope ps(h, MM_KERNEL_SPLIT, st);
-    e = launch_absmax(nullptr, 0, k, 0, dB, n, n, nullptr, colmax, st);
+    if (!dec) e = launch_absmax(nullptr, 0, k, 0, dB, n, n, nullptr, colmax, st);
     if (e == cudaSuccess)
       e = launch_slice_cols(fp64 ? 0 : 1, dB, k, n, n, colmax, L.S, L.kp, reinterpret_cast<uint16_t*>(ws + L.off_sb),
-                            reinterpret_cast<int32_t*>(ws + L.off_F), h->d_err, st);
-    count_launch(h, 2);
+                            reinterpret_cast<int32_t*>(ws + L.off_F), err, st, dec);
+    count_launch(h, dec ? 1 : 2);
   }
   // each panel: its rows' slices, its slice GEMM, then its C back
   for (int p = 0; p < 2 && e == cudaSuccess && rc == MM_OK; ++p) {
@@ -521,13 +609,15 @@ int gemm_host_pipelined(mm_handle_s* h, int64_t m, int64_t n, int64_t k, const d
     if (e == cudaSuccess && mr > 0) {
       {
         ProfScope ps(h, MM_KERNEL_SPLIT, st);
-        e = launch_absmax(dA + r0 * k, mr, k, k, nullptr, 0, 0, rowmax + r0, nullptr, st);
+        if (!dec) e = launch_absmax(dA + r0 * k, mr, k, k, nullptr, 0, 0, rowmax + r0, nullptr, st);
         if (e == cudaSuccess)
           e = launch_slice_rows(fp64 ? 0 : 1, dA + r0 * k, mr, k, k, rowmax + r0, L.S, L.kp, sa + r0 * L.kp, E + r0,
-                                h->d_err, st, m);
-        count_launch(h, 2);
+                                err, st, m, dec);
+        count_launch(h, dec ? 1 : 2);
       }
       if (e == cudaSuccess) rc = emu_gemm_rows(h, precision, L, ws, s, r0, mr, dC, n, nullptr, TileCfg(), st);
+      if (e == cudaSuccess && rc == MM_OK && dec)
+        rc = plain_fallback(h, mr, n, k, dA + r0 * k, k, dB, n, dC + r0 * n, n, &dec->s, st);
     }
     if (e == cudaSuccess && rc == MM_OK) e = cudaEventRecord(ev[4 + p], st);
     if (e == cudaSuccess && rc == MM_OK) e = cudaStreamWaitEvent(cs, ev[4 + p], 0);
@@ -593,7 +683,7 @@ int mm_gemm_host(mm_handle h, int64_t m, int64_t n, int64_t k, const double* A, 
   }
   e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_status(e, "synchronize");
-  return read_and_clear_err(h);
+  return read_and_clear_err(h, st);
 }
 
 int mm_sync(mm_handle h, void* stream) {
@@ -601,7 +691,7 @@ int mm_sync(mm_handle h, void* stream) {
   DeviceGuard g(h->device);
   cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_status(e, "synchronize");
-  return read_and_clear_err(h);
+  return read_and_clear_err(h, static_cast<cudaStream_t>(stream));
 }
 
 // ------------------------------------------------------------ configuration
@@ -634,10 +724,6 @@ int mm_set_option(mm_handle h, int option, int64_t value) {
       if (value < 0 || value > 2) return MM_ERR_INVALID_ARG;
       h->opt_cta_pair = static_cast<int>(value);
       return MM_OK;
-    case MM_OPT_SLICE_RULE:
-      if (value != 0 && value != 1) return MM_ERR_INVALID_ARG;
-      h->opt_slice_rule = static_cast<int>(value);
-      return MM_OK;
     case MM_OPT_TILE_N:
       if (value != 0 && !slice_gemm_tile_ok(SLICE_FP64EMU, static_cast<int>(value), 1)) return MM_ERR_INVALID_ARG;
       h->opt_tile_n = static_cast<int>(value);
@@ -658,13 +744,14 @@ int mm_get_option(mm_handle h, int option, int64_t* value) {
     case MM_OPT_PROFILE: *value = h->opt_profile; return MM_OK;
     case MM_OPT_CTA_PAIR: *value = h->opt_cta_pair; return MM_OK;
     case MM_OPT_TILE_N: *value = h->opt_tile_n; return MM_OK;
-    case MM_OPT_SLICE_RULE: *value = h->opt_slice_rule; return MM_OK;
     default: return MM_ERR_INVALID_ARG;
   }
 }
 
-int mm_slices_for_k(int64_t k) { return slices_for_k(k, 0); }
-int mm_slices_for_k_rule(int64_t k, int rule) { return (rule == 0 || rule == 1) ? slices_for_k(k, rule) : -1; }
+int mm_slice_count_rule(int64_t k, float alpha_min, float beta_min) {
+  if (k < 1) return -1;
+  return slice_count_rule(k, alpha_min, beta_min);
+}
 
 // ------------------------------------------------------------- diagnostics
 int mm_fill_uniform(double* X, int64_t rows, int64_t cols, int64_t ld, uint64_t seed, uint64_t stream_id,
@@ -701,7 +788,7 @@ int mm_debug_slices(mm_handle h, int which, int mode, int s, int64_t rows, int64
     e = launch_absmax(X, nvec, klen, ldx, nullptr, 0, 0, reinterpret_cast<uint64_t*>(ws + L.off_rowmax), nullptr, st);
     if (e == cudaSuccess)
       e = launch_slice_rows(mode01, X, nvec, klen, ldx, reinterpret_cast<uint64_t*>(ws + L.off_rowmax), S, L.kp,
-                            reinterpret_cast<uint16_t*>(ws + L.off_sa), exps, h->d_err, st);
+                            reinterpret_cast<uint16_t*>(ws + L.off_sa), exps, err_word(h, st), st);
     if (e == cudaSuccess)
       e = cudaMemcpy2DAsync(slices, 2 * klen, ws + L.off_sa, 2 * L.kp, 2 * klen, static_cast<size_t>(S) * nvec,
                             cudaMemcpyDeviceToDevice, st);
@@ -709,7 +796,7 @@ int mm_debug_slices(mm_handle h, int which, int mode, int s, int64_t rows, int64
     e = launch_absmax(nullptr, 0, klen, 0, X, nvec, ldx, nullptr, reinterpret_cast<uint64_t*>(ws + L.off_colmax), st);
     if (e == cudaSuccess)
       e = launch_slice_cols(mode01, X, klen, nvec, ldx, reinterpret_cast<uint64_t*>(ws + L.off_colmax), S, L.kp,
-                            reinterpret_cast<uint16_t*>(ws + L.off_sb), exps, h->d_err, st);
+                            reinterpret_cast<uint16_t*>(ws + L.off_sb), exps, err_word(h, st), st);
     if (e == cudaSuccess)
       e = cudaMemcpy2DAsync(slices, 2 * klen, ws + L.off_sb, 2 * L.kp, 2 * klen, static_cast<size_t>(S) * nvec,
                             cudaMemcpyDeviceToDevice, st);
@@ -719,7 +806,34 @@ int mm_debug_slices(mm_handle h, int which, int mode, int s, int64_t rows, int64
   if (e != cudaSuccess) return cuda_status(e, "debug slices");
   e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_status(e, "synchronize");
-  return read_and_clear_err(h);
+  return read_and_clear_err(h, st);
+}
+
+int mm_debug_slice_count(mm_handle h, int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
+                         int64_t ldb, int* s, float* alpha_min, float* beta_min, void* stream) {
+  if (!h || !s || !alpha_min || !beta_min || m <= 0 || n <= 0 || k <= 0 || !A || !B || lda < k || ldb < n)
+    return MM_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  SplitLayout L;
+  L.plan(m, n, k, 0);
+  void* wsv = nullptr;
+  int rc = ws_alloc(h, L.bytes, st, &wsv);
+  if (rc != MM_OK) return rc;
+  char* ws = static_cast<char*>(wsv);
+  rc = run_split(h, 0, L, ws, A, lda, B, ldb, st);
+  SliceDecision d;
+  memset(&d, 0, sizeof(d));
+  cudaError_t e = cudaSuccess;
+  if (rc == MM_OK) e = cudaMemcpyAsync(&d, L.dec(ws), sizeof(d), cudaMemcpyDeviceToHost, st);
+  ws_free(h, wsv, L.bytes, st);
+  if (rc != MM_OK) return rc;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_status(e, "debug slice count");
+  *s = d.s;
+  *alpha_min = spread_from_room(d.amin_room);
+  *beta_min = spread_from_room(d.bmin_room);
+  return read_and_clear_err(h, st);
 }
 
 int mm_debug_level_products(mm_handle h, int64_t m, int64_t n, int64_t k, const double* A, int64_t lda,
@@ -737,7 +851,7 @@ int mm_debug_level_products(mm_handle h, int64_t m, int64_t n, int64_t k, const 
   if (rc != MM_OK) return rc;
   e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_status(e, "synchronize");
-  return read_and_clear_err(h);
+  return read_and_clear_err(h, st);
 }
 
 int mm_debug_wait_timeout(mm_handle h, int64_t timeout_ms, void* stream) {
@@ -746,7 +860,7 @@ int mm_debug_wait_timeout(mm_handle h, int64_t timeout_ms, void* stream) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   int* gave_up = nullptr;
   if (cudaMalloc(&gave_up, sizeof(int)) != cudaSuccess) return MM_ERR_CUDA;
-  int rc = cuda_status(launch_wait_probe(h->d_err, static_cast<uint64_t>(timeout_ms) * 1000000ull, gave_up, st),
+  int rc = cuda_status(launch_wait_probe(err_word(h, st), static_cast<uint64_t>(timeout_ms) * 1000000ull, gave_up, st),
                        "wait probe");
   count_launch(h, 1);
   int host = 0;
@@ -754,7 +868,7 @@ int mm_debug_wait_timeout(mm_handle h, int64_t timeout_ms, void* stream) {
   if (rc == MM_OK && cudaMemcpy(&host, gave_up, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) rc = MM_ERR_CUDA;
   cudaFree(gave_up);
   if (rc != MM_OK) return rc;
-  rc = read_and_clear_err(h);
+  rc = read_and_clear_err(h, st);
   if (rc == MM_OK && host) rc = MM_ERR_CUDA;   // gave up without raising the error bit: inconsistent
   return rc;
 }

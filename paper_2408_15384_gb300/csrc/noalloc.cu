@@ -73,17 +73,6 @@ void setup_device(NoAllocDevice& d) {
   d.status = MM_OK;
 }
 
-bool encode(EncodeTiledFn fn, CUtensorMap* tm, const void* base, int64_t k, int64_t rows, int S, int64_t kp,
-            int box_rows) {
-  cuuint64_t dims[3] = {static_cast<cuuint64_t>(k), static_cast<cuuint64_t>(rows), static_cast<cuuint64_t>(S)};
-  cuuint64_t strides[2] = {static_cast<cuuint64_t>(kp * 2), static_cast<cuuint64_t>(rows * kp * 2)};
-  cuuint32_t box[3] = {64u, static_cast<cuuint32_t>(box_rows), 1u};
-  cuuint32_t estr[3] = {1u, 1u, 1u};
-  return fn(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
 }  // namespace
 
 using namespace mmhost;
@@ -108,7 +97,7 @@ int mm_gemm_emu_static(int64_t m, int64_t n, int64_t k, const double* A, int64_t
     return cuda_status(launch_fp64_gemm(2, a, st), "fp64 gemm");
   }
   const bool fp64 = precision == MM_FP64_EMU;
-  const int s = fp64 ? slices_for_k(k, 0) : 3;
+  const int s = fp64 ? 0 : 3;   // FP64-accuracy: the automatic slice count, as mm_gemm's default
   SplitLayout L;
   L.plan(m, n, k, s);
   const size_t status_bytes = 256;
@@ -116,30 +105,38 @@ int mm_gemm_emu_static(int64_t m, int64_t n, int64_t k, const double* A, int64_t
 
   uint32_t* err = reinterpret_cast<uint32_t*>(d.scratch);
   char* ws = reinterpret_cast<char*>(d.scratch + status_bytes);
+  SliceDecision* dec = L.dec(ws);
   cudaError_t e = cudaMemsetAsync(err, 0, sizeof(uint32_t), st);
+  if (e == cudaSuccess && dec) e = cudaMemsetAsync(dec, 0, sizeof(SliceDecision), st);
   if (e != cudaSuccess) return cuda_status(e, "clear status");
   uint64_t* rowmax = reinterpret_cast<uint64_t*>(ws + L.off_rowmax);
   uint64_t* colmax = reinterpret_cast<uint64_t*>(ws + L.off_colmax);   // zeroed by launch_absmax
-  e = launch_absmax(A, m, k, lda, B, n, ldb, rowmax, colmax, st);
+  e = launch_absmax(A, m, k, lda, B, n, ldb, rowmax, colmax, st, nullptr, dec, L.part(ws));
   if (e == cudaSuccess)
-    e = launch_slice_rows(fp64 ? 0 : 1, A, m, k, lda, rowmax, s, L.kp, reinterpret_cast<uint16_t*>(ws + L.off_sa),
-                          reinterpret_cast<int32_t*>(ws + L.off_E), err, st);
+    e = launch_slice_rows(fp64 ? 0 : 1, A, m, k, lda, rowmax, L.S, L.kp, reinterpret_cast<uint16_t*>(ws + L.off_sa),
+                          reinterpret_cast<int32_t*>(ws + L.off_E), err, st, 0, dec);
   if (e == cudaSuccess)
-    e = launch_slice_cols(fp64 ? 0 : 1, B, k, n, ldb, colmax, s, L.kp, reinterpret_cast<uint16_t*>(ws + L.off_sb),
-                          reinterpret_cast<int32_t*>(ws + L.off_F), err, st);
+    e = launch_slice_cols(fp64 ? 0 : 1, B, k, n, ldb, colmax, L.S, L.kp, reinterpret_cast<uint16_t*>(ws + L.off_sb),
+                          reinterpret_cast<int32_t*>(ws + L.off_F), err, st, dec);
   if (e != cudaSuccess) return cuda_status(e, "split");
-  const int bn = 128;   // 128-wide tiles in both modes
+  const int bn = 128;   // 128-wide tiles in both modes: one kernel takes every slice count
   CUtensorMap tmA, tmB;
-  if (!encode(d.encode, &tmA, ws + L.off_sa, k, m, s, L.kp, 128) ||
-      !encode(d.encode, &tmB, ws + L.off_sb, k, n, s, L.kp, bn))
+  if (!encode_slices_tmap_with(d.encode, &tmA, ws + L.off_sa, k, m, L.S, L.kp, 128) ||
+      !encode_slices_tmap_with(d.encode, &tmB, ws + L.off_sb, k, n, L.S, L.kp, bn))
     return MM_ERR_CUDA;
   SliceGemmArgs a;
   memset(&a, 0, sizeof(a));
   SliceProblem& P = a.single;
   P.m = m; P.n = n; P.k = k;
   P.nkb = static_cast<int>((k + 63) / 64);
-  P.s = s;
-  P.fix_shift = fp64 ? fixed_shift(s, k) : 0;
+  P.s = L.S;
+  P.fix_shift = fp64 ? fixed_shift(L.S, k) : 0;
+  if (dec) {
+    P.s_dev = &dec->s;
+    for (int c = SLICE_S_MIN; c <= SLICE_S_MAX; ++c) P.fix_tab[c] = static_cast<int8_t>(fixed_shift(c, k));
+    a.s_lo = SLICE_S_MIN;
+    a.s_hi = SLICE_S_MAX;
+  }
   P.tiles_m = static_cast<int>((m + 127) / 128);
   P.tiles_n = static_cast<int>((n + bn - 1) / bn);
   P.E = reinterpret_cast<const int32_t*>(ws + L.off_E);
@@ -149,7 +146,11 @@ int mm_gemm_emu_static(int64_t m, int64_t n, int64_t k, const double* A, int64_t
   a.err = err;
   a.timeout_ns = 2000ull * 1000000ull;
   const int grid = std::min(P.tiles_m * P.tiles_n, d.sm_count);
-  const int mode = !fp64 ? SLICE_FP32EMU : slice_fp64_mode(s, k, P.fix_shift);
-  e = launch_slice_gemm(mode, bn, 1, &tmA, &tmB, a, grid, st);
+  e = launch_slice_gemm(fp64 ? SLICE_FP64EMU : SLICE_FP32EMU, bn, 1, &tmA, &tmB, a, grid, st);
+  if (e == cudaSuccess && dec) {
+    // the plain FP64 kernel where the count came out as SLICE_S_PLAIN (no scratch)
+    Fp64GemmArgs f{m, n, k, A, lda, B, ldb, C, ldc, &dec->s};
+    e = launch_fp64_gemm(2, f, st);
+  }
   return cuda_status(e, "slice gemm");
 }

@@ -33,6 +33,8 @@ struct ServeReq {
   int status = MM_PENDING;
   size_t charge = 0;
   double t_submit = 0, t_admit = 0, t_launch = 0, t_done = 0;
+  int stream = -1;
+  double t_gpu_start = 0, t_gpu_end = 0;
 };
 
 struct ServeEngine;
@@ -45,7 +47,26 @@ struct Batch {
   void* pinned = nullptr;
   size_t pinned_cap = 0;
   int status = MM_OK;
+  GroupedErrReport rep;     // the launch's error words, copied back into `pinned`
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;   // device time at the batch's start and end
 };
+
+// The status of request i of a finished batch: the batch's launch status, else
+// the device's report: a timed-out wait fails every request of the launch,
+// non-finite input only the request that had it.
+static int request_status(const Batch* b, std::vector<int>& out) {
+  out.assign(b->tickets.size(), b->status);
+  if (b->status != MM_OK || b->rep.bytes == 0) return b->status;
+  const uint32_t* hdr = static_cast<const uint32_t*>(b->pinned);
+  const uint32_t* perr = reinterpret_cast<const uint32_t*>(static_cast<const char*>(b->pinned) + b->rep.off_perr);
+  const bool timeout = (hdr[3] & MM_DEV_ERR_TIMEOUT_H) != 0;
+  for (size_t i = 0; i < b->rep.main_idx.size(); ++i) {
+    const int r = b->rep.main_idx[i];
+    if (timeout || (perr[i] & MM_DEV_ERR_TIMEOUT_H)) out[r] = MM_ERR_TIMEOUT;
+    else if (perr[i] & MM_DEV_ERR_NONFINITE_H) out[r] = MM_ERR_NONFINITE;
+  }
+  return MM_OK;
+}
 
 struct ServeEngine {
   mm_handle_s* h = nullptr;
@@ -64,15 +85,44 @@ struct ServeEngine {
   std::vector<cudaStream_t> streams;
   std::vector<int> load;
   std::vector<std::pair<void*, size_t>> pinned_pool;
+  cudaEvent_t ref = nullptr;              // device-clock origin of the batches' GPU times
+  std::vector<cudaEvent_t> event_pool;
 };
+
+static cudaEvent_t take_event(ServeEngine& e) {
+  if (!e.event_pool.empty()) {
+    cudaEvent_t ev = e.event_pool.back();
+    e.event_pool.pop_back();
+    return ev;
+  }
+  cudaEvent_t ev = nullptr;
+  if (cudaEventCreate(&ev) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return ev;
+}
+
+// Microseconds of device time from the engine's reference event to ev (0 if
+// either is missing).
+static double gpu_us(const ServeEngine& e, cudaEvent_t ev) {
+  float ms = 0.f;
+  if (!e.ref || !ev || cudaEventElapsedTime(&ms, e.ref, ev) != cudaSuccess) {
+    cudaGetLastError();
+    return 0.0;
+  }
+  return 1000.0 * static_cast<double>(ms);
+}
 
 static size_t request_charge(mm_handle_s* h, const mm_request& r) {
   const mm_problem& p = r.prob;
   size_t bytes = 8 * static_cast<size_t>(p.m * p.k + p.k * p.n + p.m * p.n);
   if (r.precision != MM_FP64 && p.k > 0) {
-    const int s = (r.precision == MM_FP64_EMU) ? (h->opt_slices > 0 ? h->opt_slices : slices_for_k(p.k, h->opt_slice_rule)) : 3;
+    // slice planes (seven for the automatic count), scan and spread records
+    const int s = (r.precision == MM_FP64_EMU) ? emu_planes(h->opt_slices) : 3;
     const size_t kp = align_up(static_cast<size_t>(p.k), 8);
-    bytes += 2 * static_cast<size_t>(s) * (p.m + p.n) * kp + 16 * static_cast<size_t>(p.m + p.n) + 8192;
+    bytes += 2 * static_cast<size_t>(s) * (p.m + p.n) * kp + 16 * static_cast<size_t>(p.m + p.n) +
+             8 * static_cast<size_t>((p.k + 255) / 256) * p.n + 8192;
   }
   return bytes;
 }
@@ -90,12 +140,20 @@ static void CUDART_CB batch_done(void* arg) {
 
 static void retire(ServeEngine& e, Batch* b) {
   const double t = now_us(e.h);
-  for (uint64_t tk : b->tickets) {
-    auto it = e.reqs.find(tk);
+  std::vector<int> status;
+  request_status(b, status);
+  const double g0 = gpu_us(e, b->ev0), g1 = gpu_us(e, b->ev1);
+  for (size_t i = 0; i < b->tickets.size(); ++i) {
+    auto it = e.reqs.find(b->tickets[i]);
     if (it == e.reqs.end()) continue;
-    it->second.status = b->status;
+    it->second.status = status[i];
     it->second.t_done = t;
+    it->second.stream = b->stream;
+    it->second.t_gpu_start = g0;
+    it->second.t_gpu_end = g1;
   }
+  if (b->ev0) e.event_pool.push_back(b->ev0);
+  if (b->ev1) e.event_pool.push_back(b->ev1);
   e.charged -= b->charge;
   e.unfinished -= b->tickets.size();
   e.load[b->stream]--;
@@ -150,6 +208,8 @@ static void engine_loop(ServeEngine* ep) {
       b->tickets = take;
       b->charge = add;
       b->stream = si;
+      b->ev0 = take_event(e);
+      b->ev1 = take_event(e);
       // pinned staging for the batch's descriptor blob
       size_t host_bytes = 0;
       const TileCfg cfg = grouped_cfg(h, static_cast<int>(probs.size()), probs.data(), prec);
@@ -174,8 +234,11 @@ static void engine_loop(ServeEngine* ep) {
       }
       const double tl = now_us(h);
       cudaStream_t st = e.streams[si];
+      if (rc == MM_OK && b->ev0) cudaEventRecord(b->ev0, st);
       if (rc == MM_OK)
-        rc = grouped_direct(h, static_cast<int>(probs.size()), probs.data(), prec, cfg, b->pinned, b->pinned_cap, st);
+        rc = grouped_direct(h, static_cast<int>(probs.size()), probs.data(), prec, cfg, b->pinned, b->pinned_cap, st,
+                            &b->rep);
+      if (rc == MM_OK && b->ev1) cudaEventRecord(b->ev1, st);
       b->status = rc;
       if (rc != MM_OK || cudaLaunchHostFunc(st, batch_done, b) != cudaSuccess) {
         cudaGetLastError();
@@ -239,6 +302,11 @@ static ServeEngine* engine(mm_handle_s* h) {
       else cudaGetLastError();
     }
   }
+  if (cudaEventCreate(&e->ref) == cudaSuccess && cudaEventRecord(e->ref, e->streams[0]) == cudaSuccess) {
+    cudaEventSynchronize(e->ref);
+  } else {
+    cudaGetLastError();
+  }
   e->th = std::thread(engine_loop, e);
   h->serve = e;
   return e;
@@ -272,6 +340,8 @@ void serve_shutdown(mm_handle_s* h) {
     cudaStreamDestroy(s);
   }
   for (auto& p : e->pinned_pool) cudaFreeHost(p.first);
+  for (cudaEvent_t ev : e->event_pool) cudaEventDestroy(ev);
+  if (e->ref) cudaEventDestroy(e->ref);
   delete e;
 }
 
@@ -326,6 +396,9 @@ int mm_serve_poll(mm_handle h, uint64_t ticket, mm_req_status* st) {
     st->t_admit_us = q.t_admit;
     st->t_launch_us = q.t_launch;
     st->t_done_us = q.t_done;
+    st->stream = q.stream;
+    st->t_gpu_start_us = q.t_gpu_start;
+    st->t_gpu_end_us = q.t_gpu_end;
   }
   const int rc = q.status;
   e->reqs.erase(it);

@@ -183,7 +183,23 @@ struct TileJob {
   const CUtensorMap* ta;
   const CUtensorMap* tb;
   int tm, tn;
+  int s, fix;    // the problem's slice count and fixed-point shift
+  bool skip;     // the problem's slice count is outside this launch's range
 };
+
+// A problem's slice count: its automatic count from device memory (written by
+// the splitting kernels before this launch), else the host's.
+__device__ __forceinline__ void resolve_slices(const SliceGemmArgs& a, const SliceProblem& P, TileJob& j) {
+  if (P.s_dev != nullptr) {
+    j.s = *P.s_dev;
+    j.skip = j.s < a.s_lo || j.s > a.s_hi || j.s > SLICE_S_MAX;
+    j.fix = j.skip ? 0 : P.fix_tab[j.s & 7];
+  } else {
+    j.s = P.s;
+    j.fix = P.fix_shift;
+    j.skip = false;
+  }
+}
 
 __device__ __forceinline__ TileJob get_job(const SliceGemmArgs& a, const CUtensorMap* pa, const CUtensorMap* pb,
                                            int t) {
@@ -201,6 +217,7 @@ __device__ __forceinline__ TileJob get_job(const SliceGemmArgs& a, const CUtenso
     j.P = &a.single;
     j.ta = pa;
     j.tb = pb;
+    resolve_slices(a, P, j);
   } else {
     const TileRef r = a.tiles[t];
     j.P = a.probs + r.prob;
@@ -208,6 +225,7 @@ __device__ __forceinline__ TileJob get_job(const SliceGemmArgs& a, const CUtenso
     j.tb = a.tmaps + 2 * r.prob + 1;
     j.tm = r.tm;
     j.tn = r.tn;
+    resolve_slices(a, *j.P, j);
   }
   return j;
 }
@@ -226,6 +244,12 @@ __global__ void __launch_bounds__(Cfg<BN, MODE, CG>::NUM_THREADS, 1)
   __shared__ uint32_t tmem_base_slot;
   __shared__ volatile uint32_t abort_flag;
 
+  // a single product whose automatic slice count another launch handles:
+  // nothing to do (the whole grid returns before any setup)
+  if (args.probs == nullptr && args.single.s_dev != nullptr) {
+    const int s = *args.single.s_dev;
+    if (s < args.s_lo || s > args.s_hi || s > SLICE_S_MAX) return;
+  }
   const uint32_t warp = warp_id(), lane = lane_id();
   const uint32_t smem_base = (smem_u32(smem_raw) + 1023u) & ~1023u;
   uint8_t* smem_gen = smem_raw + (smem_base - smem_u32(smem_raw));
@@ -283,9 +307,10 @@ __global__ void __launch_bounds__(Cfg<BN, MODE, CG>::NUM_THREADS, 1)
       bool ok = true;
       for (int t = walker; t < ntiles && ok; t += walkers) {
         const TileJob job = get_job(args, &tmA, &tmB, t);
+        if (job.skip) continue;
         const int ya = job.tm * C_::TILE_M + static_cast<int>(rank) * BM;
         const int yb = job.tn * BN + static_cast<int>(rank) * (BN / CG);
-        for_each_step<MODE>(job.P->s, job.P->nkb, [&](const Step& st, int) {
+        for_each_step<MODE>(job.s, job.P->nkb, [&](const Step& st, int) {
           if (!ok) return;
           const int stage = it % C_::STAGES;
           const uint32_t use = static_cast<uint32_t>(it / C_::STAGES);
@@ -324,7 +349,8 @@ __global__ void __launch_bounds__(Cfg<BN, MODE, CG>::NUM_THREADS, 1)
       bool issued_any = false;
       for (int t = walker; t < ntiles && ok; t += walkers) {
         const TileJob job = get_job(args, &tmA, &tmB, t);
-        const int s = job.P->s, nkb = job.P->nkb;
+        if (job.skip) continue;
+        const int s = job.s, nkb = job.P->nkb;
         for_each_step<MODE>(s, nkb, [&](const Step& st, int cofs) {
           if (!ok) return;
           const int chunk = chunk_base + cofs;
@@ -392,6 +418,7 @@ __global__ void __launch_bounds__(Cfg<BN, MODE, CG>::NUM_THREADS, 1)
     const uint32_t acce_remote1 = (CG == 2) ? mapa_shared(smem_u32(&acce_bar[1]), 0) : 0u;
     for (int t = walker; t < ntiles && ok; t += walkers) {
       const TileJob job = get_job(args, &tmA, &tmB, t);
+      if (job.skip) continue;
       const SliceProblem& P = *job.P;
       const int64_t row = static_cast<int64_t>(job.tm) * C_::TILE_M + static_cast<int64_t>(rank) * BM + row_in_tile;
       const int64_t col0 = static_cast<int64_t>(job.tn) * BN + col_off;
@@ -439,9 +466,9 @@ __global__ void __launch_bounds__(Cfg<BN, MODE, CG>::NUM_THREADS, 1)
         // per element per chunk) and folds them into the int64 total, kept in
         // C's storage, at the end of each level.
         int64_t* const xrow = reinterpret_cast<int64_t*>(P.C) + row * P.ldc;
-        const int s = P.s;
+        const int s = job.s;
         const int nkb = P.nkb;
-        const int fix_shift = P.fix_shift;
+        const int fix_shift = job.fix;
         constexpr int NG = C_::COLS_PER_THREAD / 8;
         int32_t lsum[NG][8];
 #pragma unroll
@@ -706,9 +733,9 @@ __global__ void __launch_bounds__(Cfg<BN, MODE, CG>::NUM_THREADS, 1)
         }
       } else {
         double* const crow = P.C + row * P.ldc;
-        const int s = P.s;
+        const int s = job.s;
         const int nkb = P.nkb;
-        const int fix_shift = P.fix_shift;
+        const int fix_shift = job.fix;
         const uint32_t txlo = tmem_base + t_lane + static_cast<uint32_t>(C_::XLO_COL + col_off);
         const uint32_t txhi = tmem_base + t_lane + static_cast<uint32_t>(C_::XHI_COL + col_off);
         bool fresh = true;   // X holds nothing yet (reads as zero)

@@ -225,13 +225,88 @@ __device__ __forceinline__ void slice8_store(const uint64_t (&vb)[8], int32_t X,
   }
 }
 
+// ------------------------------------------------------ spread statistic
+// 2^x as a float for x <= 127 (0 below the normal range).
+__device__ __forceinline__ float pow2f(int x) {
+  return x >= -126 ? __uint_as_float(static_cast<uint32_t>(x + 127) << 23) : 0.0f;
+}
+
+// Running sum of |x| / 2^(ref - 1023) in float, ref the largest biased
+// exponent seen so far (subnormals count at exponent 1). A larger exponent
+// first rescales the sum by a power of two (exact); each term keeps the top 23
+// bits of its significand (truncated), entries more than 2^126 below the
+// reference add nothing. With SPREAD = false everything compiles away.
+struct SpreadAcc {
+  int ref = 1;
+  float sum = 0.0f;
+};
+
+template <bool SPREAD>
+__device__ __forceinline__ void spread_add(SpreadAcc& a, uint64_t ab) {
+  if constexpr (SPREAD) {
+    const int e = static_cast<int>(ab >> 52);
+    const int ee = e > 1 ? e : 1;
+    if (ee > a.ref) {
+      a.sum *= pow2f(a.ref - ee);
+      a.ref = ee;
+    }
+    float f;
+    if (e != 0) {
+      const int x = e - a.ref;
+      f = x >= -126 ? __uint_as_float((static_cast<uint32_t>(x + 127) << 23) |
+                                      static_cast<uint32_t>((ab >> 29) & 0x7FFFFFull))
+                    : 0.0f;
+    } else {
+      // |x| = mant 2^-1074 = mant 2^(-51 - ref) in units of 2^(ref - 1023)
+      f = __ull2float_rn(static_cast<unsigned long long>(ab)) * pow2f(-51 - a.ref);
+    }
+    a.sum += f;
+  }
+}
+
+__device__ __forceinline__ SpreadAcc spread_merge(const SpreadAcc& a, const SpreadAcc& b) {
+  SpreadAcc r;
+  r.ref = max(a.ref, b.ref);
+  r.sum = a.sum * pow2f(a.ref - r.ref) + b.sum * pow2f(b.ref - r.ref);
+  return r;
+}
+
+// alpha = (sum |x|) / (k 2^E) with E = floor(log2 max) + 2, from a sum whose
+// reference is the maximum's exponent; +inf (no constraint on the slice count)
+// for an all-zero or non-finite row or column.
+__device__ __forceinline__ float spread_final(const SpreadAcc& a, uint64_t mx, int64_t k) {
+  if (mx == 0 || mx >= INF_BITS) return __uint_as_float(0x7F800000u);
+  return a.sum * pow2f(a.ref - 1023 - (floor_log2_bits(mx) + 2)) / static_cast<float>(k);
+}
+
+// Minimum over the block's threads of v (non-negative), merged into the
+// decision word *dst as its distance below +inf (atomicMax). Every thread of
+// the block calls it.
+__device__ __forceinline__ void block_min_to(float v, uint32_t* dst) {
+  __shared__ float wmin[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int w = static_cast<int>(threadIdx.x >> 5), nw = static_cast<int>((blockDim.x + 31) >> 5);
+  if ((threadIdx.x & 31u) == 0) wmin[w] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float m = wmin[0];
+    for (int i = 1; i < nw; ++i) m = fminf(m, wmin[i]);
+    if (m < __uint_as_float(0x7F800000u)) atomicMax(dst, 0x7F800000u - __float_as_uint(m));
+  }
+  __syncthreads();
+}
+
 // ---------------------------------------------------------- kernel bodies
 // Row maximum of |a| bits for one row by one warp (16-byte loads when the row
-// start is 16-byte aligned).
-__device__ __forceinline__ void row_absmax_body(const double* __restrict__ A, int64_t k, int64_t lda, int64_t row,
-                                                uint64_t* __restrict__ rowmax) {
+// start is 16-byte aligned). With SPREAD, returns the row's alpha (every lane),
+// else +inf.
+template <bool SPREAD>
+__device__ __forceinline__ float row_absmax_body(const double* __restrict__ A, int64_t k, int64_t lda, int64_t row,
+                                                 uint64_t* __restrict__ rowmax) {
   const double* a = A + row * lda;
   uint64_t mx = 0;
+  SpreadAcc acc;
   const uint32_t lane = threadIdx.x & 31u;
   int64_t c0 = 0;
   if ((reinterpret_cast<uintptr_t>(a) & 15u) == 0) {
@@ -240,34 +315,105 @@ __device__ __forceinline__ void row_absmax_body(const double* __restrict__ A, in
     int64_t c = lane;
     for (; c + 96 < k2; c += 128) {
       const double2 v0 = __ldg(a2 + c), v1 = __ldg(a2 + c + 32), v2 = __ldg(a2 + c + 64), v3 = __ldg(a2 + c + 96);
-      mx = max(mx, max(max(dbits(v0.x) & ABS_MASK, dbits(v0.y) & ABS_MASK), max(dbits(v1.x) & ABS_MASK, dbits(v1.y) & ABS_MASK)));
-      mx = max(mx, max(max(dbits(v2.x) & ABS_MASK, dbits(v2.y) & ABS_MASK), max(dbits(v3.x) & ABS_MASK, dbits(v3.y) & ABS_MASK)));
+      const uint64_t b[8] = {dbits(v0.x) & ABS_MASK, dbits(v0.y) & ABS_MASK, dbits(v1.x) & ABS_MASK,
+                             dbits(v1.y) & ABS_MASK, dbits(v2.x) & ABS_MASK, dbits(v2.y) & ABS_MASK,
+                             dbits(v3.x) & ABS_MASK, dbits(v3.y) & ABS_MASK};
+      mx = max(mx, max(max(max(b[0], b[1]), max(b[2], b[3])), max(max(b[4], b[5]), max(b[6], b[7]))));
+#pragma unroll
+      for (int u = 0; u < 8; ++u) spread_add<SPREAD>(acc, b[u]);
     }
     for (; c < k2; c += 32) {
       const double2 v = __ldg(a2 + c);
-      mx = max(mx, max(dbits(v.x) & ABS_MASK, dbits(v.y) & ABS_MASK));
+      const uint64_t b0 = dbits(v.x) & ABS_MASK, b1 = dbits(v.y) & ABS_MASK;
+      mx = max(mx, max(b0, b1));
+      spread_add<SPREAD>(acc, b0);
+      spread_add<SPREAD>(acc, b1);
     }
     c0 = 2 * k2;   // an odd last entry is left for the scalar loop
   }
-  for (int64_t c = c0 + lane; c < k; c += 32) mx = max(mx, dbits(__ldg(a + c)) & ABS_MASK);
+  for (int64_t c = c0 + lane; c < k; c += 32) {
+    const uint64_t b = dbits(__ldg(a + c)) & ABS_MASK;
+    mx = max(mx, b);
+    spread_add<SPREAD>(acc, b);
+  }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1)
+  for (int o = 16; o > 0; o >>= 1) {
     mx = max(mx, static_cast<uint64_t>(__shfl_xor_sync(0xffffffffu, static_cast<unsigned long long>(mx), o)));
+    if constexpr (SPREAD) {
+      SpreadAcc other;
+      other.ref = __shfl_xor_sync(0xffffffffu, acc.ref, o);
+      other.sum = __shfl_xor_sync(0xffffffffu, acc.sum, o);
+      acc = spread_merge(acc, other);
+    }
+  }
   if (lane == 0) rowmax[row] = mx;
+  if constexpr (SPREAD) return spread_final(acc, mx, k);
+  return __uint_as_float(0x7F800000u);
 }
 
-// Column maximum of |b| bits for column j over rows [r0, r1), merged with atomicMax.
+// Column maximum of |b| bits for column j over rows [r0, r1), merged with
+// atomicMax; with part != nullptr also the column's partial spread sum over
+// these rows, stored as (reference exponent, float bits) at *part. The sum is
+// formed in the grouped kernel's order: eight running sums, one per row
+// residue mod 8 (r0 is a multiple of 8), each in row order, merged in residue
+// order, so single and grouped products decide the same slice count.
+template <bool SPREAD>
 __device__ __forceinline__ void col_absmax_body(const double* __restrict__ B, int64_t ldb, int64_t j, int64_t r0,
-                                                int64_t r1, unsigned long long* __restrict__ colmax) {
+                                                int64_t r1, unsigned long long* __restrict__ colmax,
+                                                uint2* __restrict__ part) {
   uint64_t mx = 0;
+  SpreadAcc acc[8];
   int64_t r = r0;
-  for (; r + 3 < r1; r += 4) {
-    const uint64_t v0 = dbits(__ldg(B + r * ldb + j)), v1 = dbits(__ldg(B + (r + 1) * ldb + j));
-    const uint64_t v2 = dbits(__ldg(B + (r + 2) * ldb + j)), v3 = dbits(__ldg(B + (r + 3) * ldb + j));
-    mx = max(mx, max(max(v0 & ABS_MASK, v1 & ABS_MASK), max(v2 & ABS_MASK, v3 & ABS_MASK)));
+  for (; r + 7 < r1; r += 8) {
+    uint64_t v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = dbits(__ldg(B + (r + u) * ldb + j)) & ABS_MASK;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      mx = max(mx, v[u]);
+      spread_add<SPREAD>(acc[u], v[u]);
+    }
   }
-  for (; r < r1; ++r) mx = max(mx, dbits(__ldg(B + r * ldb + j)) & ABS_MASK);
+#pragma unroll
+  for (int u = 0; u < 7; ++u) {
+    if (r + u < r1) {
+      const uint64_t v = dbits(__ldg(B + (r + u) * ldb + j)) & ABS_MASK;
+      mx = max(mx, v);
+      spread_add<SPREAD>(acc[u], v);
+    }
+  }
   if (mx) atomicMax(colmax + j, static_cast<unsigned long long>(mx));
+  if constexpr (SPREAD) {
+    SpreadAcc t;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) t = spread_merge(t, acc[u]);
+    *part = make_uint2(static_cast<uint32_t>(t.ref), __float_as_uint(t.sum));
+  }
+}
+
+// beta of column j from its final maximum and its partial sums (parts records
+// of stride n, summed in order).
+__device__ __forceinline__ float col_spread_body(const uint64_t* __restrict__ colmax, const uint2* __restrict__ part,
+                                                 int64_t n, int64_t k, int64_t parts, int64_t j) {
+  const uint64_t mx = colmax[j];
+  SpreadAcc acc;
+  if (mx != 0 && mx < INF_BITS) {
+    acc.ref = max(static_cast<int>(mx >> 52), 1);
+    for (int64_t p = 0; p < parts; ++p) {
+      const uint2 r = part[p * n + j];
+      acc.sum += __uint_as_float(r.y) * pow2f(static_cast<int>(r.x) - acc.ref);
+    }
+  }
+  return spread_final(acc, mx, k);
+}
+
+// The slice count a splitting kernel uses: the automatic rule's when dec is
+// set (the thread with first set records it), else s.
+__device__ __forceinline__ int decided_slices(const SliceDecision* dec, int s, int64_t k, bool first) {
+  if (dec == nullptr) return s;
+  const int d = slice_count_rule(k, spread_from_room(dec->amin_room), spread_from_room(dec->bmin_room));
+  if (first) const_cast<SliceDecision*>(dec)->s = d;
+  return d;
 }
 
 // Slices of 8 consecutive entries A[row][c0 .. c0+8) (rows scaled by E).
@@ -282,6 +428,7 @@ __device__ __forceinline__ void slice_rows_body(const double* __restrict__ A, in
     E[row] = Ei;
     if (Ei == EXP_NONFINITE) atomicOr(err, MM_DEV_ERR_NONFINITE);
   }
+  if (MODE == 0 && s > SLICE_S_MAX) return;   // the product runs through the plain FP64 kernel
   const double* a = A + row * lda + c0;
   uint64_t vb[8];
   const int cnt = static_cast<int>((k - c0) < 8 ? (k - c0) : 8);
@@ -312,6 +459,7 @@ __device__ __forceinline__ void slice_cols_body(const double* __restrict__ B, in
     }
     fexp[t] = Fj;
   }
+  if (MODE == 0 && s > SLICE_S_MAX) return;   // plain FP64 fallback: F only (uniform over the block)
   {
     // load 64 x 32 doubles: thread -> row t/4, columns (t%4)*8 .. +8
     const int r = t >> 2, cb = (t & 3) * 8;
@@ -338,57 +486,83 @@ __device__ __forceinline__ void slice_cols_body(const double* __restrict__ B, in
 }
 
 // -------------------------------------------------- single-product kernels
-__global__ void row_absmax_kernel(const double* __restrict__ A, int64_t m, int64_t k, int64_t lda,
-                                  uint64_t* __restrict__ rowmax) {
+// SPREAD: also the rows' spreads, merged into *amin.
+template <bool SPREAD>
+__global__ void __launch_bounds__(256) row_absmax_kernel(const double* __restrict__ A, int64_t m, int64_t k,
+                                                         int64_t lda, uint64_t* __restrict__ rowmax,
+                                                         uint32_t* __restrict__ amin) {
   const int64_t row = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (row < m) row_absmax_body(A, k, lda, row, rowmax);
+  float al = __uint_as_float(0x7F800000u);
+  if (row < m) al = row_absmax_body<SPREAD>(A, k, lda, row, rowmax);
+  if constexpr (SPREAD) block_min_to(al, amin);
 }
 
+template <bool SPREAD>
 __global__ void col_absmax_kernel(const double* __restrict__ B, int64_t k, int64_t n, int64_t ldb,
-                                  int64_t rows_per_block, unsigned long long* __restrict__ colmax) {
+                                  int64_t rows_per_block, unsigned long long* __restrict__ colmax,
+                                  uint2* __restrict__ colpart) {
   const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (j >= n) return;
   const int64_t r0 = static_cast<int64_t>(blockIdx.y) * rows_per_block;
-  col_absmax_body(B, ldb, j, r0, min(k, r0 + rows_per_block), colmax);
+  col_absmax_body<SPREAD>(B, ldb, j, r0, min(k, r0 + rows_per_block), colmax,
+                          SPREAD ? colpart + static_cast<int64_t>(blockIdx.y) * n + j : nullptr);
 }
 
 // Both maxima in one launch: blocks [0, row_blocks) take 8 rows of A each (a
 // warp per row), the rest 256 columns x rows_per_block rows of B each, so the
 // two read streams overlap and the launch's ramp and tail are paid once.
+// SPREAD: rows' spreads into *amin, columns' partial sums into colpart
+// (record p * n + j for rows [p rows_per_block, (p+1) rows_per_block)).
+template <bool SPREAD>
 __global__ void __launch_bounds__(256) absmax_both_kernel(const double* __restrict__ A, int64_t m, int64_t k,
                                                           int64_t lda, uint64_t* __restrict__ rowmax,
                                                           const double* __restrict__ B, int64_t n, int64_t ldb,
                                                           int64_t rows_per_block, unsigned long long* __restrict__ colmax,
-                                                          int row_blocks, int col_bx) {
+                                                          int row_blocks, int col_bx, uint32_t* __restrict__ amin,
+                                                          uint2* __restrict__ colpart) {
   const int b = static_cast<int>(blockIdx.x);
   if (b < row_blocks) {
     const int64_t row = static_cast<int64_t>(b) * 8 + (threadIdx.x >> 5);
-    if (row < m) row_absmax_body(A, k, lda, row, rowmax);
+    float al = __uint_as_float(0x7F800000u);
+    if (row < m) al = row_absmax_body<SPREAD>(A, k, lda, row, rowmax);
+    if constexpr (SPREAD) block_min_to(al, amin);
     return;
   }
   const int cb = b - row_blocks;
   const int64_t j = static_cast<int64_t>(cb % col_bx) * 256 + threadIdx.x;
   if (j >= n) return;
-  const int64_t r0 = static_cast<int64_t>(cb / col_bx) * rows_per_block;
-  col_absmax_body(B, ldb, j, r0, min(k, r0 + rows_per_block), colmax);
+  const int64_t p = cb / col_bx, r0 = p * rows_per_block;
+  col_absmax_body<SPREAD>(B, ldb, j, r0, min(k, r0 + rows_per_block), colmax, SPREAD ? colpart + p * n + j : nullptr);
+}
+
+// The columns' spreads from their partial sums, merged into *bmin.
+__global__ void __launch_bounds__(256) col_spread_kernel(const uint64_t* __restrict__ colmax,
+                                                         const uint2* __restrict__ colpart, int64_t n, int64_t k,
+                                                         int64_t parts, uint32_t* __restrict__ bmin) {
+  const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const float be = (j < n) ? col_spread_body(colmax, colpart, n, k, parts, j) : __uint_as_float(0x7F800000u);
+  block_min_to(be, bmin);
 }
 
 template <int MODE>
 __global__ void slice_rows_kernel(const double* __restrict__ A, int64_t m, int64_t k, int64_t lda,
                                   const uint64_t* __restrict__ rowmax, int s, int64_t kp,
                                   uint16_t* __restrict__ slices, int32_t* __restrict__ E,
-                                  uint32_t* __restrict__ err, int64_t plane_rows) {
+                                  uint32_t* __restrict__ err, int64_t plane_rows, SliceDecision* dec) {
   const int64_t row = blockIdx.x;
   const int64_t c0 = (static_cast<int64_t>(blockIdx.y) * blockDim.x + threadIdx.x) * 8;
-  if (row < m && c0 < k) slice_rows_body<MODE>(A, plane_rows, k, lda, rowmax, s, kp, slices, E, err, row, c0);
+  const int se = decided_slices(dec, s, k, blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0);
+  if (row < m && c0 < k) slice_rows_body<MODE>(A, plane_rows, k, lda, rowmax, se, kp, slices, E, err, row, c0);
 }
 
 template <int MODE>
 __global__ void __launch_bounds__(256) slice_cols_kernel(const double* __restrict__ B, int64_t k, int64_t n,
                                                          int64_t ldb, const uint64_t* __restrict__ colmax, int s,
                                                          int64_t kp, uint16_t* __restrict__ slices,
-                                                         int32_t* __restrict__ F, uint32_t* __restrict__ err) {
-  slice_cols_body<MODE>(B, k, n, ldb, colmax, s, kp, slices, F, err, static_cast<int64_t>(blockIdx.y) * 64,
+                                                         int32_t* __restrict__ F, uint32_t* __restrict__ err,
+                                                         const SliceDecision* dec) {
+  const int se = decided_slices(dec, s, k, false);
+  slice_cols_body<MODE>(B, k, n, ldb, colmax, se, kp, slices, F, err, static_cast<int64_t>(blockIdx.y) * 64,
                         static_cast<int64_t>(blockIdx.x) * 32);
 }
 
@@ -406,6 +580,8 @@ __device__ __forceinline__ int find_problem(const int64_t* __restrict__ off, int
 // Phase 1: row maxima (8 rows per block) then column maxima (256 columns x
 // 256 rows per block) of every problem.
 __global__ void __launch_bounds__(256) grouped_absmax_kernel(const GroupedSplitArgs a) {
+  __shared__ int pref[8][32];
+  __shared__ float psum[8][32];
   const int count = *a.count_dev;
   const int64_t t0 = a.off[0][count], t1 = a.off[1][count];
   for (int64_t vb = blockIdx.x; vb < t0 + t1; vb += gridDim.x) {
@@ -413,7 +589,13 @@ __global__ void __launch_bounds__(256) grouped_absmax_kernel(const GroupedSplitA
       const int p = find_problem(a.off[0], count, vb);
       const GroupedSplit& g = a.probs[p];
       const int64_t row = (vb - a.off[0][p]) * 8 + (threadIdx.x >> 5);
-      if (row < g.m) row_absmax_body(g.A, g.k, g.lda, row, g.rowmax);
+      if (g.dec != nullptr) {
+        float al = __uint_as_float(0x7F800000u);
+        if (row < g.m) al = row_absmax_body<true>(g.A, g.k, g.lda, row, g.rowmax);
+        block_min_to(al, &g.dec->amin_room);
+      } else if (row < g.m) {
+        row_absmax_body<false>(g.A, g.k, g.lda, row, g.rowmax);
+      }
     } else {
       const int64_t v = vb - t0;
       const int p = find_problem(a.off[1], count, v);
@@ -421,14 +603,53 @@ __global__ void __launch_bounds__(256) grouped_absmax_kernel(const GroupedSplitA
       const int64_t lb = v - a.off[1][p];
       // 32 columns x 256 rows per block: warp w takes rows r0 + w, r0 + w + 8, ...
       const int64_t ncb = (g.n + 31) / 32;
-      const int64_t j = (lb % ncb) * 32 + (threadIdx.x & 31), r0 = (lb / ncb) * 256 + (threadIdx.x >> 5);
+      const int lane = static_cast<int>(threadIdx.x & 31), w = static_cast<int>(threadIdx.x >> 5);
+      const int64_t j = (lb % ncb) * 32 + lane, r0 = (lb / ncb) * 256 + w;
+      uint64_t mx = 0;
+      SpreadAcc acc;
       if (j < g.n) {
-        uint64_t mx = 0;
         const int64_t r1 = min(g.k, (lb / ncb) * 256 + 256);
-        for (int64_t r = r0; r < r1; r += 8) mx = max(mx, dbits(__ldg(g.B + r * g.ldb + j)) & ABS_MASK);
+        for (int64_t r = r0; r < r1; r += 8) {
+          const uint64_t b = dbits(__ldg(g.B + r * g.ldb + j)) & ABS_MASK;
+          mx = max(mx, b);
+          spread_add<true>(acc, b);
+        }
         if (mx) atomicMax(reinterpret_cast<unsigned long long*>(g.colmax) + j, static_cast<unsigned long long>(mx));
       }
+      if (g.dec != nullptr) {
+        // the 8 warps' sums of each column, merged in warp order
+        pref[w][lane] = acc.ref;
+        psum[w][lane] = acc.sum;
+        __syncthreads();
+        if (w == 0 && j < g.n) {
+          SpreadAcc t;
+          for (int i = 0; i < 8; ++i) {
+            SpreadAcc o;
+            o.ref = pref[i][lane];
+            o.sum = psum[i][lane];
+            t = spread_merge(t, o);
+          }
+          g.colpart[(lb / ncb) * g.n + j] = make_uint2(static_cast<uint32_t>(t.ref), __float_as_uint(t.sum));
+        }
+        __syncthreads();
+      }
     }
+  }
+}
+
+// Phase 1b (automatic slice count): every column's spread from its partial
+// sums, 256 columns per block.
+__global__ void __launch_bounds__(256) grouped_spread_kernel(const GroupedSplitArgs a) {
+  const int count = *a.count_dev;
+  const int64_t t4 = a.off[4][count];
+  for (int64_t vb = blockIdx.x; vb < t4; vb += gridDim.x) {
+    const int p = find_problem(a.off[4], count, vb);
+    const GroupedSplit& g = a.probs[p];
+    if (g.dec == nullptr) continue;   // uniform over the block
+    const int64_t j = (vb - a.off[4][p]) * 256 + threadIdx.x;
+    const float be = (j < g.n) ? col_spread_body(g.colmax, g.colpart, g.n, g.k, (g.k + 255) / 256, j)
+                               : __uint_as_float(0x7F800000u);
+    block_min_to(be, &g.dec->bmin_room);
   }
 }
 
@@ -446,14 +667,17 @@ __global__ void __launch_bounds__(256) grouped_slice_kernel(const GroupedSplitAr
       const int64_t runs = (g.k + 7) / 8;   // runs of 8 entries per row
       const int64_t u = lb * 256 + threadIdx.x;
       const int64_t row = u / runs, c0 = (u - row * runs) * 8;
-      if (row < g.m) slice_rows_body<MODE>(g.A, g.m, g.k, g.lda, g.rowmax, g.s, g.kp, g.slA, g.E, a.err, row, c0);
+      const int se = decided_slices(g.dec, g.s, g.k, lb == 0 && threadIdx.x == 0);
+      if (row < g.m)
+        slice_rows_body<MODE>(g.A, g.m, g.k, g.lda, g.rowmax, se, g.kp, g.slA, g.E, g.perr ? g.perr : a.err, row, c0);
     } else {
       const int64_t v = vb - t2;
       const int p = find_problem(a.off[3], count, v);
       const GroupedSplit& g = a.probs[p];
       const int64_t lb = v - a.off[3][p];
       const int64_t nnb = (g.n + 31) / 32;
-      slice_cols_body<MODE>(g.B, g.k, g.n, g.ldb, g.colmax, g.s, g.kp, g.slB, g.F, a.err, (lb / nnb) * 64,
+      const int se = decided_slices(g.dec, g.s, g.k, false);
+      slice_cols_body<MODE>(g.B, g.k, g.n, g.ldb, g.colmax, se, g.kp, g.slB, g.F, g.perr ? g.perr : a.err, (lb / nnb) * 64,
                             (lb % nnb) * 32);
     }
   }
@@ -497,62 +721,88 @@ __global__ void fill_uniform_kernel(double* __restrict__ X, int64_t rows, int64_
 // --------------------------------------------------------------- launchers
 using namespace mmdev;
 
+int64_t launch_absmax_parts(int64_t k) { return (k + 255) / 256; }
+
 cudaError_t launch_absmax(const double* A, int64_t m, int64_t k, int64_t lda, const double* B, int64_t n,
-                          int64_t ldb, uint64_t* rowmax, uint64_t* colmax, cudaStream_t st, int* nlaunch) {
+                          int64_t ldb, uint64_t* rowmax, uint64_t* colmax, cudaStream_t st, int* nlaunch,
+                          SliceDecision* dec, uint2* colpart) {
   if (nlaunch) *nlaunch = 0;
+  const bool spread = dec != nullptr;
+  uint32_t* amin = spread ? &dec->amin_room : nullptr;
+  const int64_t rpb = 256;   // rows of B per column block: one partial record each
+  bool cols_done = false;
   if (m > 0 && n > 0 && k > 0) {
     cudaError_t e = cudaMemsetAsync(colmax, 0, sizeof(uint64_t) * n, st);
     if (e != cudaSuccess) return e;
-    const int64_t rpb = 256;
     const int64_t row_blocks = (m + 7) / 8, col_bx = (n + 255) / 256, col_by = (k + rpb - 1) / rpb;
     const int64_t blocks = row_blocks + col_bx * col_by;
     if (blocks <= 0x7fffffff) {
-      absmax_both_kernel<<<static_cast<unsigned>(blocks), 256, 0, st>>>(
-          A, m, k, lda, rowmax, B, n, ldb, rpb, reinterpret_cast<unsigned long long*>(colmax),
-          static_cast<int>(row_blocks), static_cast<int>(col_bx));
+      if (spread)
+        absmax_both_kernel<true><<<static_cast<unsigned>(blocks), 256, 0, st>>>(
+            A, m, k, lda, rowmax, B, n, ldb, rpb, reinterpret_cast<unsigned long long*>(colmax),
+            static_cast<int>(row_blocks), static_cast<int>(col_bx), amin, colpart);
+      else
+        absmax_both_kernel<false><<<static_cast<unsigned>(blocks), 256, 0, st>>>(
+            A, m, k, lda, rowmax, B, n, ldb, rpb, reinterpret_cast<unsigned long long*>(colmax),
+            static_cast<int>(row_blocks), static_cast<int>(col_bx), nullptr, nullptr);
       if (nlaunch) *nlaunch = 1;
-      return cudaGetLastError();
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      m = 0;   // both done
+      cols_done = true;
     }
   }
   if (m > 0) {
     dim3 blk(256), grd(static_cast<unsigned>((m + 7) / 8));
-    row_absmax_kernel<<<grd, blk, 0, st>>>(A, m, k, lda, rowmax);
+    if (spread)
+      row_absmax_kernel<true><<<grd, blk, 0, st>>>(A, m, k, lda, rowmax, amin);
+    else
+      row_absmax_kernel<false><<<grd, blk, 0, st>>>(A, m, k, lda, rowmax, nullptr);
     if (nlaunch) ++*nlaunch;
   }
-  if (n > 0) {
+  if (n > 0 && !cols_done) {
     cudaError_t e = cudaMemsetAsync(colmax, 0, sizeof(uint64_t) * n, st);
     if (e != cudaSuccess) return e;
-    int64_t rpb = 256;
     dim3 blk(128), grd(static_cast<unsigned>((n + 127) / 128), static_cast<unsigned>((k + rpb - 1) / rpb));
     if (k > 0) {
-      col_absmax_kernel<<<grd, blk, 0, st>>>(B, k, n, ldb, rpb, reinterpret_cast<unsigned long long*>(colmax));
+      if (spread)
+        col_absmax_kernel<true><<<grd, blk, 0, st>>>(B, k, n, ldb, rpb, reinterpret_cast<unsigned long long*>(colmax),
+                                                     colpart);
+      else
+        col_absmax_kernel<false><<<grd, blk, 0, st>>>(B, k, n, ldb, rpb, reinterpret_cast<unsigned long long*>(colmax),
+                                                      nullptr);
       if (nlaunch) ++*nlaunch;
     }
+  }
+  if (spread && n > 0 && k > 0) {
+    col_spread_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, st>>>(colmax, colpart, n, k,
+                                                                               launch_absmax_parts(k), &dec->bmin_room);
+    if (nlaunch) ++*nlaunch;
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_slice_rows(int mode, const double* A, int64_t m, int64_t k, int64_t lda, const uint64_t* rowmax,
                               int s, int64_t kp, uint16_t* slices, int32_t* E, uint32_t* err, cudaStream_t st,
-                              int64_t plane_rows) {
+                              int64_t plane_rows, SliceDecision* dec) {
   if (m <= 0 || k <= 0) return cudaSuccess;
   if (plane_rows < m) plane_rows = m;
   dim3 blk(128), grd(static_cast<unsigned>(m), static_cast<unsigned>((k + 1023) / 1024));
   if (mode == 0)
-    slice_rows_kernel<0><<<grd, blk, 0, st>>>(A, m, k, lda, rowmax, s, kp, slices, E, err, plane_rows);
+    slice_rows_kernel<0><<<grd, blk, 0, st>>>(A, m, k, lda, rowmax, s, kp, slices, E, err, plane_rows, dec);
   else
-    slice_rows_kernel<1><<<grd, blk, 0, st>>>(A, m, k, lda, rowmax, s, kp, slices, E, err, plane_rows);
+    slice_rows_kernel<1><<<grd, blk, 0, st>>>(A, m, k, lda, rowmax, s, kp, slices, E, err, plane_rows, nullptr);
   return cudaGetLastError();
 }
 
 cudaError_t launch_slice_cols(int mode, const double* B, int64_t k, int64_t n, int64_t ldb, const uint64_t* colmax,
-                              int s, int64_t kp, uint16_t* slices, int32_t* F, uint32_t* err, cudaStream_t st) {
+                              int s, int64_t kp, uint16_t* slices, int32_t* F, uint32_t* err, cudaStream_t st,
+                              SliceDecision* dec) {
   if (n <= 0 || k <= 0) return cudaSuccess;
   dim3 blk(256), grd(static_cast<unsigned>((n + 31) / 32), static_cast<unsigned>((k + 63) / 64));
   if (mode == 0)
-    slice_cols_kernel<0><<<grd, blk, 0, st>>>(B, k, n, ldb, colmax, s, kp, slices, F, err);
+    slice_cols_kernel<0><<<grd, blk, 0, st>>>(B, k, n, ldb, colmax, s, kp, slices, F, err, dec);
   else
-    slice_cols_kernel<1><<<grd, blk, 0, st>>>(B, k, n, ldb, colmax, s, kp, slices, F, err);
+    slice_cols_kernel<1><<<grd, blk, 0, st>>>(B, k, n, ldb, colmax, s, kp, slices, F, err, nullptr);
   return cudaGetLastError();
 }
 
@@ -560,6 +810,10 @@ cudaError_t launch_grouped_split(int mode01, const GroupedSplitArgs& a, int grid
   grouped_absmax_kernel<<<grid, 256, 0, st>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  if (mode01 == 0) {
+    grouped_spread_kernel<<<grid, 256, 0, st>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
   if (mode01 == 0)
     grouped_slice_kernel<0><<<grid, 256, 0, st>>>(a);
   else

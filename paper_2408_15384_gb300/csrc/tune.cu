@@ -228,7 +228,7 @@ int tune_pick(mm_handle_s* h, const int key[5], const std::vector<TileCfg>& cand
   if (!std::isfinite(best_ms)) return MM_ERR_BUDGET;
   // a timeout or other device error during the runs makes the timings meaningless
   uint32_t dev_err = 0;
-  if (cudaMemcpy(&dev_err, h->d_err, sizeof(dev_err), cudaMemcpyDeviceToHost) != cudaSuccess) return MM_ERR_CUDA;
+  if (cudaMemcpy(&dev_err, err_word(h, st), sizeof(dev_err), cudaMemcpyDeviceToHost) != cudaSuccess) return MM_ERR_CUDA;
   if (dev_err == 0) tune_store(h, key, *best, best_ms);
   return MM_OK;
 }

@@ -46,41 +46,19 @@ def test_status_strings(lib):
     assert lib.mm_status_string(999) == b"unknown status"
 
 
-def test_slice_rule(lib):
-    assert [lib.mm_slices_for_k(k) for k in (5, 95, 96, 4095, 4096, 8192)] == [7, 7, 6, 6, 5, 5]
-    ks = (5, 159, 160, 12287, 12288, 20000)
-    assert [lib.mm_slices_for_k_rule(k, 0) for k in ks] == [7, 6, 6, 5, 5, 5]
-    assert [lib.mm_slices_for_k_rule(k, 1) for k in ks] == [7, 7, 6, 6, 5, 5]
-    assert lib.mm_slices_for_k_rule(100, 2) == -1
-
-
-# Each rule's thresholds, checked on the oracle: at the smallest k of every
-# slice count the emulated product stays within half the componentwise bound
-# on inputs of the distribution the rule is calibrated for.
-RULE_CASES = [
-    (0, "uniform", 96), (0, "uniform", 4096),
-    (1, "normal", 160), (1, "normal", 12288),
-]
-
-
-@pytest.mark.parametrize("rule,dist,k", RULE_CASES)
-def test_slice_rule_keeps_half_the_bound(lib, rule, dist, k):
+def test_slice_count_rule_matches_the_oracle(lib):
+    """The library's decision function (the one the kernels run) against the
+    oracle's, on a grid of k and spreads given as float32 values, decision for
+    decision."""
     import numpy as np
-    import oracle
     from oracle import emulation as em
-    from paper_2408_15384_gb300 import inputs
-    s = lib.mm_slices_for_k_rule(k, rule)
-    m = 64 if k < 1000 else 24
-    seed = 77 + k
-    if dist == "uniform":
-        A = inputs.uniform(m, k, seed, inputs.STREAM_A)
-        B = inputs.uniform(k, m, seed, inputs.STREAM_B)
-    else:
-        A = inputs.box_muller(m, k, seed, inputs.STREAM_A)
-        B = inputs.box_muller(k, m, seed, inputs.STREAM_B)
-    C = em.gemm_fp64_emu(A, B, s)
-    ratio = np.max(np.abs(C - oracle.gemm(A, B)) / (em.gamma(k, "fp64_emu") * oracle.absprod(A, B)))
-    assert ratio <= 0.5, (rule, dist, k, s, ratio)
+    spreads = np.float32([0.5, 0.3, 0.25, 0.1, 0.05, 0.02, 1e-3, 1e-5, 0.0, np.inf])
+    for k in [1, 5, 7, 64, 96, 700, 1000, 2048, 4096, 8192, 12288, 65536, 1 << 22]:
+        for a in spreads:
+            for b in spreads:
+                assert lib.mm_slice_count_rule(k, float(a), float(b)) == \
+                    em.slice_count_from_spread(k, float(a), float(b)), (k, a, b)
+    assert lib.mm_slice_count_rule(0, 0.25, 0.25) == -1
 
 
 def test_create_without_gpu_fails_cleanly(lib):

@@ -63,12 +63,22 @@ def device_inputs(mm, N, seed, scaled):
     return A, B
 
 
-def check_rows(C, Ah, Bh, rows, mode):
+def check_rows(C, Ah, Bh, rows, mode, frac=1.0):
     k = Ah.shape[1]
     got = C[rows].cpu().numpy()
     ref = oracle.gemm_rows(Ah, Bh, rows)
     D = oracle.absprod_rows(Ah, Bh, rows)
-    g = em.gamma(k, mode)
+    g = frac * em.gamma(k, mode)
+    assert bound_ok(got, ref, D, g), max_ratio(got, ref, D, g)
+
+
+def check_cols(C, Ah, Bh, cols, mode, frac=1.0):
+    k = Ah.shape[1]
+    got = C[:, cols].cpu().numpy()
+    Bc = np.ascontiguousarray(Bh[:, cols])
+    ref = oracle.gemm(Ah, Bc)
+    D = oracle.absprod(Ah, Bc)
+    g = frac * em.gamma(k, mode)
     assert bound_ok(got, ref, D, g), max_ratio(got, ref, D, g)
 
 
@@ -92,14 +102,58 @@ def test_config_plain_sweep_sampled(h, mm, N):
 
 @pytest.mark.parametrize("N", [4096, 8192])
 def test_config_split_precision_sampled(h, mm, N):
+    # 64 sampled rows and 64 sampled columns of every mode's result
     A, B = device_inputs(mm, N, 3, True)
     Ah, Bh = A.cpu().numpy(), B.cpu().numpy()
-    rows = sample_rows(N, 3 + N, 3)
+    rows = sample_rows(N, 3 + N, 61)
+    cols = sample_rows(N, 4 + N, 61)
     for prec in (mm.FP64_EMU, mm.FP32_EMU, mm.FP64):
         C = h.gemm(A, B, precision=prec)
         assert h.sync() == 0
         check_rows(C, Ah, Bh, rows, MODE[prec])
+        check_cols(C, Ah, Bh, cols, MODE[prec])
         del C
+
+
+def test_uniform_workload_takes_five_slices_on_the_device(h, mm):
+    # the benchmark workload keeps s = 5 under the automatic count
+    A, B = device_inputs(mm, 8192, 3, True)
+    s, a, b = h.debug_slice_count(A, B)
+    assert s == 5, (s, a, b)
+
+
+@pytest.mark.parametrize("N", [4096, 8192])
+def test_default_options_normal_inputs_within_bound(h, mm, N):
+    """The paper's Box-Muller normal entries (Sec. IV) at k = 4096 and 8192 with
+    default options: 64 sampled rows within the bound (the automatic count
+    takes s = 6 here, where a count from k alone gave 5 and left the bound)."""
+    A = inputs.box_muller(N, N, 40 + N, inputs.STREAM_A)
+    B = inputs.box_muller(N, N, 40 + N, inputs.STREAM_B)
+    Ad, Bd = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    s, _, _ = h.debug_slice_count(Ad, Bd)
+    assert s == 6
+    C = h.gemm(Ad, Bd, precision=mm.FP64_EMU)
+    assert h.sync() == 0
+    check_rows(C, A, B, sample_rows(N, 41 + N, 61), "fp64_emu")
+
+
+@pytest.mark.parametrize("dist,N", [("t3", 4096), ("spread", 2048), ("cauchy", 1024)])
+def test_default_options_heavy_tailed_within_bound(h, mm, dist, N):
+    """Heavy tails (Student-t with 3 degrees of freedom; entries spread over 16
+    octaves within each row; Cauchy) with default options: within the bound on
+    sampled rows; Cauchy rows need more than 7 slices and take the plain FP64
+    kernel."""
+    gen = {"t3": inputs.student_t3, "spread": inputs.wide_spread, "cauchy": inputs.cauchy}[dist]
+    A = gen(N, N, 60 + N, inputs.STREAM_A)
+    B = gen(N, N, 60 + N, inputs.STREAM_B)
+    Ad, Bd = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    s, _, _ = h.debug_slice_count(Ad, Bd)
+    assert s >= 6
+    if dist == "cauchy":
+        assert s == 8
+    C = h.gemm(Ad, Bd, precision=mm.FP64_EMU)
+    assert h.sync() == 0
+    check_rows(C, A, B, sample_rows(N, 61 + N, 29), "fp64_emu")
 
 
 def grouped_set(count, lo, hi, seed):
@@ -166,11 +220,7 @@ def test_paper_sizes_box_muller_every_output(h, mm, N):
         C = h.gemm(Ad, Bd, precision=prec)
         assert h.sync() == 0
         assert bound_ok(C.cpu().numpy(), ref, D, em.gamma(N, MODE[prec])), (N, prec)
-    # the slice rule calibrated on normal rows keeps half the bound
-    h.set_option(mm.OPT_SLICE_RULE, 1)
-    try:
-        C = h.gemm(Ad, Bd, precision=mm.FP64_EMU)
-        assert h.sync() == 0
-    finally:
-        h.set_option(mm.OPT_SLICE_RULE, 0)
+    # the automatic slice count keeps half the bound on normal rows
+    C = h.gemm(Ad, Bd, precision=mm.FP64_EMU)
+    assert h.sync() == 0
     assert bound_ok(C.cpu().numpy(), ref, D, 0.5 * em.gamma(N, "fp64_emu")), N

@@ -164,7 +164,10 @@ def test_fp64_emu_within_bound_and_exact(h, mm, m, n, k):
     C_ref = oracle.gemm(A, B)
     D = oracle.absprod(A, B)
     assert bound_ok(C, C_ref, D, em.gamma(k, "fp64")), max_ratio(C, C_ref, D, em.gamma(k, "fp64"))
-    s = mm.slices_for_k(k)
+    s, _, _ = h.debug_slice_count(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda())
+    assert s == em.slice_count(A, B)   # far from the rule's thresholds for these inputs
+    if s == em.S_PLAIN:
+        return
     E, sA = em.fp64_slices_A(A, s)
     F, sB = em.fp64_slices_B(B, s)
     rows = list(range(0, m, max(1, m // 16)))[:16]
@@ -297,6 +300,18 @@ def test_nonfinite_inputs(h, mm):
         ok[:, 6] = False
         assert np.all(np.isfinite(C[ok]))
     assert h.sync() == 0  # status was cleared
+    # the error word belongs to the stream: a failing call on one stream and a
+    # clean call on another report independently
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    Ad, Bd = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    Ac, Bc = torch.from_numpy(inputs.row_scaled(20, 30, 3)).cuda(), torch.from_numpy(inputs.col_scaled(30, 10, 3)).cuda()
+    torch.cuda.synchronize()
+    C1 = h.gemm(Ad, Bd, precision=mm.FP64_EMU, stream=s1)
+    C2 = h.gemm(Ac, Bc, precision=mm.FP64_EMU, stream=s2)
+    assert h.sync(s2) == 0
+    assert h.sync(s1) == 4
+    assert h.sync(s1) == 0 and h.sync(s2) == 0
+    del C1, C2
     C, rc = run(h, A, B, mm.FP64)
     assert rc == 0
     ref = oracle.gemm(A, B)
@@ -515,7 +530,7 @@ def test_byte_carry_segment_limit(h, mm, k):
     m, n = 260, 512
     A = inputs.row_scaled(m, k, 1600)
     B = inputs.col_scaled(k, n, 1600)
-    assert mm.slices_for_k(k) == 5
+    assert h.debug_slice_count(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda())[0] == 5
     out = _tilings(h, mm, A, B, cgs=(1, 2))
     first = out[(1, 128)]
     for key, C in out.items():

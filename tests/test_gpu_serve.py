@@ -150,3 +150,76 @@ def test_destroy_with_queued_requests(mm):
     t0 = time.time()
     h.close()                                     # cancels what is queued, finishes what runs
     assert time.time() - t0 < 30
+
+
+def test_serve_reports_nonfinite_per_request(mm):
+    """A served FP64-accuracy request with a NaN entry among clean ones: that
+    request polls MM_ERR_NONFINITE, the others MM_OK with their correct
+    results, and no error is left behind for any stream of the handle."""
+    with mm.Handle(0) as h:
+        reqs = []
+        for i in range(12):
+            A = inputs.uniform(96 + 8 * i, 200, 300 + i, inputs.STREAM_A)
+            B = inputs.uniform(200, 80, 300 + i, inputs.STREAM_B)
+            if i == 5:
+                A[7, 13] = np.nan
+            reqs.append((A, B, torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(),
+                         torch.full((A.shape[0], 80), np.nan, dtype=torch.float64, device="cuda")))
+        torch.cuda.synchronize()
+        tickets = [h.serve_submit(Ad, Bd, Cd, precision=1) for _, _, Ad, Bd, Cd in reqs]
+        done = wait_all(h, tickets)
+        assert len(done) == len(tickets)
+        for i, t in enumerate(tickets):
+            rc, _ = done[t]
+            assert rc == (4 if i == 5 else 0), (i, rc)
+        for i, (A, B, _, _, Cd) in enumerate(reqs):
+            C = Cd.cpu().numpy()
+            if i == 5:
+                assert np.all(np.isnan(C[7]))
+            else:
+                assert bound_ok(C, oracle.gemm(A, B), oracle.absprod(A, B), em.gamma(200, "fp64_emu"))
+        assert h.sync() == 0
+        s2 = torch.cuda.Stream()
+        assert h.sync(s2) == 0
+
+
+def test_serve_batches_overlap_while_others_run(mm):
+    """Continuous batching: a large FP64-accuracy request goes first; small
+    FP32-accuracy requests submitted right after it are admitted and launched
+    on other streams while it is still on the GPU, and their device intervals
+    overlap its interval. Results stay the same as alone."""
+    with mm.Handle(0) as h:
+        N = 4096
+        Ab = torch.empty((2 * N, N), dtype=torch.float64, device="cuda")
+        Bb = torch.empty((N, N), dtype=torch.float64, device="cuda")
+        mm.fill_uniform(Ab, 77, inputs.STREAM_A)
+        mm.fill_uniform(Bb, 77, inputs.STREAM_B)
+        Cb = torch.empty((2 * N, N), dtype=torch.float64, device="cuda")
+        small = []
+        for i in range(24):
+            A = torch.from_numpy(inputs.uniform(128, 256, 900 + i, inputs.STREAM_A)).cuda()
+            B = torch.from_numpy(inputs.uniform(256, 192, 900 + i, inputs.STREAM_B)).cuda()
+            small.append((A, B, torch.empty((128, 192), dtype=torch.float64, device="cuda")))
+        torch.cuda.synchronize()
+        tb = h.serve_submit(Ab, Bb, Cb, precision=1)
+        ts = []
+        for A, B, C in small:
+            ts.append(h.serve_submit(A, B, C, precision=2))
+            time.sleep(0.0002)
+        done = wait_all(h, [tb] + ts)
+        rcb, stb = done[tb]
+        assert rcb == 0
+        later = [done[t][1] for t in ts]
+        assert all(done[t][0] == 0 for t in ts)
+        # launched while the large batch was in flight, on another stream ...
+        during = [st for st in later if st.t_launch_us < stb.t_done_us and st.stream != stb.stream]
+        assert during, [(st.t_launch_us, st.stream) for st in later[:4]] + [(stb.t_launch_us, stb.t_done_us, stb.stream)]
+        # ... and running on the device inside the large batch's device interval
+        assert any(stb.t_gpu_start_us < st.t_gpu_end_us and st.t_gpu_start_us < stb.t_gpu_end_us for st in during)
+        # the mix changed no bits
+        for (A, B, C) in small[:4]:
+            Ca = torch.empty_like(C)
+            t = h.serve_submit(A, B, Ca, precision=2)
+            h.serve_drain()
+            assert h.serve_poll(t)[0] == 0
+            assert torch.equal(Ca, C)

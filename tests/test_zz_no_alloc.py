@@ -7,7 +7,8 @@ in the library image. These checks compare it with mm_gemm on two calls in a row
 (different shapes and data, so stale scratch contents from the first call would
 show), within the tolerance the other GPU tests use: 4k*2^-53 |A||B| for
 FP64-accuracy (where the two must in fact agree bit for bit) and 4k*2^-24 |A||B|
-for FP32-accuracy. This file runs last so a failure here does not hide the rest.
+for FP32-accuracy, and each against the CPU oracle within the same bound.
+This file runs last so a failure here does not hide the rest.
 """
 import numpy as np
 import pytest
@@ -40,23 +41,43 @@ def call_static(lib, A, B, prec):
     return rc, C
 
 
+# shapes that cover the paths: the automatic slice count at s = 6 and 7 and at
+# s = 5 (k >= 4096, where the 128-wide kernel folds while mm_gemm's wider
+# tiles recombine by byte carry), the plain-FP64 fallback (Cauchy rows), the
+# FP64 kernel for k <= 4, and k = 0
+CASES = [(300, 260, 700, 1, "scaled"), (130, 70, 1500, 2, "scaled"), (128, 128, 4096, 3, "scaled"),
+         (128, 96, 5000, 4, "scaled"), (64, 80, 600, 5, "cauchy"), (40, 30, 3, 6, "scaled"), (33, 17, 0, 7, "scaled")]
+
+
+def _operands(m, n, k, seed, kind):
+    if kind == "cauchy":
+        return inputs.cauchy(m, k, seed, inputs.STREAM_A), inputs.cauchy(k, n, seed, inputs.STREAM_B)
+    return inputs.row_scaled(m, k, seed), inputs.col_scaled(k, n, seed)
+
+
 @pytest.mark.parametrize("prec,mode", [(1, "fp64_emu"), (2, "fp32_emu")])
 def test_static_scratch_matches_mm_gemm_twice(mm, prec, mode):
     with mm.Handle(0) as h:
-        for m, n, k, seed in ((300, 260, 700, 1), (130, 70, 1500, 2)):
-            A = inputs.row_scaled(m, k, seed)
-            B = inputs.col_scaled(k, n, seed)
+        for m, n, k, seed, kind in CASES:
+            A, B = _operands(m, n, k, seed, kind)
             Ad = torch.from_numpy(A).cuda()
             Bd = torch.from_numpy(B).cuda()
-            rc, Cs = call_static(h.lib, Ad, Bd, prec)
-            assert rc == 0
-            Cg = h.gemm(Ad, Bd, precision=prec)
-            assert h.sync() == 0
-            cs, cg = Cs.cpu().numpy(), Cg.cpu().numpy()
-            D = oracle.absprod(A, B)
-            assert np.all(np.abs(cs - cg) <= em.gamma(k, mode) * D)
-            if prec == 1:
-                assert np.array_equal(cs, cg)
+            for _ in range(2):   # the second call meets the first one's scratch contents
+                rc, Cs = call_static(h.lib, Ad, Bd, prec)
+                assert rc == 0
+                Cg = h.gemm(Ad, Bd, precision=prec)
+                assert h.sync() == 0
+                cs, cg = Cs.cpu().numpy(), Cg.cpu().numpy()
+                if k == 0:
+                    assert np.all(cs == 0.0) and np.all(cg == 0.0)
+                    continue
+                # both against the oracle within the mode's bound ...
+                ref, D = oracle.gemm(A, B), oracle.absprod(A, B)
+                assert np.all(np.abs(cs - ref) <= em.gamma(k, mode) * D), (m, n, k, kind)
+                assert np.all(np.abs(cs - cg) <= em.gamma(k, mode) * D)
+                # ... and FP64-accuracy bit for bit with mm_gemm
+                if prec == 1:
+                    assert np.array_equal(cs, cg), (m, n, k, kind)
 
 
 def test_static_scratch_rejects_oversize(mm):
