@@ -185,15 +185,22 @@ def balanced_digits(R: np.ndarray, s: int, t: int = T_BITS) -> np.ndarray:
     return sig
 
 
-def fp64_slices_A(A: np.ndarray, s: int, t: int = T_BITS):
+# Exponent offset of the digit forms: 2 for digits held in bfloat16 (every
+# digit in [-128, 128]); 3 for digits held in signed bytes (the INT8 form):
+# with |a / 2^E| < 1/4 the top digit stays within [-64, 64] and every other
+# digit within [-128, 128), so all fit in [-128, 127].
+OFFSET_BF16, OFFSET_INT8 = 2, 3
+
+
+def fp64_slices_A(A: np.ndarray, s: int, t: int = T_BITS, offset: int = OFFSET_BF16):
     """(E, sigma) for A: sigma has shape (s, m, k)."""
-    E = row_exponents(A, 2)
+    E = row_exponents(A, offset)
     return E, balanced_digits(integer_repr(A, E, s, t), s, t)
 
 
-def fp64_slices_B(B: np.ndarray, s: int, t: int = T_BITS):
+def fp64_slices_B(B: np.ndarray, s: int, t: int = T_BITS, offset: int = OFFSET_BF16):
     """(F, sigma) for B: sigma has shape (s, k, n) (column j scaled by F_j)."""
-    F = col_exponents(B, 2)
+    F = col_exponents(B, offset)
     RT = integer_repr(np.asarray(B, dtype=np.float64).T, F, s, t)   # (n, k)
     return F, np.transpose(balanced_digits(RT, s, t), (0, 2, 1))     # (s, k, n)
 
@@ -238,12 +245,25 @@ def recombine_exact(L: np.ndarray, E: np.ndarray, F: np.ndarray, s: int,
     return C
 
 
-def gemm_fp64_emu(A: np.ndarray, B: np.ndarray, s: int, t: int = T_BITS) -> np.ndarray:
-    """The FP64-accuracy emulated product, steps 1-4 in order."""
-    E, sA = fp64_slices_A(A, s, t)
-    F, sB = fp64_slices_B(B, s, t)
+def gemm_fp64_emu(A: np.ndarray, B: np.ndarray, s: int, t: int = T_BITS, offset: int = OFFSET_BF16) -> np.ndarray:
+    """The FP64-accuracy emulated product, steps 1-4 in order (offset 3: the
+    INT8 digit form)."""
+    E, sA = fp64_slices_A(A, s, t, offset)
+    F, sB = fp64_slices_B(B, s, t, offset)
     L = level_products(sA, sB, s)
     return recombine_exact(L, E, F, s, t)
+
+
+def slice_count_int8(A: np.ndarray, B: np.ndarray) -> int:
+    """The automatic slice count of the INT8 digit form: its digit grid is twice
+    as coarse relative to the row maximum, so the spreads enter the rule halved."""
+    A = np.asarray(A, dtype=np.float64)
+    B = np.asarray(B, dtype=np.float64)
+    alpha = row_spread(A, row_exponents(A, 2))
+    beta = col_spread(B, col_exponents(B, 2))
+    amin = float(alpha.min()) if alpha.size else math.inf
+    bmin = float(beta.min()) if beta.size else math.inf
+    return slice_count_from_spread(A.shape[1], 0.5 * amin, 0.5 * bmin)
 
 
 # ---------------------------------------------------------------------------
