@@ -180,6 +180,36 @@ def whole_job_tflops(world_size: int, flop_per_product: float, steps: int, t_ms:
     return world_size * flop_per_product * steps / (t_ms * 1e-3) / 1e12
 
 
+def median_ci(xs, conf: float = 0.95):
+    """(median, lo, hi): the sample median and the distribution-free interval of
+    order statistics [x_(j), x_(n+1-j)] that covers the population median with
+    probability >= conf (binomial(n, 1/2) counts), the widest j reaching it."""
+    xs = sorted(xs)
+    n = len(xs)
+    if n == 0:
+        return None, None, None
+    med = statistics.median(xs)
+    lo, hi = xs[0], xs[-1]
+    for j in range(1, n // 2 + 1):
+        cover = sum(math.comb(n, i) for i in range(j, n + 1 - j)) / 2.0 ** n
+        if cover < conf:
+            break
+        lo, hi = xs[j - 1], xs[n - j]
+    return med, lo, hi
+
+
+def event_times(stream, reps, fn):
+    """Device time (ms) of each of `reps` calls of fn(), CUDA events on `stream`."""
+    import torch
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(reps + 1)]
+    ev[0].record(stream)
+    for i in range(reps):
+        fn()
+        ev[i + 1].record(stream)
+    ev[-1].synchronize()
+    return [ev[i].elapsed_time(ev[i + 1]) for i in range(reps)]
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -292,19 +322,20 @@ def ours(args):
     time.sleep(0.3)
     barrier()
     torch.cuda.synchronize(dev)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     tw0 = time.time()
-    e0.record(stream)
-    for _ in range(args.steps):
+    ev[0].record(stream)
+    for i in range(args.steps):
         h.gemm(A, B, C, precision=mm.FP64_EMU, stream=stream)
-    e1.record(stream)
+        ev[i + 1].record(stream)
     torch.cuda.synchronize(dev)
     tw1 = time.time()
     barrier()
     sampler.mark(tw0, tw1)
     clocks = sampler.stop()
-    t_ms = e0.elapsed_time(e1)
+    t_ms = ev[0].elapsed_time(ev[-1])
+    step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    med, lo, hi = median_ci(step_ms)
     launches = h.stats() - launches0
     status = h.sync()
     gemm_ms, gemm_n = h.profile_read(mm.KERNEL_SLICE_GEMM, reset=True)
@@ -334,30 +365,34 @@ def ours(args):
         def time_mode(prec, reps):
             h.gemm(A, B, C, precision=prec)
             torch.cuda.synchronize(dev)
-            ts = []
-            for _ in range(reps):
-                a0 = torch.cuda.Event(enable_timing=True)
-                a1 = torch.cuda.Event(enable_timing=True)
-                a0.record(stream)
-                h.gemm(A, B, C, precision=prec, stream=stream)
-                a1.record(stream)
-                a1.synchronize()
-                ts.append(a0.elapsed_time(a1))
-            return statistics.median(ts)
+            ts = event_times(stream, reps, lambda: h.gemm(A, B, C, precision=prec, stream=stream))
+            m_, l_, u_ = median_ci(ts)
+            return m_, {"median": m_, "lo": l_, "hi": u_, "n": reps}
 
-        fp32_ms = time_mode(mm.FP32_EMU, 5)
-        fp64_ms = time_mode(mm.FP64, 2)
+        fp32_ms, fp32_ci = time_mode(mm.FP32_EMU, 15)
+        fp64_ms, fp64_ci = time_mode(mm.FP64, 15)
+        # the INT8 digit form on the legacy integer tensor path, for comparison
+        h.set_option(mm.OPT_INT8_SLICES, 1)
+        try:
+            int8_ms, int8_ci = time_mode(mm.FP64_EMU, 3)
+        finally:
+            h.set_option(mm.OPT_INT8_SLICES, 0)
         dfma, dmma = h.peak_fp64()
         fp64_peak = max(dfma, dmma)
         extra["modes"] = {
             "fp64_emu_tflops": flop / (ms_step * 1e-3) / 1e12,
             "fp32_emu_tflops": flop / (fp32_ms * 1e-3) / 1e12,
             "plain_fp64_tflops": flop / (fp64_ms * 1e-3) / 1e12,
+            "fp32_emu_ms_median_ci95": fp32_ci, "plain_fp64_ms_median_ci95": fp64_ci,
+            "fp64_emu_int8_mma_sync_tflops": flop / (int8_ms * 1e-3) / 1e12, "fp64_emu_int8_ms_median_ci95": int8_ci,
             "emu_over_plain": fp64_ms / ms_step,
             "fp64_peak_tflops_measured": {"dfma": dfma, "dmma": dmma},
             "plain_fp64_frac_of_fp64_peak": (flop / (fp64_ms * 1e-3) / 1e12) / fp64_peak,
             "slices": s, "slice_pairs": pairs,
         }
+        # ---------------- the configurations' other sizes: plain FP64 sweep and the
+        # split-precision product at 4096, median and interval of 15 reps each
+        extra["config_sweep"] = config_sweep_leg(h, args, mm, inputs, torch, dev, stream)
         # ---------------- end to end through the host-buffer entry point
         Ah = torch.empty((N, N), dtype=torch.float64, pin_memory=True)
         Bh = torch.empty_like(Ah, pin_memory=True)
@@ -378,7 +413,7 @@ def ours(args):
             extra["paper_sweep"] = paper_sweep_leg(h, args, mm, inputs, torch, dev, stream)
         # ---------------- grouped: 512 products, dims log-uniform on [32, 1024], one graph replay each
         if not args.no_grouped:
-            extra["grouped"] = grouped_leg(h, args, mm, inputs, torch, dev, stream)
+            extra["grouped"] = grouped_leg(h, args, mm, inputs, torch, dev, stream, fp64_peak)
         # ---------------- serving: capacity (closed loop), then Poisson arrivals at 80 % of it
         if not args.no_serve:
             extra["serve"] = serve_leg(h, args, mm, inputs)
@@ -387,10 +422,28 @@ def ours(args):
             rows, Cr, dt, used = cpu_oracle_rows(An, Bn, args.cpu_seconds, 2048)
             import oracle
             from oracle import emulation as em
-            D = oracle.absprod_rows(An, Bn, list(range(min(rows, 8))))
+            D = oracle.absprod_rows_par(An, Bn, list(range(min(rows, 8))))
             got = Cn[:min(rows, 8)]
             ref = Cr[:min(rows, 8)]
             ratio = float(np.max(np.abs(got - ref) / (em.gamma(N, "fp64") * D)))
+            # every mode's result at N on 64 sampled rows and 64 sampled columns
+            def sample64(seed):
+                picked = {0, N - 1}
+                for v in inputs.int_uniform(0, N - 1, 256, seed, inputs.STREAM_DIMS):
+                    if len(picked) >= 64:
+                        break
+                    picked.add(int(v))
+                return sorted(picked)
+            srows, scols = sample64(31), sample64(32)
+            r_ref, r_D = oracle.gemm_rows_par(An, Bn, srows), oracle.absprod_rows_par(An, Bn, srows)
+            Bc = np.ascontiguousarray(Bn[:, scols])
+            c_ref = oracle.gemm_rows_par(An, Bc, list(range(N)))
+            c_D = oracle.absprod_rows_par(An, Bc, list(range(N)))
+            errs = {}
+            for prec, name in ((mm.FP64_EMU, "fp64_emu"), (mm.FP32_EMU, "fp32_emu"), (mm.FP64, "plain_fp64")):
+                errs[name] = sampled_error(h, mm, torch, A, B, C, prec, stream, srows, r_ref, r_D, scols, c_ref, c_D)
+            extra["modes"]["max_err_over_bound"] = errs
+            extra["modes"]["err_sample"] = f"{len(srows)} rows and {len(scols)} columns of each {N}^3 product vs the oracle"
             extra["cpu_baseline"] = {"value": 2.0 * rows * N * N / dt / 1e12, "unit": "TFLOP/s", "cores": used,
                                      "kind": "oracle",
                                      "sample": f"{rows} rows of the {N}^3 product by the OpenMP triple loop "
@@ -420,6 +473,9 @@ def ours(args):
                          "frac": achieved / peak, "traffic": traffic, "peak_note": peak_note,
                          "kernel": "slice_gemm (tcgen05 bf16 slice products, FP64-accuracy epilogue)",
                          "kernel_ms": kernel_ms, "algorithmic": f"2*N^3*{pairs} slice flop per launch"},
+            "step_ms_median_ci95": {"median": med, "lo": lo, "hi": hi, "n": args.steps,
+                                    "tflops_at_median": flop / (med * 1e-3) / 1e12 if med else None,
+                                    "method": "order-statistic interval of the per-step device times (CUDA events)"},
             "split_kernels_ms_per_step": split_ms / max(args.steps, 1),
             "clocks": clocks, "gpu_launches": launches, "device_status": status,
         }
@@ -478,13 +534,75 @@ def paper_sweep_leg(h, args, mm, inputs, torch, dev, stream):
     return out
 
 
-def grouped_leg(h, args, mm, inputs, torch, dev, stream):
+def sampled_error(h, mm, torch, A, B, C, prec, stream, rows, ref_rows, D_rows, cols=None, ref_cols=None, D_cols=None):
+    """max |C - C_oracle| / (gamma |A||B|) over the sampled rows (and columns) of one mode's product."""
+    import numpy as np
+    from oracle import emulation as em
+    h.gemm(A, B, C, precision=prec, stream=stream)
+    torch.cuda.synchronize()
+    mode = {mm.FP64: "fp64", mm.FP64_EMU: "fp64_emu", mm.FP32_EMU: "fp32_emu"}[prec]
+    g = em.gamma(A.shape[1], mode)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        r = float(np.nanmax(np.abs(C[rows].cpu().numpy() - ref_rows) / (g * D_rows)))
+        if cols is not None:
+            r = max(r, float(np.nanmax(np.abs(C[:, cols].cpu().numpy() - ref_cols) / (g * D_cols))))
+    return r
+
+
+def config_sweep_leg(h, args, mm, inputs, torch, dev, stream):
+    """The configurations' sizes besides the headline: plain FP64 at 1024, 2048
+    and 4096 on uniform[-1,1) entries, and the split-precision workload at 4096
+    in all three modes; each the median and 95 % interval of 15 timed products
+    (the paper's 15 repetitions, Sec. V) and, with the CPU leg on, the measured
+    error of 16 sampled rows against the oracle."""
+    out = {}
+    cases = [("plain_fp64", n, False, mm.FP64) for n in (1024, 2048, 4096)]
+    cases += [("split_" + nm, 4096, True, p) for nm, p in (("fp64_emu", mm.FP64_EMU), ("fp32_emu", mm.FP32_EMU),
+                                                          ("plain_fp64", mm.FP64))]
+    cache = {}
+    for name, N, scaled, prec in cases:
+        key = (N, scaled)
+        if key not in cache:
+            seed = 3 if scaled else 2 + int(math.log2(N))
+            A = torch.empty((N, N), dtype=torch.float64, device=dev)
+            B = torch.empty_like(A)
+            if scaled:
+                mm.fill_uniform(A, seed, inputs.STREAM_A, 1, inputs.STREAM_EXP_A)
+                mm.fill_uniform(B, seed, inputs.STREAM_B, 2, inputs.STREAM_EXP_B)
+            else:
+                mm.fill_uniform(A, seed, inputs.STREAM_A)
+                mm.fill_uniform(B, seed, inputs.STREAM_B)
+            ref = None
+            if not args.no_cpu_baseline:
+                import oracle
+                An, Bn = A.cpu().numpy(), B.cpu().numpy()
+                rows = sorted({int(r) for r in inputs.int_uniform(0, N - 1, 14, seed, inputs.STREAM_DIMS)} | {0, N - 1})
+                ref = (rows, oracle.gemm_rows_par(An, Bn, rows), oracle.absprod_rows_par(An, Bn, rows))
+            cache = {key: (A, B, torch.empty_like(A), ref)}
+        A, B, C, ref = cache[key]
+        h.gemm(A, B, C, precision=prec, stream=stream)
+        torch.cuda.synchronize(dev)
+        ts = event_times(stream, 15, lambda: h.gemm(A, B, C, precision=prec, stream=stream))
+        med, lo, hi = median_ci(ts)
+        row = {"n": N, "ms_median": med, "ms_ci95": [lo, hi], "reps": 15,
+               "tflops_at_median": 2.0 * N ** 3 / (med * 1e-3) / 1e12,
+               "inputs": "uniform[-1,1)*2^e per row/column" if scaled else "uniform[-1,1)"}
+        if ref is not None:
+            row["max_err_over_bound"] = sampled_error(h, mm, torch, A, B, C, prec, stream, ref[0], ref[1], ref[2])
+            row["err_sample"] = f"{len(ref[0])} rows x {N} columns"
+        out[f"{name}_{N}"] = row
+    return out
+
+
+def grouped_leg(h, args, mm, inputs, torch, dev, stream, fp64_peak=None):
     """The grouped workload: 512 independent products with M, N, K each
     log-uniform on [32, 1024], entries uniform[-1,1), in one grouped call
     (persistent kernels replayed from a CUDA graph). TFLOP/s = sum 2mnk over
     the group / device time of a call, per mode, with the default tiles and
-    with autotuned tiles; sampled rows of a few problems are checked against
-    the oracle."""
+    with autotuned tiles; the emulated modes also as slice-product TFLOP/s
+    (each problem's pairs) against the bf16 peak (measured burst; the whole
+    call's time, split stages included), the plain mode against the FP64 peak;
+    sampled rows of a few problems are checked against the oracle."""
     import numpy as np
     dims = inputs.problem_set(512, 32, 1024, 4)
     probs, flop = [], 0.0
@@ -514,11 +632,28 @@ def grouped_leg(h, args, mm, inputs, torch, dev, stream):
         return e0.elapsed_time(e1) / reps
 
     out = {"problems": 512, "dims": "log-uniform [32, 1024]", "flop_per_call": flop}
+    # slice products per call: each problem's automatic count (FP64-accuracy), 6 pairs (FP32-accuracy)
+    slice_flop = {mm.FP64_EMU: 0.0, mm.FP32_EMU: 6.0 * flop}
+    counts = {}
+    for (A, B, _), (m, n, k) in zip(probs, dims):
+        sc = h.debug_slice_count(A, B)[0] if int(k) > 4 else 0
+        counts[sc] = counts.get(sc, 0) + 1
+        if 3 <= sc <= 7:
+            slice_flop[mm.FP64_EMU] += 2.0 * int(m) * int(n) * int(k) * sc * (sc + 1) // 2
+    out["fp64_emu_slice_counts"] = {str(c): v for c, v in sorted(counts.items())}
+    peaks = measured_peaks()
+    bf16 = peaks.get("bf16_tflops", 1900.0)
     names = {mm.FP64: "fp64", mm.FP64_EMU: "fp64_emu", mm.FP32_EMU: "fp32_emu"}
     for prec, name in names.items():
         ms = timed(prec)
         out[name + "_tflops"] = flop / (ms * 1e-3) / 1e12
         out[name + "_ms"] = ms
+        if prec in slice_flop:
+            rate = slice_flop[prec] / (ms * 1e-3) / 1e12
+            out[name + "_slice_tflops"] = rate
+            out[name + "_frac_of_bf16"] = rate / bf16
+        elif fp64_peak:
+            out[name + "_frac_of_fp64_peak"] = out[name + "_tflops"] / fp64_peak
     h.set_option(mm.OPT_AUTOTUNE, 1)
     for prec, name in names.items():
         ms = timed(prec)
@@ -580,6 +715,51 @@ def serve_leg(h, args, mm, inputs):
     return out
 
 
+def profile_case(args):
+    """One workload alone, for profiler captures (prints a short status line,
+    not a benchmark line): a single product of size --n in one mode on the
+    benchmark's inputs, or the 512-problem grouped call in one mode; --warmup
+    untimed calls, then --steps calls."""
+    import torch
+    import paper_2408_15384_gb300 as mm
+    from paper_2408_15384_gb300 import inputs
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    h = mm.Handle(0, budget_bytes=40 << 30)
+    stream = torch.cuda.current_stream(dev)
+    kind, mode = args.profile_case.split(":")
+    prec = {"fp64": mm.FP64, "fp64_emu": mm.FP64_EMU, "fp32_emu": mm.FP32_EMU}[mode]
+    if kind == "single":
+        N = args.n
+        A = torch.empty((N, N), dtype=torch.float64, device=dev)
+        B = torch.empty_like(A)
+        C = torch.empty_like(A)
+        mm.fill_uniform(A, 3, inputs.STREAM_A, 1, inputs.STREAM_EXP_A)
+        mm.fill_uniform(B, 3, inputs.STREAM_B, 2, inputs.STREAM_EXP_B)
+        run = lambda: h.gemm(A, B, C, precision=prec, stream=stream)   # noqa: E731
+    else:
+        probs = []
+        for i, (m, n, k) in enumerate(inputs.problem_set(512, 32, 1024, 4)):
+            A = torch.empty((int(m), int(k)), dtype=torch.float64, device=dev)
+            B = torch.empty((int(k), int(n)), dtype=torch.float64, device=dev)
+            mm.fill_uniform(A, 4000 + i, inputs.STREAM_A)
+            mm.fill_uniform(B, 4000 + i, inputs.STREAM_B)
+            probs.append((A, B, torch.empty((int(m), int(n)), dtype=torch.float64, device=dev)))
+        arr = mm.Handle.problem_array(probs)
+        run = lambda: h.grouped(arr, precision=prec, stream=stream)   # noqa: E731
+    for _ in range(args.warmup):
+        run()
+    torch.cuda.synchronize(dev)
+    for _ in range(args.steps):
+        run()
+    torch.cuda.synchronize(dev)
+    status = h.sync()
+    h.close()
+    print(json.dumps({"profile_case": args.profile_case, "n": args.n, "status": status}), flush=True)
+    if status != 0:
+        sys.exit(1)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -594,8 +774,14 @@ def main():
     ap.add_argument("--no-grouped", action="store_true", help="skip the grouped leg")
     ap.add_argument("--no-paper-sweep", action="store_true", help="skip the paper-size sweep")
     ap.add_argument("--serve-requests", type=int, default=100000)
+    ap.add_argument("--profile-case", default=None,
+                    help="single:MODE or grouped:MODE (MODE fp64, fp64_emu, fp32_emu): run only that workload")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.profile_case:
+        from paper_2408_15384_gb300 import build
+        build.build()
+        profile_case(args)
+    elif args.impl == "reference":
         reference_arm(args)
     else:
         from paper_2408_15384_gb300 import build

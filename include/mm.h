@@ -216,8 +216,16 @@ enum {
     MM_OPT_PROFILE = 7,           /* 1 = time every kernel launch with CUDA events (see mm_profile_read) */
     MM_OPT_CTA_PAIR = 8,          /* emulated products: 0 = automatic, 1 = one CTA per 128-row tile,
                                      2 = CTA pairs (cta_group::2) on 256-row tiles */
-    MM_OPT_TILE_N = 9             /* FP64-accuracy tile width: 0 = automatic, 128, 192, 240 or 256
+    MM_OPT_TILE_N = 9,            /* FP64-accuracy tile width: 0 = automatic, 128, 192, 240 or 256
                                      columns. Every choice gives the same bits. */
+    MM_OPT_INT8_SLICES = 11       /* 1 = FP64-accuracy single products (mm_gemm, mm_gemm_host) on
+                                     signed-byte digits with the legacy integer tensor path
+                                     (mma.sync m16n8k32 s8, int32 sums): scale exponent one larger
+                                     (E = floor(log2 max) + 3, every digit in [-128, 127]), the
+                                     automatic count from halved spreads, the same exact
+                                     recombination. Slower on GB300 than the default bfloat16
+                                     digits on tcgen05; kept for comparison. Grouped and served
+                                     products always use the default. */
 };
 
 /* Kernel classes for mm_profile_read. */
@@ -303,6 +311,13 @@ int mm_debug_slice_count(mm_handle h, int64_t m, int64_t n, int64_t k,
 int mm_debug_level_products(mm_handle h, int64_t m, int64_t n, int64_t k,
                             const double *A, int64_t lda, const double *B, int64_t ldb,
                             int s, int64_t *levels, void *stream);
+
+/* The level products of the INT8 digit form (E = floor(log2 max) + 3,
+ * digits as signed bytes) as the mma.sync s8 kernel accumulates them (exact
+ * integers), int64 [s][m][n] to `levels` (device). Synchronous. */
+int mm_debug_level_products_int8(mm_handle h, int64_t m, int64_t n, int64_t k,
+                                 const double *A, int64_t lda, const double *B, int64_t ldb,
+                                 int s, int64_t *levels, void *stream);
 
 /* Failure-detection check of the device-side waits: launches one thread
  * that waits, with the same bounded wait every kernel of the library uses, on

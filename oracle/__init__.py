@@ -55,7 +55,7 @@ def _load():
         for name in ("oracle_gemm_rows", "oracle_absprod_rows"):
             getattr(lib, name).argtypes = [i64, i64, i64, i64, P, i64, P, i64, P, i64]
             getattr(lib, name).restype = None
-        for name in ("oracle_gemm_omp", "cpu_gemm_colprefetch", "cpu_gemm_tiled"):
+        for name in ("oracle_gemm_omp", "oracle_absprod_omp", "cpu_gemm_colprefetch", "cpu_gemm_tiled"):
             getattr(lib, name).argtypes = [i64, i64, i64, i64, P, i64, P, i64, P, i64, ctypes.c_int]
             getattr(lib, name).restype = ctypes.c_int
         lib.oracle_dot.argtypes = [i64, i64, i64, P, i64, P, i64]
@@ -138,6 +138,26 @@ def gemm_omp_rows(A, B, r0: int, r1: int, nthreads: int = 0):
     used = _load().oracle_gemm_omp(r0, r1, n, k, _p(A), max(k, 1), _p(B), max(n, 1),
                                    _p(out), max(n, 1), nthreads)
     return out, used
+
+
+def gemm_rows_par(A, B, rows) -> np.ndarray:
+    """Rows `rows` of A*B by the OpenMP row loop (each element the serial
+    triple loop's, bit for bit), for sampled rows of large products."""
+    A, B = _prep(A, B)
+    As = np.ascontiguousarray(A[list(rows)])
+    out, _ = gemm_omp_rows(As, B, 0, As.shape[0])
+    return out
+
+
+def absprod_rows_par(A, B, rows) -> np.ndarray:
+    """Rows `rows` of |A|*|B| by the OpenMP row loop."""
+    A, B = _prep(A, B)
+    As = np.ascontiguousarray(A[list(rows)])
+    k, n = B.shape
+    out = np.zeros((As.shape[0], n))
+    if As.shape[0] and n:
+        _load().oracle_absprod_omp(0, As.shape[0], n, k, _p(As), max(k, 1), _p(B), max(n, 1), _p(out), max(n, 1), 0)
+    return out
 
 
 def _rows_variant(fn, A, B, r0, r1, nthreads):

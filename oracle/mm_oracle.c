@@ -133,3 +133,27 @@ void oracle_absprod_rows(int64_t r0, int64_t r1, int64_t n, int64_t k,
         }
     }
 }
+
+/* |A|*|B| for rows [r0, r1) with the same OpenMP parallel-for over rows as
+ * oracle_gemm_omp; every element is the serial loop's. Returns the threads. */
+int oracle_absprod_omp(int64_t r0, int64_t r1, int64_t n, int64_t k,
+                       const double *A, int64_t lda, const double *B, int64_t ldb,
+                       double *D, int64_t ldd, int nthreads)
+{
+    int used = 1;
+#ifdef _OPENMP
+    if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel num_threads(nthreads)
+    {
+#pragma omp single
+        used = omp_get_num_threads();
+#pragma omp for schedule(static)
+        for (int64_t i = r0; i < r1; ++i)
+            oracle_absprod_rows(i, i + 1, n, k, A, lda, B, ldb, D + (i - r0) * ldd, ldd);
+    }
+#else
+    (void)nthreads;
+    oracle_absprod_rows(r0, r1, n, k, A, lda, B, ldb, D, ldd);
+#endif
+    return used;
+}

@@ -25,6 +25,7 @@ OPT_SLICES, OPT_TIMEOUT_MS, OPT_AUTOTUNE, OPT_SERVE_MAX_BATCH, OPT_SERVE_STREAMS
 OPT_PROFILE = 7
 OPT_CTA_PAIR = 8
 OPT_TILE_N = 9
+OPT_INT8_SLICES = 11
 KERNEL_SLICE_GEMM, KERNEL_SPLIT, KERNEL_FP64_GEMM = 0, 1, 2
 
 
@@ -255,6 +256,16 @@ class Handle:
         if rc not in (OK, 4):
             raise MMError(rc, "mm_debug_slices")
         return exps, sl, rc
+
+    def debug_levels_int8(self, A, B, s: int, stream=None):
+        """Level products of the INT8 digit form as int64 [s][m][n]."""
+        import torch
+        pa, m, k, lda = _mat(A, "A")
+        pb, _, n, ldb = _mat(B, "B")
+        L = torch.empty((s, m, n), dtype=torch.int64, device=A.device)
+        _check(self.lib.mm_debug_level_products_int8(self.h, m, n, k, pa, lda, pb, ldb, s, L.data_ptr(),
+                                                     _stream_handle(stream)), "mm_debug_level_products_int8")
+        return L
 
     def debug_slice_count(self, A, B, stream=None):
         """(s, alpha_min, beta_min) as the device decides them for A*B."""

@@ -74,6 +74,7 @@ SIGNATURES = {
     "mm_debug_slice_count": (c_int, [c_vp, c_i64, c_i64, c_i64, c_vp, c_i64, c_vp, c_i64, ctypes.POINTER(c_int),
                                      ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float), c_vp]),
     "mm_debug_level_products": (c_int, [c_vp, c_i64, c_i64, c_i64, c_vp, c_i64, c_vp, c_i64, c_int, c_vp, c_vp]),
+    "mm_debug_level_products_int8": (c_int, [c_vp, c_i64, c_i64, c_i64, c_vp, c_i64, c_vp, c_i64, c_int, c_vp, c_vp]),
     "mm_debug_wait_timeout": (c_int, [c_vp, c_i64, c_vp]),
     "mm_peak_fp64": (c_int, [c_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "mm_stats": (c_int, [c_vp, ctypes.POINTER(c_u64)]),

@@ -184,22 +184,47 @@ __device__ __forceinline__ void fp64_tile(const Fp64GemmArgs& a, int64_t m0, int
 
 template <int KIND>
 __global__ void __launch_bounds__(FTHREADS) fp64_gemm_kernel(const Fp64GemmArgs a) {
-  // the fallback of an emulated product: only when its slice count asks for it
-  if (a.only_if_plain != nullptr && *a.only_if_plain != SLICE_S_PLAIN) return;
   extern __shared__ __align__(16) uint8_t fsm_raw[];
   Fp64Smem& sm = *reinterpret_cast<Fp64Smem*>(fsm_raw);
   fp64_tile<KIND>(a, static_cast<int64_t>(blockIdx.y) * FT, static_cast<int64_t>(blockIdx.x) * FT, sm);
 }
 
+// The fallback of an emulated product: a persistent grid over the tiles that
+// does nothing unless the product's recorded slice count asks for it, so the
+// usual case costs one small grid that returns at once.
+template <int KIND>
+__global__ void __launch_bounds__(FTHREADS) fp64_fallback_kernel(const Fp64GemmArgs a, int tiles_n, int tiles) {
+  if (*a.only_if_plain != SLICE_S_PLAIN) return;
+  extern __shared__ __align__(16) uint8_t fsm_raw[];
+  Fp64Smem& sm = *reinterpret_cast<Fp64Smem*>(fsm_raw);
+  for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
+    fp64_tile<KIND>(a, static_cast<int64_t>(t / tiles_n) * FT, static_cast<int64_t>(t % tiles_n) * FT, sm);
+    __syncthreads();
+  }
+}
+
 // Grouped: a persistent grid walks the tile list of many products; the tile
 // count is read from device memory so a captured graph can be replayed with
 // new work.
+// With count_dev set, the problems carry fallback guards: a block first looks
+// at every problem's guard and returns at once when no problem asks for the
+// plain kernel (the usual case), else runs the tiles of those that do.
 template <int KIND>
 __global__ void __launch_bounds__(FTHREADS) fp64_grouped_kernel(const Fp64GemmArgs* __restrict__ probs,
                                                                 const TileRef* __restrict__ tiles,
-                                                                const int* __restrict__ ntiles_dev) {
+                                                                const int* __restrict__ ntiles_dev,
+                                                                const int* __restrict__ count_dev) {
   extern __shared__ __align__(16) uint8_t fsm_raw[];
   Fp64Smem& sm = *reinterpret_cast<Fp64Smem*>(fsm_raw);
+  if (count_dev != nullptr) {
+    const int count = *count_dev;
+    int any = 0;
+    for (int p = threadIdx.x; p < count; p += blockDim.x) {
+      const int32_t* g = probs[p].only_if_plain;
+      any |= (g != nullptr && *g == SLICE_S_PLAIN) ? 1 : 0;
+    }
+    if (!__syncthreads_or(any)) return;
+  }
   const int nt = *ntiles_dev;
   for (int t = blockIdx.x; t < nt; t += gridDim.x) {
     const TileRef r = tiles[t];
@@ -265,26 +290,41 @@ cudaError_t fp64_gemm_prepare() {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(fp64_gemm_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(fp64_grouped_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(fp64_grouped_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(fp64_fallback_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(fp64_fallback_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   return e;
 }
 
 int fp64_tile_size() { return FT; }
 
 cudaError_t launch_fp64_grouped(int kind, const Fp64GemmArgs* probs, const TileRef* tiles, const int* ntiles_dev,
-                                int grid, cudaStream_t st) {
+                                int grid, cudaStream_t st, const int* count_dev) {
   const int smem = static_cast<int>(sizeof(Fp64Smem));
   if (kind == 1)
-    fp64_grouped_kernel<1><<<grid, FTHREADS, smem, st>>>(probs, tiles, ntiles_dev);
+    fp64_grouped_kernel<1><<<grid, FTHREADS, smem, st>>>(probs, tiles, ntiles_dev, count_dev);
   else
-    fp64_grouped_kernel<2><<<grid, FTHREADS, smem, st>>>(probs, tiles, ntiles_dev);
+    fp64_grouped_kernel<2><<<grid, FTHREADS, smem, st>>>(probs, tiles, ntiles_dev, count_dev);
   return cudaGetLastError();
 }
 
 cudaError_t launch_fp64_gemm(int kind, const Fp64GemmArgs& a, cudaStream_t st) {
   if (a.m <= 0 || a.n <= 0) return cudaSuccess;
   if (a.k <= 0) return launch_zero_c(a.C, a.m, a.n, a.ldc, st);
-  dim3 grid(static_cast<unsigned>((a.n + FT - 1) / FT), static_cast<unsigned>((a.m + FT - 1) / FT));
   const int smem = static_cast<int>(sizeof(Fp64Smem));
+  if (a.only_if_plain != nullptr) {
+    const int64_t tn = (a.n + FT - 1) / FT, tiles = tn * ((a.m + FT - 1) / FT);
+    if (tiles > 0x7fffffff) return cudaErrorInvalidValue;
+    int dev = 0, sms = 148;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return cudaErrorInvalidValue;
+    const unsigned grid = static_cast<unsigned>(tiles < 2 * sms ? tiles : 2 * sms);
+    if (kind == 1)
+      fp64_fallback_kernel<1><<<grid, FTHREADS, smem, st>>>(a, static_cast<int>(tn), static_cast<int>(tiles));
+    else
+      fp64_fallback_kernel<2><<<grid, FTHREADS, smem, st>>>(a, static_cast<int>(tn), static_cast<int>(tiles));
+    return cudaGetLastError();
+  }
+  dim3 grid(static_cast<unsigned>((a.n + FT - 1) / FT), static_cast<unsigned>((a.m + FT - 1) / FT));
   if (kind == 1)
     fp64_gemm_kernel<1><<<grid, FTHREADS, smem, st>>>(a);
   else

@@ -302,7 +302,8 @@ static cudaError_t launch_emu_group(mm_handle_s* h, bool fp64, const GroupLaunch
   if (e == cudaSuccess && gl.fallback)
     e = launch_fp64_grouped(fp64_kind(h), reinterpret_cast<const Fp64GemmArgs*>(db + L.off_fargs),
                             reinterpret_cast<const TileRef*>(db + L.off_ftiles),
-                            reinterpret_cast<const int*>(db + L.off_hdr) + 2, h->sm_count * 2, st);
+                            reinterpret_cast<const int*>(db + L.off_hdr) + 2, h->sm_count * 2, st,
+                            reinterpret_cast<const int*>(db + L.off_hdr));
   return e;
 }
 

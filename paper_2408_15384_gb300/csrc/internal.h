@@ -67,6 +67,7 @@ struct mm_handle_s {
   bool opt_profile = false;
   int opt_cta_pair = 0;
   int opt_tile_n = 0;        // FP64-accuracy tile width (0 = automatic, 128, 192, 240, 256)
+  bool opt_int8 = false;     // FP64-accuracy single products on INT8-form digits (mma.sync s8)
   int max_pairs_fp32 = 0, max_pairs_fp64 = 0;   // co-resident CTA pairs of the pair kernels
 
   // profiling: (start, end) event pairs per kernel class, drained by mm_profile_read
@@ -145,7 +146,8 @@ struct SplitLayout {
   bool autos = false;
   size_t off_rowmax = 0, off_colmax = 0, off_E = 0, off_F = 0, off_sa = 0, off_sb = 0, off_dec = 0, off_part = 0,
          bytes = 0;
-  void plan(int64_t m_, int64_t n_, int64_t k_, int s);
+  int elem = 2;   // bytes per slice entry: 2 (bfloat16), 1 (INT8-form digits)
+  void plan(int64_t m_, int64_t n_, int64_t k_, int s, int elem_bytes = 2);
   SliceDecision* dec(char* ws) const { return autos ? reinterpret_cast<SliceDecision*>(ws + off_dec) : nullptr; }
   uint2* part(char* ws) const { return autos ? reinterpret_cast<uint2*>(ws + off_part) : nullptr; }
 };

@@ -86,11 +86,14 @@ int64_t launch_absmax_parts(int64_t k);
 // (FP64-accuracy) the slice count is slice_count_rule(k, amin, bmin) of the
 // scan's spreads instead of s; the first block records it in dec->s, and no
 // slices are written when it is SLICE_S_PLAIN.
+// mode: 0 FP64-accuracy digits as bfloat16 (uint16 planes), 1 FP32-accuracy
+// bfloat16 slices, 2 FP64-accuracy digits as signed bytes (int8 planes; the
+// INT8 form, scale exponent one larger, automatic count from halved spreads).
 cudaError_t launch_slice_rows(int mode, const double* A, int64_t m, int64_t k, int64_t lda, const uint64_t* rowmax,
-                              int s, int64_t kp, uint16_t* slices, int32_t* E, uint32_t* err, cudaStream_t st,
+                              int s, int64_t kp, void* slices, int32_t* E, uint32_t* err, cudaStream_t st,
                               int64_t plane_rows = 0, SliceDecision* dec = nullptr);
 cudaError_t launch_slice_cols(int mode, const double* B, int64_t k, int64_t n, int64_t ldb, const uint64_t* colmax,
-                              int s, int64_t kp, uint16_t* slices, int32_t* F, uint32_t* err, cudaStream_t st,
+                              int s, int64_t kp, void* slices, int32_t* F, uint32_t* err, cudaStream_t st,
                               SliceDecision* dec = nullptr);
 cudaError_t launch_fill_uniform(double* X, int64_t rows, int64_t cols, int64_t ld, uint64_t seed, uint64_t stream_id,
                                 int scale_mode, uint64_t exp_stream_id, cudaStream_t st);
@@ -204,6 +207,26 @@ int slice_gemm_max_pairs(int mode);
 // whether launch_slice_gemm has a kernel for (mode, tile width, CTAs per tile)
 bool slice_gemm_tile_ok(int mode, int bn, int cg);
 
+// ------------------------------------------------------------- int8_gemm.cu
+// FP64-accuracy product from INT8-form digit planes on mma.sync m16n8k32 s8.
+struct Int8GemmArgs {
+  int64_t m, n, k, kp;       // kp: bytes between rows of a digit plane (a multiple of 16)
+  const int8_t* A;           // A's digits [s][m][kp]
+  int64_t plane_a;           // bytes between A's planes
+  const int8_t* B;           // B's digits, transposed: [s][n][kp]
+  int64_t plane_b;
+  const int32_t* E;          // row scale exponents of A (INT8 form)
+  const int32_t* F;          // column scale exponents of B
+  double* C;
+  int64_t ldc;
+  int64_t* levels;           // level output [s][m][n] int64 (added to; zeroed by the caller), else null
+  int s;                     // slice count when s_dev is null
+  int fix_shift;             // fixed-point shift for s (when s_dev is null)
+  const int32_t* s_dev;      // automatic slice count in device memory, else null
+  int8_t fix_tab[8];         // with s_dev: the shift for each count
+};
+cudaError_t launch_int8_slice_gemm(const Int8GemmArgs& a, cudaStream_t st);
+
 // ------------------------------------------------------------- fp64_gemm.cu
 struct Fp64GemmArgs {
   int64_t m, n, k;
@@ -219,8 +242,10 @@ struct Fp64GemmArgs {
 cudaError_t launch_fp64_gemm(int kind, const Fp64GemmArgs& a, cudaStream_t st);
 // Grouped: one persistent launch over a tile list of many problems (device
 // arrays; the tile count is read from device memory).
+// count_dev (the problem count in device memory) marks a launch of fallback
+// guards: the grid returns at once unless some problem's guard is set.
 cudaError_t launch_fp64_grouped(int kind, const Fp64GemmArgs* probs, const TileRef* tiles, const int* ntiles_dev,
-                                int grid, cudaStream_t st);
+                                int grid, cudaStream_t st, const int* count_dev = nullptr);
 int fp64_tile_size();
 cudaError_t fp64_gemm_prepare();
 cudaError_t launch_zero_c(double* C, int64_t m, int64_t n, int64_t ldc, cudaStream_t st);

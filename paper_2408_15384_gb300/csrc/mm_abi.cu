@@ -190,11 +190,13 @@ ProfScope::~ProfScope() {
 }
 
 // Layout of the emulated-mode workspace of one product.
-void SplitLayout::plan(int64_t m_, int64_t n_, int64_t k_, int s) {
+void SplitLayout::plan(int64_t m_, int64_t n_, int64_t k_, int s, int elem_bytes) {
   m = m_; n = n_; k = k_;
   autos = (s == 0);
   S = emu_planes(s);
-  kp = static_cast<int64_t>(align_up(static_cast<size_t>(std::max<int64_t>(k, 1)), 8));
+  elem = elem_bytes;
+  // rows of whole 16-byte vectors: 8 bfloat16 entries, 16 INT8-form digits
+  kp = static_cast<int64_t>(align_up(static_cast<size_t>(std::max<int64_t>(k, 1)), elem == 1 ? 16 : 8));
   size_t off = 0;
   off_rowmax = off; off = align_up(off + 8 * static_cast<size_t>(m), 256);
   off_colmax = off; off = align_up(off + 8 * static_cast<size_t>(n), 256);
@@ -202,8 +204,8 @@ void SplitLayout::plan(int64_t m_, int64_t n_, int64_t k_, int s) {
   off_F = off; off = align_up(off + 4 * static_cast<size_t>(n), 256);
   off_dec = off; off = align_up(off + (autos ? sizeof(SliceDecision) : 0), 256);
   off_part = off; off = align_up(off + (autos ? 8 * static_cast<size_t>(launch_absmax_parts(k)) * n : 0), 256);
-  off_sa = off; off = align_up(off + 2 * static_cast<size_t>(S) * m * kp, 1024);
-  off_sb = off; off = align_up(off + 2 * static_cast<size_t>(S) * n * kp, 1024);
+  off_sa = off; off = align_up(off + static_cast<size_t>(elem) * S * m * kp, 1024);
+  off_sb = off; off = align_up(off + static_cast<size_t>(elem) * S * n * kp, 1024);
   bytes = off;
 }
 
@@ -220,10 +222,10 @@ int run_split(mm_handle_s* h, int mode01, const SplitLayout& L, char* ws, const 
   if (dec) e = cudaMemsetAsync(dec, 0, sizeof(SliceDecision), st);   // no row or column seen yet
   if (e == cudaSuccess) e = launch_absmax(A, L.m, L.k, lda, B, L.n, ldb, rowmax, colmax, st, &nscan, dec, L.part(ws));
   if (e != cudaSuccess) return cuda_status(e, "absmax");
-  e = launch_slice_rows(mode01, A, L.m, L.k, lda, rowmax, L.S, L.kp, reinterpret_cast<uint16_t*>(ws + L.off_sa),
+  e = launch_slice_rows(mode01, A, L.m, L.k, lda, rowmax, L.S, L.kp, ws + L.off_sa,
                         reinterpret_cast<int32_t*>(ws + L.off_E), err, st, 0, dec);
   if (e != cudaSuccess) return cuda_status(e, "slice rows");
-  e = launch_slice_cols(mode01, B, L.k, L.n, ldb, colmax, L.S, L.kp, reinterpret_cast<uint16_t*>(ws + L.off_sb),
+  e = launch_slice_cols(mode01, B, L.k, L.n, ldb, colmax, L.S, L.kp, ws + L.off_sb,
                         reinterpret_cast<int32_t*>(ws + L.off_F), err, st, dec);
   if (e != cudaSuccess) return cuda_status(e, "slice cols");
   count_launch(h, 2 + static_cast<uint64_t>(nscan));
@@ -366,6 +368,54 @@ int run_emulated(mm_handle_s* h, int precision, int64_t m, int64_t n, int64_t k,
   return rc;
 }
 
+// The FP64-accuracy product on INT8-form digits (mma.sync s8 tensor path):
+// the same scan, slice count rule (on halved spreads) and plain fallback; the
+// level products, or with levels != nullptr their int64 values [s][m][n].
+int run_emulated_int8(mm_handle_s* h, int64_t m, int64_t n, int64_t k, const double* A, int64_t lda,
+                      const double* B, int64_t ldb, double* C, int64_t ldc, cudaStream_t st, int64_t* levels,
+                      int s_override) {
+  const int s = emu_slices(h, MM_FP64_EMU, k, s_override);
+  SplitLayout L;
+  L.plan(m, n, k, s, 1);
+  void* wsv = nullptr;
+  int rc = ws_alloc(h, L.bytes, st, &wsv);
+  if (rc != MM_OK) return rc;
+  char* ws = static_cast<char*>(wsv);
+  {
+    ProfScope ps(h, MM_KERNEL_SPLIT, st);
+    rc = run_split(h, 2, L, ws, A, lda, B, ldb, st);
+  }
+  if (rc == MM_OK) {
+    Int8GemmArgs a;
+    memset(&a, 0, sizeof(a));
+    a.m = m; a.n = n; a.k = k; a.kp = L.kp;
+    a.A = reinterpret_cast<const int8_t*>(ws + L.off_sa);
+    a.plane_a = m * L.kp;
+    a.B = reinterpret_cast<const int8_t*>(ws + L.off_sb);
+    a.plane_b = n * L.kp;
+    a.E = reinterpret_cast<const int32_t*>(ws + L.off_E);
+    a.F = reinterpret_cast<const int32_t*>(ws + L.off_F);
+    a.C = C; a.ldc = ldc;
+    a.levels = levels;
+    a.s = s;
+    a.fix_shift = s > 0 ? fixed_shift(s, k) : 0;
+    if (L.autos) {
+      a.s_dev = &L.dec(ws)->s;
+      for (int c = SLICE_S_MIN; c <= SLICE_S_MAX; ++c) a.fix_tab[c] = static_cast<int8_t>(fixed_shift(c, k));
+    }
+    cudaError_t e;
+    {
+      ProfScope ps(h, MM_KERNEL_SLICE_GEMM, st);
+      e = launch_int8_slice_gemm(a, st);
+    }
+    count_launch(h, 1);
+    rc = cuda_status(e, "int8 slice gemm");
+  }
+  if (rc == MM_OK && L.autos && !levels) rc = plain_fallback(h, m, n, k, A, lda, B, ldb, C, ldc, &L.dec(ws)->s, st);
+  ws_free(h, wsv, L.bytes, st);
+  return rc;
+}
+
 int fp64_kind(mm_handle_s* h) { return h->opt_fp64_kernel == 1 ? 1 : 2; }
 
 int run_fp64(mm_handle_s* h, int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
@@ -386,6 +436,8 @@ int gemm_with_cfg(mm_handle_s* h, int64_t m, int64_t n, int64_t k, const double*
   }
   if (precision == MM_FP64 || (precision == MM_FP64_EMU && k <= 4))
     return run_fp64(h, m, n, k, A, lda, B, ldb, C, ldc, st, cfg.kern);
+  if (precision == MM_FP64_EMU && h->opt_int8)
+    return run_emulated_int8(h, m, n, k, A, lda, B, ldb, C, ldc, st, nullptr, 0);
   return run_emulated(h, precision, m, n, k, A, lda, B, ldb, C, ldc, st, nullptr, 0, cfg);
 }
 
@@ -659,7 +711,7 @@ int mm_gemm_host(mm_handle h, int64_t m, int64_t n, int64_t k, const double* A, 
   cudaError_t e = cudaSuccess;
   // large emulated products: two row panels with the copies overlapping the kernels
   const bool emulated = precision == MM_FP32_EMU || (precision == MM_FP64_EMU && k > 4);
-  if (emulated && m >= 2048 && k > 0 && !tile_options_set(h)) {
+  if (emulated && m >= 2048 && k > 0 && !tile_options_set(h) && !(precision == MM_FP64_EMU && h->opt_int8)) {
     rc = gemm_host_pipelined(h, m, n, k, A, lda, B, ldb, C, ldc, precision, st, static_cast<double*>(dA),
                              static_cast<double*>(dB), static_cast<double*>(dC));
   } else {
@@ -728,6 +780,10 @@ int mm_set_option(mm_handle h, int option, int64_t value) {
       if (value != 0 && !slice_gemm_tile_ok(SLICE_FP64EMU, static_cast<int>(value), 1)) return MM_ERR_INVALID_ARG;
       h->opt_tile_n = static_cast<int>(value);
       return MM_OK;
+    case MM_OPT_INT8_SLICES:
+      if (value != 0 && value != 1) return MM_ERR_INVALID_ARG;
+      h->opt_int8 = value != 0;
+      return MM_OK;
     default: return MM_ERR_INVALID_ARG;
   }
 }
@@ -744,6 +800,7 @@ int mm_get_option(mm_handle h, int option, int64_t* value) {
     case MM_OPT_PROFILE: *value = h->opt_profile; return MM_OK;
     case MM_OPT_CTA_PAIR: *value = h->opt_cta_pair; return MM_OK;
     case MM_OPT_TILE_N: *value = h->opt_tile_n; return MM_OK;
+    case MM_OPT_INT8_SLICES: *value = h->opt_int8 ? 1 : 0; return MM_OK;
     default: return MM_ERR_INVALID_ARG;
   }
 }
@@ -848,6 +905,22 @@ int mm_debug_level_products(mm_handle h, int64_t m, int64_t n, int64_t k, const 
   // C is not written in level mode; pass the level buffer as a placeholder
   rc = run_emulated(h, MM_FP64_EMU, m, n, k, A, lda, B, ldb, reinterpret_cast<double*>(levels), n, st, levels, s,
                     TileCfg());
+  if (rc != MM_OK) return rc;
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_status(e, "synchronize");
+  return read_and_clear_err(h, st);
+}
+
+int mm_debug_level_products_int8(mm_handle h, int64_t m, int64_t n, int64_t k, const double* A, int64_t lda,
+                                 const double* B, int64_t ldb, int s, int64_t* levels, void* stream) {
+  if (!h || !levels || s < 1 || s > 7 || m <= 0 || n <= 0 || k <= 0) return MM_ERR_INVALID_ARG;
+  int rc = validate_problem(m, n, k, A, lda, B, ldb, reinterpret_cast<double*>(levels), n, MM_FP64_EMU);
+  if (rc != MM_OK) return rc;
+  DeviceGuard g(h->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemsetAsync(levels, 0, sizeof(int64_t) * static_cast<size_t>(s) * m * n, st);
+  if (e != cudaSuccess) return cuda_status(e, "memset");
+  rc = run_emulated_int8(h, m, n, k, A, lda, B, ldb, reinterpret_cast<double*>(levels), n, st, levels, s);
   if (rc != MM_OK) return rc;
   e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_status(e, "synchronize");

@@ -778,7 +778,9 @@ __global__ void __launch_bounds__(Cfg<BN, MODE, CG>::NUM_THREADS, 1)
                 tmem_st16(txlo + cg * 16, lo);
                 tmem_st16(txhi + cg * 16, hi);
               } else if (row_ok) {
-#pragma unroll 4
+                // fully unrolled: lo and hi stay in registers (a partial unroll
+                // would index them at run time and move them to local memory)
+#pragma unroll
                 for (int v = 0; v < 16; ++v) {
                   const int64_t col = col0 + cg * 16 + v;
                   if (col < n) {

@@ -165,6 +165,19 @@ __device__ __forceinline__ void fp32_slices3(uint64_t bits, int E, uint32_t& s0,
   s2 = bf16_rne_take(M, e);
 }
 
+// Slice modes: 0 FP64-accuracy digits as bfloat16, 1 FP32-accuracy bfloat16
+// slices, 2 FP64-accuracy digits as signed bytes (the INT8 form: one more
+// bit of headroom in the scale exponent keeps every digit within [-128, 127]).
+template <int MODE>
+struct SliceElem {
+  using T = uint16_t;
+};
+template <>
+struct SliceElem<2> {
+  using T = int8_t;
+};
+__host__ __device__ constexpr int exp_offset(int mode) { return mode == 1 ? 1 : (mode == 2 ? 3 : 2); }
+
 // The slices of 8 consecutive entries (bit patterns vb, scale exponent X of
 // their row or column), stored to dst + P * plane for P = 0 .. S-1 (plane 0
 // the most significant): one 16-byte vector per plane when the run is whole
@@ -176,10 +189,37 @@ __device__ __forceinline__ void fp32_slices3(uint64_t bits, int E, uint32_t& s0,
 // (arithmetic shift), the same digits the one-at-a-time expansion
 // d = ((R + 128) mod 256) - 128, R = (R - d) / 256 produces.
 template <int MODE>
-__device__ __forceinline__ void slice8_store(const uint64_t (&vb)[8], int32_t X, int s, uint16_t* __restrict__ dst,
-                                             size_t plane, int cnt) {
-  const bool vec = (cnt == 8) && ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0);
-  if constexpr (MODE == 0) {
+__device__ __forceinline__ void slice8_store(const uint64_t (&vb)[8], int32_t X, int s,
+                                             typename SliceElem<MODE>::T* __restrict__ dst, size_t plane, int cnt) {
+  const bool vec = (cnt == 8) && ((reinterpret_cast<uintptr_t>(dst) & (MODE == 2 ? 7u : 15u)) == 0);
+  if constexpr (MODE == 2) {
+    int64_t bias = 0;
+    for (int j = 0; j < s - 1; ++j) bias = (bias << 8) | 128;
+    int64_t Rb[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) Rb[u] = scaled_rne(vb[u], 8 * s - X) + bias;
+#pragma unroll
+    for (int P = 0; P < 7; ++P) {
+      if (P >= s) break;
+      const int sh = 8 * (s - 1 - P);
+      uint32_t lo = 0u, hi = 0u;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int32_t d = (P == 0) ? static_cast<int32_t>(Rb[u] >> sh)
+                                   : static_cast<int32_t>((Rb[u] >> sh) & 255) - 128;
+        const uint32_t byte = static_cast<uint32_t>(d) & 255u;
+        if (u < 4) lo |= byte << (8 * u); else hi |= byte << (8 * (u - 4));
+      }
+      int8_t* o = dst + P * plane;
+      if (vec) {
+        *reinterpret_cast<uint2*>(o) = make_uint2(lo, hi);
+      } else {
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (u < cnt) o[u] = static_cast<int8_t>(((u < 4 ? lo : hi) >> (8 * (u & 3))) & 255u);
+      }
+    }
+  } else if constexpr (MODE == 0) {
     int64_t bias = 0;
     for (int j = 0; j < s - 1; ++j) bias = (bias << 8) | 128;
     int64_t Rb[8];
@@ -408,27 +448,35 @@ __device__ __forceinline__ float col_spread_body(const uint64_t* __restrict__ co
 }
 
 // The slice count a splitting kernel uses: the automatic rule's when dec is
-// set (the thread with first set records it), else s.
-__device__ __forceinline__ int decided_slices(const SliceDecision* dec, int s, int64_t k, bool first) {
+// set (the block's thread 0 evaluates it, in double, and shares it; the thread
+// with first set also records it), else s. scale 1/2: the INT8 form, whose
+// digit grid is twice as coarse. Every thread of the block calls it.
+__device__ __forceinline__ int decided_slices(SliceDecision* dec, int s, int64_t k, bool first, float scale = 1.0f) {
   if (dec == nullptr) return s;
-  const int d = slice_count_rule(k, spread_from_room(dec->amin_room), spread_from_room(dec->bmin_room));
-  if (first) const_cast<SliceDecision*>(dec)->s = d;
-  return d;
+  __shared__ int shared_s;
+  __syncthreads();   // an earlier call's value has been read by every thread
+  if (threadIdx.x == 0) {
+    shared_s = slice_count_rule(k, scale * spread_from_room(dec->amin_room), scale * spread_from_room(dec->bmin_room));
+    if (first) dec->s = shared_s;
+  }
+  __syncthreads();
+  return shared_s;
 }
 
 // Slices of 8 consecutive entries A[row][c0 .. c0+8) (rows scaled by E).
-template <int MODE>  // 0: FP64-accuracy digits, 1: FP32-accuracy bf16 slices
+template <int MODE>  // see SliceElem
 __device__ __forceinline__ void slice_rows_body(const double* __restrict__ A, int64_t plane_rows, int64_t k,
                                                 int64_t lda, const uint64_t* __restrict__ rowmax, int s, int64_t kp,
-                                                uint16_t* __restrict__ slices, int32_t* __restrict__ E,
+                                                typename SliceElem<MODE>::T* __restrict__ slices,
+                                                int32_t* __restrict__ E,
                                                 uint32_t* __restrict__ err, int64_t row, int64_t c0) {
   const uint64_t mx = rowmax[row];
-  const int32_t Ei = exponent_from_max(mx, MODE == 0 ? 2 : 1);
+  const int32_t Ei = exponent_from_max(mx, exp_offset(MODE));
   if (c0 == 0) {
     E[row] = Ei;
     if (Ei == EXP_NONFINITE) atomicOr(err, MM_DEV_ERR_NONFINITE);
   }
-  if (MODE == 0 && s > SLICE_S_MAX) return;   // the product runs through the plain FP64 kernel
+  if (MODE != 1 && s > SLICE_S_MAX) return;   // the product runs through the plain FP64 kernel
   const double* a = A + row * lda + c0;
   uint64_t vb[8];
   const int cnt = static_cast<int>((k - c0) < 8 ? (k - c0) : 8);
@@ -442,7 +490,8 @@ __device__ __forceinline__ void slice_rows_body(const double* __restrict__ A, in
 template <int MODE>
 __device__ __forceinline__ void slice_cols_body(const double* __restrict__ B, int64_t k, int64_t n, int64_t ldb,
                                                 const uint64_t* __restrict__ colmax, int s, int64_t kp,
-                                                uint16_t* __restrict__ slices, int32_t* __restrict__ F,
+                                                typename SliceElem<MODE>::T* __restrict__ slices,
+                                                int32_t* __restrict__ F,
                                                 uint32_t* __restrict__ err, int64_t k0, int64_t n0) {
   __shared__ uint64_t tile[64][33];
   __shared__ int32_t fexp[32];
@@ -451,7 +500,7 @@ __device__ __forceinline__ void slice_cols_body(const double* __restrict__ B, in
     const int64_t j = n0 + t;
     int32_t Fj = 0;
     if (j < n) {
-      Fj = exponent_from_max(colmax[j], MODE == 0 ? 2 : 1);
+      Fj = exponent_from_max(colmax[j], exp_offset(MODE));
       if (k0 == 0) {
         F[j] = Fj;
         if (Fj == EXP_NONFINITE) atomicOr(err, MM_DEV_ERR_NONFINITE);
@@ -459,7 +508,7 @@ __device__ __forceinline__ void slice_cols_body(const double* __restrict__ B, in
     }
     fexp[t] = Fj;
   }
-  if (MODE == 0 && s > SLICE_S_MAX) return;   // plain FP64 fallback: F only (uniform over the block)
+  if (MODE != 1 && s > SLICE_S_MAX) return;   // plain FP64 fallback: F only (uniform over the block)
   {
     // load 64 x 32 doubles: thread -> row t/4, columns (t%4)*8 .. +8
     const int r = t >> 2, cb = (t & 3) * 8;
@@ -546,24 +595,26 @@ __global__ void __launch_bounds__(256) col_spread_kernel(const uint64_t* __restr
 
 template <int MODE>
 __global__ void slice_rows_kernel(const double* __restrict__ A, int64_t m, int64_t k, int64_t lda,
-                                  const uint64_t* __restrict__ rowmax, int s, int64_t kp,
-                                  uint16_t* __restrict__ slices, int32_t* __restrict__ E,
-                                  uint32_t* __restrict__ err, int64_t plane_rows, SliceDecision* dec) {
+                                  const uint64_t* __restrict__ rowmax, int s, int64_t kp, void* __restrict__ slices,
+                                  int32_t* __restrict__ E, uint32_t* __restrict__ err, int64_t plane_rows,
+                                  SliceDecision* dec) {
   const int64_t row = blockIdx.x;
   const int64_t c0 = (static_cast<int64_t>(blockIdx.y) * blockDim.x + threadIdx.x) * 8;
-  const int se = decided_slices(dec, s, k, blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0);
-  if (row < m && c0 < k) slice_rows_body<MODE>(A, plane_rows, k, lda, rowmax, se, kp, slices, E, err, row, c0);
+  const int se = decided_slices(dec, s, k, blockIdx.x == 0 && blockIdx.y == 0, MODE == 2 ? 0.5f : 1.0f);
+  if (row < m && c0 < k)
+    slice_rows_body<MODE>(A, plane_rows, k, lda, rowmax, se, kp, static_cast<typename SliceElem<MODE>::T*>(slices), E,
+                          err, row, c0);
 }
 
 template <int MODE>
 __global__ void __launch_bounds__(256) slice_cols_kernel(const double* __restrict__ B, int64_t k, int64_t n,
                                                          int64_t ldb, const uint64_t* __restrict__ colmax, int s,
-                                                         int64_t kp, uint16_t* __restrict__ slices,
+                                                         int64_t kp, void* __restrict__ slices,
                                                          int32_t* __restrict__ F, uint32_t* __restrict__ err,
-                                                         const SliceDecision* dec) {
-  const int se = decided_slices(dec, s, k, false);
-  slice_cols_body<MODE>(B, k, n, ldb, colmax, se, kp, slices, F, err, static_cast<int64_t>(blockIdx.y) * 64,
-                        static_cast<int64_t>(blockIdx.x) * 32);
+                                                         SliceDecision* dec) {
+  const int se = decided_slices(dec, s, k, false, MODE == 2 ? 0.5f : 1.0f);
+  slice_cols_body<MODE>(B, k, n, ldb, colmax, se, kp, static_cast<typename SliceElem<MODE>::T*>(slices), F, err,
+                        static_cast<int64_t>(blockIdx.y) * 64, static_cast<int64_t>(blockIdx.x) * 32);
 }
 
 // --------------------------------------------------------- grouped kernels
@@ -572,9 +623,32 @@ __device__ __forceinline__ int find_problem(const int64_t* __restrict__ off, int
   int lo = 0, hi = count - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
-    if (__ldg(off + mid) <= vb) lo = mid; else hi = mid - 1;
+    if (off[mid] <= vb) lo = mid; else hi = mid - 1;
   }
   return lo;
+}
+
+// A block's copy of two kinds' block offsets in shared memory, so the search
+// for each virtual block costs shared loads, not a chain of dependent global
+// ones. Groups of more than GS_MAXC problems search the global arrays.
+constexpr int GS_MAXC = 1024;
+struct OffCache {
+  int64_t v[2][GS_MAXC + 1];
+};
+
+__device__ __forceinline__ void load_offsets(OffCache& oc, const GroupedSplitArgs& a, int k0, int k1, int count) {
+  if (count <= GS_MAXC) {
+    for (int i = threadIdx.x; i <= count; i += blockDim.x) {
+      oc.v[0][i] = __ldg(a.off[k0] + i);
+      oc.v[1][i] = __ldg(a.off[k1] + i);
+    }
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ const int64_t* offsets(const OffCache& oc, const GroupedSplitArgs& a, int which, int kind,
+                                                  int count) {
+  return count <= GS_MAXC ? oc.v[which] : a.off[kind];
 }
 
 // Phase 1: row maxima (8 rows per block) then column maxima (256 columns x
@@ -582,13 +656,17 @@ __device__ __forceinline__ int find_problem(const int64_t* __restrict__ off, int
 __global__ void __launch_bounds__(256) grouped_absmax_kernel(const GroupedSplitArgs a) {
   __shared__ int pref[8][32];
   __shared__ float psum[8][32];
+  __shared__ OffCache oc;
   const int count = *a.count_dev;
-  const int64_t t0 = a.off[0][count], t1 = a.off[1][count];
+  load_offsets(oc, a, 0, 1, count);
+  const int64_t* off0 = offsets(oc, a, 0, 0, count);
+  const int64_t* off1 = offsets(oc, a, 1, 1, count);
+  const int64_t t0 = off0[count], t1 = off1[count];
   for (int64_t vb = blockIdx.x; vb < t0 + t1; vb += gridDim.x) {
     if (vb < t0) {
-      const int p = find_problem(a.off[0], count, vb);
+      const int p = find_problem(off0, count, vb);
       const GroupedSplit& g = a.probs[p];
-      const int64_t row = (vb - a.off[0][p]) * 8 + (threadIdx.x >> 5);
+      const int64_t row = (vb - off0[p]) * 8 + (threadIdx.x >> 5);
       if (g.dec != nullptr) {
         float al = __uint_as_float(0x7F800000u);
         if (row < g.m) al = row_absmax_body<true>(g.A, g.k, g.lda, row, g.rowmax);
@@ -598,9 +676,9 @@ __global__ void __launch_bounds__(256) grouped_absmax_kernel(const GroupedSplitA
       }
     } else {
       const int64_t v = vb - t0;
-      const int p = find_problem(a.off[1], count, v);
+      const int p = find_problem(off1, count, v);
       const GroupedSplit& g = a.probs[p];
-      const int64_t lb = v - a.off[1][p];
+      const int64_t lb = v - off1[p];
       // 32 columns x 256 rows per block: warp w takes rows r0 + w, r0 + w + 8, ...
       const int64_t ncb = (g.n + 31) / 32;
       const int lane = static_cast<int>(threadIdx.x & 31), w = static_cast<int>(threadIdx.x >> 5);
@@ -609,7 +687,19 @@ __global__ void __launch_bounds__(256) grouped_absmax_kernel(const GroupedSplitA
       SpreadAcc acc;
       if (j < g.n) {
         const int64_t r1 = min(g.k, (lb / ncb) * 256 + 256);
-        for (int64_t r = r0; r < r1; r += 8) {
+        int64_t r = r0;
+        // four rows in flight per thread, then the rest
+        for (; r + 24 < r1; r += 32) {
+          uint64_t b[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) b[u] = dbits(__ldg(g.B + (r + 8 * u) * g.ldb + j)) & ABS_MASK;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            mx = max(mx, b[u]);
+            spread_add<true>(acc, b[u]);
+          }
+        }
+        for (; r < r1; r += 8) {
           const uint64_t b = dbits(__ldg(g.B + r * g.ldb + j)) & ABS_MASK;
           mx = max(mx, b);
           spread_add<true>(acc, b);
@@ -640,13 +730,16 @@ __global__ void __launch_bounds__(256) grouped_absmax_kernel(const GroupedSplitA
 // Phase 1b (automatic slice count): every column's spread from its partial
 // sums, 256 columns per block.
 __global__ void __launch_bounds__(256) grouped_spread_kernel(const GroupedSplitArgs a) {
+  __shared__ OffCache oc;
   const int count = *a.count_dev;
-  const int64_t t4 = a.off[4][count];
+  load_offsets(oc, a, 4, 4, count);
+  const int64_t* off4 = offsets(oc, a, 0, 4, count);
+  const int64_t t4 = off4[count];
   for (int64_t vb = blockIdx.x; vb < t4; vb += gridDim.x) {
-    const int p = find_problem(a.off[4], count, vb);
+    const int p = find_problem(off4, count, vb);
     const GroupedSplit& g = a.probs[p];
     if (g.dec == nullptr) continue;   // uniform over the block
-    const int64_t j = (vb - a.off[4][p]) * 256 + threadIdx.x;
+    const int64_t j = (vb - off4[p]) * 256 + threadIdx.x;
     const float be = (j < g.n) ? col_spread_body(g.colmax, g.colpart, g.n, g.k, (g.k + 255) / 256, j)
                                : __uint_as_float(0x7F800000u);
     block_min_to(be, &g.dec->bmin_room);
@@ -657,24 +750,28 @@ __global__ void __launch_bounds__(256) grouped_spread_kernel(const GroupedSplitA
 // (so short rows share a block), then of every 64 x 32 block of B.
 template <int MODE>
 __global__ void __launch_bounds__(256) grouped_slice_kernel(const GroupedSplitArgs a) {
+  __shared__ OffCache oc;
   const int count = *a.count_dev;
-  const int64_t t2 = a.off[2][count], t3 = a.off[3][count];
+  load_offsets(oc, a, 2, 3, count);
+  const int64_t* off2 = offsets(oc, a, 0, 2, count);
+  const int64_t* off3 = offsets(oc, a, 1, 3, count);
+  const int64_t t2 = off2[count], t3 = off3[count];
   for (int64_t vb = blockIdx.x; vb < t2 + t3; vb += gridDim.x) {
     if (vb < t2) {
-      const int p = find_problem(a.off[2], count, vb);
+      const int p = find_problem(off2, count, vb);
       const GroupedSplit& g = a.probs[p];
-      const int64_t lb = vb - a.off[2][p];
+      const int64_t lb = vb - off2[p];
       const int64_t runs = (g.k + 7) / 8;   // runs of 8 entries per row
       const int64_t u = lb * 256 + threadIdx.x;
       const int64_t row = u / runs, c0 = (u - row * runs) * 8;
-      const int se = decided_slices(g.dec, g.s, g.k, lb == 0 && threadIdx.x == 0);
+      const int se = decided_slices(g.dec, g.s, g.k, lb == 0);
       if (row < g.m)
         slice_rows_body<MODE>(g.A, g.m, g.k, g.lda, g.rowmax, se, g.kp, g.slA, g.E, g.perr ? g.perr : a.err, row, c0);
     } else {
       const int64_t v = vb - t2;
-      const int p = find_problem(a.off[3], count, v);
+      const int p = find_problem(off3, count, v);
       const GroupedSplit& g = a.probs[p];
-      const int64_t lb = v - a.off[3][p];
+      const int64_t lb = v - off3[p];
       const int64_t nnb = (g.n + 31) / 32;
       const int se = decided_slices(g.dec, g.s, g.k, false);
       slice_cols_body<MODE>(g.B, g.k, g.n, g.ldb, g.colmax, se, g.kp, g.slB, g.F, g.perr ? g.perr : a.err, (lb / nnb) * 64,
@@ -782,25 +879,29 @@ cudaError_t launch_absmax(const double* A, int64_t m, int64_t k, int64_t lda, co
 }
 
 cudaError_t launch_slice_rows(int mode, const double* A, int64_t m, int64_t k, int64_t lda, const uint64_t* rowmax,
-                              int s, int64_t kp, uint16_t* slices, int32_t* E, uint32_t* err, cudaStream_t st,
+                              int s, int64_t kp, void* slices, int32_t* E, uint32_t* err, cudaStream_t st,
                               int64_t plane_rows, SliceDecision* dec) {
   if (m <= 0 || k <= 0) return cudaSuccess;
   if (plane_rows < m) plane_rows = m;
   dim3 blk(128), grd(static_cast<unsigned>(m), static_cast<unsigned>((k + 1023) / 1024));
   if (mode == 0)
     slice_rows_kernel<0><<<grd, blk, 0, st>>>(A, m, k, lda, rowmax, s, kp, slices, E, err, plane_rows, dec);
+  else if (mode == 2)
+    slice_rows_kernel<2><<<grd, blk, 0, st>>>(A, m, k, lda, rowmax, s, kp, slices, E, err, plane_rows, dec);
   else
     slice_rows_kernel<1><<<grd, blk, 0, st>>>(A, m, k, lda, rowmax, s, kp, slices, E, err, plane_rows, nullptr);
   return cudaGetLastError();
 }
 
 cudaError_t launch_slice_cols(int mode, const double* B, int64_t k, int64_t n, int64_t ldb, const uint64_t* colmax,
-                              int s, int64_t kp, uint16_t* slices, int32_t* F, uint32_t* err, cudaStream_t st,
+                              int s, int64_t kp, void* slices, int32_t* F, uint32_t* err, cudaStream_t st,
                               SliceDecision* dec) {
   if (n <= 0 || k <= 0) return cudaSuccess;
   dim3 blk(256), grd(static_cast<unsigned>((n + 31) / 32), static_cast<unsigned>((k + 63) / 64));
   if (mode == 0)
     slice_cols_kernel<0><<<grd, blk, 0, st>>>(B, k, n, ldb, colmax, s, kp, slices, F, err, dec);
+  else if (mode == 2)
+    slice_cols_kernel<2><<<grd, blk, 0, st>>>(B, k, n, ldb, colmax, s, kp, slices, F, err, dec);
   else
     slice_cols_kernel<1><<<grd, blk, 0, st>>>(B, k, n, ldb, colmax, s, kp, slices, F, err, nullptr);
   return cudaGetLastError();

@@ -63,21 +63,33 @@ def device_inputs(mm, N, seed, scaled):
     return A, B
 
 
+_REF = {}
+
+
+def _oracle_rows(Ah, Bh, rows):
+    key = ("r", id(Ah), id(Bh), tuple(rows))
+    if key not in _REF:
+        _REF.clear()
+        _REF[key] = (oracle.gemm_rows_par(Ah, Bh, rows), oracle.absprod_rows_par(Ah, Bh, rows))
+    return _REF[key]
+
+
 def check_rows(C, Ah, Bh, rows, mode, frac=1.0):
     k = Ah.shape[1]
     got = C[rows].cpu().numpy()
-    ref = oracle.gemm_rows(Ah, Bh, rows)
-    D = oracle.absprod_rows(Ah, Bh, rows)
+    ref, D = _oracle_rows(Ah, Bh, rows)
     g = frac * em.gamma(k, mode)
     assert bound_ok(got, ref, D, g), max_ratio(got, ref, D, g)
 
 
 def check_cols(C, Ah, Bh, cols, mode, frac=1.0):
+    # columns of A*B are the rows of the oracle's product of A with those columns of B
     k = Ah.shape[1]
     got = C[:, cols].cpu().numpy()
     Bc = np.ascontiguousarray(Bh[:, cols])
-    ref = oracle.gemm(Ah, Bc)
-    D = oracle.absprod(Ah, Bc)
+    all_rows = list(range(Ah.shape[0]))
+    ref = oracle.gemm_rows_par(Ah, Bc, all_rows)
+    D = oracle.absprod_rows_par(Ah, Bc, all_rows)
     g = frac * em.gamma(k, mode)
     assert bound_ok(got, ref, D, g), max_ratio(got, ref, D, g)
 

@@ -121,6 +121,9 @@ def test_rows_dot_and_omp_agree_with_full():
     assert np.array_equal(Cr, C[5:35]) and used >= 1
     D = oracle.absprod(A, B)
     assert np.array_equal(oracle.absprod_rows(A, B, [3, 9]), D[[3, 9]])
+    # the parallel sampled-row helpers give the serial loop's bits
+    assert np.array_equal(oracle.gemm_rows_par(A, B, [39, 2, 17]), C[[39, 2, 17]])
+    assert np.array_equal(oracle.absprod_rows_par(A, B, [39, 2, 17]), D[[39, 2, 17]])
 
 
 def test_ieee_special_values_propagate():
