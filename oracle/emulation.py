@@ -16,7 +16,9 @@ methods from their mathematics:
   s+1 are dropped; the kept levels are recombined with their powers of two.
 * FP32-accuracy ("fp32_emu"): three bfloat16 slices per entry, each the
   round-to-nearest bfloat16 of the residual left by the slices before it, and
-  the six slice products whose slice indices add to at most 2.
+  the six slice products whose slice indices add to at most 2; from k = 512
+  on the first two slices and the three products with indices adding to at
+  most 1 (the bound is wide enough there, see FP32_TWO_SLICE_K).
 
 Notation (row-major, A is m x k, B is k x n):
   t      digit width in bits (8 here: every digit fits in a bfloat16 exactly)
@@ -307,9 +309,26 @@ def fp32_slices_B(B: np.ndarray):
 
 FP32_PAIRS = [(0, 0), (0, 1), (1, 0), (0, 2), (1, 1), (2, 0)]
 
+# Two slices suffice once the bound is wide enough. Rounding to the nearest
+# bfloat16 keeps 8 significant bits, so |a - a0| <= 2^-8 |a| and
+# |a - a0 - a1| <= 2^-16 |a|. Writing a = a0 + a1 + da and b likewise, the
+# products left out beside (0,0), (0,1), (1,0) are a1 b1, a0 db, da b0 and
+# smaller terms, together at most 3.03 * 2^-16 |a b| for every term of the
+# sum, whatever the signs. That is at most half of 4k 2^-24 |A||B| when
+# k >= 3.03 * 2^8 / 2 = 388; from k = 512 on (0.38 of the bound) the product
+# takes two slices a operand and the three pairs with p + q <= 1.
+FP32_TWO_SLICE_K = 512
+FP32_PAIRS_TWO = [(0, 0), (0, 1), (1, 0)]
+
+
+def fp32_pairs(k: int):
+    """The slice pairs of the FP32-accuracy product of inner dimension k."""
+    return FP32_PAIRS_TWO if k >= FP32_TWO_SLICE_K else FP32_PAIRS
+
 
 def gemm_fp32_emu(A: np.ndarray, B: np.ndarray) -> np.ndarray:
-    """sum over the six pairs (p, q), p+q <= 2, of slice products, scaled back.
+    """sum over the slice pairs of fp32_pairs(k) (the six with p+q <= 2, or
+    from k = 512 the three with p+q <= 1) of slice products, scaled back.
 
     Products of bfloat16 values are exact in double; the k-sums here are in
     double, so this is the FP32-accuracy value without the float32 rounding the
@@ -317,7 +336,7 @@ def gemm_fp32_emu(A: np.ndarray, B: np.ndarray) -> np.ndarray:
     E, sA = fp32_slices_A(A)
     F, sB = fp32_slices_B(B)
     acc = np.zeros((sA.shape[1], sB.shape[2]))
-    for p, q in FP32_PAIRS:
+    for p, q in fp32_pairs(np.asarray(A).shape[1]):
         acc += sA[p] @ sB[q]
     return np.ldexp(np.ldexp(acc, E[:, None]), F[None, :])
 

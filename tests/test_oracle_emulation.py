@@ -290,3 +290,32 @@ def test_pins_catch_planted_mistakes():
     # a wrong level weight in the recombination
     Cbad = em.recombine_exact(L[::-1].copy(), E, F, s)
     assert not pin_recombine(sA, sB, E, F, Cbad, s)
+
+
+# ---------------------------------------------------------------- FP32-accuracy pair count
+def test_fp32_pair_count_by_k():
+    assert em.fp32_pairs(511) == em.FP32_PAIRS and len(em.FP32_PAIRS) == 6
+    assert em.fp32_pairs(512) == [(0, 0), (0, 1), (1, 0)]
+
+
+@pytest.mark.parametrize("k", [500, 512, 2048])
+def test_fp32_within_half_the_bound_worst_signs(k):
+    # all entries positive: the left-out products all add up, nothing cancels
+    from test_oracle_slice_count import exact_product
+    A = np.abs(inputs.wide_spread(6, k, 70 + k, inputs.STREAM_A)) + 2.0 ** -30
+    B = np.abs(inputs.uniform(k, 5, 70 + k, inputs.STREAM_B)) + 2.0 ** -30
+    ratio = np.max(np.abs(em.gemm_fp32_emu(A, B) - exact_product(A, B)) / (em.gamma(k, "fp32_emu") * (A @ B)))
+    assert ratio <= 0.5, (k, ratio)
+
+
+def test_fp32_planted_single_pair_fails():
+    # planted: only (0, 0) kept -- the 2^-8 rounding of the first slice shows
+    from test_oracle_slice_count import exact_product
+    k = 512
+    A = np.abs(inputs.uniform(4, k, 5, inputs.STREAM_A)) + 0.1
+    B = np.abs(inputs.uniform(k, 3, 5, inputs.STREAM_B)) + 0.1
+    E, sA = em.fp32_slices_A(A)
+    F, sB = em.fp32_slices_B(B)
+    C = np.ldexp(np.ldexp(sA[0] @ sB[0], E[:, None]), F[None, :])
+    ratio = np.max(np.abs(C - exact_product(A, B)) / (em.gamma(k, "fp32_emu") * (A @ B)))
+    assert ratio > 1.0
