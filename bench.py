@@ -406,8 +406,24 @@ def ours(args):
         for _ in range(reps):
             h.gemm_host(An, Bn, Cn, precision=mm.FP64_EMU)
         e2e_s = (time.perf_counter() - t0) / reps
+        # the copies alone on this machine, for context (a pinned buffer of their
+        # own: the product's result in Ch is checked against the oracle below)
+        Ad2 = torch.empty_like(A)
+        Xh = torch.empty_like(Ah, pin_memory=True)
+        torch.cuda.synchronize(dev)
+        c0 = time.perf_counter()
+        Ad2.copy_(Ah, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        c1 = time.perf_counter()
+        Xh.copy_(Ad2, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        c2 = time.perf_counter()
+        del Ad2, Xh
         extra["e2e"] = {"value": flop / e2e_s / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": 16 * N * N,
-                        "d2h_bytes_per_step": 8 * N * N}
+                        "d2h_bytes_per_step": 8 * N * N,
+                        "ms_per_step": e2e_s * 1e3,
+                        "copy_gbs": {"h2d": 8 * N * N / (c1 - c0) / 1e9, "d2h": 8 * N * N / (c2 - c1) / 1e9,
+                                     "note": "one 512 MiB pinned copy each way"}}
         # ---------------- the paper's own sizes and inputs (Sec. IV), every mode
         if not args.no_paper_sweep:
             extra["paper_sweep"] = paper_sweep_leg(h, args, mm, inputs, torch, dev, stream)

@@ -215,7 +215,10 @@ enum {
     MM_OPT_FP64_KERNEL = 6,       /* 0 = automatic, 1 = DFMA tiles, 2 = DMMA (mma.sync f64) tiles */
     MM_OPT_PROFILE = 7,           /* 1 = time every kernel launch with CUDA events (see mm_profile_read) */
     MM_OPT_CTA_PAIR = 8,          /* emulated products: 0 = automatic, 1 = one CTA per 128-row tile,
-                                     2 = CTA pairs (cta_group::2) on 256-row tiles */
+                                     2 = CTA pairs (cta_group::2) on 256-row tiles, 3 = CTA pairs in
+                                     clusters of two on adjacent 256-wide tiles sharing A (each CTA
+                                     loads half of its A rows for both pairs; single products whose
+                                     tile-column count is even, else pairs) */
     MM_OPT_TILE_N = 9,            /* FP64-accuracy tile width: 0 = automatic, 128, 192, 240 or 256
                                      columns. Every choice gives the same bits. */
     MM_OPT_INT8_SLICES = 11       /* 1 = FP64-accuracy single products (mm_gemm, mm_gemm_host) on

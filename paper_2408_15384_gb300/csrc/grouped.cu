@@ -126,7 +126,7 @@ struct EmuPlan {
       r.sb = o; o = align_up(o + 2 * static_cast<size_t>(planes) * q.n * r.kp, 1024);
       const int tm = static_cast<int>((q.m + 127) / 128), tn = static_cast<int>((q.n + bn - 1) / bn);
       const int64_t nkb = (q.k + 63) / 64;
-      const int64_t pairs = fp64 ? static_cast<int64_t>(r.s_floor) * (r.s_floor + 1) / 2 : 6;
+      const int64_t pairs = fp64 ? static_cast<int64_t>(r.s_floor) * (r.s_floor + 1) / 2 : (r.s == 2 ? 3 : 6);
       for (int a = 0; a < tm; ++a)
         for (int b = 0; b < tn; ++b)
           tiles.push_back({nkb * pairs, i, a * tn + b, TileRef{i, static_cast<int16_t>(a), static_cast<int16_t>(b)}});

@@ -69,6 +69,7 @@ struct mm_handle_s {
   int opt_tile_n = 0;        // FP64-accuracy tile width (0 = automatic, 128, 192, 240, 256)
   bool opt_int8 = false;     // FP64-accuracy single products on INT8-form digits (mma.sync s8)
   int max_pairs_fp32 = 0, max_pairs_fp64 = 0;   // co-resident CTA pairs of the pair kernels
+  int max_clusters4_fp32 = 0, max_clusters4_fp64 = 0;   // co-resident clusters of two pairs (cg = 4)
 
   // profiling: (start, end) event pairs per kernel class, drained by mm_profile_read
   std::mutex prof_mu;

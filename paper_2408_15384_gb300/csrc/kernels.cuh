@@ -67,6 +67,13 @@ __host__ __device__ inline int slice_count_rule(int64_t k, float amin, float bmi
 // spread any row or column can have is below 1/2).
 inline int slice_count_floor(int64_t k) { return slice_count_rule(k, 0.5f, 0.5f); }
 
+// FP32-accuracy slice count: three bfloat16 slices (the six products with
+// p + q <= 2) below k = 512, two slices (the three with p + q <= 1) from
+// there on: the left-out products are at most 3.03 * 2^-16 |a b| a term, half
+// of the bound 4k 2^-24 |A||B| already at k = 388.
+constexpr int64_t FP32_TWO_SLICE_K = 512;
+inline int fp32_slice_count(int64_t k) { return k >= FP32_TWO_SLICE_K ? 2 : 3; }
+
 // ---------------------------------------------------------------- split.cu
 // Row maxima of |A| and column maxima of |B| (bit patterns); one fused launch
 // when both operands are non-empty, else one per operand. *nlaunch, if given,
@@ -196,14 +203,20 @@ struct SliceGemmArgs {
 };
 
 // bn: tile width (columns of C); cg: CTAs per tile (1, or 2 for a CTA pair on
-// 256-row tiles). grid = persistent CTA count (a multiple of 2 when cg = 2).
-// With cg = 2, tiles_m counts 256-row tiles and B's tensor map box has bn/2 rows.
+// 256-row tiles), or 4 for CTA pairs in clusters of two on horizontally
+// adjacent tiles (single products with an even tiles_n; A's tensor map box has
+// 64 rows, each CTA loading half of its rows for both pairs). grid =
+// persistent CTA count (a multiple of 2 when cg = 2, of 4 when cg = 4). With
+// cg = 2 or 4, tiles_m counts 256-row tiles and B's tensor map box has bn/2 rows.
 cudaError_t launch_slice_gemm(int mode, int bn, int cg, const CUtensorMap* tmA, const CUtensorMap* tmB,
                               const SliceGemmArgs& a, int grid, cudaStream_t st);
 // Set the dynamic shared memory limits of every instantiation (once per device).
 cudaError_t slice_gemm_prepare();
 // Largest number of co-resident CTA pairs of the pair kernel for a mode.
 int slice_gemm_max_pairs(int mode);
+// Largest number of co-resident clusters of two CTA pairs (cg = 4: 256-wide
+// tiles, A multicast between the pairs) for FP32-accuracy or the byte-carry modes.
+int slice_gemm_max_clusters4(int mode);
 // whether launch_slice_gemm has a kernel for (mode, tile width, CTAs per tile)
 bool slice_gemm_tile_ok(int mode, int bn, int cg);
 

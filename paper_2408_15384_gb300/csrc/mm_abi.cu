@@ -233,8 +233,7 @@ int run_split(mm_handle_s* h, int mode01, const SplitLayout& L, char* ws, const 
 }
 
 int emu_slices(mm_handle_s* h, int precision, int64_t k, int s_override) {
-  (void)k;
-  if (precision != MM_FP64_EMU) return 3;
+  if (precision != MM_FP64_EMU) return fp32_slice_count(k);
   if (s_override > 0) return s_override;
   return h->opt_slices > 0 ? h->opt_slices : 0;
 }
@@ -266,11 +265,18 @@ static SliceLaunch slice_launch_for(mm_handle_s* h, int precision, int64_t mr, i
   r.cg = cfg_in.cg ? cfg_in.cg : dflt.cg;
   r.bn = cfg_in.bn ? cfg_in.bn : dflt.bn;
   if (pairs_avail <= 0) r.cg = 1;
-  if (!slice_gemm_tile_ok(fp64 ? SLICE_FP64EMU : SLICE_FP32EMU, r.bn, r.cg)) {
+  if (!slice_gemm_tile_ok(fp64 ? SLICE_FP64EMU : SLICE_FP32EMU, r.bn, r.cg == 4 ? 2 : r.cg)) {
     r.bn = dflt.bn;
     r.cg = dflt.cg;
   }
   r.mode = levels ? SLICE_LEVELS : (!fp64 ? SLICE_FP32EMU : slice_fp64_mode(s, k, fixed_shift(s, k)));
+  if (r.cg == 4) {
+    // clusters of two pairs: 256-wide tiles in an even number of tile columns,
+    // a kernel mode that has them, and clusters that fit; else CTA pairs
+    const int clusters = fp64 ? h->max_clusters4_fp64 : h->max_clusters4_fp32;
+    if (r.bn != 256 || ((n + 255) / 256) % 2 != 0 || clusters <= 0 || !slice_gemm_tile_ok(r.mode, 256, 4)) r.cg = 2;
+  }
+  if (r.cg == 2 && (pairs_avail <= 0 || !slice_gemm_tile_ok(fp64 ? SLICE_FP64EMU : SLICE_FP32EMU, r.bn, 2))) r.cg = 1;
   return r;
 }
 
@@ -285,8 +291,10 @@ static int slice_gemm_launch(mm_handle_s* h, const SplitLayout& L, char* ws, int
   const int64_t n = L.n, k = L.k;
   const int pairs_avail = fp64 ? h->max_pairs_fp64 : h->max_pairs_fp32;
   CUtensorMap tmA, tmB;
-  if (!encode_slices_tmap(h, &tmA, ws + L.off_sa + 2 * static_cast<size_t>(r0) * L.kp, k, mr, L.S, L.kp, 128, L.m) ||
-      !encode_slices_tmap(h, &tmB, ws + L.off_sb, k, n, L.S, L.kp, sl.bn / sl.cg))
+  const int pair = sl.cg >= 2 ? 2 : 1;   // CTAs per tile
+  if (!encode_slices_tmap(h, &tmA, ws + L.off_sa + 2 * static_cast<size_t>(r0) * L.kp, k, mr, L.S, L.kp,
+                          sl.cg == 4 ? 64 : 128, L.m) ||
+      !encode_slices_tmap(h, &tmB, ws + L.off_sb, k, n, L.S, L.kp, sl.bn / pair))
     return MM_ERR_CUDA;
   SliceGemmArgs a;
   memset(&a, 0, sizeof(a));
@@ -301,7 +309,7 @@ static int slice_gemm_launch(mm_handle_s* h, const SplitLayout& L, char* ws, int
     a.s_lo = s_lo;
     a.s_hi = s_hi;
   }
-  P.tiles_m = static_cast<int>((mr + 128 * sl.cg - 1) / (128 * sl.cg));
+  P.tiles_m = static_cast<int>((mr + 128 * pair - 1) / (128 * pair));
   P.tiles_n = static_cast<int>((n + sl.bn - 1) / sl.bn);
   P.E = reinterpret_cast<const int32_t*>(ws + L.off_E) + r0;
   P.F = reinterpret_cast<const int32_t*>(ws + L.off_F);
@@ -311,7 +319,9 @@ static int slice_gemm_launch(mm_handle_s* h, const SplitLayout& L, char* ws, int
   a.err = err_word(h, st);
   a.timeout_ns = static_cast<uint64_t>(h->opt_timeout_ms) * 1000000ull;
   const int ntiles = P.tiles_m * P.tiles_n;
-  const int grid = (sl.cg == 2) ? 2 * std::min(ntiles, pairs_avail) : std::min(ntiles, h->sm_count);
+  const int clusters4 = fp64 ? h->max_clusters4_fp64 : h->max_clusters4_fp32;
+  const int grid = (sl.cg == 4) ? 4 * std::min(ntiles / 2, clusters4)
+                   : (sl.cg == 2) ? 2 * std::min(ntiles, pairs_avail) : std::min(ntiles, h->sm_count);
   cudaError_t e;
   {
     ProfScope ps(h, MM_KERNEL_SLICE_GEMM, st);
@@ -330,7 +340,7 @@ static int slice_gemm_launch(mm_handle_s* h, const SplitLayout& L, char* ws, int
 int emu_gemm_rows(mm_handle_s* h, int precision, const SplitLayout& L, char* ws, int s, int64_t r0, int64_t mr,
                   double* C, int64_t ldc, int64_t* levels, const TileCfg& cfg_in, cudaStream_t st) {
   if (s > 0 || precision != MM_FP64_EMU) {
-    const int sf = s > 0 ? s : 3;
+    const int sf = s > 0 ? s : fp32_slice_count(L.k);
     const SliceLaunch sl = slice_launch_for(h, precision, mr, L.n, L.k, sf, levels != nullptr, cfg_in);
     return slice_gemm_launch(h, L, ws, sf, 0, 0, sl, r0, mr, C, ldc, levels, st);
   }
@@ -548,6 +558,8 @@ int mm_create(mm_handle* out, int device, size_t mem_budget_bytes) {
   cudaError_t e2 = fp64_gemm_prepare();
   h->max_pairs_fp32 = slice_gemm_max_pairs(SLICE_FP32EMU);
   h->max_pairs_fp64 = slice_gemm_max_pairs(SLICE_FP64EMU);
+  h->max_clusters4_fp32 = slice_gemm_max_clusters4(SLICE_FP32EMU);
+  h->max_clusters4_fp64 = slice_gemm_max_clusters4(SLICE_FP64EMU_CARRY);
   if (e1 != cudaSuccess || e2 != cudaSuccess) {
     cudaFree(h->d_err);
     cudaMemPoolDestroy(h->pool);
@@ -773,7 +785,7 @@ int mm_set_option(mm_handle h, int option, int64_t value) {
       return MM_OK;
     case MM_OPT_PROFILE: h->opt_profile = value != 0; return MM_OK;
     case MM_OPT_CTA_PAIR:
-      if (value < 0 || value > 2) return MM_ERR_INVALID_ARG;
+      if (value < 0 || value > 3) return MM_ERR_INVALID_ARG;
       h->opt_cta_pair = static_cast<int>(value);
       return MM_OK;
     case MM_OPT_TILE_N:

@@ -97,7 +97,8 @@ int mm_gemm_emu_static(int64_t m, int64_t n, int64_t k, const double* A, int64_t
     return cuda_status(launch_fp64_gemm(2, a, st), "fp64 gemm");
   }
   const bool fp64 = precision == MM_FP64_EMU;
-  const int s = fp64 ? 0 : 3;   // FP64-accuracy: the automatic slice count, as mm_gemm's default
+  // FP64-accuracy: the automatic slice count, as mm_gemm's default; FP32-accuracy: 3 or 2 slices by k
+  const int s = fp64 ? 0 : fp32_slice_count(k);
   SplitLayout L;
   L.plan(m, n, k, s);
   const size_t status_bytes = 256;

@@ -182,6 +182,17 @@ __device__ __forceinline__ void tma_load_3d_pair(void* smem_dst, const void* tma
       "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(z), "r"(bar_cluster)
       : "memory");
 }
+// 3D tiled load by one CTA of a pair, multicast to the CTAs of ctaMask (the
+// same shared-memory offset in each); each destination's bytes complete on the
+// barrier at bar_cluster's offset in that destination's pair leader.
+__device__ __forceinline__ void tma_load_3d_pair_mc(void* smem_dst, const void* tmap, int32_t x, int32_t y, int32_t z,
+                                                    uint32_t bar_cluster, uint16_t cta_mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster.cta_group::2 "
+      "[%0], [%1, {%2, %3, %4}], [%5], %6;" ::"r"(smem_u32(smem_dst)),
+      "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(z), "r"(bar_cluster), "h"(cta_mask)
+      : "memory");
+}
 __device__ __forceinline__ void tmem_alloc_pair(uint32_t* dst_smem, uint32_t ncols) {
   asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst_smem)),
                "r"(ncols)
@@ -206,6 +217,14 @@ __device__ __forceinline__ void umma_bf16_pair(uint32_t d_tmem, uint64_t a_desc,
 __device__ __forceinline__ void umma_commit_pair_local(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
+}
+// Arrive on `bar` in every CTA of `mask` (cluster ranks) once the pair's MMAs are done.
+__device__ __forceinline__ void umma_commit_pair_mask(uint64_t* bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_u32(bar)),
+      "h"(mask)
+      : "memory");
 }
 // Arrive on `bar` in both CTAs of the pair once the leader's MMAs are done.
 __device__ __forceinline__ void umma_commit_pair(uint64_t* bar) {

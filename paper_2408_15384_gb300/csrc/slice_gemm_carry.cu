@@ -24,17 +24,25 @@ cudaError_t prepare_bn() {
   return set_smem_attr<BN, SLICE_FP64EMU_CARRY7, 2>();
 }
 
+// 256-wide tiles also on clusters of two CTA pairs (A multicast)
+cudaError_t prepare_clusters4() {
+  cudaError_t e;
+  if ((e = set_smem_attr<256, SLICE_FP64EMU_CARRY, 4>()) != cudaSuccess) return e;
+  return set_smem_attr<256, SLICE_FP64EMU_CARRY7, 4>();
+}
+
 }  // namespace
 
 cudaError_t slice_launch_carry(int mode, int bn, int cg, const CUtensorMap* tmA, const CUtensorMap* tmB,
                                const SliceGemmArgs& a, int grid, cudaStream_t st) {
-  switch (bn * 4 + cg) {
+  switch (cg == 4 ? bn * 8 + 4 : bn * 4 + cg) {
     case 192 * 4 + 1: return launch_bn<192, 1>(mode, tmA, tmB, a, grid, st);
     case 192 * 4 + 2: return launch_bn<192, 2>(mode, tmA, tmB, a, grid, st);
     case 240 * 4 + 1: return launch_bn<240, 1>(mode, tmA, tmB, a, grid, st);
     case 240 * 4 + 2: return launch_bn<240, 2>(mode, tmA, tmB, a, grid, st);
     case 256 * 4 + 1: return launch_bn<256, 1>(mode, tmA, tmB, a, grid, st);
     case 256 * 4 + 2: return launch_bn<256, 2>(mode, tmA, tmB, a, grid, st);
+    case 256 * 8 + 4: return launch_bn<256, 4>(mode, tmA, tmB, a, grid, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -43,7 +51,10 @@ cudaError_t slice_prepare_carry() {
   cudaError_t e;
   if ((e = prepare_bn<192>()) != cudaSuccess) return e;
   if ((e = prepare_bn<240>()) != cudaSuccess) return e;
-  return prepare_bn<256>();
+  if ((e = prepare_bn<256>()) != cudaSuccess) return e;
+  return prepare_clusters4();
 }
+
+int slice_max_clusters4_carry() { return max_pairs_t<256, SLICE_FP64EMU_CARRY, 4>(); }
 
 }  // namespace mmdev

@@ -5,8 +5,9 @@
 //
 // Warp roles:
 //   warp 0      TMA producer: one A-slice tile (128 x 64) and one B-slice tile
-//               (BN x 64, or BN/2 x 64 per CTA of a pair) per pipeline step
-//               into a STAGES-deep shared ring.
+//               (BN x 64, or BN/2 x 64 per CTA of a pair) per slice pair, one or
+//               two pairs of the same K block per pipeline step, into a
+//               STAGES-deep shared ring.
 //   warp 1      allocates TMEM; one thread issues tcgen05.mma (M = 128 or 256,
 //               N = BN, K = 16, bf16 x bf16 -> f32) and tcgen05.commit.
 //   warps 2..   epilogue: 8 warps, or 12 / 16 when the FP64-accuracy level sums
@@ -16,9 +17,10 @@
 // tensor cores run the next chunk (or the next tile) while the epilogue drains
 // the previous one.
 //
-// FP32-accuracy (three bfloat16 slices per operand): the six slice pairs
-// (p, q) with p + q <= 2 accumulate into one f32 accumulator, smallest
-// products first; the epilogue scales by 2^(E_i + F_j) and stores doubles.
+// FP32-accuracy (three bfloat16 slices per operand, or two from k = 512): the
+// six slice pairs (p, q) with p + q <= 2 (the three with p + q <= 1) accumulate
+// into one f32 accumulator, smallest products first; the epilogue scales by
+// 2^(E_i + F_j) and stores doubles.
 //
 // FP64-accuracy (integer slices, levels d = p + q = 2..s+1, Ozaki-style): the
 // kernel walks the levels one after the other, smallest first (d = s+1 down
@@ -56,11 +58,17 @@ static constexpr int BM = 128;
 static constexpr int BK = 64;                 // bf16 elements per K block (128 bytes)
 static constexpr int SEG_CHUNKS = SLICE_SEG_CHUNKS;   // chunks per int32 level sum
 
+
 // CG = CTAs per output tile: 1, or 2 for a CTA pair (cta_group::2) computing a
 // 256-row tile, each CTA holding 128 rows of A and BN/2 rows of B in shared
-// memory and its 128 rows of the accumulator in its own TMEM.
+// memory and its 128 rows of the accumulator in its own TMEM. CG = 4: CTA
+// pairs as for 2, two pairs to a cluster on horizontally adjacent tiles
+// (same rows of A): each CTA loads half of its 128 rows of A and multicasts
+// them to its counterpart in the other pair, so A crosses from L2 once for
+// both tiles.
 template <int BN, int MODE, int CG>
 struct Cfg {
+  static constexpr int PAIR = (CG >= 2) ? 2 : 1;   // CTAs computing one tile
   // epilogue warps: 8 (two per TMEM lane quadrant). FP64-accuracy tiles wider
   // than 128 keep their columns' int32 level sums in registers: 16 warps for
   // 256 columns (64 sums a thread), 12 for 192 or 240 (64 or 80 sums a thread;
@@ -70,9 +78,13 @@ struct Cfg {
   static constexpr int EPI_WARP0 = 2;
   static constexpr int NUM_THREADS = 32 * (EPI_WARP0 + EPI_WARPS);
   static constexpr int A_BYTES = BM * BK * 2;
-  static constexpr int B_BYTES = (BN / CG) * BK * 2;
-  static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+  static constexpr int B_BYTES = (BN / PAIR) * BK * 2;
+  static constexpr int PAIR_BYTES = A_BYTES + B_BYTES;    // one slice pair's tiles of one K block
   static constexpr int SMEM_LIMIT = 232448 - 1024 - 256;   // max dynamic smem - alignment - static
+  // slice pairs a pipeline step carries: two (8 MMAs a step, half the single
+  // issuing threads' per-step work) while three such stages fit, else one
+  static constexpr int PPS = (SMEM_LIMIT / (2 * PAIR_BYTES) >= 3) ? 2 : 1;
+  static constexpr int STAGE_BYTES = PPS * PAIR_BYTES;
   static constexpr int STAGES_FIT = SMEM_LIMIT / STAGE_BYTES;
   static constexpr int STAGES = STAGES_FIT > 10 ? 10 : STAGES_FIT;
   static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
@@ -81,7 +93,7 @@ struct Cfg {
   static constexpr int XLO_COL = 2 * BN;
   static constexpr int XHI_COL = 3 * BN;
   static constexpr int COLS_PER_THREAD = BN / (EPI_WARPS / 4);
-  static constexpr int TILE_M = BM * CG;
+  static constexpr int TILE_M = BM * PAIR;
 };
 
 // K blocks per chunk at level d (d - 1 pairs): Kc * (d-1) <= 1024.
@@ -118,50 +130,74 @@ __device__ __forceinline__ double f32_to_f64_scaled(uint32_t fb, int e) {
 }
 
 struct Step {
-  int kb, pa, pb;      // K block, A slice index, B slice index
+  int kb;              // K block
+  int pa, pb;          // A and B slice indices of the step's first pair
+  int pa2, pb2;        // of its second pair (pa2 < 0: one pair)
   bool first, last;    // first / last step of its chunk
 };
 
 // The steps of one FP64-accuracy level D: K chunks of KC blocks, in each K
-// block the D-1 pairs (p, D-p). D is a compile-time constant so the pair loop
-// unrolls into straight-line issue with constant slice indices; a runtime pair
-// loop costs the single issuing threads about a quarter of the tensor rate.
-template <int D, typename Fn>
+// block the D-1 pairs (p, D-p), PPS of them a step. D is a compile-time
+// constant so the pair loop unrolls into straight-line issue with constant
+// slice indices; a runtime pair loop costs the single issuing threads about a
+// quarter of the tensor rate.
+template <int D, int PPS, typename Fn>
 __device__ __forceinline__ void walk_level(int nkb, int& chunk, Fn& f) {
   constexpr int KC = (16 / (D - 1)) < 1 ? 1 : 16 / (D - 1);
   for (int kb0 = 0; kb0 < nkb; kb0 += KC, ++chunk) {
     const int kb1 = min(kb0 + KC, nkb);
     for (int kb = kb0; kb < kb1; ++kb) {
 #pragma unroll
-      for (int p = 1; p < D; ++p) f(Step{kb, p - 1, D - p - 1, kb == kb0 && p == 1, kb == kb1 - 1 && p == D - 1}, chunk);
+      for (int p = 1; p < D; p += PPS) {
+        const bool two = PPS == 2 && p + 1 < D;
+        f(Step{kb, p - 1, D - p - 1, two ? p : -1, two ? D - p - 2 : -1, kb == kb0 && p == 1,
+               kb == kb1 - 1 && p + (two ? 1 : 0) == D - 1},
+          chunk);
+      }
     }
   }
 }
 
 // Walk the pipeline steps of one tile in order; f(Step, chunk offset in tile).
-template <int MODE, typename Fn>
+template <int MODE, int PPS, typename Fn>
 __device__ __forceinline__ void for_each_step(int s, int nkb, Fn&& f) {
   if (MODE == SLICE_FP32EMU) {
-    // pairs (p, q), p + q <= 2, smallest products first
+    // pairs (p, q), p + q <= 2 (three slices) or p + q <= 1 (s = 2), smallest
+    // products first (the same order whether a step carries one pair or two)
     for (int kb = 0; kb < nkb; ++kb) {
-      f(Step{kb, 2, 0, kb == 0, false}, 0);
-      f(Step{kb, 1, 1, false, false}, 0);
-      f(Step{kb, 0, 2, false, false}, 0);
-      f(Step{kb, 1, 0, false, false}, 0);
-      f(Step{kb, 0, 1, false, false}, 0);
-      f(Step{kb, 0, 0, false, kb == nkb - 1}, 0);
+      if (PPS == 2) {
+        if (s >= 3) {
+          f(Step{kb, 2, 0, 1, 1, kb == 0, false}, 0);
+          f(Step{kb, 0, 2, 1, 0, false, false}, 0);
+          f(Step{kb, 0, 1, 0, 0, false, kb == nkb - 1}, 0);
+        } else {
+          f(Step{kb, 1, 0, 0, 1, kb == 0, false}, 0);
+          f(Step{kb, 0, 0, -1, -1, false, kb == nkb - 1}, 0);
+        }
+      } else {
+        if (s >= 3) {
+          f(Step{kb, 2, 0, -1, -1, kb == 0, false}, 0);
+          f(Step{kb, 1, 1, -1, -1, false, false}, 0);
+          f(Step{kb, 0, 2, -1, -1, false, false}, 0);
+          f(Step{kb, 1, 0, -1, -1, false, false}, 0);
+        } else {
+          f(Step{kb, 1, 0, -1, -1, kb == 0, false}, 0);
+        }
+        f(Step{kb, 0, 1, -1, -1, false, false}, 0);
+        f(Step{kb, 0, 0, -1, -1, false, kb == nkb - 1}, 0);
+      }
     }
   } else {
     int chunk = 0;
     for (int d = s + 1; d >= 2; --d) {   // smallest level first; s is 3 .. 7
       switch (d) {
-        case 8: walk_level<8>(nkb, chunk, f); break;
-        case 7: walk_level<7>(nkb, chunk, f); break;
-        case 6: walk_level<6>(nkb, chunk, f); break;
-        case 5: walk_level<5>(nkb, chunk, f); break;
-        case 4: walk_level<4>(nkb, chunk, f); break;
-        case 3: walk_level<3>(nkb, chunk, f); break;
-        default: walk_level<2>(nkb, chunk, f); break;
+        case 8: walk_level<8, PPS>(nkb, chunk, f); break;
+        case 7: walk_level<7, PPS>(nkb, chunk, f); break;
+        case 6: walk_level<6, PPS>(nkb, chunk, f); break;
+        case 5: walk_level<5, PPS>(nkb, chunk, f); break;
+        case 4: walk_level<4, PPS>(nkb, chunk, f); break;
+        case 3: walk_level<3, PPS>(nkb, chunk, f); break;
+        default: walk_level<2, PPS>(nkb, chunk, f); break;
       }
     }
   }
@@ -201,19 +237,23 @@ __device__ __forceinline__ void resolve_slices(const SliceGemmArgs& a, const Sli
   }
 }
 
+// col_pairs = 2 (clusters of two CTA pairs): t numbers pairs of horizontally
+// adjacent tiles and the cluster's pair `pair_col` takes tile column
+// 2 * (pair of columns) + pair_col; single products only.
 __device__ __forceinline__ TileJob get_job(const SliceGemmArgs& a, const CUtensorMap* pa, const CUtensorMap* pb,
-                                           int t) {
+                                           int t, int col_pairs = 1, int pair_col = 0) {
   TileJob j;
   if (a.probs == nullptr) {
     // raster in groups of 8 tile rows so consecutive tiles share B panels
     const SliceProblem& P = a.single;
     const int GROUP = 8;
-    const int in_group = GROUP * P.tiles_n;
+    const int tiles_n = P.tiles_n / col_pairs;
+    const int in_group = GROUP * tiles_n;
     const int gid = t / in_group;
     const int first_m = gid * GROUP;
     const int gsize = min(P.tiles_m - first_m, GROUP);
     j.tm = first_m + (t % in_group) % gsize;
-    j.tn = (t % in_group) / gsize;
+    j.tn = ((t % in_group) / gsize) * col_pairs + pair_col;
     j.P = &a.single;
     j.ta = pa;
     j.tb = pb;
@@ -253,11 +293,18 @@ __global__ void __launch_bounds__(Cfg<BN, MODE, CG>::NUM_THREADS, 1)
   const uint32_t warp = warp_id(), lane = lane_id();
   const uint32_t smem_base = (smem_u32(smem_raw) + 1023u) & ~1023u;
   uint8_t* smem_gen = smem_raw + (smem_base - smem_u32(smem_raw));
-  const int ntiles = (args.probs == nullptr) ? args.single.tiles_m * args.single.tiles_n : *args.ntiles_dev;
-  // tile walk: CTAs (CG = 1) or CTA pairs (CG = 2) stride over the tile list
-  const uint32_t rank = (CG == 2) ? cluster_ctarank() : 0u;
-  const int walker = (CG == 2) ? static_cast<int>(cluster_id_x()) : static_cast<int>(blockIdx.x);
-  const int walkers = (CG == 2) ? static_cast<int>(cluster_count_x()) : static_cast<int>(gridDim.x);
+  // clusters of two pairs (CG = 4) walk pairs of adjacent tiles, one each
+  constexpr int COL_PAIRS = (CG == 4) ? 2 : 1;
+  const int ntiles =
+      (args.probs == nullptr) ? args.single.tiles_m * (args.single.tiles_n / COL_PAIRS) : *args.ntiles_dev;
+  // tile walk: CTAs (CG = 1), CTA pairs (CG = 2) or clusters of two pairs
+  // (CG = 4) stride over the tile list
+  const uint32_t crank = (CG >= 2) ? cluster_ctarank() : 0u;
+  const uint32_t rank = crank & 1u;              // rank within the CTA pair
+  const uint32_t pair_rank0 = crank & ~1u;       // cluster rank of the pair's leader
+  const int pair_col = static_cast<int>(crank >> 1);   // CG = 4: which tile of the cluster's two
+  const int walker = (CG >= 2) ? static_cast<int>(cluster_id_x()) : static_cast<int>(blockIdx.x);
+  const int walkers = (CG >= 2) ? static_cast<int>(cluster_count_x()) : static_cast<int>(gridDim.x);
   const bool leader = (rank == 0);
 
   WaitCtl wc;
@@ -268,11 +315,12 @@ __global__ void __launch_bounds__(Cfg<BN, MODE, CG>::NUM_THREADS, 1)
   if (threadIdx.x == 0) {
     for (int i = 0; i < C_::STAGES; ++i) {
       mbar_init(&full_bar[i], 1);
-      mbar_init(&empty_bar[i], 1);
+      // CG = 4: both pairs' MMAs read data this CTA's copies wrote
+      mbar_init(&empty_bar[i], CG == 4 ? 2 : 1);
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&accf_bar[i], 1);
-      mbar_init(&acce_bar[i], C_::EPI_WARPS * CG);   // the pair's epilogue warps all report to the leader
+      mbar_init(&acce_bar[i], C_::EPI_WARPS * C_::PAIR);   // the pair's epilogue warps all report to the leader
     }
     mbar_init(&drain_bar, 1);
     abort_flag = 0u;
@@ -283,7 +331,7 @@ __global__ void __launch_bounds__(Cfg<BN, MODE, CG>::NUM_THREADS, 1)
     tma_prefetch_desc(&tmB);
   }
   if (warp == 1) {
-    if constexpr (CG == 2) {
+    if constexpr (CG >= 2) {
       tmem_alloc_pair(&tmem_base_slot, C_::TMEM_COLS);   // collective: the same columns in both CTAs
       tmem_relinquish_pair();
     } else {
@@ -292,8 +340,8 @@ __global__ void __launch_bounds__(Cfg<BN, MODE, CG>::NUM_THREADS, 1)
     }
   }
   tc_fence_before();
-  if constexpr (CG == 2)
-    cluster_sync_all();   // both CTAs' barriers exist before any cross-CTA signal
+  if constexpr (CG >= 2)
+    cluster_sync_all();   // every CTA's barriers exist before any cross-CTA signal
   else
     __syncthreads();
   tc_fence_after();
@@ -306,27 +354,48 @@ __global__ void __launch_bounds__(Cfg<BN, MODE, CG>::NUM_THREADS, 1)
       int it = 0;
       bool ok = true;
       for (int t = walker; t < ntiles && ok; t += walkers) {
-        const TileJob job = get_job(args, &tmA, &tmB, t);
+        const TileJob job = get_job(args, &tmA, &tmB, t, COL_PAIRS, pair_col);
         if (job.skip) continue;
         const int ya = job.tm * C_::TILE_M + static_cast<int>(rank) * BM;
-        const int yb = job.tn * BN + static_cast<int>(rank) * (BN / CG);
-        for_each_step<MODE>(job.s, job.P->nkb, [&](const Step& st, int) {
+        const int yb = job.tn * BN + static_cast<int>(rank) * (BN / C_::PAIR);
+        for_each_step<MODE, C_::PPS>(job.s, job.P->nkb, [&](const Step& st, int) {
           if (!ok) return;
           const int stage = it % C_::STAGES;
           const uint32_t use = static_cast<uint32_t>(it / C_::STAGES);
           if (!mbar_wait(&empty_bar[stage], (use & 1u) ^ 1u, wc)) { ok = false; return; }
-          uint8_t* sa = smem_gen + stage * C_::STAGE_BYTES;
-          uint8_t* sb = sa + C_::A_BYTES;
-          if constexpr (CG == 2) {
+          // the stage holds [A tile | B tile] per slice pair of the step
+          const int npairs = (C_::PPS == 2 && st.pa2 >= 0) ? 2 : 1;
+          const uint32_t bytes = static_cast<uint32_t>(npairs * C_::PAIR_BYTES);
+          uint8_t* const s0 = smem_gen + stage * C_::STAGE_BYTES;
+          if constexpr (CG == 4) {
+            // the pair's bytes complete on its leader's barrier; this CTA's
+            // half of its 128 rows of A also lands in the other pair's
+            // counterpart CTA (same rows of A), and that CTA's half lands here
+            if (leader) mbar_arrive_expect_tx(&full_bar[stage], 2 * bytes);
+            const uint32_t fb = mapa_shared(smem_u32(&full_bar[stage]), pair_rank0);
+            const uint16_t mask = static_cast<uint16_t>((1u << rank) | (1u << (rank + 2u)));
+            for (int q = 0; q < npairs; ++q) {
+              uint8_t* sa = s0 + q * C_::PAIR_BYTES;
+              tma_load_3d_pair_mc(sa + pair_col * (C_::A_BYTES / 2), job.ta, st.kb * BK, ya + pair_col * (BM / 2),
+                                  q ? st.pa2 : st.pa, fb, mask);
+              tma_load_3d_pair(sa + C_::A_BYTES, job.tb, st.kb * BK, yb, q ? st.pb2 : st.pb, fb);
+            }
+          } else if constexpr (CG >= 2) {
             // both CTAs' bytes complete on the leader's barrier; only the leader arrives
-            if (leader) mbar_arrive_expect_tx(&full_bar[stage], 2 * C_::STAGE_BYTES);
+            if (leader) mbar_arrive_expect_tx(&full_bar[stage], 2 * bytes);
             const uint32_t fb = mapa_shared(smem_u32(&full_bar[stage]), 0);
-            tma_load_3d_pair(sa, job.ta, st.kb * BK, ya, st.pa, fb);
-            tma_load_3d_pair(sb, job.tb, st.kb * BK, yb, st.pb, fb);
+            for (int q = 0; q < npairs; ++q) {
+              uint8_t* sa = s0 + q * C_::PAIR_BYTES;
+              tma_load_3d_pair(sa, job.ta, st.kb * BK, ya, q ? st.pa2 : st.pa, fb);
+              tma_load_3d_pair(sa + C_::A_BYTES, job.tb, st.kb * BK, yb, q ? st.pb2 : st.pb, fb);
+            }
           } else {
-            mbar_arrive_expect_tx(&full_bar[stage], C_::STAGE_BYTES);
-            tma_load_3d(sa, job.ta, st.kb * BK, ya, st.pa, &full_bar[stage]);
-            tma_load_3d(sb, job.tb, st.kb * BK, yb, st.pb, &full_bar[stage]);
+            mbar_arrive_expect_tx(&full_bar[stage], bytes);
+            for (int q = 0; q < npairs; ++q) {
+              uint8_t* sa = s0 + q * C_::PAIR_BYTES;
+              tma_load_3d(sa, job.ta, st.kb * BK, ya, q ? st.pa2 : st.pa, &full_bar[stage]);
+              tma_load_3d(sa + C_::A_BYTES, job.tb, st.kb * BK, yb, q ? st.pb2 : st.pb, &full_bar[stage]);
+            }
           }
           ++it;
         });
@@ -348,17 +417,17 @@ __global__ void __launch_bounds__(Cfg<BN, MODE, CG>::NUM_THREADS, 1)
       bool ok = true;
       bool issued_any = false;
       for (int t = walker; t < ntiles && ok; t += walkers) {
-        const TileJob job = get_job(args, &tmA, &tmB, t);
+        const TileJob job = get_job(args, &tmA, &tmB, t, COL_PAIRS, pair_col);
         if (job.skip) continue;
         const int s = job.s, nkb = job.P->nkb;
-        for_each_step<MODE>(s, nkb, [&](const Step& st, int cofs) {
+        for_each_step<MODE, C_::PPS>(s, nkb, [&](const Step& st, int cofs) {
           if (!ok) return;
           const int chunk = chunk_base + cofs;
           const int slot = chunk & 1;
           if (st.first) {
             const uint32_t use = static_cast<uint32_t>(chunk >> 1);
             bool w;
-            if constexpr (CG == 2)
+            if constexpr (CG >= 2)
               w = mbar_wait_cluster(&acce_bar[slot], (use & 1u) ^ 1u, wc);
             else
               w = mbar_wait(&acce_bar[slot], (use & 1u) ^ 1u, wc);
@@ -369,21 +438,29 @@ __global__ void __launch_bounds__(Cfg<BN, MODE, CG>::NUM_THREADS, 1)
           const uint32_t use = static_cast<uint32_t>(it / C_::STAGES);
           if (!mbar_wait(&full_bar[stage], use & 1u, wc)) { ok = false; return; }
           tc_fence_after();
-          const uint32_t sa = smem_base + stage * C_::STAGE_BYTES;
-          const uint32_t sb = sa + C_::A_BYTES;
-          const uint64_t da = smem_desc_sw128(sa), db = smem_desc_sw128(sb);
           const uint32_t dt = tmem_base + static_cast<uint32_t>(slot * BN);
+          const int npairs = (C_::PPS == 2 && st.pa2 >= 0) ? 2 : 1;
 #pragma unroll
-          for (int kk = 0; kk < BK / 16; ++kk) {
-            // 16 bf16 (32 bytes) further along K inside the 128-byte swizzled rows
-            const uint32_t acc = (st.first && kk == 0) ? 0u : 1u;
-            if constexpr (CG == 2)
-              umma_bf16_pair(dt, da + static_cast<uint64_t>(kk * 2), db + static_cast<uint64_t>(kk * 2), idesc, acc);
-            else
-              umma_bf16(dt, da + static_cast<uint64_t>(kk * 2), db + static_cast<uint64_t>(kk * 2), idesc, acc);
+          for (int q = 0; q < C_::PPS; ++q) {
+            if (q >= npairs) break;
+            const uint32_t sa = smem_base + stage * C_::STAGE_BYTES + q * C_::PAIR_BYTES;
+            const uint64_t da = smem_desc_sw128(sa), db = smem_desc_sw128(sa + C_::A_BYTES);
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk) {
+              // 16 bf16 (32 bytes) further along K inside the 128-byte swizzled rows
+              const uint32_t acc = (st.first && q == 0 && kk == 0) ? 0u : 1u;
+              if constexpr (CG >= 2)
+                umma_bf16_pair(dt, da + static_cast<uint64_t>(kk * 2), db + static_cast<uint64_t>(kk * 2), idesc, acc);
+              else
+                umma_bf16(dt, da + static_cast<uint64_t>(kk * 2), db + static_cast<uint64_t>(kk * 2), idesc, acc);
+            }
           }
           issued_any = true;
-          if constexpr (CG == 2) {
+          if constexpr (CG == 4) {
+            // the stage is free in all four CTAs (each holds data of both pairs' copies)
+            umma_commit_pair_mask(&empty_bar[stage], 0xF);
+            if (st.last) umma_commit_pair_mask(&accf_bar[slot], static_cast<uint16_t>(3u << (2 * pair_col)));
+          } else if constexpr (CG >= 2) {
             umma_commit_pair(&empty_bar[stage]);
             if (st.last) umma_commit_pair(&accf_bar[slot]);
           } else {
@@ -395,7 +472,7 @@ __global__ void __launch_bounds__(Cfg<BN, MODE, CG>::NUM_THREADS, 1)
         chunk_base += chunks_per_tile<MODE>(s, nkb);
       }
       if (!ok && issued_any) {
-        if constexpr (CG == 2)
+        if constexpr (CG >= 2)
           umma_commit_pair_local(&drain_bar);
         else
           umma_commit(&drain_bar);
@@ -414,10 +491,10 @@ __global__ void __launch_bounds__(Cfg<BN, MODE, CG>::NUM_THREADS, 1)
     int chunk = 0;
     bool ok = true;
     // where this warp reports "slot drained": the leader's barrier
-    const uint32_t acce_remote0 = (CG == 2) ? mapa_shared(smem_u32(&acce_bar[0]), 0) : 0u;
-    const uint32_t acce_remote1 = (CG == 2) ? mapa_shared(smem_u32(&acce_bar[1]), 0) : 0u;
+    const uint32_t acce_remote0 = (CG >= 2) ? mapa_shared(smem_u32(&acce_bar[0]), pair_rank0) : 0u;
+    const uint32_t acce_remote1 = (CG >= 2) ? mapa_shared(smem_u32(&acce_bar[1]), pair_rank0) : 0u;
     for (int t = walker; t < ntiles && ok; t += walkers) {
-      const TileJob job = get_job(args, &tmA, &tmB, t);
+      const TileJob job = get_job(args, &tmA, &tmB, t, COL_PAIRS, pair_col);
       if (job.skip) continue;
       const SliceProblem& P = *job.P;
       const int64_t row = static_cast<int64_t>(job.tm) * C_::TILE_M + static_cast<int64_t>(rank) * BM + row_in_tile;
@@ -454,7 +531,7 @@ __global__ void __launch_bounds__(Cfg<BN, MODE, CG>::NUM_THREADS, 1)
         tc_fence_before();
         __syncwarp();
         if (lane == 0) {
-          if constexpr (CG == 2)
+          if constexpr (CG >= 2)
             mbar_arrive_remote(slot ? acce_remote1 : acce_remote0);
           else
             mbar_arrive(&acce_bar[slot]);
@@ -583,7 +660,7 @@ __global__ void __launch_bounds__(Cfg<BN, MODE, CG>::NUM_THREADS, 1)
               tc_fence_before();
               __syncwarp();
               if (lane == 0) {
-                if constexpr (CG == 2)
+                if constexpr (CG >= 2)
                   mbar_arrive_remote(slot ? acce_remote1 : acce_remote0);
                 else
                   mbar_arrive(&acce_bar[slot]);
@@ -677,7 +754,7 @@ __global__ void __launch_bounds__(Cfg<BN, MODE, CG>::NUM_THREADS, 1)
             tc_fence_before();
             __syncwarp();
             if (lane == 0) {
-              if constexpr (CG == 2)
+              if constexpr (CG >= 2)
                 mbar_arrive_remote(slot ? acce_remote1 : acce_remote0);
               else
                 mbar_arrive(&acce_bar[slot]);
@@ -804,7 +881,7 @@ __global__ void __launch_bounds__(Cfg<BN, MODE, CG>::NUM_THREADS, 1)
             tc_fence_before();
             __syncwarp();
             if (lane == 0) {
-          if constexpr (CG == 2)
+          if constexpr (CG >= 2)
             mbar_arrive_remote(slot ? acce_remote1 : acce_remote0);
           else
             mbar_arrive(&acce_bar[slot]);
@@ -817,13 +894,13 @@ __global__ void __launch_bounds__(Cfg<BN, MODE, CG>::NUM_THREADS, 1)
   }
 
   tc_fence_before();
-  if constexpr (CG == 2)
+  if constexpr (CG >= 2)
     cluster_sync_all();   // the leader's MMAs into this CTA's TMEM and all remote arrivals are done
   else
     __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    if constexpr (CG == 2)
+    if constexpr (CG >= 2)
       tmem_dealloc_pair(tmem_base, C_::TMEM_COLS);
     else
       tmem_dealloc(tmem_base, C_::TMEM_COLS);
@@ -851,7 +928,7 @@ static cudaError_t launch_t(const CUtensorMap* tmA, const CUtensorMap* tmB, cons
   cfg.stream = st;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.x = CG;
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
@@ -859,22 +936,24 @@ static cudaError_t launch_t(const CUtensorMap* tmA, const CUtensorMap* tmB, cons
   return cudaLaunchKernelEx(&cfg, slice_gemm_kernel<BN, MODE, CG>, *tmA, *tmB, a);
 }
 
-template <int BN, int MODE>
+// Largest number of co-resident clusters of CG CTAs (CG = 2: CTA pairs; 4:
+// clusters of two pairs) of the kernel for (BN, MODE).
+template <int BN, int MODE, int CG = 2>
 static int max_pairs_t() {
-  using C_ = Cfg<BN, MODE, 2>;
+  using C_ = Cfg<BN, MODE, CG>;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(2);
+  cfg.gridDim = dim3(CG);
   cfg.blockDim = dim3(C_::NUM_THREADS);
   cfg.dynamicSmemBytes = C_::SMEM_BYTES;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.x = CG;
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
   int n = 0;
-  if (cudaOccupancyMaxActiveClusters(&n, slice_gemm_kernel<BN, MODE, 2>, &cfg) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveClusters(&n, slice_gemm_kernel<BN, MODE, CG>, &cfg) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
@@ -889,5 +968,6 @@ int slice_max_pairs_fold(int mode);
 cudaError_t slice_launch_carry(int mode, int bn, int cg, const CUtensorMap* tmA, const CUtensorMap* tmB,
                                const SliceGemmArgs& a, int grid, cudaStream_t st);
 cudaError_t slice_prepare_carry();
+int slice_max_clusters4_carry();
 
 }  // namespace mmdev

@@ -252,6 +252,7 @@ __device__ __forceinline__ void slice8_store(const uint64_t (&vb)[8], int32_t X,
     for (int u = 0; u < 8; ++u) fp32_slices3(vb[u], X, h[0][u], h[1][u], h[2][u]);
 #pragma unroll
     for (int P = 0; P < 3; ++P) {
+      if (P >= s) break;   // two slices: the third is not stored
       uint16_t* o = dst + P * plane;
       if (vec) {
         *reinterpret_cast<uint4*>(o) = make_uint4(h[P][0] | (h[P][1] << 16), h[P][2] | (h[P][3] << 16),

@@ -65,13 +65,14 @@ TileCfg default_cfg(const mm_handle_s* h, int precision, int64_t m, int64_t n, i
   // otherwise single CTAs (measured at M = N = K = 2048, 4096 and 8192)
   const int64_t pair_tiles = ((m + 255) / 256) * ((n + 255) / 256);
   const int fp64_cg = (n > 128 && s <= 5 && pair_tiles >= h->sm_count) ? 2 : 1;
-  c.cg = (h->opt_cta_pair == 1) ? 1 : (h->opt_cta_pair == 2 ? 2 : (fp64 ? fp64_cg : (m > 128 ? 2 : 1)));
+  c.cg = (h->opt_cta_pair == 1) ? 1 : (h->opt_cta_pair == 2 ? 2 : (h->opt_cta_pair == 3 ? 4 :
+          (fp64 ? fp64_cg : (m > 128 ? 2 : 1))));
   if (pairs <= 0) c.cg = 1;
   if (fp64) {
     // 256-wide tiles whenever the product is wider than one 128-wide tile
     // (the tensor cores need N = 256 per MMA for full rate)
     c.bn = h->opt_tile_n ? h->opt_tile_n : (n > 128 ? 256 : 128);
-  } else if (c.cg == 2) {
+  } else if (c.cg >= 2) {
     c.bn = 256;
   } else if (h->opt_fp32_bn == 128 || h->opt_fp32_bn == 256) {
     c.bn = h->opt_fp32_bn;

@@ -538,3 +538,27 @@ def test_byte_carry_segment_limit(h, mm, k):
     rows = [0, 131, 259]
     assert bound_ok(first[rows], oracle.gemm_rows(A, B, rows), oracle.absprod_rows(A, B, rows),
                     em.gamma(k, "fp64_emu"))
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_clustered_pairs_same_bits(h, mm, prec):
+    # CTA pairs in clusters of two on adjacent 256-wide tiles, each CTA loading
+    # half of its rows of A for both pairs (TMA multicast): the same bits as
+    # plain CTA pairs; an odd tile-column count falls back to pairs
+    for m, n, k in ((1000, 2048, 1000), (700, 1280, 300)):
+        A = inputs.row_scaled(m, k, 1700 + k)
+        B = inputs.col_scaled(k, n, 1700 + k)
+        out = {}
+        for cp in (2, 3):
+            h.set_option(mm.OPT_CTA_PAIR, cp)
+            try:
+                out[cp], rc = run(h, A, B, prec)
+            finally:
+                h.set_option(mm.OPT_CTA_PAIR, 0)
+            assert rc == 0
+        assert np.array_equal(out[2], out[3]), (m, n, k)
+    mode = "fp64_emu" if prec == 1 else "fp32_emu"
+    A = inputs.row_scaled(700, 300, 2000)
+    B = inputs.col_scaled(300, 1280, 2000)
+    rows = [0, 350, 699]
+    assert bound_ok(out[3][rows], oracle.gemm_rows(A, B, rows), oracle.absprod_rows(A, B, rows), em.gamma(300, mode))
