@@ -14,6 +14,10 @@ methods from their mathematics:
   t*s bits), written as s signed radix-2^t digits ("slices"). Slice products
   are integer matrix products; products whose digit levels add to more than
   s+1 are dropped; the kept levels are recombined with their powers of two.
+  The modular form (Ozaki, Uchino, Imamura 2025, "Ozaki scheme II") keeps the
+  same scaled integers but multiplies their residues modulo N small coprime
+  moduli and rebuilds the exact integer product by the Chinese remainder
+  theorem (N products instead of s(s+1)/2).
 * FP32-accuracy ("fp32_emu"): three bfloat16 slices per entry, each the
   round-to-nearest bfloat16 of the residual left by the slices before it, and
   the six slice products whose slice indices add to at most 2; from k = 512
@@ -266,6 +270,168 @@ def slice_count_int8(A: np.ndarray, B: np.ndarray) -> int:
     amin = float(alpha.min()) if alpha.size else math.inf
     bmin = float(beta.min()) if beta.size else math.inf
     return slice_count_from_spread(A.shape[1], 0.5 * amin, 0.5 * bmin)
+
+
+# ---------------------------------------------------------------------------
+# FP64-accuracy, modular form (Ozaki scheme II: Ozaki, Uchino, Imamura 2025)
+# ---------------------------------------------------------------------------
+# Instead of splitting each scaled integer into digits and multiplying digit
+# pairs, the modular form takes the scaled integers' residues modulo N pairwise
+# coprime moduli m_1 .. m_N, multiplies the residue matrices (one product a
+# modulus), reduces each product modulo its own modulus and rebuilds the exact
+# integer product by the Chinese remainder theorem. With M = m_1 ... m_N the
+# rebuilt value is exact as long as every output's integer product lies in
+# (-M/2, M/2). N products replace the s(s+1)/2 digit-pair products.
+#
+# Notation (E_i, F_j as for the digit form, floor(log2 max) + 2):
+#   b        bits of the scaled integers: R = round-half-even(a * 2^(b - E_i)),
+#            so |R| <= 2^(b-1) (|a| < 2^(E_i - 1))
+#   rho^(l)  centred residue of R modulo m_l, in [-floor(m_l/2), ceil(m_l/2) - 1]
+#   P^(l)    rho_A^(l) @ rho_B^(l), an exact integer matrix product
+#   c^(l)    P^(l) mod m_l, in [0, m_l)
+#   Y        the integer in [-M/2, M/2) congruent to c^(l) modulo every m_l
+#   C_ij     round-to-nearest(Y_ij * 2^(E_i + F_j - 2b))
+# Readings taken here: moduli no larger than 256, so every centred residue
+# lies in [-128, 127] and is exact in bfloat16 (and each residue product is at
+# most 2^14, as for the digit form); the moduli are the largest pairwise
+# coprime integers <= 256, taken greedily from 256 down; Y in [-M/2, M/2).
+CRT_MODULI = (256, 255, 253, 251, 247, 241, 239, 233, 229, 227, 223, 217, 211, 199)
+CRT_N_MAX = len(CRT_MODULI)
+CRT_B_MIN, CRT_B_MAX = 24, 53
+
+# The error of the modular form comes only from rounding each scaled entry to
+# its integer (the products and the rebuild are exact): one term a_ik b_kj
+# carries an error of standard deviation at most sqrt(2/12 * 1/4) * 2^(E_i +
+# F_j - b) = 0.204 * ... for digits uniform in their rounding interval, so the
+# rule of the digit form applies with this constant and 8s replaced by b.
+CRT_KAPPA = 0.21
+
+
+def crt_modulus_product(N: int) -> int:
+    """M_N = m_1 * ... * m_N (exact integer)."""
+    M = 1
+    for m in CRT_MODULI[:N]:
+        M *= m
+    return M
+
+
+def crt_fits(k: int, b: int, N: int) -> bool:
+    """Whether every output of an inner dimension k product of b-bit scaled
+    integers lies strictly inside (-M_N/2, M_N/2): |Y| <= k 2^(2b-2) < M_N / 2."""
+    return k * (1 << (2 * b - 1)) < crt_modulus_product(N)
+
+
+def crt_params_from_spread(k: int, alpha_min: float, beta_min: float):
+    """(b, N) of the modular form for inner dimension k and the smallest row and
+    column spreads, or None when it cannot reach the estimate's target.
+
+    b0 = the smallest b in CRT_B_MIN..CRT_B_MAX with
+         CRT_KAPPA * Z_MAX * 2^(53-b) <= THETA * 4 * k * sqrt(k) * alpha_min * beta_min
+    (evaluated in double, as the digit form's rule), N = the smallest count
+    whose moduli hold k-term sums of b0-bit integers, and b = the largest bit
+    count (at most CRT_B_MAX) those N moduli still hold."""
+    rhs = THETA * 4.0 * float(k) * math.sqrt(float(k)) * float(alpha_min) * float(beta_min)
+    b0 = None
+    for b in range(CRT_B_MIN, CRT_B_MAX + 1):
+        if CRT_KAPPA * Z_MAX * math.ldexp(1.0, 53 - b) <= rhs:
+            b0 = b
+            break
+    if b0 is None:
+        return None
+    N = next((n for n in range(1, CRT_N_MAX + 1) if crt_fits(k, b0, n)), None)
+    if N is None:
+        return None
+    b = b0
+    while b + 1 <= CRT_B_MAX and crt_fits(k, b + 1, N):
+        b += 1
+    return b, N
+
+
+def crt_params(A: np.ndarray, B: np.ndarray):
+    """(b, N) of the product A*B from its operands' spreads (None: no fit)."""
+    A = np.asarray(A, dtype=np.float64)
+    B = np.asarray(B, dtype=np.float64)
+    alpha = row_spread(A, row_exponents(A, 2))
+    beta = col_spread(B, col_exponents(B, 2))
+    amin = float(alpha.min()) if alpha.size else math.inf
+    bmin = float(beta.min()) if beta.size else math.inf
+    return crt_params_from_spread(A.shape[1], amin, bmin)
+
+
+def fp64_scheme(A: np.ndarray, B: np.ndarray, modular: bool = True):
+    """The automatic FP64-accuracy decision for A*B: ("crt", b, N) when the
+    modular form fits (and is allowed), else ("digits", s) for a digit count
+    s <= S_MAX, else ("plain",)."""
+    if modular:
+        bN = crt_params(A, B)
+        if bN is not None:
+            return ("crt",) + tuple(bN)
+    s = slice_count(A, B)
+    return ("digits", s) if s <= S_MAX else ("plain",)
+
+
+def crt_integer_repr(X: np.ndarray, E: np.ndarray, b: int) -> np.ndarray:
+    """R = round-half-even(x * 2^(b - E)) per row of X, as int64 (|R| <= 2^(b-1) <= 2^52)."""
+    X = np.asarray(X, dtype=np.float64)
+    R = np.rint(np.ldexp(X, (b - np.asarray(E, dtype=np.int64))[:, None]))
+    assert np.all(np.abs(R) <= 2.0 ** (b - 1)), "scaled entry out of range"
+    return R.astype(np.int64)
+
+
+def crt_residues(R: np.ndarray, N: int) -> np.ndarray:
+    """rho[l] = R mod m_l, centred into [-floor(m/2), ceil(m/2) - 1]; shape (N,) + R.shape."""
+    R = np.asarray(R, dtype=np.int64)
+    out = np.zeros((N,) + R.shape, dtype=np.int64)
+    for l, m in enumerate(CRT_MODULI[:N]):
+        h = m // 2
+        out[l] = np.mod(R + h, m) - h
+    return out
+
+
+def crt_products(rhoA: np.ndarray, rhoB: np.ndarray) -> np.ndarray:
+    """P[l] = rhoA[l] @ rhoB[l], exact in int64 (|P| <= k 2^14)."""
+    return np.stack([rhoA[l] @ rhoB[l] for l in range(rhoA.shape[0])])
+
+
+def crt_reconstruct(P: np.ndarray) -> np.ndarray:
+    """Y: the integer in [-M/2, M/2) with Y = P[l] (mod m_l) for every l, from
+    the textbook CRT sum X = sum_l c_l * W_l mod M, W_l = (M/m_l) * ((M/m_l)^-1
+    mod m_l). Python integers (object array)."""
+    N = P.shape[0]
+    M = crt_modulus_product(N)
+    W = []
+    for m in CRT_MODULI[:N]:
+        Ml = M // m
+        W.append(Ml * pow(Ml % m, -1, m))
+    Y = np.empty(P.shape[1:], dtype=object)
+    for idx in np.ndindex(*P.shape[1:]):
+        X = sum((int(P[(l,) + idx]) % CRT_MODULI[l]) * W[l] for l in range(N)) % M
+        Y[idx] = X if 2 * X < M else X - M
+    return Y
+
+
+def crt_round(Y: np.ndarray, E: np.ndarray, F: np.ndarray, b: int) -> np.ndarray:
+    """C_ij = round-to-nearest(Y_ij * 2^(E_i + F_j - 2b)) (Fraction -> float)."""
+    m, n = Y.shape
+    C = np.zeros((m, n), dtype=np.float64)
+    for i in range(m):
+        for j in range(n):
+            C[i, j] = float(Fraction(int(Y[i, j])) * (Fraction(2) ** (int(E[i]) + int(F[j]) - 2 * b)))
+    return C
+
+
+def gemm_fp64_crt(A: np.ndarray, B: np.ndarray, b: int, N: int) -> np.ndarray:
+    """The FP64-accuracy product in the modular form with b-bit scaled integers
+    and N moduli (k 2^(2b-1) < M_N), the steps above in order."""
+    A = np.asarray(A, dtype=np.float64)
+    B = np.asarray(B, dtype=np.float64)
+    assert crt_fits(A.shape[1], b, N), "moduli too few for this b and k"
+    E = row_exponents(A, 2)
+    F = col_exponents(B, 2)
+    RA = crt_integer_repr(A, E, b)                    # (m, k)
+    RB = crt_integer_repr(B.T, F, b).T                # (k, n), column j scaled by F_j
+    P = crt_products(crt_residues(RA, N), crt_residues(RB, N))
+    return crt_round(crt_reconstruct(P), E, F, b)
 
 
 # ---------------------------------------------------------------------------
