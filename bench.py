@@ -297,8 +297,16 @@ def ours(args):
     C = torch.empty_like(A)
     mm.fill_uniform(A, seed, inputs.STREAM_A, 1, inputs.STREAM_EXP_A)
     mm.fill_uniform(B, seed, inputs.STREAM_B, 2, inputs.STREAM_EXP_B)
-    s = h.debug_slice_count(A, B)[0]   # the automatic count the device decides for these inputs
-    pairs = s * (s + 1) // 2
+    # the form the device decides for these inputs: the modular form (one
+    # residue product per modulus) or the digit form (s(s+1)/2 digit pairs)
+    _, code, bits, _, _, _ = h.debug_fp64_product(A, B, C, residues=False)
+    if code > mm.CRT_BASE:
+        s, pairs = None, code - mm.CRT_BASE
+        form = {"form": "modular (Chinese remainder)", "moduli": pairs, "bits": bits, "products": pairs}
+    else:
+        s = code
+        pairs = s * (s + 1) // 2
+        form = {"form": "digits", "slices": s, "products": pairs}
     flop = 2.0 * N ** 3
 
     def barrier():
@@ -371,6 +379,13 @@ def ours(args):
 
         fp32_ms, fp32_ci = time_mode(mm.FP32_EMU, 15)
         fp64_ms, fp64_ci = time_mode(mm.FP64, 15)
+        # the digit form on the same inputs, for comparison
+        h.set_option(mm.OPT_FP64_SCHEME, 1)
+        try:
+            dig_ms, dig_ci = time_mode(mm.FP64_EMU, 15)
+            dig_s = h.debug_slice_count(A, B)[0]
+        finally:
+            h.set_option(mm.OPT_FP64_SCHEME, 0)
         # the INT8 digit form on the legacy integer tensor path, for comparison
         h.set_option(mm.OPT_INT8_SLICES, 1)
         try:
@@ -388,7 +403,9 @@ def ours(args):
             "emu_over_plain": fp64_ms / ms_step,
             "fp64_peak_tflops_measured": {"dfma": dfma, "dmma": dmma},
             "plain_fp64_frac_of_fp64_peak": (flop / (fp64_ms * 1e-3) / 1e12) / fp64_peak,
-            "slices": s, "slice_pairs": pairs,
+            "fp64_form": form,
+            "fp64_emu_digit_form_tflops": flop / (dig_ms * 1e-3) / 1e12, "fp64_emu_digit_form_ms_median_ci95": dig_ci,
+            "digit_form_slices": dig_s, "digit_form_pairs": dig_s * (dig_s + 1) // 2,
         }
         # ---------------- the configurations' other sizes: plain FP64 sweep and the
         # split-precision product at 4096, median and interval of 15 reps each
@@ -488,7 +505,8 @@ def ours(args):
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_note": peak_note,
                          "kernel": "slice_gemm (tcgen05 bf16 slice products, FP64-accuracy epilogue)",
-                         "kernel_ms": kernel_ms, "algorithmic": f"2*N^3*{pairs} slice flop per launch"},
+                         "kernel_ms": kernel_ms, "algorithmic": f"2*N^3*{pairs} slice flop per launch",
+                         "fp64_form": form},
             "step_ms_median_ci95": {"median": med, "lo": lo, "hi": hi, "n": args.steps,
                                     "tflops_at_median": flop / (med * 1e-3) / 1e12 if med else None,
                                     "method": "order-statistic interval of the per-step device times (CUDA events)"},

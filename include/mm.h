@@ -24,6 +24,15 @@
  *                so that the error stays near half of the componentwise
  *                bound 4k*2^-53 * (|A||B|); where no s <= 7 would, the product
  *                runs on the plain FP64 kernel instead (see mm_gemm).
+ *                Single products take the modular form instead where it fits
+ *                (Ozaki, Uchino, Imamura 2025, "Ozaki scheme II"): the same
+ *                scaled integers, b bits each, reduced modulo N <= 14 pairwise
+ *                coprime moduli <= 256 (residues held in bfloat16), one
+ *                residue product per modulus on tcgen05, each product reduced
+ *                modulo its modulus, the exact integer product rebuilt by the
+ *                Chinese remainder theorem and rounded once: N products
+ *                instead of s(s+1)/2 (11 against 15 at M = N = K = 8192 on
+ *                the benchmark inputs); see mm_crt_rule and MM_OPT_FP64_SCHEME.
  *   MM_FP32_EMU  FP32-accuracy emulation: three bfloat16 slices per scaled
  *                entry and the six slice products with index sum <= 2, FP32
  *                accumulation on tcgen05. Bound 4k*2^-24 * (|A||B|).
@@ -221,7 +230,7 @@ enum {
                                      tile-column count is even, else pairs) */
     MM_OPT_TILE_N = 9,            /* FP64-accuracy tile width: 0 = automatic, 128, 192, 240 or 256
                                      columns. Every choice gives the same bits. */
-    MM_OPT_INT8_SLICES = 11       /* 1 = FP64-accuracy single products (mm_gemm, mm_gemm_host) on
+    MM_OPT_INT8_SLICES = 11,      /* 1 = FP64-accuracy single products (mm_gemm, mm_gemm_host) on
                                      signed-byte digits with the legacy integer tensor path
                                      (mma.sync m16n8k32 s8, int32 sums): scale exponent one larger
                                      (E = floor(log2 max) + 3, every digit in [-128, 127]), the
@@ -229,6 +238,10 @@ enum {
                                      recombination. Slower on GB300 than the default bfloat16
                                      digits on tcgen05; kept for comparison. Grouped and served
                                      products always use the default. */
+    MM_OPT_FP64_SCHEME = 12       /* FP64-accuracy single products with the automatic slice count
+                                     (MM_OPT_SLICES = 0): 0 = the modular form wherever mm_crt_rule
+                                     fits, else the digit form (default); 1 = the digit form only.
+                                     Grouped and served products use the digit form. */
 };
 
 /* Kernel classes for mm_profile_read. */
@@ -252,6 +265,20 @@ int mm_get_option(mm_handle h, int option, int64_t *value);
  * product then runs on the plain FP64 kernel), -1 for k < 1. The same function
  * runs on the device; the decision is evaluated in double. */
 int mm_slice_count_rule(int64_t k, float alpha_min, float beta_min);
+
+/* The modular form's parameters for inner dimension k and the smallest
+ * spreads (as for mm_slice_count_rule). Its error comes only from rounding
+ * each scaled entry to a b-bit integer (the residue products and the rebuild
+ * are exact): one term carries an error of standard deviation at most
+ * 0.21 * 2^(E_i+F_j-b). b0 is the smallest b in 24..53 with
+ * 0.21 * 6.5 * 2^(53-b) <= 0.5 * 4 k sqrt(k) alpha beta (double arithmetic);
+ * N the fewest moduli, taken in the order 256, 255, 253, 251, 247, 241, 239,
+ * 233, 229, 227, 223, 217, 211, 199, whose product M_N exceeds k 2^(2 b0 - 1)
+ * (so every output's integer sum lies inside (-M_N/2, M_N/2)); b then the
+ * largest bit count, at most 53, those N moduli still hold. Returns N and
+ * *bits = b, or 0 when no b in range qualifies or 14 moduli do not hold it
+ * (the product then takes the digit form); -1 for k < 1 or bits == NULL. */
+int mm_crt_rule(int64_t k, float alpha_min, float beta_min, int *bits);
 
 /* ---------------------------------------------------------------- autotuner */
 
@@ -307,6 +334,27 @@ int mm_debug_slices(mm_handle h, int which, int mode, int s,
 int mm_debug_slice_count(mm_handle h, int64_t m, int64_t n, int64_t k,
                          const double *A, int64_t lda, const double *B, int64_t ldb,
                          int *s, float *alpha_min, float *beta_min, void *stream);
+
+/* The modular form's centred residues as the splitting kernel computes them,
+ * for N moduli and b-bit scaled integers (given, not decided): for A (which =
+ * 0, rows of an m x k matrix) or B (which = 1, columns of a k x n matrix),
+ * exps[rows or cols] (int32, floor(log2 max) + 2) and planes[N][rows or
+ * cols][k] as bfloat16 bit patterns (residue modulo the l-th modulus of
+ * round-half-even(x 2^(b - E)), in [-floor(m/2), ceil(m/2) - 1]). Device
+ * pointers; synchronous. */
+int mm_debug_crt_residues(mm_handle h, int which, int N, int bits, int64_t rows, int64_t cols,
+                          const double *X, int64_t ldx, int32_t *exps, uint16_t *planes, void *stream);
+
+/* One automatic FP64-accuracy product (k > 4) as mm_gemm runs it, with the
+ * device's decision: *code = SLICE count 3..7 (digit form), 8 (plain FP64
+ * kernel) or 16 + N (modular form with N moduli and *bits = b), the smallest
+ * spreads it used, and for the modular form the products' residues modulo
+ * their moduli (bytes, [N][m][n], to res when res != NULL; capacity
+ * 14*m*n). Device pointers; synchronous. */
+int mm_debug_fp64_product(mm_handle h, int64_t m, int64_t n, int64_t k,
+                          const double *A, int64_t lda, const double *B, int64_t ldb,
+                          double *C, int64_t ldc, uint8_t *res, int *code, int *bits,
+                          float *alpha_min, float *beta_min, void *stream);
 
 /* The level products L_d (d = 2..s+1) of the FP64-accuracy mode as the
  * tensor-core kernel accumulates them (exact integers), written as int64

@@ -26,6 +26,8 @@ OPT_PROFILE = 7
 OPT_CTA_PAIR = 8
 OPT_TILE_N = 9
 OPT_INT8_SLICES = 11
+OPT_FP64_SCHEME = 12
+CRT_BASE = 16   # decision code of the modular form: CRT_BASE + N
 KERNEL_SLICE_GEMM, KERNEL_SPLIT, KERNEL_FP64_GEMM = 0, 1, 2
 
 
@@ -279,6 +281,42 @@ class Handle:
         _check(rc, "mm_debug_slice_count")
         return s.value, a.value, b.value
 
+    def debug_crt_residues(self, X, which: int, N: int, bits: int, stream=None):
+        """(exps int32, residues uint16 [N][vectors][k] as bfloat16 bits) of the
+        modular form for A (which=0) or B (which=1), N moduli, b-bit integers."""
+        import torch
+        px, rows, cols, ldx = _mat(X, "X")
+        nvec, klen = (rows, cols) if which == 0 else (cols, rows)
+        exps = torch.zeros(nvec, dtype=torch.int32, device=X.device)
+        pl = torch.zeros((N, nvec, klen), dtype=torch.int16, device=X.device)
+        rc = self.lib.mm_debug_crt_residues(self.h, which, N, bits, rows, cols, px, ldx, exps.data_ptr(),
+                                            pl.data_ptr(), _stream_handle(stream))
+        if rc not in (OK, 4):
+            raise MMError(rc, "mm_debug_crt_residues")
+        return exps, pl, rc
+
+    def debug_fp64_product(self, A, B, C=None, residues=True, stream=None):
+        """One automatic FP64-accuracy product as mm_gemm runs it: (C, code,
+        bits, alpha_min, beta_min, residues uint8 [N][m][n] or None)."""
+        import torch
+        pa, m, k, lda = _mat(A, "A")
+        pb, _, n, ldb = _mat(B, "B")
+        if C is None:
+            C = torch.empty((m, n), dtype=torch.float64, device=A.device)
+        pc, _, _, ldc = _mat(C, "C")
+        res = torch.zeros((14 * m * n if residues else 1,), dtype=torch.uint8, device=A.device)
+        code, bits = ctypes.c_int(0), ctypes.c_int(0)
+        a, b = ctypes.c_float(0.0), ctypes.c_float(0.0)
+        rc = self.lib.mm_debug_fp64_product(self.h, m, n, k, pa, lda, pb, ldb, pc, ldc,
+                                            res.data_ptr() if residues else None,
+                                            ctypes.byref(code), ctypes.byref(bits), ctypes.byref(a), ctypes.byref(b),
+                                            _stream_handle(stream))
+        if rc not in (OK, 4):
+            raise MMError(rc, "mm_debug_fp64_product")
+        N = code.value - CRT_BASE
+        r = res[: N * m * n].view(N, m, n) if (N > 0 and residues) else None
+        return C, code.value, bits.value, a.value, b.value, r
+
     def debug_levels(self, A, B, s: int, stream=None):
         """Level products L_d (d = 2..s+1) as int64 [s][m][n]."""
         import torch
@@ -294,6 +332,14 @@ def slice_count_rule(k: int, alpha_min: float, beta_min: float) -> int:
     """The automatic FP64-accuracy slice count for inner dimension k and the
     smallest row / column spreads (8: the plain FP64 kernel)."""
     return _lib.load().mm_slice_count_rule(int(k), float(alpha_min), float(beta_min))
+
+
+def crt_rule(k: int, alpha_min: float, beta_min: float):
+    """(N, b) of the modular form for inner dimension k and the smallest spreads
+    (N = 0: it does not fit)."""
+    b = ctypes.c_int(0)
+    N = _lib.load().mm_crt_rule(int(k), float(alpha_min), float(beta_min), ctypes.byref(b))
+    return N, b.value
 
 
 def fill_uniform(X, seed: int, stream_id: int, scale_mode: int = 0, exp_stream_id: int = 0, stream=None):

@@ -65,6 +65,7 @@ SIGNATURES = {
     "mm_set_option": (c_int, [c_vp, c_int, c_i64]),
     "mm_get_option": (c_int, [c_vp, c_int, ctypes.POINTER(c_i64)]),
     "mm_slice_count_rule": (c_int, [c_i64, ctypes.c_float, ctypes.c_float]),
+    "mm_crt_rule": (c_int, [c_i64, ctypes.c_float, ctypes.c_float, ctypes.POINTER(c_int)]),
     "mm_tune_save": (c_int, [c_vp, ctypes.c_char_p]),
     "mm_tune_load": (c_int, [c_vp, ctypes.c_char_p]),
     "mm_tune_lookup": (c_int, [c_vp, c_int, c_int, c_i64, c_i64, c_i64, ctypes.POINTER(c_int), ctypes.POINTER(c_int),
@@ -73,6 +74,10 @@ SIGNATURES = {
     "mm_debug_slices": (c_int, [c_vp, c_int, c_int, c_int, c_i64, c_i64, c_vp, c_i64, c_vp, c_vp, c_vp]),
     "mm_debug_slice_count": (c_int, [c_vp, c_i64, c_i64, c_i64, c_vp, c_i64, c_vp, c_i64, ctypes.POINTER(c_int),
                                      ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float), c_vp]),
+    "mm_debug_crt_residues": (c_int, [c_vp, c_int, c_int, c_int, c_i64, c_i64, c_vp, c_i64, c_vp, c_vp, c_vp]),
+    "mm_debug_fp64_product": (c_int, [c_vp, c_i64, c_i64, c_i64, c_vp, c_i64, c_vp, c_i64, c_vp, c_i64, c_vp,
+                                      ctypes.POINTER(c_int), ctypes.POINTER(c_int), ctypes.POINTER(ctypes.c_float),
+                                      ctypes.POINTER(ctypes.c_float), c_vp]),
     "mm_debug_level_products": (c_int, [c_vp, c_i64, c_i64, c_i64, c_vp, c_i64, c_vp, c_i64, c_int, c_vp, c_vp]),
     "mm_debug_level_products_int8": (c_int, [c_vp, c_i64, c_i64, c_i64, c_vp, c_i64, c_vp, c_i64, c_int, c_vp, c_vp]),
     "mm_debug_wait_timeout": (c_int, [c_vp, c_i64, c_vp]),

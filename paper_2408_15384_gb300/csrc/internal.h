@@ -68,7 +68,8 @@ struct mm_handle_s {
   int opt_cta_pair = 0;
   int opt_tile_n = 0;        // FP64-accuracy tile width (0 = automatic, 128, 192, 240, 256)
   bool opt_int8 = false;     // FP64-accuracy single products on INT8-form digits (mma.sync s8)
-  int max_pairs_fp32 = 0, max_pairs_fp64 = 0;   // co-resident CTA pairs of the pair kernels
+  int opt_fp64_scheme = 0;   // 0: modular form where it fits (single products), else digits; 1: digits only
+  int max_pairs_fp32 = 0, max_pairs_fp64 = 0, max_pairs_crt = 0;   // co-resident CTA pairs of the pair kernels
   int max_clusters4_fp32 = 0, max_clusters4_fp64 = 0;   // co-resident clusters of two pairs (cg = 4)
 
   // profiling: (start, end) event pairs per kernel class, drained by mm_profile_read
@@ -140,21 +141,26 @@ struct DeviceGuard {
 };
 
 // Workspace layout of one emulated product. s = 0: automatic slice count
-// (7 planes, plus the decision record and the column partial sums).
+// (7 planes, plus the decision record and the column partial sums); crt: the
+// modular form allowed (CRT_N_MAX planes, and the products' residue bytes,
+// CRT_N_MAX planes of m rows of ldr bytes).
 struct SplitLayout {
-  int64_t m = 0, n = 0, k = 0, kp = 0;
+  int64_t m = 0, n = 0, k = 0, kp = 0, ldr = 0;
   int S = 0;
-  bool autos = false;
+  bool autos = false, crt = false;
   size_t off_rowmax = 0, off_colmax = 0, off_E = 0, off_F = 0, off_sa = 0, off_sb = 0, off_dec = 0, off_part = 0,
-         bytes = 0;
+         off_res = 0, bytes = 0;
   int elem = 2;   // bytes per slice entry: 2 (bfloat16), 1 (INT8-form digits)
-  void plan(int64_t m_, int64_t n_, int64_t k_, int s, int elem_bytes = 2);
+  void plan(int64_t m_, int64_t n_, int64_t k_, int s, int elem_bytes = 2, bool crt_ = false);
   SliceDecision* dec(char* ws) const { return autos ? reinterpret_cast<SliceDecision*>(ws + off_dec) : nullptr; }
   uint2* part(char* ws) const { return autos ? reinterpret_cast<uint2*>(ws + off_part) : nullptr; }
 };
 
-int run_split(mm_handle_s* h, int mode01, const SplitLayout& L, char* ws, const double* A, int64_t lda,
+// mode: a launch_slice_rows mode (3 for a layout with crt)
+int run_split(mm_handle_s* h, int mode, const SplitLayout& L, char* ws, const double* A, int64_t lda,
               const double* B, int64_t ldb, cudaStream_t st);
+// whether a single FP64-accuracy product may take the modular form
+bool crt_allowed(const mm_handle_s* h, int precision, int s);
 
 // tune.cu: the autotuner. Keys are shape buckets (ceil(log2) of the single
 // product's m, n, k; of a group's problem count and mean dimension).

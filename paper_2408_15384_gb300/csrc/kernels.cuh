@@ -38,11 +38,13 @@ constexpr int SLICE_S_MIN = 3, SLICE_S_MAX = 7, SLICE_S_PLAIN = 8;
 // value, means no row or column constrains the count); s is the slice count,
 // written by the splitting kernels and read by the slice GEMM and the
 // plain-FP64 fallback.
+// With the modular form allowed, s is SLICE_CRT_BASE + N for a product that
+// takes it (N moduli) and bits its bit count b.
 struct SliceDecision {
   uint32_t amin_room;
   uint32_t bmin_room;
   int32_t s;
-  int32_t pad;
+  int32_t bits;
 };
 
 __host__ __device__ inline float spread_from_room(uint32_t room) {
@@ -66,6 +68,84 @@ __host__ __device__ inline int slice_count_rule(int64_t k, float amin, float bmi
 // The smallest count the rule can give for inner dimension k (the largest
 // spread any row or column can have is below 1/2).
 inline int slice_count_floor(int64_t k) { return slice_count_rule(k, 0.5f, 0.5f); }
+
+// ------------------------------------------- modular (CRT) FP64-accuracy form
+// Ozaki scheme II (Ozaki, Uchino, Imamura 2025) on bfloat16 tensor cores: the
+// scaled integers R = round-half-even(a 2^(b - E_i)), |R| <= 2^(b-1) (E_i as
+// for the digit form), are reduced modulo N pairwise coprime moduli m_l <= 256
+// (centred residues in [-128, 127], exact in bfloat16); one residue product a
+// modulus (each term at most 2^14, so the K-chunks of the digit form's level 2
+// hold exact f32 sums); every product reduced modulo its own modulus; the
+// integer product rebuilt by the Chinese remainder theorem, exact while
+// k 2^(2b-1) < M_N = m_1 ... m_N, and rounded to double once. The moduli are
+// the largest pairwise coprime integers <= 256, taken from 256 down.
+constexpr int CRT_N_MAX = 14;
+constexpr int CRT_B_MIN = 24, CRT_B_MAX = 53;
+// decision code of a product that takes the modular form: SLICE_CRT_BASE + N
+constexpr int SLICE_CRT_BASE = 16;
+// rounding-only error constant: sqrt(2/12 * 1/4) = 0.204, rounded up
+#define CRT_KAPPA 0.21
+
+__host__ __device__ constexpr int crt_modulus(int l) {
+  return l == 0 ? 256 : l == 1 ? 255 : l == 2 ? 253 : l == 3 ? 251 : l == 4 ? 247 : l == 5 ? 241 : l == 6 ? 239
+       : l == 7 ? 233 : l == 8 ? 229 : l == 9 ? 227 : l == 10 ? 223 : l == 11 ? 217 : l == 12 ? 211 : 199;
+}
+
+// Whether k 2^(2b-1) < M_N (every k-term sum of b-bit integers lies strictly
+// inside (-M_N/2, M_N/2)), in exact 128-bit integer arithmetic.
+__host__ __device__ inline bool crt_fits(int64_t k, int b, int N) {
+  unsigned __int128 M = 1;
+  for (int l = 0; l < N; ++l) M *= static_cast<unsigned>(crt_modulus(l));
+  const int sh = 2 * b - 1;
+  int kbits = 0;
+  for (uint64_t t = static_cast<uint64_t>(k); t; t >>= 1) ++kbits;
+  if (kbits + sh > 127) return false;
+  return (static_cast<unsigned __int128>(static_cast<uint64_t>(k)) << sh) < M;
+}
+
+// The modular form's parameters for inner dimension k and the smallest spreads:
+// b0 = the smallest b in CRT_B_MIN..CRT_B_MAX with
+//   CRT_KAPPA * SLICE_ZMAX * 2^(53-b) <= SLICE_THETA * 4 * k * sqrt(k) * amin * bmin
+// (the digit form's estimate with only the rounding term), N = the fewest
+// moduli that hold it, b = the most bits those moduli hold (at most
+// CRT_B_MAX). Returns N (0: the modular form does not fit) and *bits = b.
+__host__ __device__ inline int crt_rule(int64_t k, float amin, float bmin, int* bits) {
+  const double rhs = SLICE_THETA * 4.0 * static_cast<double>(k) * sqrt(static_cast<double>(k)) *
+                     static_cast<double>(amin) * static_cast<double>(bmin);
+  double pw = 536870912.0;   // 2^(53 - CRT_B_MIN)
+  int b0 = 0;
+  for (int b = CRT_B_MIN; b <= CRT_B_MAX; ++b, pw *= 0.5) {
+    if (CRT_KAPPA * SLICE_ZMAX * pw <= rhs) {
+      b0 = b;
+      break;
+    }
+  }
+  if (b0 == 0) return 0;
+  int N = 0;
+  for (int c = 1; c <= CRT_N_MAX; ++c) {
+    if (crt_fits(k, b0, c)) {
+      N = c;
+      break;
+    }
+  }
+  if (N == 0) return 0;
+  int b = b0;
+  while (b < CRT_B_MAX && crt_fits(k, b + 1, N)) ++b;
+  *bits = b;
+  return N;
+}
+
+// The automatic FP64-accuracy decision: SLICE_CRT_BASE + N (modular form, *bits
+// = b) when it is allowed and fits, else the digit count (SLICE_S_PLAIN: the
+// plain FP64 kernel).
+__host__ __device__ inline int fp64_decision(int64_t k, float amin, float bmin, bool modular, int* bits) {
+  *bits = 0;
+  if (modular) {
+    const int N = crt_rule(k, amin, bmin, bits);
+    if (N > 0) return SLICE_CRT_BASE + N;
+  }
+  return slice_count_rule(k, amin, bmin);
+}
 
 // FP32-accuracy slice count: three bfloat16 slices (the six products with
 // p + q <= 2) below k = 512, two slices (the three with p + q <= 1) from
@@ -95,13 +175,19 @@ int64_t launch_absmax_parts(int64_t k);
 // slices are written when it is SLICE_S_PLAIN.
 // mode: 0 FP64-accuracy digits as bfloat16 (uint16 planes), 1 FP32-accuracy
 // bfloat16 slices, 2 FP64-accuracy digits as signed bytes (int8 planes; the
-// INT8 form, scale exponent one larger, automatic count from halved spreads).
+// INT8 form, scale exponent one larger, automatic count from halved spreads),
+// 3 automatic FP64-accuracy with the modular form allowed: the residues (N
+// planes, code SLICE_CRT_BASE + N) or the digits the decision record holds,
+// written beforehand by launch_decide_fp64.
 cudaError_t launch_slice_rows(int mode, const double* A, int64_t m, int64_t k, int64_t lda, const uint64_t* rowmax,
                               int s, int64_t kp, void* slices, int32_t* E, uint32_t* err, cudaStream_t st,
                               int64_t plane_rows = 0, SliceDecision* dec = nullptr);
 cudaError_t launch_slice_cols(int mode, const double* B, int64_t k, int64_t n, int64_t ldb, const uint64_t* colmax,
                               int s, int64_t kp, void* slices, int32_t* F, uint32_t* err, cudaStream_t st,
                               SliceDecision* dec = nullptr);
+// The automatic FP64-accuracy decision of one product with the modular form
+// allowed (fp64_decision on the record's spreads): dec->s and dec->bits.
+cudaError_t launch_decide_fp64(SliceDecision* dec, int64_t k, cudaStream_t st);
 cudaError_t launch_fill_uniform(double* X, int64_t rows, int64_t cols, int64_t ld, uint64_t seed, uint64_t stream_id,
                                 int scale_mode, uint64_t exp_stream_id, cudaStream_t st);
 
@@ -140,12 +226,14 @@ cudaError_t launch_grouped_split(int mode01, const GroupedSplitArgs& a, int grid
 // SLICE_FP64EMU_CARRY (s <= 5) and SLICE_FP64EMU_CARRY7 (s = 6, 7):
 // FP64-accuracy with the byte-carry recombination, for products
 // slice_fp64_carry_ok accepts (same results as SLICE_FP64EMU).
+// SLICE_CRT: the modular form (residue products, CRT rebuild in the epilogue).
 enum SliceMode {
   SLICE_FP32EMU = 0,
   SLICE_FP64EMU = 1,
   SLICE_LEVELS = 2,
   SLICE_FP64EMU_CARRY = 3,
-  SLICE_FP64EMU_CARRY7 = 4
+  SLICE_FP64EMU_CARRY7 = 4,
+  SLICE_CRT = 5
 };
 
 // Chunks per int32 level-sum segment (SLICE_SEG_CHUNKS * 2^24 < 2^31).
@@ -183,12 +271,24 @@ struct SliceProblem {
   double* C;
   int64_t ldc;
   int64_t* levels;       // SLICE_LEVELS: [s][m][n] int64
+  uint8_t* res;          // SLICE_CRT: residues of the products, bytes [N][rows][ldr] (plane l at l * rplane)
+  int64_t ldr, rplane;   // bytes between rows (a multiple of 16) and between planes
 };
 
 // A tile of a grouped launch: problem index and tile coordinates.
 struct TileRef {
   int32_t prob;
   int16_t tm, tn;
+};
+
+// The modular form's rebuild constants for N = 1 .. CRT_N_MAX moduli:
+// W[N][l] = (M/m_l) ((M/m_l)^-1 mod m_l) mod M as four 32-bit words (least
+// significant first), M = M_N and M/2 as two 64-bit words, invM = 1/M as a float.
+struct CrtTab {
+  uint32_t W[CRT_N_MAX + 1][CRT_N_MAX][4];
+  uint64_t M[CRT_N_MAX + 1][2];
+  uint64_t H[CRT_N_MAX + 1][2];
+  float invM[CRT_N_MAX + 1];
 };
 
 struct SliceGemmArgs {

@@ -190,10 +190,12 @@ ProfScope::~ProfScope() {
 }
 
 // Layout of the emulated-mode workspace of one product.
-void SplitLayout::plan(int64_t m_, int64_t n_, int64_t k_, int s, int elem_bytes) {
+void SplitLayout::plan(int64_t m_, int64_t n_, int64_t k_, int s, int elem_bytes, bool crt_) {
   m = m_; n = n_; k = k_;
   autos = (s == 0);
-  S = emu_planes(s);
+  crt = crt_ && autos;
+  S = crt ? std::max(CRT_N_MAX, SLICE_S_MAX) : emu_planes(s);
+  ldr = static_cast<int64_t>(align_up(static_cast<size_t>(std::max<int64_t>(n, 1)), 16));
   elem = elem_bytes;
   // rows of whole 16-byte vectors: 8 bfloat16 entries, 16 INT8-form digits
   kp = static_cast<int64_t>(align_up(static_cast<size_t>(std::max<int64_t>(k, 1)), elem == 1 ? 16 : 8));
@@ -206,6 +208,7 @@ void SplitLayout::plan(int64_t m_, int64_t n_, int64_t k_, int s, int elem_bytes
   off_part = off; off = align_up(off + (autos ? 8 * static_cast<size_t>(launch_absmax_parts(k)) * n : 0), 256);
   off_sa = off; off = align_up(off + static_cast<size_t>(elem) * S * m * kp, 1024);
   off_sb = off; off = align_up(off + static_cast<size_t>(elem) * S * n * kp, 1024);
+  off_res = off; off = align_up(off + (crt ? static_cast<size_t>(CRT_N_MAX) * m * ldr : 0), 256);
   bytes = off;
 }
 
@@ -213,6 +216,7 @@ void SplitLayout::plan(int64_t m_, int64_t n_, int64_t k_, int s, int elem_bytes
 // automatic slice count: one more memset and the column-spread launch).
 int run_split(mm_handle_s* h, int mode01, const SplitLayout& L, char* ws, const double* A, int64_t lda,
               const double* B, int64_t ldb, cudaStream_t st) {
+  if (L.crt) mode01 = 3;
   uint64_t* rowmax = reinterpret_cast<uint64_t*>(ws + L.off_rowmax);
   uint64_t* colmax = reinterpret_cast<uint64_t*>(ws + L.off_colmax);
   uint32_t* err = err_word(h, st);
@@ -222,6 +226,11 @@ int run_split(mm_handle_s* h, int mode01, const SplitLayout& L, char* ws, const 
   if (dec) e = cudaMemsetAsync(dec, 0, sizeof(SliceDecision), st);   // no row or column seen yet
   if (e == cudaSuccess) e = launch_absmax(A, L.m, L.k, lda, B, L.n, ldb, rowmax, colmax, st, &nscan, dec, L.part(ws));
   if (e != cudaSuccess) return cuda_status(e, "absmax");
+  if (mode01 == 3) {
+    e = launch_decide_fp64(dec, L.k, st);
+    if (e != cudaSuccess) return cuda_status(e, "decide");
+    ++nscan;
+  }
   e = launch_slice_rows(mode01, A, L.m, L.k, lda, rowmax, L.S, L.kp, ws + L.off_sa,
                         reinterpret_cast<int32_t*>(ws + L.off_E), err, st, 0, dec);
   if (e != cudaSuccess) return cuda_status(e, "slice rows");
@@ -230,6 +239,10 @@ int run_split(mm_handle_s* h, int mode01, const SplitLayout& L, char* ws, const 
   if (e != cudaSuccess) return cuda_status(e, "slice cols");
   count_launch(h, 2 + static_cast<uint64_t>(nscan));
   return MM_OK;
+}
+
+bool crt_allowed(const mm_handle_s* h, int precision, int s) {
+  return precision == MM_FP64_EMU && s == 0 && h->opt_fp64_scheme != 1;
 }
 
 int emu_slices(mm_handle_s* h, int precision, int64_t k, int s_override) {
@@ -256,6 +269,20 @@ struct SliceLaunch {
   int mode, bn, cg;
   bool operator==(const SliceLaunch& o) const { return mode == o.mode && bn == o.bn && cg == o.cg; }
 };
+// The modular form's launch: 128- or 256-wide tiles, one CTA or a CTA pair.
+static SliceLaunch crt_launch_for(mm_handle_s* h, int64_t mr, int64_t n, const TileCfg& cfg_in) {
+  const TileCfg dflt = default_cfg(h, MM_FP64_EMU, mr, n, 5);
+  SliceLaunch r;
+  r.mode = SLICE_CRT;
+  r.bn = cfg_in.bn ? cfg_in.bn : dflt.bn;
+  r.cg = cfg_in.cg ? cfg_in.cg : dflt.cg;
+  if (r.bn != 128 && r.bn != 256) r.bn = n > 128 ? 256 : 128;
+  if (r.cg == 4) r.cg = 2;
+  if (r.cg != 1 && r.cg != 2) r.cg = 1;
+  if (h->max_pairs_crt <= 0) r.cg = 1;
+  return r;
+}
+
 static SliceLaunch slice_launch_for(mm_handle_s* h, int precision, int64_t mr, int64_t n, int64_t k, int s,
                                     bool levels, const TileCfg& cfg_in) {
   const bool fp64 = (precision == MM_FP64_EMU);
@@ -289,7 +316,7 @@ static int slice_gemm_launch(mm_handle_s* h, const SplitLayout& L, char* ws, int
                              cudaStream_t st) {
   const bool fp64 = sl.mode != SLICE_FP32EMU;
   const int64_t n = L.n, k = L.k;
-  const int pairs_avail = fp64 ? h->max_pairs_fp64 : h->max_pairs_fp32;
+  const int pairs_avail = sl.mode == SLICE_CRT ? h->max_pairs_crt : fp64 ? h->max_pairs_fp64 : h->max_pairs_fp32;
   CUtensorMap tmA, tmB;
   const int pair = sl.cg >= 2 ? 2 : 1;   // CTAs per tile
   if (!encode_slices_tmap(h, &tmA, ws + L.off_sa + 2 * static_cast<size_t>(r0) * L.kp, k, mr, L.S, L.kp,
@@ -316,6 +343,11 @@ static int slice_gemm_launch(mm_handle_s* h, const SplitLayout& L, char* ws, int
   P.C = C + r0 * ldc;
   P.ldc = ldc;
   P.levels = levels;
+  if (sl.mode == SLICE_CRT) {
+    P.res = reinterpret_cast<uint8_t*>(ws + L.off_res) + r0 * L.ldr;
+    P.ldr = L.ldr;
+    P.rplane = L.m * L.ldr;
+  }
   a.err = err_word(h, st);
   a.timeout_ns = static_cast<uint64_t>(h->opt_timeout_ms) * 1000000ull;
   const int ntiles = P.tiles_m * P.tiles_n;
@@ -352,6 +384,12 @@ int emu_gemm_rows(mm_handle_s* h, int precision, const SplitLayout& L, char* ws,
     rc = slice_gemm_launch(h, L, ws, 0, lo, hi, sl, r0, mr, C, ldc, nullptr, st);
     lo = hi + 1;
   }
+  if (rc == MM_OK && L.crt) {
+    // the modular form: one launch, whatever its modulus count
+    const SliceLaunch sl = crt_launch_for(h, mr, L.n, cfg_in);
+    rc = slice_gemm_launch(h, L, ws, 0, SLICE_CRT_BASE + 1, SLICE_CRT_BASE + CRT_N_MAX, sl, r0, mr, C, ldc, nullptr,
+                           st);
+  }
   return rc;
 }
 
@@ -363,7 +401,7 @@ int run_emulated(mm_handle_s* h, int precision, int64_t m, int64_t n, int64_t k,
   const bool fp64 = (precision == MM_FP64_EMU);
   const int s = emu_slices(h, precision, k, s_override);
   SplitLayout L;
-  L.plan(m, n, k, s);
+  L.plan(m, n, k, s, 2, !levels && crt_allowed(h, precision, s));
   void* wsv = nullptr;
   int rc = ws_alloc(h, L.bytes, st, &wsv);
   if (rc != MM_OK) return rc;
@@ -558,6 +596,7 @@ int mm_create(mm_handle* out, int device, size_t mem_budget_bytes) {
   cudaError_t e2 = fp64_gemm_prepare();
   h->max_pairs_fp32 = slice_gemm_max_pairs(SLICE_FP32EMU);
   h->max_pairs_fp64 = slice_gemm_max_pairs(SLICE_FP64EMU);
+  h->max_pairs_crt = slice_gemm_max_pairs(SLICE_CRT);
   h->max_clusters4_fp32 = slice_gemm_max_clusters4(SLICE_FP32EMU);
   h->max_clusters4_fp64 = slice_gemm_max_clusters4(SLICE_FP64EMU_CARRY);
   if (e1 != cudaSuccess || e2 != cudaSuccess) {
@@ -606,7 +645,8 @@ int gemm_host_pipelined(mm_handle_s* h, int64_t m, int64_t n, int64_t k, const d
   const bool fp64 = precision == MM_FP64_EMU;
   const int s = emu_slices(h, precision, k, 0);
   SplitLayout L;
-  L.plan(m, n, k, s);
+  L.plan(m, n, k, s, 2, crt_allowed(h, precision, s));
+  const int smode = !fp64 ? 1 : (L.crt ? 3 : 0);
   void* wsv = nullptr;
   int rc = ws_alloc(h, L.bytes, st, &wsv);
   if (rc != MM_OK) return rc;
@@ -655,6 +695,10 @@ int gemm_host_pipelined(mm_handle_s* h, int64_t m, int64_t n, int64_t k, const d
         count_launch(h, static_cast<uint64_t>(nl));
       }
     }
+    if (e == cudaSuccess && L.crt) {
+      e = launch_decide_fp64(dec, k, st);
+      count_launch(h, 1);
+    }
   } else if (e == cudaSuccess) {
     e = cudaStreamWaitEvent(st, ev[1], 0);   // B's exponents and slices as soon as B is in
   }
@@ -662,7 +706,7 @@ int gemm_host_pipelined(mm_handle_s* h, int64_t m, int64_t n, int64_t k, const d
     ProfScope ps(h, MM_KERNEL_SPLIT, st);
     if (!dec) e = launch_absmax(nullptr, 0, k, 0, dB, n, n, nullptr, colmax, st);
     if (e == cudaSuccess)
-      e = launch_slice_cols(fp64 ? 0 : 1, dB, k, n, n, colmax, L.S, L.kp, reinterpret_cast<uint16_t*>(ws + L.off_sb),
+      e = launch_slice_cols(smode, dB, k, n, n, colmax, L.S, L.kp, reinterpret_cast<uint16_t*>(ws + L.off_sb),
                             reinterpret_cast<int32_t*>(ws + L.off_F), err, st, dec);
     count_launch(h, dec ? 1 : 2);
   }
@@ -675,7 +719,7 @@ int gemm_host_pipelined(mm_handle_s* h, int64_t m, int64_t n, int64_t k, const d
         ProfScope ps(h, MM_KERNEL_SPLIT, st);
         if (!dec) e = launch_absmax(dA + r0 * k, mr, k, k, nullptr, 0, 0, rowmax + r0, nullptr, st);
         if (e == cudaSuccess)
-          e = launch_slice_rows(fp64 ? 0 : 1, dA + r0 * k, mr, k, k, rowmax + r0, L.S, L.kp, sa + r0 * L.kp, E + r0,
+          e = launch_slice_rows(smode, dA + r0 * k, mr, k, k, rowmax + r0, L.S, L.kp, sa + r0 * L.kp, E + r0,
                                 err, st, m, dec);
         count_launch(h, dec ? 1 : 2);
       }
@@ -796,6 +840,10 @@ int mm_set_option(mm_handle h, int option, int64_t value) {
       if (value != 0 && value != 1) return MM_ERR_INVALID_ARG;
       h->opt_int8 = value != 0;
       return MM_OK;
+    case MM_OPT_FP64_SCHEME:
+      if (value != 0 && value != 1) return MM_ERR_INVALID_ARG;
+      h->opt_fp64_scheme = static_cast<int>(value);
+      return MM_OK;
     default: return MM_ERR_INVALID_ARG;
   }
 }
@@ -813,6 +861,7 @@ int mm_get_option(mm_handle h, int option, int64_t* value) {
     case MM_OPT_CTA_PAIR: *value = h->opt_cta_pair; return MM_OK;
     case MM_OPT_TILE_N: *value = h->opt_tile_n; return MM_OK;
     case MM_OPT_INT8_SLICES: *value = h->opt_int8 ? 1 : 0; return MM_OK;
+    case MM_OPT_FP64_SCHEME: *value = h->opt_fp64_scheme; return MM_OK;
     default: return MM_ERR_INVALID_ARG;
   }
 }
@@ -820,6 +869,12 @@ int mm_get_option(mm_handle h, int option, int64_t* value) {
 int mm_slice_count_rule(int64_t k, float alpha_min, float beta_min) {
   if (k < 1) return -1;
   return slice_count_rule(k, alpha_min, beta_min);
+}
+
+int mm_crt_rule(int64_t k, float alpha_min, float beta_min, int* bits) {
+  if (k < 1 || !bits) return -1;
+  *bits = 0;
+  return crt_rule(k, alpha_min, beta_min, bits);
 }
 
 // ------------------------------------------------------------- diagnostics
@@ -900,6 +955,88 @@ int mm_debug_slice_count(mm_handle h, int64_t m, int64_t n, int64_t k, const dou
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_status(e, "debug slice count");
   *s = d.s;
+  *alpha_min = spread_from_room(d.amin_room);
+  *beta_min = spread_from_room(d.bmin_room);
+  return read_and_clear_err(h, st);
+}
+
+int mm_debug_crt_residues(mm_handle h, int which, int N, int bits, int64_t rows, int64_t cols, const double* X,
+                          int64_t ldx, int32_t* exps, uint16_t* planes, void* stream) {
+  if (!h || (which != 0 && which != 1) || N < 1 || N > CRT_N_MAX || bits < 1 || bits > CRT_B_MAX) return MM_ERR_INVALID_ARG;
+  if (rows <= 0 || cols <= 0 || !X || !exps || !planes || ldx < cols) return MM_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int64_t nvec = (which == 0) ? rows : cols;
+  const int64_t klen = (which == 0) ? cols : rows;
+  SplitLayout L;
+  L.plan(which == 0 ? nvec : 1, which == 1 ? nvec : 1, klen, 0, 2, true);
+  void* wsv = nullptr;
+  int rc = ws_alloc(h, L.bytes, st, &wsv);
+  if (rc != MM_OK) return rc;
+  char* ws = static_cast<char*>(wsv);
+  // a decision record naming the modular form with N moduli and these bits
+  SliceDecision d;
+  d.amin_room = d.bmin_room = 0u;
+  d.s = SLICE_CRT_BASE + N;
+  d.bits = bits;
+  cudaError_t e = cudaMemcpyAsync(L.dec(ws), &d, sizeof(d), cudaMemcpyHostToDevice, st);
+  if (which == 0) {
+    if (e == cudaSuccess)
+      e = launch_absmax(X, nvec, klen, ldx, nullptr, 0, 0, reinterpret_cast<uint64_t*>(ws + L.off_rowmax), nullptr, st);
+    if (e == cudaSuccess)
+      e = launch_slice_rows(3, X, nvec, klen, ldx, reinterpret_cast<uint64_t*>(ws + L.off_rowmax), 0, L.kp,
+                            ws + L.off_sa, exps, err_word(h, st), st, 0, L.dec(ws));
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(planes, 2 * klen, ws + L.off_sa, 2 * L.kp, 2 * klen, static_cast<size_t>(N) * nvec,
+                            cudaMemcpyDeviceToDevice, st);
+  } else {
+    if (e == cudaSuccess)
+      e = launch_absmax(nullptr, 0, klen, 0, X, nvec, ldx, nullptr, reinterpret_cast<uint64_t*>(ws + L.off_colmax), st);
+    if (e == cudaSuccess)
+      e = launch_slice_cols(3, X, klen, nvec, ldx, reinterpret_cast<uint64_t*>(ws + L.off_colmax), 0, L.kp,
+                            ws + L.off_sb, exps, err_word(h, st), st, L.dec(ws));
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(planes, 2 * klen, ws + L.off_sb, 2 * L.kp, 2 * klen, static_cast<size_t>(N) * nvec,
+                            cudaMemcpyDeviceToDevice, st);
+  }
+  count_launch(h, 2);
+  ws_free(h, wsv, L.bytes, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_status(e, "debug residues");
+  return read_and_clear_err(h, st);
+}
+
+int mm_debug_fp64_product(mm_handle h, int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
+                          int64_t ldb, double* C, int64_t ldc, uint8_t* res, int* code, int* bits, float* alpha_min,
+                          float* beta_min, void* stream) {
+  if (!h || !code || !bits || !alpha_min || !beta_min || m <= 0 || n <= 0 || k <= 4) return MM_ERR_INVALID_ARG;
+  int rc = validate_problem(m, n, k, A, lda, B, ldb, C, ldc, MM_FP64_EMU);
+  if (rc != MM_OK) return rc;
+  DeviceGuard g(h->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  SplitLayout L;
+  L.plan(m, n, k, 0, 2, h->opt_fp64_scheme != 1);
+  void* wsv = nullptr;
+  rc = ws_alloc(h, L.bytes, st, &wsv);
+  if (rc != MM_OK) return rc;
+  char* ws = static_cast<char*>(wsv);
+  rc = run_split(h, 0, L, ws, A, lda, B, ldb, st);
+  if (rc == MM_OK) rc = emu_gemm_rows(h, MM_FP64_EMU, L, ws, 0, 0, m, C, ldc, nullptr, TileCfg(), st);
+  if (rc == MM_OK) rc = plain_fallback(h, m, n, k, A, lda, B, ldb, C, ldc, &L.dec(ws)->s, st);
+  SliceDecision d;
+  memset(&d, 0, sizeof(d));
+  cudaError_t e = cudaSuccess;
+  if (rc == MM_OK) e = cudaMemcpyAsync(&d, L.dec(ws), sizeof(d), cudaMemcpyDeviceToHost, st);
+  if (rc == MM_OK && e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (rc == MM_OK && e == cudaSuccess && res && L.crt && d.s > SLICE_CRT_BASE)
+    e = cudaMemcpy2DAsync(res, n, ws + L.off_res, L.ldr, n, static_cast<size_t>(d.s - SLICE_CRT_BASE) * m,
+                          cudaMemcpyDeviceToDevice, st);
+  if (rc == MM_OK && e == cudaSuccess) e = cudaStreamSynchronize(st);
+  ws_free(h, wsv, L.bytes, st);
+  if (rc != MM_OK) return rc;
+  if (e != cudaSuccess) return cuda_status(e, "debug fp64 product");
+  *code = d.s;
+  *bits = d.bits;
   *alpha_min = spread_from_room(d.amin_room);
   *beta_min = spread_from_room(d.bmin_room);
   return read_and_clear_err(h, st);

@@ -13,11 +13,13 @@ cudaError_t slice_gemm_prepare() {
   if ((e = set_smem_attr<256, SLICE_FP32EMU, 2>()) != cudaSuccess) return e;
   if ((e = set_smem_attr<256, SLICE_FP32EMU, 4>()) != cudaSuccess) return e;
   if ((e = slice_prepare_fold()) != cudaSuccess) return e;
+  if ((e = slice_prepare_crt()) != cudaSuccess) return e;
   return slice_prepare_carry();
 }
 
 int slice_gemm_max_pairs(int mode) {
   if (mode == SLICE_FP32EMU) return max_pairs_t<256, SLICE_FP32EMU>();
+  if (mode == SLICE_CRT) return slice_max_pairs_crt();
   return slice_max_pairs_fold(mode == SLICE_LEVELS ? SLICE_LEVELS : SLICE_FP64EMU);
 }
 
@@ -31,6 +33,7 @@ bool slice_gemm_tile_ok(int mode, int bn, int cg) {
     return bn == 256 && (mode == SLICE_FP32EMU || mode == SLICE_FP64EMU_CARRY || mode == SLICE_FP64EMU_CARRY7);
   if (cg != 1 && cg != 2) return false;
   if (mode == SLICE_FP32EMU) return bn == 256 || (bn == 128 && cg == 1);
+  if (mode == SLICE_CRT) return bn == 128 || bn == 256;
   return bn == 128 || bn == 192 || bn == 240 || bn == 256;
 }
 
@@ -50,6 +53,7 @@ cudaError_t launch_slice_gemm(int mode, int bn, int cg, const CUtensorMap* tmA, 
     if (bn == 256) return launch_t<256, SLICE_FP32EMU, 1>(tmA, tmB, a, grid, st);
     return launch_t<128, SLICE_FP32EMU, 1>(tmA, tmB, a, grid, st);
   }
+  if (mode == SLICE_CRT) return slice_launch_crt(bn, cg, tmA, tmB, a, grid, st);
   if (mode == SLICE_FP64EMU_CARRY || mode == SLICE_FP64EMU_CARRY7) {
     if (bn != 128) return slice_launch_carry(mode, bn, cg, tmA, tmB, a, grid, st);
     mode = SLICE_FP64EMU;

@@ -58,6 +58,10 @@ static constexpr int BM = 128;
 static constexpr int BK = 64;                 // bf16 elements per K block (128 bytes)
 static constexpr int SEG_CHUNKS = SLICE_SEG_CHUNKS;   // chunks per int32 level sum
 
+// The modular form's rebuild constants (filled once per device by
+// slice_prepare_crt; only the SLICE_CRT instances read them).
+static __constant__ CrtTab c_crt;
+
 
 // CG = CTAs per output tile: 1, or 2 for a CTA pair (cta_group::2) computing a
 // 256-row tile, each CTA holding 128 rows of A and BN/2 rows of B in shared
@@ -73,8 +77,10 @@ struct Cfg {
   // than 128 keep their columns' int32 level sums in registers: 16 warps for
   // 256 columns (64 sums a thread), 12 for 192 or 240 (64 or 80 sums a thread;
   // 14 warps leave 128 registers a thread)
-  static constexpr bool REG_SUMS = (BN != 128) && (MODE != SLICE_FP32EMU);
-  static constexpr int EPI_WARPS = !REG_SUMS ? 8 : (BN == 256 ? 16 : 12);
+  // The modular form keeps int32 sums in registers on every tile width (8
+  // warps on 128-wide tiles: 64 sums a thread).
+  static constexpr bool REG_SUMS = (MODE == SLICE_CRT) || ((BN != 128) && (MODE != SLICE_FP32EMU));
+  static constexpr int EPI_WARPS = !REG_SUMS ? 8 : (BN == 256 ? 16 : (BN == 128 ? 8 : 12));
   static constexpr int EPI_WARP0 = 2;
   static constexpr int NUM_THREADS = 32 * (EPI_WARP0 + EPI_WARPS);
   static constexpr int A_BYTES = BM * BK * 2;
@@ -89,7 +95,7 @@ struct Cfg {
   static constexpr int STAGES = STAGES_FIT > 10 ? 10 : STAGES_FIT;
   static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
   // two accumulator slots; FP64-accuracy adds the int64 total's planes (BN = 128)
-  static constexpr int TMEM_COLS = (MODE == SLICE_FP32EMU) ? 2 * BN : 512;
+  static constexpr int TMEM_COLS = (MODE == SLICE_FP32EMU || MODE == SLICE_CRT) ? 2 * BN : 512;
   static constexpr int XLO_COL = 2 * BN;
   static constexpr int XHI_COL = 3 * BN;
   static constexpr int COLS_PER_THREAD = BN / (EPI_WARPS / 4);
@@ -134,6 +140,7 @@ struct Step {
   int pa, pb;          // A and B slice indices of the step's first pair
   int pa2, pb2;        // of its second pair (pa2 < 0: one pair)
   bool first, last;    // first / last step of its chunk
+  int dkb;             // K block of the second pair: kb + dkb
 };
 
 // The steps of one FP64-accuracy level D: K chunks of KC blocks, in each K
@@ -159,9 +166,28 @@ __device__ __forceinline__ void walk_level(int nkb, int& chunk, Fn& f) {
 }
 
 // Walk the pipeline steps of one tile in order; f(Step, chunk offset in tile).
+// The steps of the modular form: for each modulus l, K chunks of 16 blocks
+// (at most 1024 terms of at most 2^14: exact f32 sums), one residue pair
+// (l, l) a K block, PPS consecutive K blocks a step.
+template <int PPS, typename Fn>
+__device__ __forceinline__ void walk_crt(int N, int nkb, Fn& f) {
+  int chunk = 0;
+  for (int l = 0; l < N; ++l) {
+    for (int kb0 = 0; kb0 < nkb; kb0 += 16, ++chunk) {
+      const int kb1 = min(kb0 + 16, nkb);
+      for (int kb = kb0; kb < kb1; kb += PPS) {
+        const bool two = PPS == 2 && kb + 1 < kb1;
+        f(Step{kb, l, l, two ? l : -1, two ? l : -1, kb == kb0, kb + (two ? 1 : 0) == kb1 - 1, 1}, chunk);
+      }
+    }
+  }
+}
+
 template <int MODE, int PPS, typename Fn>
 __device__ __forceinline__ void for_each_step(int s, int nkb, Fn&& f) {
-  if (MODE == SLICE_FP32EMU) {
+  if (MODE == SLICE_CRT) {
+    walk_crt<PPS>(s, nkb, f);
+  } else if (MODE == SLICE_FP32EMU) {
     // pairs (p, q), p + q <= 2 (three slices) or p + q <= 1 (s = 2), smallest
     // products first (the same order whether a step carries one pair or two)
     for (int kb = 0; kb < nkb; ++kb) {
@@ -206,6 +232,7 @@ __device__ __forceinline__ void for_each_step(int s, int nkb, Fn&& f) {
 template <int MODE>
 __device__ __forceinline__ int chunks_per_tile(int s, int nkb) {
   if (MODE == SLICE_FP32EMU) return 1;
+  if (MODE == SLICE_CRT) return s * ((nkb + 15) / 16);
   int c = 0;
   for (int d = 2; d <= s + 1; ++d) {
     const int kc = chunk_blocks(d);
@@ -219,17 +246,26 @@ struct TileJob {
   const CUtensorMap* ta;
   const CUtensorMap* tb;
   int tm, tn;
-  int s, fix;    // the problem's slice count and fixed-point shift
+  int s, fix;    // the problem's slice count and fixed-point shift (modular form: N and b)
   bool skip;     // the problem's slice count is outside this launch's range
 };
 
 // A problem's slice count: its automatic count from device memory (written by
 // the splitting kernels before this launch), else the host's.
+// A decision code above SLICE_CRT_BASE names the modular form: N moduli, its
+// bit count in the record's next word.
 __device__ __forceinline__ void resolve_slices(const SliceGemmArgs& a, const SliceProblem& P, TileJob& j) {
   if (P.s_dev != nullptr) {
-    j.s = *P.s_dev;
-    j.skip = j.s < a.s_lo || j.s > a.s_hi || j.s > SLICE_S_MAX;
-    j.fix = j.skip ? 0 : P.fix_tab[j.s & 7];
+    const int code = *P.s_dev;
+    if (code > SLICE_CRT_BASE) {
+      j.s = code - SLICE_CRT_BASE;
+      j.skip = code < a.s_lo || code > a.s_hi;
+      j.fix = P.s_dev[1];
+    } else {
+      j.s = code;
+      j.skip = j.s < a.s_lo || j.s > a.s_hi || j.s > SLICE_S_MAX;
+      j.fix = j.skip ? 0 : P.fix_tab[j.s & 7];
+    }
   } else {
     j.s = P.s;
     j.fix = P.fix_shift;
@@ -288,7 +324,7 @@ __global__ void __launch_bounds__(Cfg<BN, MODE, CG>::NUM_THREADS, 1)
   // nothing to do (the whole grid returns before any setup)
   if (args.probs == nullptr && args.single.s_dev != nullptr) {
     const int s = *args.single.s_dev;
-    if (s < args.s_lo || s > args.s_hi || s > SLICE_S_MAX) return;
+    if (s < args.s_lo || s > args.s_hi || (s > SLICE_S_MAX && s <= SLICE_CRT_BASE)) return;
   }
   const uint32_t warp = warp_id(), lane = lane_id();
   const uint32_t smem_base = (smem_u32(smem_raw) + 1023u) & ~1023u;
@@ -376,9 +412,10 @@ __global__ void __launch_bounds__(Cfg<BN, MODE, CG>::NUM_THREADS, 1)
             const uint16_t mask = static_cast<uint16_t>((1u << rank) | (1u << (rank + 2u)));
             for (int q = 0; q < npairs; ++q) {
               uint8_t* sa = s0 + q * C_::PAIR_BYTES;
-              tma_load_3d_pair_mc(sa + pair_col * (C_::A_BYTES / 2), job.ta, st.kb * BK, ya + pair_col * (BM / 2),
+              const int kx = (st.kb + (q ? st.dkb : 0)) * BK;
+              tma_load_3d_pair_mc(sa + pair_col * (C_::A_BYTES / 2), job.ta, kx, ya + pair_col * (BM / 2),
                                   q ? st.pa2 : st.pa, fb, mask);
-              tma_load_3d_pair(sa + C_::A_BYTES, job.tb, st.kb * BK, yb, q ? st.pb2 : st.pb, fb);
+              tma_load_3d_pair(sa + C_::A_BYTES, job.tb, kx, yb, q ? st.pb2 : st.pb, fb);
             }
           } else if constexpr (CG >= 2) {
             // both CTAs' bytes complete on the leader's barrier; only the leader arrives
@@ -386,15 +423,17 @@ __global__ void __launch_bounds__(Cfg<BN, MODE, CG>::NUM_THREADS, 1)
             const uint32_t fb = mapa_shared(smem_u32(&full_bar[stage]), 0);
             for (int q = 0; q < npairs; ++q) {
               uint8_t* sa = s0 + q * C_::PAIR_BYTES;
-              tma_load_3d_pair(sa, job.ta, st.kb * BK, ya, q ? st.pa2 : st.pa, fb);
-              tma_load_3d_pair(sa + C_::A_BYTES, job.tb, st.kb * BK, yb, q ? st.pb2 : st.pb, fb);
+              const int kx = (st.kb + (q ? st.dkb : 0)) * BK;
+              tma_load_3d_pair(sa, job.ta, kx, ya, q ? st.pa2 : st.pa, fb);
+              tma_load_3d_pair(sa + C_::A_BYTES, job.tb, kx, yb, q ? st.pb2 : st.pb, fb);
             }
           } else {
             mbar_arrive_expect_tx(&full_bar[stage], bytes);
             for (int q = 0; q < npairs; ++q) {
               uint8_t* sa = s0 + q * C_::PAIR_BYTES;
-              tma_load_3d(sa, job.ta, st.kb * BK, ya, q ? st.pa2 : st.pa, &full_bar[stage]);
-              tma_load_3d(sa + C_::A_BYTES, job.tb, st.kb * BK, yb, q ? st.pb2 : st.pb, &full_bar[stage]);
+              const int kx = (st.kb + (q ? st.dkb : 0)) * BK;
+              tma_load_3d(sa, job.ta, kx, ya, q ? st.pa2 : st.pa, &full_bar[stage]);
+              tma_load_3d(sa + C_::A_BYTES, job.tb, kx, yb, q ? st.pb2 : st.pb, &full_bar[stage]);
             }
           }
           ++it;
@@ -537,6 +576,172 @@ __global__ void __launch_bounds__(Cfg<BN, MODE, CG>::NUM_THREADS, 1)
             mbar_arrive(&acce_bar[slot]);
         }
         ++chunk;
+      } else if constexpr (MODE == SLICE_CRT) {
+        // Modular form. For each modulus the thread keeps int32 sums of its
+        // columns over the K chunks (reduced modulo m at every int32 segment
+        // end: a segment adds at most SEG_CHUNKS 2^24 < 2^31), stores their
+        // remainders in [0, m) as bytes, and after the last modulus rebuilds
+        // every output: S = sum_l c_l W_l (four 64-bit column sums of 32-bit
+        // words), q = round(S / M) from a float estimate good to 2^-10, Y = S -
+        // q M moved into [-M/2, M/2) (one step at most), converted to double
+        // with one rounding and scaled by 2^(E_i + F_j - 2b).
+        const int N = job.s, bits = job.fix;
+        const int nkb = P.nkb;
+        const int nch = (nkb + 15) / 16;
+        constexpr int NG = C_::COLS_PER_THREAD / 8;
+        constexpr int NQ = C_::COLS_PER_THREAD / 16;
+        int32_t lsum[NG][8];
+#pragma unroll
+        for (int g = 0; g < NG; ++g)
+#pragma unroll
+          for (int v = 0; v < 8; ++v) lsum[g][v] = 0;
+        uint8_t* const rrow = P.res + row * P.ldr + col0;
+        for (int l = 0; l < N && ok; ++l) {
+          const uint32_t mdl = static_cast<uint32_t>(crt_modulus(l));
+          const uint64_t mg = ~0ull / mdl + 1ull;          // floor(2^64 / m) + 1: exact quotients below 2^32
+          const int32_t c31 = static_cast<int32_t>((1u << 31) % mdl);
+          // x mod m in [0, m) for any int32 x: (x + 2^31) mod m, less 2^31 mod m
+          auto reduce = [&](int32_t x) -> int32_t {
+            const uint32_t u = static_cast<uint32_t>(x) ^ 0x80000000u;
+            const uint32_t q = static_cast<uint32_t>(__umul64hi(static_cast<uint64_t>(u), mg));
+            const int32_t r = static_cast<int32_t>(u - q * mdl) - c31;
+            return r < 0 ? r + static_cast<int32_t>(mdl) : r;
+          };
+          for (int c = 0; c < nch; ++c, ++chunk) {
+            const int slot = chunk & 1;
+            if (!mbar_wait(&accf_bar[slot], static_cast<uint32_t>(chunk >> 1) & 1u, wc)) { ok = false; break; }
+            tc_fence_after();
+#pragma unroll
+            for (int g = 0; g < NG; ++g)
+              tmem_ld8_add_i32(tmem_base + t_lane + static_cast<uint32_t>(slot * BN + col_off + g * 8), lsum[g]);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) {
+              if constexpr (CG >= 2)
+                mbar_arrive_remote(slot ? acce_remote1 : acce_remote0);
+              else
+                mbar_arrive(&acce_bar[slot]);
+            }
+            if (((c + 1) % SEG_CHUNKS) == 0 && c + 1 < nch) {
+#pragma unroll
+              for (int g = 0; g < NG; ++g)
+#pragma unroll
+                for (int v = 0; v < 8; ++v) lsum[g][v] = reduce(lsum[g][v]);
+            }
+          }
+          if (!ok) break;
+          if (row_ok) {
+            uint8_t* const rp = rrow + static_cast<int64_t>(l) * P.rplane;
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+              uint32_t w[4];
+#pragma unroll
+              for (int j = 0; j < 4; ++j) {
+                uint32_t x = 0u;
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                  const int i = q * 16 + j * 4 + b;
+                  x |= static_cast<uint32_t>(reduce(lsum[i >> 3][i & 7])) << (8 * b);
+                }
+                w[j] = x;
+              }
+              if (col0 + 16 * q < P.ldr) *reinterpret_cast<uint4*>(rp + 16 * q) = make_uint4(w[0], w[1], w[2], w[3]);
+            }
+          }
+#pragma unroll
+          for (int g = 0; g < NG; ++g)
+#pragma unroll
+            for (int v = 0; v < 8; ++v) lsum[g][v] = 0;
+        }
+        if (ok && row_ok) {
+          double* const crow = P.C + row * P.ldc;
+          const uint64_t Ml = c_crt.M[N][0], Mh = c_crt.M[N][1];
+          const uint64_t Hl = c_crt.H[N][0], Hh = c_crt.H[N][1];
+          const float invM = c_crt.invM[N];
+          const int ebase = Ei - 2 * bits;
+#pragma unroll 1
+          for (int g4 = 0; g4 < C_::COLS_PER_THREAD / 4; ++g4) {
+            const int64_t cc = col0 + 4 * g4;
+            if (cc >= n) break;
+            uint64_t T[4][4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+              for (int i = 0; i < 4; ++i) T[j][i] = 0ull;
+#pragma unroll 2
+            for (int l = 0; l < N; ++l) {
+              const uint32_t w = *reinterpret_cast<const uint32_t*>(rrow + static_cast<int64_t>(l) * P.rplane + 4 * g4);
+              const uint32_t W0 = c_crt.W[N][l][0], W1 = c_crt.W[N][l][1], W2 = c_crt.W[N][l][2],
+                             W3 = c_crt.W[N][l][3];
+#pragma unroll
+              for (int j = 0; j < 4; ++j) {
+                const uint64_t cl = (w >> (8 * j)) & 255u;
+                T[j][0] += cl * W0;
+                T[j][1] += cl * W1;
+                T[j][2] += cl * W2;
+                T[j][3] += cl * W3;
+              }
+            }
+            const int4 f4 = (cc + 3 < n && ((reinterpret_cast<uintptr_t>(P.F + cc) & 15u) == 0))
+                                ? __ldg(reinterpret_cast<const int4*>(P.F + cc))
+                                : make_int4(__ldg(P.F + cc), cc + 1 < n ? __ldg(P.F + cc + 1) : 0,
+                                            cc + 2 < n ? __ldg(P.F + cc + 2) : 0, cc + 3 < n ? __ldg(P.F + cc + 3) : 0);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              if (cc + j >= n) break;
+              // carries: S = s3:s2:s1:s0 (S < 14 * 2^8 * M < 2^123)
+              uint64_t t1 = T[j][1] + (T[j][0] >> 32);
+              uint64_t t2 = T[j][2] + (t1 >> 32);
+              uint64_t t3 = T[j][3] + (t2 >> 32);
+              const uint64_t lo = (t1 << 32) | (T[j][0] & 0xFFFFFFFFull);
+              const uint64_t hi = (t3 << 32) | (t2 & 0xFFFFFFFFull);
+              const float sf = __ull2float_rn(hi) * 18446744073709551616.0f + __ull2float_rn(lo);
+              const uint64_t q = static_cast<uint64_t>(__float2uint_rn(sf * invM));
+              // Y = S - q M (two's complement, 128 bits)
+              const uint64_t qml = q * Ml, qmh = __umul64hi(q, Ml) + q * Mh;
+              uint64_t yl = lo - qml;
+              uint64_t yh = hi - qmh - (lo < qml ? 1ull : 0ull);
+              // Y >= M/2: Y - M; Y < -M/2: Y + M
+              {
+                const uint64_t th = yh - Hh - (yl < Hl ? 1ull : 0ull);
+                if (static_cast<int64_t>(th) >= 0) {
+                  const uint64_t nl = yl - Ml;
+                  yh = yh - Mh - (yl < Ml ? 1ull : 0ull);
+                  yl = nl;
+                } else {
+                  const uint64_t ul = yl + Hl;
+                  const uint64_t uh = yh + Hh + (ul < yl ? 1ull : 0ull);
+                  if (static_cast<int64_t>(uh) < 0) {
+                    const uint64_t nl = yl + Ml;
+                    yh = yh + Mh + (nl < yl ? 1ull : 0ull);
+                    yl = nl;
+                  }
+                }
+              }
+              // |Y| < 2^127: one rounding to double
+              const bool neg = static_cast<int64_t>(yh) < 0;
+              if (neg) {
+                yl = ~yl + 1ull;
+                yh = ~yh + (yl == 0ull ? 1ull : 0ull);
+              }
+              double d;
+              int e2 = 0;
+              if (yh == 0ull) {
+                d = __ull2double_rn(yl);
+              } else {
+                const int lz = __clzll(static_cast<long long>(yh));
+                uint64_t top = lz ? ((yh << lz) | (yl >> (64 - lz))) : yh;
+                top |= ((lz ? (yl << lz) : yl) != 0ull) ? 1ull : 0ull;   // sticky: below the rounding bit
+                d = __ull2double_rn(top);
+                e2 = 64 - lz;
+              }
+              const int32_t Fj = j == 0 ? f4.x : j == 1 ? f4.y : j == 2 ? f4.z : f4.w;
+              crow[cc + j] = (Ei == EXP_NONFINITE || Fj == EXP_NONFINITE)
+                                 ? __longlong_as_double(0x7FF8000000000000ll)
+                                 : scale_pow2(neg ? -d : d, ebase + Fj + e2);
+            }
+          }
+        }
       } else if constexpr (C_::REG_SUMS) {
         // wide tiles: TMEM holds just the two accumulator slots. Each thread
         // keeps int32 level sums of its columns in registers (one TMEM load
@@ -969,5 +1174,9 @@ cudaError_t slice_launch_carry(int mode, int bn, int cg, const CUtensorMap* tmA,
                                const SliceGemmArgs& a, int grid, cudaStream_t st);
 cudaError_t slice_prepare_carry();
 int slice_max_clusters4_carry();
+cudaError_t slice_launch_crt(int bn, int cg, const CUtensorMap* tmA, const CUtensorMap* tmB, const SliceGemmArgs& a,
+                             int grid, cudaStream_t st);
+cudaError_t slice_prepare_crt();
+int slice_max_pairs_crt();
 
 }  // namespace mmdev

@@ -18,6 +18,7 @@
 //   a0 = bf16_rn(r), a1 = bf16_rn(r - a0), a2 = bf16_rn(r - a0 - a1); the
 //   residuals are exact (kept as integers scaled by 2^e).
 #include <cstdint>
+#include <utility>
 #include <cuda_runtime.h>
 
 #include "kernels.cuh"
@@ -266,6 +267,100 @@ __device__ __forceinline__ void slice8_store(const uint64_t (&vb)[8], int32_t X,
   }
 }
 
+// The modular form's residues of 8 consecutive entries: R = round-half-even(
+// x 2^(b - X)), |R| <= 2^(b-1) <= 2^52, and for every modulus m_l (l < N) the
+// centred residue rho = ((R + h) mod m) - h, h = floor(m/2), as bfloat16 in
+// plane l. The biased u = R + 2^55 (below 2^56) is cut into four 14-bit pieces
+// w_j, held exactly in float; (R + h) mod m is the remainder of
+//   x = w0 + w1 (2^14 mod m) + w2 (2^28 mod m) + w3 (2^42 mod m) + ((h - 2^55) mod m),
+// an integer below 2^24, so every float step is exact; the quotient estimate
+// floor(x * fl(1/m)) is off by at most one (x/m < 2^17: relative error 2^-23),
+// and one correction each way brings the remainder into [0, m). Modulus 256
+// divides 2^55: its residue is u's low byte, centred.
+__host__ __device__ constexpr uint32_t pow2_mod(int e, uint32_t m) {
+  uint32_t r = 1u % m;
+  for (int i = 0; i < e; ++i) r = (2u * r) % m;
+  return r;
+}
+
+// exact float of an integer below 2^23
+__device__ __forceinline__ float small_u2f(uint32_t w) { return __uint_as_float(0x4B000000u | w) - 8388608.0f; }
+
+template <int L>
+__device__ __forceinline__ void crt_plane(const float (&f0)[8], const float (&f1)[8], const float (&f2)[8],
+                                          const float (&f3)[8], const uint32_t (&lo)[8], uint16_t* __restrict__ o,
+                                          bool vec, int cnt) {
+  constexpr uint32_t m = static_cast<uint32_t>(crt_modulus(L));
+  constexpr uint32_t h = m / 2u;
+  uint32_t hb[8];
+  if constexpr (m == 256u) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) hb[u] = bf16_of_small_int(static_cast<int32_t>((lo[u] & 255u) ^ 128u) - 128);
+  } else {
+    constexpr float fm = static_cast<float>(m);
+    constexpr float inv = 1.0f / static_cast<float>(m);
+    constexpr float c1 = static_cast<float>(pow2_mod(14, m)), c2 = static_cast<float>(pow2_mod(28, m)),
+                    c3 = static_cast<float>(pow2_mod(42, m));
+    constexpr float cb = static_cast<float>((h + m - pow2_mod(55, m)) % m);
+    constexpr float fh = static_cast<float>(h);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const float x = fmaf(f3[u], c3, fmaf(f2[u], c2, fmaf(f1[u], c1, f0[u] + cb)));
+      const float q = floorf(x * inv);
+      float r = fmaf(-q, fm, x);
+      r = r < 0.0f ? r + fm : r;
+      r = r >= fm ? r - fm : r;
+      // rho = r - h: an integer of at most 8 significant bits, so its float's
+      // upper half is its bfloat16 (a zero is +0)
+      hb[u] = __float_as_uint(r - fh) >> 16;
+    }
+  }
+  if (vec) {
+    *reinterpret_cast<uint4*>(o) =
+        make_uint4(hb[0] | (hb[1] << 16), hb[2] | (hb[3] << 16), hb[4] | (hb[5] << 16), hb[6] | (hb[7] << 16));
+  } else {
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (u < cnt) o[u] = static_cast<uint16_t>(hb[u]);
+  }
+}
+
+template <int... Ls>
+__device__ __forceinline__ void crt_planes(std::integer_sequence<int, Ls...>, int N, const float (&f0)[8],
+                                           const float (&f1)[8], const float (&f2)[8], const float (&f3)[8],
+                                           const uint32_t (&lo)[8], uint16_t* __restrict__ dst, size_t plane,
+                                           bool vec, int cnt) {
+  ((Ls < N ? crt_plane<Ls>(f0, f1, f2, f3, lo, dst + Ls * plane, vec, cnt) : void()), ...);
+}
+
+__device__ __forceinline__ void slice8_crt_store(const uint64_t (&vb)[8], int32_t X, int N, int b,
+                                                 uint16_t* __restrict__ dst, size_t plane, int cnt) {
+  const bool vec = (cnt == 8) && ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0);
+  float f0[8], f1[8], f2[8], f3[8];
+  uint32_t lo[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const uint64_t ub = static_cast<uint64_t>(scaled_rne(vb[u], b - X) + (1ll << 55));
+    lo[u] = static_cast<uint32_t>(ub);
+    f0[u] = small_u2f(static_cast<uint32_t>(ub) & 0x3FFFu);
+    f1[u] = small_u2f(static_cast<uint32_t>(ub >> 14) & 0x3FFFu);
+    f2[u] = small_u2f(static_cast<uint32_t>(ub >> 28) & 0x3FFFu);
+    f3[u] = small_u2f(static_cast<uint32_t>(ub >> 42));
+  }
+  crt_planes(std::make_integer_sequence<int, CRT_N_MAX>{}, N, f0, f1, f2, f3, lo, dst, plane, vec, cnt);
+}
+
+// Mode 3: the FP64-accuracy form the decision names -- the modular form's
+// residues (code SLICE_CRT_BASE + N, bits b) or digits (code s <= 7); nothing
+// for the plain fallback.
+__device__ __forceinline__ void slice8_auto_store(const uint64_t (&vb)[8], int32_t X, int code, int bits,
+                                                  uint16_t* __restrict__ dst, size_t plane, int cnt) {
+  if (code > SLICE_CRT_BASE)
+    slice8_crt_store(vb, X, code - SLICE_CRT_BASE, bits, dst, plane, cnt);
+  else if (code <= SLICE_S_MAX)
+    slice8_store<0>(vb, X, code, dst, plane, cnt);
+}
+
 // ------------------------------------------------------ spread statistic
 // 2^x as a float for x <= 127 (0 below the normal range).
 __device__ __forceinline__ float pow2f(int x) {
@@ -464,26 +559,48 @@ __device__ __forceinline__ int decided_slices(SliceDecision* dec, int s, int64_t
   return shared_s;
 }
 
+// Mode 3 (automatic FP64-accuracy with the modular form allowed): the decision
+// code and bit count decide_fp64_kernel recorded (uniform loads).
+__device__ __forceinline__ int decided_fp64(const SliceDecision* dec, int* bits) {
+  *bits = dec->bits;
+  return dec->s;
+}
+
+// One thread: the automatic FP64-accuracy decision of a product from the
+// scan's spreads, with the modular form allowed (fp64_decision).
+__global__ void decide_fp64_kernel(SliceDecision* dec, int64_t k) {
+  if (threadIdx.x != 0) return;
+  int b = 0;
+  const int code = fp64_decision(k, spread_from_room(dec->amin_room), spread_from_room(dec->bmin_room), true, &b);
+  dec->s = code;
+  dec->bits = b;
+}
+
 // Slices of 8 consecutive entries A[row][c0 .. c0+8) (rows scaled by E).
 template <int MODE>  // see SliceElem
 __device__ __forceinline__ void slice_rows_body(const double* __restrict__ A, int64_t plane_rows, int64_t k,
                                                 int64_t lda, const uint64_t* __restrict__ rowmax, int s, int64_t kp,
                                                 typename SliceElem<MODE>::T* __restrict__ slices,
                                                 int32_t* __restrict__ E,
-                                                uint32_t* __restrict__ err, int64_t row, int64_t c0) {
+                                                uint32_t* __restrict__ err, int64_t row, int64_t c0,
+                                                int bits = 0) {
   const uint64_t mx = rowmax[row];
   const int32_t Ei = exponent_from_max(mx, exp_offset(MODE));
   if (c0 == 0) {
     E[row] = Ei;
     if (Ei == EXP_NONFINITE) atomicOr(err, MM_DEV_ERR_NONFINITE);
   }
-  if (MODE != 1 && s > SLICE_S_MAX) return;   // the product runs through the plain FP64 kernel
+  if (MODE != 1 && MODE != 3 && s > SLICE_S_MAX) return;   // the product runs through the plain FP64 kernel
+  if (MODE == 3 && s > SLICE_S_MAX && s <= SLICE_CRT_BASE) return;
   const double* a = A + row * lda + c0;
   uint64_t vb[8];
   const int cnt = static_cast<int>((k - c0) < 8 ? (k - c0) : 8);
 #pragma unroll
   for (int u = 0; u < 8; ++u) vb[u] = (u < cnt && Ei != EXP_NONFINITE) ? dbits(__ldg(a + u)) : 0ull;
-  slice8_store<MODE>(vb, Ei, s, slices + row * kp + c0, static_cast<size_t>(plane_rows) * kp, cnt);
+  if constexpr (MODE == 3)
+    slice8_auto_store(vb, Ei, s, bits, slices + row * kp + c0, static_cast<size_t>(plane_rows) * kp, cnt);
+  else
+    slice8_store<MODE>(vb, Ei, s, slices + row * kp + c0, static_cast<size_t>(plane_rows) * kp, cnt);
 }
 
 // Slices of the 64 (k) x 32 (n) block of B at (k0, n0), transposed through
@@ -493,7 +610,8 @@ __device__ __forceinline__ void slice_cols_body(const double* __restrict__ B, in
                                                 const uint64_t* __restrict__ colmax, int s, int64_t kp,
                                                 typename SliceElem<MODE>::T* __restrict__ slices,
                                                 int32_t* __restrict__ F,
-                                                uint32_t* __restrict__ err, int64_t k0, int64_t n0) {
+                                                uint32_t* __restrict__ err, int64_t k0, int64_t n0,
+                                                int bits = 0) {
   __shared__ uint64_t tile[64][33];
   __shared__ int32_t fexp[32];
   const int t = threadIdx.x;
@@ -509,7 +627,8 @@ __device__ __forceinline__ void slice_cols_body(const double* __restrict__ B, in
     }
     fexp[t] = Fj;
   }
-  if (MODE != 1 && s > SLICE_S_MAX) return;   // plain FP64 fallback: F only (uniform over the block)
+  if (MODE != 1 && MODE != 3 && s > SLICE_S_MAX) return;   // plain FP64 fallback: F only (uniform over the block)
+  if (MODE == 3 && s > SLICE_S_MAX && s <= SLICE_CRT_BASE) return;
   {
     // load 64 x 32 doubles: thread -> row t/4, columns (t%4)*8 .. +8
     const int r = t >> 2, cb = (t & 3) * 8;
@@ -530,7 +649,10 @@ __device__ __forceinline__ void slice_cols_body(const double* __restrict__ B, in
     uint64_t vb[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) vb[u] = (Fj == EXP_NONFINITE || u >= cnt) ? 0ull : tile[kb + u][jl];
-    slice8_store<MODE>(vb, Fj, s, slices + j * kp + c0, static_cast<size_t>(n) * kp, cnt);
+    if constexpr (MODE == 3)
+      slice8_auto_store(vb, Fj, s, bits, slices + j * kp + c0, static_cast<size_t>(n) * kp, cnt);
+    else
+      slice8_store<MODE>(vb, Fj, s, slices + j * kp + c0, static_cast<size_t>(n) * kp, cnt);
   }
   __syncthreads();  // the tile is reused by the next block of a persistent loop
 }
@@ -601,10 +723,12 @@ __global__ void slice_rows_kernel(const double* __restrict__ A, int64_t m, int64
                                   SliceDecision* dec) {
   const int64_t row = blockIdx.x;
   const int64_t c0 = (static_cast<int64_t>(blockIdx.y) * blockDim.x + threadIdx.x) * 8;
-  const int se = decided_slices(dec, s, k, blockIdx.x == 0 && blockIdx.y == 0, MODE == 2 ? 0.5f : 1.0f);
+  int bits = 0;
+  const int se = (MODE == 3) ? decided_fp64(dec, &bits)
+                             : decided_slices(dec, s, k, blockIdx.x == 0 && blockIdx.y == 0, MODE == 2 ? 0.5f : 1.0f);
   if (row < m && c0 < k)
     slice_rows_body<MODE>(A, plane_rows, k, lda, rowmax, se, kp, static_cast<typename SliceElem<MODE>::T*>(slices), E,
-                          err, row, c0);
+                          err, row, c0, bits);
 }
 
 template <int MODE>
@@ -613,9 +737,10 @@ __global__ void __launch_bounds__(256) slice_cols_kernel(const double* __restric
                                                          int64_t kp, void* __restrict__ slices,
                                                          int32_t* __restrict__ F, uint32_t* __restrict__ err,
                                                          SliceDecision* dec) {
-  const int se = decided_slices(dec, s, k, false, MODE == 2 ? 0.5f : 1.0f);
+  int bits = 0;
+  const int se = (MODE == 3) ? decided_fp64(dec, &bits) : decided_slices(dec, s, k, false, MODE == 2 ? 0.5f : 1.0f);
   slice_cols_body<MODE>(B, k, n, ldb, colmax, se, kp, static_cast<typename SliceElem<MODE>::T*>(slices), F, err,
-                        static_cast<int64_t>(blockIdx.y) * 64, static_cast<int64_t>(blockIdx.x) * 32);
+                        static_cast<int64_t>(blockIdx.y) * 64, static_cast<int64_t>(blockIdx.x) * 32, bits);
 }
 
 // --------------------------------------------------------- grouped kernels
@@ -887,6 +1012,8 @@ cudaError_t launch_slice_rows(int mode, const double* A, int64_t m, int64_t k, i
   dim3 blk(128), grd(static_cast<unsigned>(m), static_cast<unsigned>((k + 1023) / 1024));
   if (mode == 0)
     slice_rows_kernel<0><<<grd, blk, 0, st>>>(A, m, k, lda, rowmax, s, kp, slices, E, err, plane_rows, dec);
+  else if (mode == 3)
+    slice_rows_kernel<3><<<grd, blk, 0, st>>>(A, m, k, lda, rowmax, s, kp, slices, E, err, plane_rows, dec);
   else if (mode == 2)
     slice_rows_kernel<2><<<grd, blk, 0, st>>>(A, m, k, lda, rowmax, s, kp, slices, E, err, plane_rows, dec);
   else
@@ -901,10 +1028,17 @@ cudaError_t launch_slice_cols(int mode, const double* B, int64_t k, int64_t n, i
   dim3 blk(256), grd(static_cast<unsigned>((n + 31) / 32), static_cast<unsigned>((k + 63) / 64));
   if (mode == 0)
     slice_cols_kernel<0><<<grd, blk, 0, st>>>(B, k, n, ldb, colmax, s, kp, slices, F, err, dec);
+  else if (mode == 3)
+    slice_cols_kernel<3><<<grd, blk, 0, st>>>(B, k, n, ldb, colmax, s, kp, slices, F, err, dec);
   else if (mode == 2)
     slice_cols_kernel<2><<<grd, blk, 0, st>>>(B, k, n, ldb, colmax, s, kp, slices, F, err, dec);
   else
     slice_cols_kernel<1><<<grd, blk, 0, st>>>(B, k, n, ldb, colmax, s, kp, slices, F, err, nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_decide_fp64(SliceDecision* dec, int64_t k, cudaStream_t st) {
+  decide_fp64_kernel<<<1, 32, 0, st>>>(dec, k);
   return cudaGetLastError();
 }
 

@@ -61,6 +61,23 @@ def test_slice_count_rule_matches_the_oracle(lib):
     assert lib.mm_slice_count_rule(0, 0.25, 0.25) == -1
 
 
+def test_crt_rule_matches_the_oracle(lib):
+    """The library's modular-form parameters (the function the decision kernel
+    runs) against the oracle's, on a grid of k and float32 spreads."""
+    import numpy as np
+    from oracle import emulation as em
+    spreads = np.float32([0.5, 0.3, 0.25, 0.1, 0.05, 0.02, 1e-3, 1e-5, 0.0, np.inf])
+    b = ctypes.c_int(0)
+    for k in [1, 5, 7, 64, 96, 700, 1000, 2048, 4096, 8192, 12288, 65536, 1 << 22]:
+        for a in spreads:
+            for c in spreads:
+                N = lib.mm_crt_rule(k, float(a), float(c), ctypes.byref(b))
+                want = em.crt_params_from_spread(k, float(a), float(c))
+                assert (N, b.value) == ((want[1], want[0]) if want else (0, 0)), (k, a, c)
+    assert lib.mm_crt_rule(0, 0.25, 0.25, ctypes.byref(b)) == -1
+    assert lib.mm_crt_rule(10, 0.25, 0.25, None) == -1
+
+
 def test_create_without_gpu_fails_cleanly(lib):
     h = ctypes.c_void_p()
     rc = lib.mm_create(ctypes.byref(h), 0, 0)

@@ -1,0 +1,234 @@
+"""GPU parity of the modular (Chinese-remainder) form of the FP64-accuracy
+product against the oracle, through the C ABI.
+
+* the centred residues of the scaled entries, bit for bit (bfloat16 patterns);
+* the device's decision (modulus count and bit count) against the oracle's;
+* the residue products reduced modulo their moduli (bytes), bit for bit, over
+  several tiles with ragged tails, several K chunks and more than one int32
+  segment;
+* the result, bit for bit against the oracle's exactly rounded value, and
+  within 4k 2^-53 |A||B| of the triple-loop oracle; every tiling gives the
+  same bits; non-finite inputs.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import emulation as em
+from paper_2408_15384_gb300 import inputs
+
+from gpu_util import bf16_bits_of, bound_ok, max_ratio
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+REL = 1e-4   # the device's float spreads against the oracle's exact ones
+
+
+@pytest.fixture(scope="module")
+def mm():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2408_15384_gb300 as mm
+    from paper_2408_15384_gb300 import build
+    build.build()
+    return mm
+
+
+@pytest.fixture(scope="module")
+def h(mm):
+    with mm.Handle(0) as hh:
+        yield hh
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+# ------------------------------------------------------------------ residues
+@pytest.mark.parametrize("N,b", [(3, 8), (11, 37), (12, 42), (14, 53)])
+def test_residues_bit_exact(h, mm, N, b):
+    A = inputs.row_scaled(70, 133, 20 + N)
+    A[3, :] = 0.0
+    A[5, 7] = 5e-324
+    A[6, 1] = -1e-310
+    A[8, :] = 2.0 ** 60 * inputs.uniform(1, 133, 5, 3)[0]
+    B = inputs.col_scaled(133, 45, 20 + N)
+    B[:, 2] = 0.0
+    E_ref = em.row_exponents(A, 2)
+    rA = em.crt_residues(em.crt_integer_repr(A, E_ref, b), N)
+    E, plA, rc = h.debug_crt_residues(dev(A), 0, N, b)
+    assert rc == 0
+    assert np.array_equal(E.cpu().numpy(), E_ref)
+    assert np.array_equal(plA.cpu().numpy().view(np.uint16), bf16_bits_of(rA))
+    F_ref = em.col_exponents(B, 2)
+    rB = em.crt_residues(em.crt_integer_repr(B.T, F_ref, b), N)        # [N][n][k]: B transposed
+    F, plB, rc = h.debug_crt_residues(dev(B), 1, N, b)
+    assert rc == 0
+    assert np.array_equal(F.cpu().numpy(), F_ref)
+    assert np.array_equal(plB.cpu().numpy().view(np.uint16), bf16_bits_of(rB))
+
+
+def test_golden_residues_on_device(h, mm, golden_dir):
+    import json, os
+    g = json.load(open(os.path.join(golden_dir, "crt_residues.json")))
+    # entries R * 2^-10 with a row maximum 2^10 * 2^-10 = 1 (E = 2): b = 12 gives R back
+    for r in g["residues"]:
+        l = em.CRT_MODULI.index(r["m"])
+        row = np.array([[r["R"] * 2.0 ** -10, 1.0]])
+        _, pl, rc = h.debug_crt_residues(dev(row), 0, l + 1, 12)
+        assert rc == 0
+        assert pl.cpu().numpy().view(np.uint16)[l, 0, 0] == bf16_bits_of([r["rho"]])[0], r
+
+
+# ------------------------------------------------------------------ decision
+def _case(name, m, n, k, seed):
+    if name == "scaled":
+        return inputs.row_scaled(m, k, seed), inputs.col_scaled(k, n, seed)
+    if name == "uniform":
+        return inputs.uniform(m, k, seed, 1), inputs.uniform(k, n, seed, 2)
+    if name == "normal":
+        return inputs.box_muller(m, k, seed, 1), inputs.box_muller(k, n, seed, 2)
+    if name == "t3":
+        return inputs.student_t3(m, k, seed, 1), inputs.student_t3(k, n, seed, 2)
+    if name == "spread":
+        return inputs.wide_spread(m, k, seed, 1), inputs.wide_spread(k, n, seed, 2)
+    raise KeyError(name)
+
+
+def _allowed(k, a, b):
+    """decision codes the rule gives within REL of the oracle's spreads"""
+    out = set()
+    for f in (1 - REL, 1, 1 + REL):
+        for g in (1 - REL, 1, 1 + REL):
+            bN = em.crt_params_from_spread(k, a * f, b * g)
+            if bN:
+                out.add((16 + bN[1], bN[0]))
+            else:
+                s = em.slice_count_from_spread(k, a * f, b * g)
+                out.add((s, 0))
+    return out
+
+
+PRODUCTS = [("scaled", 300, 520, 2000), ("scaled", 130, 257, 1100), ("uniform", 129, 130, 64),
+            ("normal", 257, 300, 700), ("t3", 64, 200, 1500), ("spread", 200, 129, 900), ("scaled", 1, 1, 5),
+            ("scaled", 260, 300, 4100)]
+
+
+@pytest.mark.parametrize("name,m,n,k", PRODUCTS)
+def test_products_bit_exact(h, mm, name, m, n, k):
+    A, B = _case(name, m, n, k, 7 + k)
+    C, code, bits, a_dev, b_dev, res = h.debug_fp64_product(dev(A), dev(B))
+    assert h.sync() == 0
+    a = float(em.row_spread(A, em.row_exponents(A, 2)).min())
+    b = float(em.col_spread(B, em.col_exponents(B, 2)).min())
+    assert abs(a_dev - a) <= REL * a and abs(b_dev - b) <= REL * b
+    assert (code, bits) in _allowed(k, a, b), (code, bits, em.fp64_scheme(A, B))
+    got = C.cpu().numpy()
+    ref, D = oracle.gemm(A, B), oracle.absprod(A, B)
+    assert bound_ok(got, ref, D, em.gamma(k, "fp64_emu")), max_ratio(got, ref, D, em.gamma(k, "fp64_emu"))
+    if code <= mm.CRT_BASE:
+        pytest.skip("this product takes the digit form")
+    N = code - mm.CRT_BASE
+    # every 7th row and the last (rows of every tile, the ragged tail), all columns
+    rows = sorted(set(range(0, m, 7)) | {m - 1})
+    E, F = em.row_exponents(A, 2), em.col_exponents(B, 2)
+    RA = em.crt_integer_repr(A[rows], E[rows], bits)
+    RB = em.crt_integer_repr(B.T, F, bits).T
+    P = em.crt_products(em.crt_residues(RA, N), em.crt_residues(RB, N))
+    want = np.stack([np.mod(P[l], em.CRT_MODULI[l]) for l in range(N)]).astype(np.uint8)
+    assert np.array_equal(res.cpu().numpy()[:, rows, :], want)
+    rows = rows[:: max(1, len(rows) // 12)]
+    assert np.array_equal(got[rows], em.gemm_fp64_crt(A[rows], B, bits, N))
+
+
+def test_more_than_one_int32_segment(h, mm):
+    # k = 130000: 127 K chunks of 1024 a modulus, so each product's int32 sums
+    # are reduced once mid-way (every 120 chunks)
+    m, n, k = 9, 20, 130000
+    A, B = _case("scaled", m, n, k, 77)
+    C, code, bits, _, _, res = h.debug_fp64_product(dev(A), dev(B))
+    assert h.sync() == 0
+    assert code > mm.CRT_BASE
+    N = code - mm.CRT_BASE
+    E, F = em.row_exponents(A, 2), em.col_exponents(B, 2)
+    P = em.crt_products(em.crt_residues(em.crt_integer_repr(A, E, bits), N),
+                        em.crt_residues(em.crt_integer_repr(B.T, F, bits).T, N))
+    want = np.stack([np.mod(P[l], em.CRT_MODULI[l]) for l in range(N)]).astype(np.uint8)
+    assert np.array_equal(res.cpu().numpy(), want)
+    assert np.array_equal(C.cpu().numpy(), em.gemm_fp64_crt(A, B, bits, N))
+
+
+@pytest.mark.parametrize("m,n,k", [(300, 260, 1100), (129, 400, 64), (257, 255, 4100), (520, 136, 700)])
+def test_tilings_agree_bitwise(h, mm, m, n, k):
+    A, B = _case("scaled", m, n, k, 900 + k)
+    out = {}
+    for cg in (1, 2):
+        for bn in (128, 256):
+            h.set_option(mm.OPT_CTA_PAIR, cg)
+            h.set_option(mm.OPT_TILE_N, bn)
+            try:
+                C, code, _, _, _, _ = h.debug_fp64_product(dev(A), dev(B), residues=False)
+                assert h.sync() == 0
+            finally:
+                h.set_option(mm.OPT_CTA_PAIR, 0)
+                h.set_option(mm.OPT_TILE_N, 0)
+            assert code > mm.CRT_BASE
+            out[(cg, bn)] = C.cpu().numpy()
+    first = out[(1, 128)]
+    for key, C in out.items():
+        assert np.array_equal(C, first), key
+    assert bound_ok(first, oracle.gemm(A, B), oracle.absprod(A, B), em.gamma(k, "fp64_emu"))
+
+
+def test_nonfinite_inputs(h, mm):
+    m, n, k = 140, 150, 900
+    A, B = _case("scaled", m, n, k, 5)
+    A[7, 11] = np.nan
+    B[3, 20] = np.inf
+    C = h.gemm(dev(A), dev(B), precision=mm.FP64_EMU)
+    assert h.sync() == mm.NONFINITE
+    got = C.cpu().numpy()
+    assert np.all(np.isnan(got[7, :])) and np.all(np.isnan(got[:, 20]))
+    keep_r = [i for i in range(m) if i != 7]
+    keep_c = [j for j in range(n) if j != 20]
+    A2, B2 = A[keep_r], B[:, keep_c]
+    ref, D = oracle.gemm(A2, B2), oracle.absprod(A2, B2)
+    assert bound_ok(got[np.ix_(keep_r, keep_c)], ref, D, em.gamma(k, "fp64_emu"))
+
+
+def test_digit_form_option(h, mm):
+    # MM_OPT_FP64_SCHEME = 1: the digit form, whatever the modular form would do
+    A, B = _case("scaled", 200, 300, 3000, 12)
+    h.set_option(mm.OPT_FP64_SCHEME, 1)
+    try:
+        C, code, _, _, _, _ = h.debug_fp64_product(dev(A), dev(B), residues=False)
+        assert h.sync() == 0
+    finally:
+        h.set_option(mm.OPT_FP64_SCHEME, 0)
+    assert code == em.slice_count(A, B)
+    s = code
+    E, sA = em.fp64_slices_A(A, s)
+    F, sB = em.fp64_slices_B(B, s)
+    rows = [0, 77, 199]
+    Ce = em.recombine_exact(em.level_products(sA[:, rows], sB, s), E[rows], F, s)
+    assert np.array_equal(C.cpu().numpy()[rows], Ce)
+    with pytest.raises(mm.MMError):
+        h.set_option(mm.OPT_FP64_SCHEME, 2)
+
+
+def test_workload_takes_twelve_moduli(h, mm):
+    # the benchmark workload at M = N = K = 8192: its smallest spreads (near
+    # 0.2436) ask for 38 bits, one more than 11 moduli hold at k = 8192, so 12
+    # moduli (12 residue products against the digit form's 15), 41 bits
+    A = torch.empty((8192, 8192), dtype=torch.float64, device="cuda")
+    B = torch.empty((8192, 8192), dtype=torch.float64, device="cuda")
+    mm.fill_uniform(A, seed=3, stream_id=inputs.STREAM_A, scale_mode=1, exp_stream_id=inputs.STREAM_EXP_A)
+    mm.fill_uniform(B, seed=3, stream_id=inputs.STREAM_B, scale_mode=2, exp_stream_id=inputs.STREAM_EXP_B)
+    C, code, bits, a, b, _ = h.debug_fp64_product(A, B, residues=False)
+    assert h.sync() == 0
+    assert (code - mm.CRT_BASE, bits) == mm.crt_rule(8192, a, b) == (12, 41), (code, bits, a, b)
+    rows = [0, 4095, 8191]
+    Ah, Bh = A.cpu().numpy(), B.cpu().numpy()
+    got = C.cpu().numpy()[rows]
+    assert bound_ok(got, oracle.gemm_rows(Ah, Bh, rows), oracle.absprod_rows(Ah, Bh, rows), em.gamma(8192, "fp64_emu"))

@@ -31,9 +31,12 @@ def mm():
     return mm
 
 
-@pytest.fixture(scope="module")
-def h(mm):
+@pytest.fixture(scope="module", params=["auto", "digits"])
+def h(mm, request):
+    # "auto": FP64-accuracy single products take the modular form where it fits
+    # (the default); "digits": the digit form only (MM_OPT_FP64_SCHEME = 1)
     with mm.Handle(0) as hh:
+        hh.set_option(mm.OPT_FP64_SCHEME, 0 if request.param == "auto" else 1)
         yield hh
 
 
@@ -164,8 +167,19 @@ def test_fp64_emu_within_bound_and_exact(h, mm, m, n, k):
     C_ref = oracle.gemm(A, B)
     D = oracle.absprod(A, B)
     assert bound_ok(C, C_ref, D, em.gamma(k, "fp64")), max_ratio(C, C_ref, D, em.gamma(k, "fp64"))
+    if k <= 4:
+        return
+    _, code, bits, _, _, _ = h.debug_fp64_product(dev(A), dev(B))
+    want = em.fp64_scheme(A, B, modular=h.get_option(mm.OPT_FP64_SCHEME) == 0)
+    if want[0] == "crt":
+        # the modular form: the exact integer product of the scaled entries, rounded once
+        assert (code, bits) == (mm.CRT_BASE + want[2], want[1])
+        rows = list(range(0, m, max(1, m // 16)))[:16]
+        assert np.array_equal(C[rows], em.gemm_fp64_crt(A[rows], B, bits, code - mm.CRT_BASE))
+        return
     s, _, _ = h.debug_slice_count(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda())
     assert s == em.slice_count(A, B)   # far from the rule's thresholds for these inputs
+    assert code == (s if want[0] == "digits" else em.S_PLAIN)
     if s == em.S_PLAIN:
         return
     E, sA = em.fp64_slices_A(A, s)

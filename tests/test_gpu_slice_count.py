@@ -35,7 +35,10 @@ def mm():
 
 @pytest.fixture(scope="module")
 def h(mm):
+    # the digit form for single products too, so that grouped and single
+    # products are compared on the same form (grouped ones always take it)
     with mm.Handle(0) as hh:
+        hh.set_option(mm.OPT_FP64_SCHEME, 1)
         yield hh
 
 

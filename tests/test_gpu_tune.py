@@ -52,12 +52,13 @@ def test_autotune_single_fp64_emu_same_bits(mm):
         bn, cg, _ = entry
         assert bn in (128, 192, 240, 256) and cg in (1, 2)
         # a later product of the same bucket uses the entry: one split pass (the
-        # fused scan of both operands, the column spreads, row and column
-        # slicing), one slice GEMM (k = 900 admits only s = 6 or 7, one kernel
-        # for both) and the plain-FP64 fallback launch, which returns at once
+        # fused scan of both operands, the column spreads, the decision, row and
+        # column slicing), one digit-form slice GEMM (k = 900 admits only s = 6
+        # or 7, one kernel for both), one modular-form slice GEMM (one of the two
+        # returns at once) and the plain-FP64 fallback launch, which returns at once
         n0 = h.stats()
         C2 = run(h, A, B, mm.FP64_EMU)
-        assert h.stats() - n0 == 6
+        assert h.stats() - n0 == 8
         assert h.tune_lookup(mm.FP64_EMU, 720, 620, 1000) == entry   # same bucket
     assert np.array_equal(C1, ref) and np.array_equal(C2, ref)
 
@@ -105,6 +106,7 @@ def group_bucket(probs):
 def test_autotune_grouped_same_bits(mm):
     probs = make_group(30, 16, 400, 63)
     with mm.Handle(0) as h0:
+        h0.set_option(mm.OPT_FP64_SCHEME, 1)   # the digit form, as grouped products take it
         ref = [run(h0, A, B, mm.FP64_EMU) for A, B in probs]
     with mm.Handle(0) as h:
         h.set_option(mm.OPT_AUTOTUNE, 1)
@@ -127,6 +129,7 @@ def test_grouped_wide_tiles_from_loaded_table(mm, tmp_path, prec):
     path.write_text("# mm tune table v1: kind precision b0 b1 b2 bn cg kern ms\n"
                     f"1 {prec} {b_cnt} {b_d} 0 256 1 0 1.0\n")
     with mm.Handle(0) as h:
+        h.set_option(mm.OPT_FP64_SCHEME, 1)   # the digit form, as grouped products take it
         ref = [run(h, A, B, prec) for A, B in probs]
         h.tune_load(str(path))
         assert h.tune_lookup(prec, cnt, d, grouped=True) == (256, 1, 0)

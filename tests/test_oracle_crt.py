@@ -233,11 +233,16 @@ def test_too_few_bits_leave_the_bound():
 
 
 def test_workload_parameters():
-    # uniform[-1,1) * 2^e rows and columns at k = 8192: spreads near 1/4, so
-    # 37 bits and 11 moduli (11 residue products against 15 digit pairs)
+    # uniform[-1,1) * 2^e rows and columns at k = 8192: spreads near 1/4. On
+    # 16 rows and columns the smallest are above 0.2437 and 37 bits do (11
+    # moduli); over all 8192 rows and columns the smallest are near 0.2436,
+    # which asks for 38 bits, one more than 11 moduli hold: 12 moduli, and
+    # then 41 bits (12 residue products against the digit form's 15 pairs)
     A = inputs.row_scaled(16, 8192, 3)
     B = inputs.col_scaled(8192, 16, 3)
     assert em.crt_params(A, B) == (37, 11)
+    assert em.crt_params_from_spread(8192, 0.2436, 0.2435) == (41, 12)
+    assert not em.crt_fits(8192, 38, 11) and em.crt_fits(8192, 37, 11)
 
 
 # ------------------------------------------------------------ the rule

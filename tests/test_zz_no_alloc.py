@@ -58,6 +58,8 @@ def _operands(m, n, k, seed, kind):
 @pytest.mark.parametrize("prec,mode", [(1, "fp64_emu"), (2, "fp32_emu")])
 def test_static_scratch_matches_mm_gemm_twice(mm, prec, mode):
     with mm.Handle(0) as h:
+        # the allocation-free call takes the digit form; so does this handle
+        h.set_option(mm.OPT_FP64_SCHEME, 1)
         for m, n, k, seed, kind in CASES:
             A, B = _operands(m, n, k, seed, kind)
             Ad = torch.from_numpy(A).cuda()
