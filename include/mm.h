@@ -24,7 +24,7 @@
  *                so that the error stays near half of the componentwise
  *                bound 4k*2^-53 * (|A||B|); where no s <= 7 would, the product
  *                runs on the plain FP64 kernel instead (see mm_gemm).
- *                Single products take the modular form instead where it fits
+ *                Products take the modular form instead where it fits
  *                (Ozaki, Uchino, Imamura 2025, "Ozaki scheme II"): the same
  *                scaled integers, b bits each, reduced modulo N <= 14 pairwise
  *                coprime moduli <= 256 (residues held in bfloat16), one
@@ -179,7 +179,8 @@ int mm_sync(mm_handle h, void *stream);
  * copies its descriptors into it first. The launch configuration comes from
  * the autotuner's table (MM_OPT_AUTOTUNE) or the defaults. Each problem's
  * result equals mm_gemm on that problem: bit-identical for MM_FP64_EMU (the
- * same slice counts and exact recombination whatever the tiles) and for
+ * same decision from the same spreads, the modular form's exact rebuild or
+ * the digit form's exact recombination, whatever the tiles) and for
  * MM_FP64 when both use the same FP64 tile kernel; within its bound for
  * MM_FP32_EMU. Problems may have any shapes; their C must not overlap any A
  * or B. Errors as for mm_gemm, checked for every problem. The call blocks only
@@ -238,10 +239,10 @@ enum {
                                      recombination. Slower on GB300 than the default bfloat16
                                      digits on tcgen05; kept for comparison. Grouped and served
                                      products always use the default. */
-    MM_OPT_FP64_SCHEME = 12       /* FP64-accuracy single products with the automatic slice count
-                                     (MM_OPT_SLICES = 0): 0 = the modular form wherever mm_crt_rule
-                                     fits, else the digit form (default); 1 = the digit form only.
-                                     Grouped and served products use the digit form. */
+    MM_OPT_FP64_SCHEME = 12       /* FP64-accuracy products with the automatic slice count
+                                     (MM_OPT_SLICES = 0), single, grouped and served: 0 = the
+                                     modular form wherever mm_crt_rule fits, else the digit form
+                                     (default); 1 = the digit form only. */
 };
 
 /* Kernel classes for mm_profile_read. */

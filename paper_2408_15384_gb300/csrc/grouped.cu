@@ -88,8 +88,8 @@ struct EmuPlan {
   struct Prob {
     int s;          // slice count, 0 = automatic
     int s_floor;    // smallest count the automatic rule can give for this k
-    int64_t kp;
-    size_t colmax, rowmax, E, F, dec, part, sa, sb;
+    int64_t kp, ldr;
+    size_t colmax, rowmax, E, F, dec, part, sa, sb, res;
   };
   std::vector<Prob> p;
   std::vector<TileCost> tiles;
@@ -97,6 +97,7 @@ struct EmuPlan {
   size_t colmax_bytes = 0, ws_bytes = 0;
   int bn = 128;   // output tile width of the group's slice GEMM (one CTA per 128 x bn tile)
   bool any_auto = false;
+  bool crt = false;               // the modular form allowed (FP64-accuracy, automatic counts)
   int auto_floor = SLICE_S_MAX;   // smallest s_floor over the automatic problems
   void build(mm_handle_s* h, const std::vector<int>& idx, const mm_problem* probs, bool fp64, int bn_) {
     bn = bn_;
@@ -106,6 +107,7 @@ struct EmuPlan {
     ftiles.clear();
     any_auto = false;
     auto_floor = SLICE_S_MAX;
+    crt = fp64 && crt_allowed(h, MM_FP64_EMU, h->opt_slices);
     const int FT = fp64_tile_size();
     size_t cm = 0, o = 0;
     for (int i = 0; i < count; ++i) {
@@ -113,8 +115,9 @@ struct EmuPlan {
       Prob& r = p[i];
       r.s = emu_slices(h, fp64 ? MM_FP64_EMU : MM_FP32_EMU, q.k, 0);
       r.s_floor = r.s > 0 ? r.s : std::max(SLICE_S_MIN, slice_count_floor(q.k));
-      const int planes = emu_planes(r.s);
+      const int planes = crt ? std::max(CRT_N_MAX, SLICE_S_MAX) : emu_planes(r.s);
       r.kp = static_cast<int64_t>(align_up(static_cast<size_t>(q.k), 8));
+      r.ldr = static_cast<int64_t>(align_up(static_cast<size_t>(std::max<int64_t>(q.n, 1)), 16));
       // column maxima and decision records in the region zeroed before each launch
       r.colmax = cm; cm += align_up(8 * static_cast<size_t>(q.n), 256);
       r.dec = cm; cm += (r.s == 0 ? 256 : 0);
@@ -124,9 +127,12 @@ struct EmuPlan {
       r.part = o; o = align_up(o + (r.s == 0 ? 8 * static_cast<size_t>(launch_absmax_parts(q.k)) * q.n : 0), 256);
       r.sa = o; o = align_up(o + 2 * static_cast<size_t>(planes) * q.m * r.kp, 1024);
       r.sb = o; o = align_up(o + 2 * static_cast<size_t>(planes) * q.n * r.kp, 1024);
+      r.res = o; o = align_up(o + (crt ? static_cast<size_t>(CRT_N_MAX) * q.m * r.ldr : 0), 256);
       const int tm = static_cast<int>((q.m + 127) / 128), tn = static_cast<int>((q.n + bn - 1) / bn);
       const int64_t nkb = (q.k + 63) / 64;
-      const int64_t pairs = fp64 ? static_cast<int64_t>(r.s_floor) * (r.s_floor + 1) / 2 : (r.s == 2 ? 3 : 6);
+      // products a tile runs (for the cost order): the modular form's typical
+      // 12 moduli, the digit form's pairs at its smallest count
+      const int64_t pairs = crt ? 12 : fp64 ? static_cast<int64_t>(r.s_floor) * (r.s_floor + 1) / 2 : (r.s == 2 ? 3 : 6);
       for (int a = 0; a < tm; ++a)
         for (int b = 0; b < tn; ++b)
           tiles.push_back({nkb * pairs, i, a * tn + b, TileRef{i, static_cast<int16_t>(a), static_cast<int16_t>(b)}});
@@ -171,7 +177,7 @@ static int fill_emu_blob(mm_handle_s* h, const EmuPlan& plan, const EmuLayout& L
   for (int i = 0; i < count; ++i) {
     const mm_problem& q = probs[idx[i]];
     const EmuPlan::Prob& r = plan.p[i];
-    const int planes = emu_planes(r.s);
+    const int planes = plan.crt ? std::max(CRT_N_MAX, SLICE_S_MAX) : emu_planes(r.s);
     GroupedSplit& g = gs[i];
     g.m = q.m; g.n = q.n; g.k = q.k; g.lda = q.lda; g.ldb = q.ldb; g.kp = r.kp;
     g.A = q.A; g.B = q.B; g.s = r.s > 0 ? r.s : SLICE_S_MAX; g.pad = 0;
@@ -202,6 +208,11 @@ static int fill_emu_blob(mm_handle_s* h, const EmuPlan& plan, const EmuLayout& L
     P.tiles_m = static_cast<int>((q.m + 127) / 128);
     P.tiles_n = static_cast<int>((q.n + plan.bn - 1) / plan.bn);
     P.E = g.E; P.F = g.F; P.C = q.C; P.ldc = q.ldc; P.levels = nullptr;
+    if (plan.crt) {
+      P.res = reinterpret_cast<uint8_t*>(wsp + r.res);
+      P.ldr = q.m * 8;
+      P.rplane = q.m * r.ldr;
+    }
     fa[i] = Fp64GemmArgs{q.m, q.n, q.k, q.A, q.lda, q.B, q.ldb, q.C, q.ldc, r.s == 0 ? &g.dec->s : nullptr};
     if (!encode_slices_tmap(h, &tm[2 * i], g.slA, q.k, q.m, planes, r.kp, 128) ||
         !encode_slices_tmap(h, &tm[2 * i + 1], g.slB, q.k, q.n, planes, r.kp, plan.bn))
@@ -221,11 +232,16 @@ static int fill_emu_blob(mm_handle_s* h, const EmuPlan& plan, const EmuLayout& L
 // on wider tiles the byte-carry kernel for s <= 5 (when some problem's k
 // allows s <= 5) and the s = 6, 7 kernel; each skips the other's problems;
 // then the plain-FP64 fallback for problems whose count came out as 8.
+// With the modular form allowed, one more launch for it (SLICE_CRT over the
+// decision codes above SLICE_CRT_BASE); the digit launches then take the
+// problems whose decision fell back to the digit form.
 struct GroupLaunches {
   int n = 0;
-  int mode[2] = {0, 0}, lo[2] = {0, 0}, hi[2] = {0, 0};
-  bool fallback = false;
-  int sig() const { return (n << 12) | (mode[0] << 8) | (mode[1] << 4) | (lo[0] << 1) | (fallback ? 1 : 0); }
+  int mode[3] = {0, 0, 0}, lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+  bool fallback = false, crt = false;
+  int sig() const {
+    return (crt ? 1 << 16 : 0) | (n << 12) | (mode[0] << 8) | (mode[1] << 4) | (lo[0] << 1) | (fallback ? 1 : 0);
+  }
 };
 
 static GroupLaunches group_launches(const mm_handle_s* h, const EmuPlan& plan, const std::vector<int>& idx,
@@ -251,10 +267,17 @@ static GroupLaunches group_launches(const mm_handle_s* h, const EmuPlan& plan, c
     return g;
   }
   g.fallback = true;
+  g.crt = plan.crt;
   if (bn == 128) {
     g.mode[0] = SLICE_FP64EMU;
     g.lo[0] = SLICE_S_MIN;
     g.hi[0] = SLICE_S_MAX;
+    if (g.crt) {
+      g.mode[1] = SLICE_CRT;
+      g.lo[1] = SLICE_CRT_BASE + 1;
+      g.hi[1] = SLICE_CRT_BASE + CRT_N_MAX;
+      g.n = 2;
+    }
     return g;
   }
   g.n = 0;
@@ -268,6 +291,12 @@ static GroupLaunches group_launches(const mm_handle_s* h, const EmuPlan& plan, c
   g.lo[g.n] = 6;
   g.hi[g.n] = SLICE_S_MAX;
   ++g.n;
+  if (g.crt) {
+    g.mode[g.n] = SLICE_CRT;
+    g.lo[g.n] = SLICE_CRT_BASE + 1;
+    g.hi[g.n] = SLICE_CRT_BASE + CRT_N_MAX;
+    ++g.n;
+  }
   return g;
 }
 
@@ -293,7 +322,7 @@ static cudaError_t launch_emu_group(mm_handle_s* h, bool fp64, const GroupLaunch
   memset(&dummy, 0, sizeof(dummy));
   // column maxima and decision records start at zero
   cudaError_t e = cudaMemsetAsync(ws, 0, colmax_cap, st);
-  if (e == cudaSuccess) e = launch_grouped_split(fp64 ? 0 : 1, ga, h->sm_count * 8, st);
+  if (e == cudaSuccess) e = launch_grouped_split(fp64 ? (gl.crt ? 3 : 0) : 1, ga, h->sm_count * 8, st);
   for (int i = 0; i < gl.n && e == cudaSuccess; ++i) {
     sa.s_lo = gl.lo[i];
     sa.s_hi = gl.hi[i];
@@ -510,7 +539,8 @@ static int graph_emulated(mm_handle_s* h, GroupedEntry& ent, const EmuPlan& plan
   cudaEventRecord(slot.done, st);
   slot.launched = true;
   ent.next ^= 1;
-  count_launch(h, 2 + static_cast<uint64_t>(fp64) + static_cast<uint64_t>(gl.n) + (gl.fallback ? 1 : 0));
+  count_launch(h, 2 + static_cast<uint64_t>(fp64) + (gl.crt ? 1 : 0) + static_cast<uint64_t>(gl.n) +
+                     (gl.fallback ? 1 : 0));
   return MM_OK;
 }
 
@@ -708,7 +738,8 @@ int grouped_direct(mm_handle_s* h, int count, const mm_problem* probs, int preci
       rep->main_idx = main_idx;
       e = cudaMemcpyAsync(hb, db, rep->bytes, cudaMemcpyDeviceToHost, st);
     }
-    count_launch(h, 2 + static_cast<uint64_t>(fp64) + static_cast<uint64_t>(gl.n) + (gl.fallback ? 1 : 0));
+    count_launch(h, 2 + static_cast<uint64_t>(fp64) + (gl.crt ? 1 : 0) + static_cast<uint64_t>(gl.n) +
+                       (gl.fallback ? 1 : 0));
   }
   ws_free(h, dev, total, st);
   if (rc != MM_OK) return rc;

@@ -188,6 +188,11 @@ cudaError_t launch_slice_cols(int mode, const double* B, int64_t k, int64_t n, i
 // The automatic FP64-accuracy decision of one product with the modular form
 // allowed (fp64_decision on the record's spreads): dec->s and dec->bits.
 cudaError_t launch_decide_fp64(SliceDecision* dec, int64_t k, cudaStream_t st);
+// The residue bytes of a modular-form product ([N] planes of rplane bytes,
+// blocks of 8 columns blk bytes apart, 8-byte row records) to a dense
+// [N][m][n] byte array (diagnostics).
+cudaError_t launch_crt_residues_out(const uint8_t* res, int64_t rplane, int64_t blk, int N, int64_t m, int64_t n,
+                                   uint8_t* out, cudaStream_t st);
 cudaError_t launch_fill_uniform(double* X, int64_t rows, int64_t cols, int64_t ld, uint64_t seed, uint64_t stream_id,
                                 int scale_mode, uint64_t exp_stream_id, cudaStream_t st);
 
@@ -218,7 +223,10 @@ struct GroupedSplitArgs {
   const int* count_dev;
   uint32_t* err;
 };
-// mode01: 0 FP64-accuracy digits, 1 FP32-accuracy slices. grid: persistent blocks.
+// mode01: 0 FP64-accuracy digits, 1 FP32-accuracy slices, 3 FP64-accuracy with
+// the modular form allowed (automatic problems only: a decision kernel
+// between the scan and the slicing records each problem's form). grid:
+// persistent blocks.
 cudaError_t launch_grouped_split(int mode01, const GroupedSplitArgs& a, int grid, cudaStream_t st);
 
 // ----------------------------------------------------------- slice_gemm.cu
@@ -271,8 +279,11 @@ struct SliceProblem {
   double* C;
   int64_t ldc;
   int64_t* levels;       // SLICE_LEVELS: [s][m][n] int64
-  uint8_t* res;          // SLICE_CRT: residues of the products, bytes [N][rows][ldr] (plane l at l * rplane)
-  int64_t ldr, rplane;   // bytes between rows (a multiple of 16) and between planes
+  // SLICE_CRT: the products' residues as bytes; plane l at res + l * rplane;
+  // within a plane, blocks of 8 columns ldr bytes apart, each block the rows'
+  // 8-byte records in row order (res points at this problem's row 0)
+  uint8_t* res;
+  int64_t ldr, rplane;
 };
 
 // A tile of a grouped launch: problem index and tile coordinates.
@@ -282,13 +293,20 @@ struct TileRef {
 };
 
 // The modular form's rebuild constants for N = 1 .. CRT_N_MAX moduli:
-// W[N][l] = (M/m_l) ((M/m_l)^-1 mod m_l) mod M as four 32-bit words (least
-// significant first), M = M_N and M/2 as two 64-bit words, invM = 1/M as a float.
+// W[N][l] = (M/m_l) ((M/m_l)^-1 mod m_l) mod M and M = M_N as four 32-bit
+// words (least significant first), M/2 as two 64-bit words; the quotient
+// estimate of a sum S < 2^12 M reads the window S >> wsh (below 2^32, wsh =
+// bit length of M minus 20) and scales it by qscale = 2^wsh / M (a float).
+// Per modulus m_l, the constants of the epilogue's reduction of an int32 sum:
+// magic = floor(2^32 / m) + 1, c16 = 2^16 mod m, c31 = 2^31 mod m.
 struct CrtTab {
   uint32_t W[CRT_N_MAX + 1][CRT_N_MAX][4];
-  uint64_t M[CRT_N_MAX + 1][2];
+  uint32_t M[CRT_N_MAX + 1][4];
   uint64_t H[CRT_N_MAX + 1][2];
-  float invM[CRT_N_MAX + 1];
+  int32_t wsh[CRT_N_MAX + 1];
+  float qscale[CRT_N_MAX + 1];
+  uint32_t magic[CRT_N_MAX], c16[CRT_N_MAX];
+  int32_t c31[CRT_N_MAX];
 };
 
 struct SliceGemmArgs {

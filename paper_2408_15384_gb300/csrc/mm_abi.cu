@@ -344,8 +344,9 @@ static int slice_gemm_launch(mm_handle_s* h, const SplitLayout& L, char* ws, int
   P.ldc = ldc;
   P.levels = levels;
   if (sl.mode == SLICE_CRT) {
-    P.res = reinterpret_cast<uint8_t*>(ws + L.off_res) + r0 * L.ldr;
-    P.ldr = L.ldr;
+    // per plane: blocks of 8 columns, each the 8-byte records of all L.m rows
+    P.res = reinterpret_cast<uint8_t*>(ws + L.off_res) + r0 * 8;
+    P.ldr = L.m * 8;
     P.rplane = L.m * L.ldr;
   }
   a.err = err_word(h, st);
@@ -1028,9 +1029,11 @@ int mm_debug_fp64_product(mm_handle h, int64_t m, int64_t n, int64_t k, const do
   cudaError_t e = cudaSuccess;
   if (rc == MM_OK) e = cudaMemcpyAsync(&d, L.dec(ws), sizeof(d), cudaMemcpyDeviceToHost, st);
   if (rc == MM_OK && e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (rc == MM_OK && e == cudaSuccess && res && L.crt && d.s > SLICE_CRT_BASE)
-    e = cudaMemcpy2DAsync(res, n, ws + L.off_res, L.ldr, n, static_cast<size_t>(d.s - SLICE_CRT_BASE) * m,
-                          cudaMemcpyDeviceToDevice, st);
+  if (rc == MM_OK && e == cudaSuccess && res && L.crt && d.s > SLICE_CRT_BASE) {
+    e = launch_crt_residues_out(reinterpret_cast<const uint8_t*>(ws + L.off_res), L.m * L.ldr, L.m * 8,
+                                d.s - SLICE_CRT_BASE, m, n, res, st);
+    count_launch(h, 1);
+  }
   if (rc == MM_OK && e == cudaSuccess) e = cudaStreamSynchronize(st);
   ws_free(h, wsv, L.bytes, st);
   if (rc != MM_OK) return rc;

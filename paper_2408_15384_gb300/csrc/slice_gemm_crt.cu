@@ -1,6 +1,9 @@
 // slice_gemm_crt.cu -- instances of the slice GEMM for the modular form of the
 // FP64-accuracy product (SLICE_CRT: one residue product a modulus, the
 // Chinese-remainder rebuild in the epilogue) and the rebuild constants.
+#include <cmath>
+#include <cstring>
+
 #include "slice_gemm_kernel.cuh"
 
 namespace mmdev {
@@ -23,14 +26,22 @@ uint32_t inverse_mod(uint32_t x, uint32_t m) {
 CrtTab make_tab() {
   CrtTab t;
   memset(&t, 0, sizeof(t));
+  for (int l = 0; l < CRT_N_MAX; ++l) {
+    const uint32_t m = static_cast<uint32_t>(crt_modulus(l));
+    t.magic[l] = static_cast<uint32_t>((1ull << 32) / m + 1ull);
+    t.c16[l] = (1u << 16) % m;
+    t.c31[l] = static_cast<int32_t>((1u << 31) % m);
+  }
   for (int N = 1; N <= CRT_N_MAX; ++N) {
     u128 M = 1;
     for (int l = 0; l < N; ++l) M *= static_cast<uint32_t>(crt_modulus(l));
-    t.M[N][0] = static_cast<uint64_t>(M);
-    t.M[N][1] = static_cast<uint64_t>(M >> 64);
+    for (int i = 0; i < 4; ++i) t.M[N][i] = static_cast<uint32_t>(M >> (32 * i));
     t.H[N][0] = static_cast<uint64_t>(M >> 1);
     t.H[N][1] = static_cast<uint64_t>(M >> 65);
-    t.invM[N] = static_cast<float>(1.0 / static_cast<double>(M));
+    int bits = 0;
+    for (u128 x = M; x != 0; x >>= 1) ++bits;
+    t.wsh[N] = bits > 20 ? bits - 20 : 0;
+    t.qscale[N] = static_cast<float>(std::ldexp(1.0, t.wsh[N]) / static_cast<double>(M));
     for (int l = 0; l < N; ++l) {
       const uint32_t m = static_cast<uint32_t>(crt_modulus(l));
       const u128 Ml = M / m;

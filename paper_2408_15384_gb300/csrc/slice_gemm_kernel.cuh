@@ -135,6 +135,41 @@ __device__ __forceinline__ double f32_to_f64_scaled(uint32_t fb, int e) {
   return scale_pow2(bitsd(sgn | (static_cast<uint64_t>(ex) << 52) | man), e);
 }
 
+// The double nearest to (-1)^neg * Y * 2^e (ties to even) for a 128-bit
+// magnitude Y = yh:yl, in integer arithmetic only (GB300's FP64 pipe is
+// narrow): normal results keep 53 bits, subnormal ones the bits down to
+// 2^-1074, so every result is rounded once; overflow gives infinity.
+__device__ __forceinline__ uint64_t rn_double_bits(uint64_t yh, uint64_t yl, int e, bool neg) {
+  const uint64_t sgn = neg ? (1ull << 63) : 0ull;
+  if ((yh | yl) == 0ull) return sgn;
+  const int lz = yh ? __clzll(static_cast<long long>(yh)) : 64 + __clzll(static_cast<long long>(yl));
+  uint64_t nh, nl;   // Y shifted up so its leading bit is bit 127
+  if (lz >= 64) {
+    nh = yl << (lz - 64);
+    nl = 0ull;
+  } else if (lz == 0) {
+    nh = yh;
+    nl = yl;
+  } else {
+    nh = (yh << lz) | (yl >> (64 - lz));
+    nl = yl << lz;
+  }
+  int L = 127 - lz + e;                              // exponent of the leading bit
+  const int keep = L >= -1022 ? 53 : L + 1075;       // significant bits kept
+  if (keep < 0) return sgn;                          // below half the least subnormal
+  uint64_t q = keep ? (nh >> (64 - keep)) : 0ull;
+  const uint64_t rbit = (nh >> (63 - keep)) & 1ull;
+  const bool sticky = (nh & ((1ull << (63 - keep)) - 1ull)) != 0ull || nl != 0ull;
+  q += (rbit && (sticky || (q & 1ull))) ? 1ull : 0ull;
+  if (keep < 53) return sgn | q;                     // subnormal (2^52: the least normal)
+  if (q == (1ull << 53)) {
+    q >>= 1;
+    ++L;
+  }
+  if (L + 1023 >= 2047) return sgn | 0x7FF0000000000000ull;
+  return sgn | (static_cast<uint64_t>(L + 1023) << 52) | (q & 0xFFFFFFFFFFFFFull);
+}
+
 struct Step {
   int kb;              // K block
   int pa, pb;          // A and B slice indices of the step's first pair
@@ -304,6 +339,114 @@ __device__ __forceinline__ TileJob get_job(const SliceGemmArgs& a, const CUtenso
     resolve_slices(a, *j.P, j);
   }
   return j;
+}
+
+// Rebuild of 4 outputs of a modular-form product: row `row`, columns c4 ..
+// c4 + 3 (c4 a multiple of 4), from the residue bytes of its N products.
+// S = sum_l c_l W_l is formed as four 64-bit column sums of 32-bit words (W4:
+// whether W_l needs its fourth word, M_N >= 2^96); q = round(S / M) from a
+// float estimate good to 2^-11; Y = S - q M moved into [-M/2, M/2) (one step
+// at most) is the exact integer product; it is rounded to double once and
+// scaled by 2^(E_i + F_j - 2b). Kept out of line: it runs at modulus ends,
+// between chunk drains, and gets the whole register budget.
+template <bool W4>
+static __device__ __noinline__ void crt_rebuild4(const SliceProblem& P, int64_t row, int64_t c4, int N, int bits) {
+  const int64_t n = P.n;
+  const int32_t Ei = P.E[row];
+  double* const crow = P.C + row * P.ldc;
+  const uint8_t* const rb = P.res + row * 8 + (c4 >> 3) * P.ldr + (c4 & 4);
+  const uint32_t m0 = c_crt.M[N][0], m1 = c_crt.M[N][1], m2 = c_crt.M[N][2], m3 = c_crt.M[N][3];
+  const uint64_t Ml = (static_cast<uint64_t>(m1) << 32) | m0, Mh = (static_cast<uint64_t>(m3) << 32) | m2;
+  const uint64_t Hl = c_crt.H[N][0], Hh = c_crt.H[N][1];
+  const int wsh = c_crt.wsh[N];
+  const float qscale = c_crt.qscale[N];
+  const int ebase = Ei - 2 * bits;
+  // every modulus's bytes of the 4 columns, all loads in flight together
+  uint32_t wc[CRT_N_MAX];
+#pragma unroll
+  for (int l = 0; l < CRT_N_MAX; ++l)
+    wc[l] = (l < N) ? *reinterpret_cast<const uint32_t*>(rb + static_cast<int64_t>(l) * P.rplane) : 0u;
+  uint64_t T[4][4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) T[j][i] = 0ull;
+#pragma unroll
+  for (int l = 0; l < CRT_N_MAX; ++l) {
+    if (l < N) {
+      const uint32_t W0 = c_crt.W[N][l][0], W1 = c_crt.W[N][l][1], W2 = c_crt.W[N][l][2];
+      const uint32_t W3 = W4 ? c_crt.W[N][l][3] : 0u;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const uint32_t cl = (wc[l] >> (8 * j)) & 255u;
+        T[j][0] += static_cast<uint64_t>(cl) * W0;
+        T[j][1] += static_cast<uint64_t>(cl) * W1;
+        T[j][2] += static_cast<uint64_t>(cl) * W2;
+        if (W4) T[j][3] += static_cast<uint64_t>(cl) * W3;
+      }
+    }
+  }
+  const int4 f4 = (c4 + 3 < n && ((reinterpret_cast<uintptr_t>(P.F + c4) & 15u) == 0))
+                      ? __ldg(reinterpret_cast<const int4*>(P.F + c4))
+                      : make_int4(__ldg(P.F + c4), c4 + 1 < n ? __ldg(P.F + c4 + 1) : 0,
+                                  c4 + 2 < n ? __ldg(P.F + c4 + 2) : 0, c4 + 3 < n ? __ldg(P.F + c4 + 3) : 0);
+  uint64_t ob[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    // carries: S = hi:lo (S < 14 * 2^8 * M < 2^123)
+    const uint64_t t1 = T[j][1] + (T[j][0] >> 32);
+    const uint64_t t2 = T[j][2] + (t1 >> 32);
+    const uint64_t t3 = T[j][3] + (t2 >> 32);
+    const uint64_t lo = (t1 << 32) | (T[j][0] & 0xFFFFFFFFull);
+    const uint64_t hi = (t3 << 32) | (t2 & 0xFFFFFFFFull);
+    // q = round(S / M) from the window S >> wsh (< 2^32)
+    const uint64_t win = wsh >= 64 ? (hi >> (wsh - 64)) : (wsh == 0 ? lo : ((lo >> wsh) | (hi << (64 - wsh))));
+    const float qf = __uint2float_rn(static_cast<uint32_t>(win)) * qscale;
+    const uint32_t q = __float_as_uint(qf + 8388608.0f) - 0x4B000000u;   // round to nearest
+    // q M in 32-bit words, then Y = S - q M (two's complement, 128 bits)
+    const uint64_t p0 = static_cast<uint64_t>(q) * m0;
+    const uint64_t p1 = static_cast<uint64_t>(q) * m1 + (p0 >> 32);
+    const uint64_t p2 = static_cast<uint64_t>(q) * m2 + (p1 >> 32);
+    const uint64_t p3 = static_cast<uint64_t>(q) * m3 + (p2 >> 32);
+    const uint64_t qml = (p1 << 32) | (p0 & 0xFFFFFFFFull), qmh = (p3 << 32) | (p2 & 0xFFFFFFFFull);
+    uint64_t yl = lo - qml;
+    uint64_t yh = hi - qmh - (lo < qml ? 1ull : 0ull);
+    // Y >= M/2: Y - M; Y < -M/2: Y + M
+    const uint64_t th = yh - Hh - (yl < Hl ? 1ull : 0ull);
+    if (static_cast<int64_t>(th) >= 0) {
+      const uint64_t nl = yl - Ml;
+      yh = yh - Mh - (yl < Ml ? 1ull : 0ull);
+      yl = nl;
+    } else {
+      const uint64_t ul = yl + Hl;
+      const uint64_t uh = yh + Hh + (ul < yl ? 1ull : 0ull);
+      if (static_cast<int64_t>(uh) < 0) {
+        const uint64_t nl = yl + Ml;
+        yh = yh + Mh + (nl < yl ? 1ull : 0ull);
+        yl = nl;
+      }
+    }
+    // |Y| < 2^127: one rounding to double, scaled by 2^(E_i + F_j - 2b)
+    const bool neg = static_cast<int64_t>(yh) < 0;
+    if (neg) {
+      yl = ~yl + 1ull;
+      yh = ~yh + (yl == 0ull ? 1ull : 0ull);
+    }
+    const int32_t Fj = j == 0 ? f4.x : j == 1 ? f4.y : j == 2 ? f4.z : f4.w;
+    ob[j] = (Ei == EXP_NONFINITE || Fj == EXP_NONFINITE) ? 0x7FF8000000000000ull
+                                                         : rn_double_bits(yh, yl, ebase + Fj, neg);
+  }
+  if (c4 + 3 < n && ((reinterpret_cast<uintptr_t>(crow + c4) & 15u) == 0)) {
+    double2* const op = reinterpret_cast<double2*>(crow + c4);
+    op[0] = make_double2(__longlong_as_double(static_cast<long long>(ob[0])),
+                         __longlong_as_double(static_cast<long long>(ob[1])));
+    op[1] = make_double2(__longlong_as_double(static_cast<long long>(ob[2])),
+                         __longlong_as_double(static_cast<long long>(ob[3])));
+  } else {
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (c4 + j < n) crow[c4 + j] = __longlong_as_double(static_cast<long long>(ob[j]));
+  }
 }
 
 template <int BN, int MODE, int CG>
@@ -532,6 +675,24 @@ __global__ void __launch_bounds__(Cfg<BN, MODE, CG>::NUM_THREADS, 1)
     // where this warp reports "slot drained": the leader's barrier
     const uint32_t acce_remote0 = (CG >= 2) ? mapa_shared(smem_u32(&acce_bar[0]), pair_rank0) : 0u;
     const uint32_t acce_remote1 = (CG >= 2) ? mapa_shared(smem_u32(&acce_bar[1]), pair_rank0) : 0u;
+    // modular form: a tile's rebuild is deferred and run 4 columns at a time
+    // at the following tile's modulus ends, spread evenly over them (pend_t:
+    // the tile, -1 for none; pend_g: its next group of 4 columns)
+    constexpr int G4 = C_::COLS_PER_THREAD / 4;
+    int pend_t = -1, pend_g = 0;
+    auto crt_step = [&]() {
+      const TileJob pj = get_job(args, &tmA, &tmB, pend_t, COL_PAIRS, pair_col);
+      const int64_t prow = static_cast<int64_t>(pj.tm) * C_::TILE_M + static_cast<int64_t>(rank) * BM + row_in_tile;
+      const int64_t pc4 = static_cast<int64_t>(pj.tn) * BN + col_off + 4 * pend_g;
+      if (prow < pj.P->m && pc4 < pj.P->n) {
+        if (pj.s > 12)
+          crt_rebuild4<true>(*pj.P, prow, pc4, pj.s, pj.fix);
+        else
+          crt_rebuild4<false>(*pj.P, prow, pc4, pj.s, pj.fix);
+      }
+      if (++pend_g == G4) pend_t = -1;
+    };
+    (void)crt_step;
     for (int t = walker; t < ntiles && ok; t += walkers) {
       const TileJob job = get_job(args, &tmA, &tmB, t, COL_PAIRS, pair_col);
       if (job.skip) continue;
@@ -579,13 +740,11 @@ __global__ void __launch_bounds__(Cfg<BN, MODE, CG>::NUM_THREADS, 1)
       } else if constexpr (MODE == SLICE_CRT) {
         // Modular form. For each modulus the thread keeps int32 sums of its
         // columns over the K chunks (reduced modulo m at every int32 segment
-        // end: a segment adds at most SEG_CHUNKS 2^24 < 2^31), stores their
-        // remainders in [0, m) as bytes, and after the last modulus rebuilds
-        // every output: S = sum_l c_l W_l (four 64-bit column sums of 32-bit
-        // words), q = round(S / M) from a float estimate good to 2^-10, Y = S -
-        // q M moved into [-M/2, M/2) (one step at most), converted to double
-        // with one rounding and scaled by 2^(E_i + F_j - 2b).
-        const int N = job.s, bits = job.fix;
+        // end: a segment adds at most SEG_CHUNKS 2^24 < 2^31) and stores their
+        // remainders in [0, m) as bytes; the tile's outputs are rebuilt from
+        // them (crt_rebuild4) 4 columns at a time at the next tile's modulus
+        // ends, so the rebuild overlaps the tensor cores' work.
+        const int N = job.s;
         const int nkb = P.nkb;
         const int nch = (nkb + 15) / 16;
         constexpr int NG = C_::COLS_PER_THREAD / 8;
@@ -595,18 +754,29 @@ __global__ void __launch_bounds__(Cfg<BN, MODE, CG>::NUM_THREADS, 1)
         for (int g = 0; g < NG; ++g)
 #pragma unroll
           for (int v = 0; v < 8; ++v) lsum[g][v] = 0;
-        uint8_t* const rrow = P.res + row * P.ldr + col0;
-        for (int l = 0; l < N && ok; ++l) {
-          const uint32_t mdl = static_cast<uint32_t>(crt_modulus(l));
-          const uint64_t mg = ~0ull / mdl + 1ull;          // floor(2^64 / m) + 1: exact quotients below 2^32
-          const int32_t c31 = static_cast<int32_t>((1u << 31) % mdl);
-          // x mod m in [0, m) for any int32 x: (x + 2^31) mod m, less 2^31 mod m
-          auto reduce = [&](int32_t x) -> int32_t {
-            const uint32_t u = static_cast<uint32_t>(x) ^ 0x80000000u;
-            const uint32_t q = static_cast<uint32_t>(__umul64hi(static_cast<uint64_t>(u), mg));
-            const int32_t r = static_cast<int32_t>(u - q * mdl) - c31;
+        // residue bytes: per plane, blocks of 8 columns, each block the rows'
+        // 8-byte records one after the other, so a warp (32 consecutive rows)
+        // moves 256 contiguous bytes per access
+        uint8_t* const rbase = P.res + row * 8 + (col0 >> 3) * P.ldr;
+        // x mod m_l in [0, m) for any int32 x: v = (floor(x / 2^16) + 2^15)
+        // (2^16 mod m) + (x mod 2^16) < 2^24 is x + 2^31 modulo m, its quotient
+        // floor(v (floor(2^32 / m) + 1) / 2^32) is exact (v / 2^32 < 1/m), and
+        // 2^31 mod m comes off at the end (constants from the table, read
+        // where they are used, so none is live across the chunk loop)
+        struct Reducer {
+          uint32_t mdl, magic, c16;
+          int32_t c31;
+          __device__ __forceinline__ explicit Reducer(int l)
+              : mdl(static_cast<uint32_t>(crt_modulus(l))), magic(c_crt.magic[l]), c16(c_crt.c16[l]),
+                c31(c_crt.c31[l]) {}
+          __device__ __forceinline__ int32_t operator()(int32_t x) const {
+            const uint32_t v = (static_cast<uint32_t>(x >> 16) + 32768u) * c16 + (static_cast<uint32_t>(x) & 0xFFFFu);
+            const uint32_t q = __umulhi(v, magic);
+            const int32_t r = static_cast<int32_t>(v - q * mdl) - c31;
             return r < 0 ? r + static_cast<int32_t>(mdl) : r;
-          };
+          }
+        };
+        for (int l = 0; l < N && ok; ++l) {
           for (int c = 0; c < nch; ++c, ++chunk) {
             const int slot = chunk & 1;
             if (!mbar_wait(&accf_bar[slot], static_cast<uint32_t>(chunk >> 1) & 1u, wc)) { ok = false; break; }
@@ -623,6 +793,7 @@ __global__ void __launch_bounds__(Cfg<BN, MODE, CG>::NUM_THREADS, 1)
                 mbar_arrive(&acce_bar[slot]);
             }
             if (((c + 1) % SEG_CHUNKS) == 0 && c + 1 < nch) {
+              const Reducer reduce(l);
 #pragma unroll
               for (int g = 0; g < NG; ++g)
 #pragma unroll
@@ -631,116 +802,34 @@ __global__ void __launch_bounds__(Cfg<BN, MODE, CG>::NUM_THREADS, 1)
           }
           if (!ok) break;
           if (row_ok) {
-            uint8_t* const rp = rrow + static_cast<int64_t>(l) * P.rplane;
+            const Reducer reduce(l);
+            uint8_t* const rp = rbase + static_cast<int64_t>(l) * P.rplane;
 #pragma unroll
-            for (int q = 0; q < NQ; ++q) {
-              uint32_t w[4];
+            for (int g = 0; g < NG; ++g) {
+              uint32_t lo = 0u, hi = 0u;
 #pragma unroll
-              for (int j = 0; j < 4; ++j) {
-                uint32_t x = 0u;
-#pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                  const int i = q * 16 + j * 4 + b;
-                  x |= static_cast<uint32_t>(reduce(lsum[i >> 3][i & 7])) << (8 * b);
-                }
-                w[j] = x;
+              for (int b = 0; b < 4; ++b) {
+                lo |= static_cast<uint32_t>(reduce(lsum[g][b])) << (8 * b);
+                hi |= static_cast<uint32_t>(reduce(lsum[g][4 + b])) << (8 * b);
               }
-              if (col0 + 16 * q < P.ldr) *reinterpret_cast<uint4*>(rp + 16 * q) = make_uint4(w[0], w[1], w[2], w[3]);
+              if (col0 + 8 * g < n) *reinterpret_cast<uint2*>(rp + g * P.ldr) = make_uint2(lo, hi);
             }
           }
 #pragma unroll
           for (int g = 0; g < NG; ++g)
 #pragma unroll
             for (int v = 0; v < 8; ++v) lsum[g][v] = 0;
+          // the previous tile's rebuild, its share for this modulus end, while
+          // the tensor cores run this modulus's first chunks (the sums start
+          // again from zero here, so none of them is live across it)
+          const int upto = (G4 * (l + 1) + N - 1) / N;
+          while (pend_t >= 0 && pend_g < upto) crt_step();
         }
-        if (ok && row_ok) {
-          double* const crow = P.C + row * P.ldc;
-          const uint64_t Ml = c_crt.M[N][0], Mh = c_crt.M[N][1];
-          const uint64_t Hl = c_crt.H[N][0], Hh = c_crt.H[N][1];
-          const float invM = c_crt.invM[N];
-          const int ebase = Ei - 2 * bits;
-#pragma unroll 1
-          for (int g4 = 0; g4 < C_::COLS_PER_THREAD / 4; ++g4) {
-            const int64_t cc = col0 + 4 * g4;
-            if (cc >= n) break;
-            uint64_t T[4][4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-#pragma unroll
-              for (int i = 0; i < 4; ++i) T[j][i] = 0ull;
-#pragma unroll 2
-            for (int l = 0; l < N; ++l) {
-              const uint32_t w = *reinterpret_cast<const uint32_t*>(rrow + static_cast<int64_t>(l) * P.rplane + 4 * g4);
-              const uint32_t W0 = c_crt.W[N][l][0], W1 = c_crt.W[N][l][1], W2 = c_crt.W[N][l][2],
-                             W3 = c_crt.W[N][l][3];
-#pragma unroll
-              for (int j = 0; j < 4; ++j) {
-                const uint64_t cl = (w >> (8 * j)) & 255u;
-                T[j][0] += cl * W0;
-                T[j][1] += cl * W1;
-                T[j][2] += cl * W2;
-                T[j][3] += cl * W3;
-              }
-            }
-            const int4 f4 = (cc + 3 < n && ((reinterpret_cast<uintptr_t>(P.F + cc) & 15u) == 0))
-                                ? __ldg(reinterpret_cast<const int4*>(P.F + cc))
-                                : make_int4(__ldg(P.F + cc), cc + 1 < n ? __ldg(P.F + cc + 1) : 0,
-                                            cc + 2 < n ? __ldg(P.F + cc + 2) : 0, cc + 3 < n ? __ldg(P.F + cc + 3) : 0);
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-              if (cc + j >= n) break;
-              // carries: S = s3:s2:s1:s0 (S < 14 * 2^8 * M < 2^123)
-              uint64_t t1 = T[j][1] + (T[j][0] >> 32);
-              uint64_t t2 = T[j][2] + (t1 >> 32);
-              uint64_t t3 = T[j][3] + (t2 >> 32);
-              const uint64_t lo = (t1 << 32) | (T[j][0] & 0xFFFFFFFFull);
-              const uint64_t hi = (t3 << 32) | (t2 & 0xFFFFFFFFull);
-              const float sf = __ull2float_rn(hi) * 18446744073709551616.0f + __ull2float_rn(lo);
-              const uint64_t q = static_cast<uint64_t>(__float2uint_rn(sf * invM));
-              // Y = S - q M (two's complement, 128 bits)
-              const uint64_t qml = q * Ml, qmh = __umul64hi(q, Ml) + q * Mh;
-              uint64_t yl = lo - qml;
-              uint64_t yh = hi - qmh - (lo < qml ? 1ull : 0ull);
-              // Y >= M/2: Y - M; Y < -M/2: Y + M
-              {
-                const uint64_t th = yh - Hh - (yl < Hl ? 1ull : 0ull);
-                if (static_cast<int64_t>(th) >= 0) {
-                  const uint64_t nl = yl - Ml;
-                  yh = yh - Mh - (yl < Ml ? 1ull : 0ull);
-                  yl = nl;
-                } else {
-                  const uint64_t ul = yl + Hl;
-                  const uint64_t uh = yh + Hh + (ul < yl ? 1ull : 0ull);
-                  if (static_cast<int64_t>(uh) < 0) {
-                    const uint64_t nl = yl + Ml;
-                    yh = yh + Mh + (nl < yl ? 1ull : 0ull);
-                    yl = nl;
-                  }
-                }
-              }
-              // |Y| < 2^127: one rounding to double
-              const bool neg = static_cast<int64_t>(yh) < 0;
-              if (neg) {
-                yl = ~yl + 1ull;
-                yh = ~yh + (yl == 0ull ? 1ull : 0ull);
-              }
-              double d;
-              int e2 = 0;
-              if (yh == 0ull) {
-                d = __ull2double_rn(yl);
-              } else {
-                const int lz = __clzll(static_cast<long long>(yh));
-                uint64_t top = lz ? ((yh << lz) | (yl >> (64 - lz))) : yh;
-                top |= ((lz ? (yl << lz) : yl) != 0ull) ? 1ull : 0ull;   // sticky: below the rounding bit
-                d = __ull2double_rn(top);
-                e2 = 64 - lz;
-              }
-              const int32_t Fj = j == 0 ? f4.x : j == 1 ? f4.y : j == 2 ? f4.z : f4.w;
-              crow[cc + j] = (Ei == EXP_NONFINITE || Fj == EXP_NONFINITE)
-                                 ? __longlong_as_double(0x7FF8000000000000ll)
-                                 : scale_pow2(neg ? -d : d, ebase + Fj + e2);
-            }
-          }
+        if (ok) {
+          // the previous tile's rebuild, what is left of it, then this tile's
+          while (pend_t >= 0) crt_step();
+          pend_t = t;
+          pend_g = 0;
         }
       } else if constexpr (C_::REG_SUMS) {
         // wide tiles: TMEM holds just the two accumulator slots. Each thread
@@ -1095,6 +1184,11 @@ __global__ void __launch_bounds__(Cfg<BN, MODE, CG>::NUM_THREADS, 1)
           }
         }
       }
+    }
+    if constexpr (MODE == SLICE_CRT) {
+      // the last tile's rebuild
+      if (ok)
+        while (pend_t >= 0) crt_step();
     }
   }
 

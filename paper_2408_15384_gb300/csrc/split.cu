@@ -270,84 +270,88 @@ __device__ __forceinline__ void slice8_store(const uint64_t (&vb)[8], int32_t X,
 // The modular form's residues of 8 consecutive entries: R = round-half-even(
 // x 2^(b - X)), |R| <= 2^(b-1) <= 2^52, and for every modulus m_l (l < N) the
 // centred residue rho = ((R + h) mod m) - h, h = floor(m/2), as bfloat16 in
-// plane l. The biased u = R + 2^55 (below 2^56) is cut into four 14-bit pieces
-// w_j, held exactly in float; (R + h) mod m is the remainder of
-//   x = w0 + w1 (2^14 mod m) + w2 (2^28 mod m) + w3 (2^42 mod m) + ((h - 2^55) mod m),
-// an integer below 2^24, so every float step is exact; the quotient estimate
-// floor(x * fl(1/m)) is off by at most one (x/m < 2^17: relative error 2^-23),
-// and one correction each way brings the remainder into [0, m). Modulus 256
-// divides 2^55: its residue is u's low byte, centred.
+// plane l. With the biased u = R + 2^55 = u2 2^40 + u1 2^20 + u0 (pieces below
+// 2^20, u < 2^56), (R + h) mod m is the remainder of
+//   v = u2 (2^40 mod m) + u1 (2^20 mod m) + u0 + ((h - 2^55) mod m) < 2^29,
+// whose quotient is floor(v * M / 2^39) with M = floor(2^39 / m) + 1 < 2^32
+// (m > 128): v M / 2^39 exceeds v / m by less than v / 2^39 < 2^-10 < 1/m, so
+// the floor is exact. Modulus 256 divides 2^55: its residue is u's low byte.
 __host__ __device__ constexpr uint32_t pow2_mod(int e, uint32_t m) {
   uint32_t r = 1u % m;
   for (int i = 0; i < e; ++i) r = (2u * r) % m;
   return r;
 }
 
-// exact float of an integer below 2^23
-__device__ __forceinline__ float small_u2f(uint32_t w) { return __uint_as_float(0x4B000000u | w) - 8388608.0f; }
+// R + 2^55 for R = round-half-even(x 2^sh), |R| <= 2^52 (the caller's scaling
+// guarantees it): normal entries shift their significand right by at least
+// one place and round half to even; zero and subnormal entries take the
+// general path.
+__device__ __forceinline__ uint64_t biased_rne(uint64_t bits, int sh) {
+  const uint32_t ex = static_cast<uint32_t>(bits >> 52) & 0x7FFu;
+  if (ex == 0u) return static_cast<uint64_t>(scaled_rne(bits, sh) + (1ll << 55));
+  const uint64_t mant = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const int rs = 1075 - static_cast<int>(ex) - sh;   // >= 1: |x| 2^sh < 2^52
+  uint64_t q = 0;
+  if (rs < 64) q = (mant + ((1ull << (rs - 1)) - 1ull) + ((mant >> rs) & 1ull)) >> rs;
+  return (bits >> 63) ? (1ull << 55) - q : (1ull << 55) + q;
+}
 
 template <int L>
-__device__ __forceinline__ void crt_plane(const float (&f0)[8], const float (&f1)[8], const float (&f2)[8],
-                                          const float (&f3)[8], const uint32_t (&lo)[8], uint16_t* __restrict__ o,
-                                          bool vec, int cnt) {
+__device__ __forceinline__ void crt_plane(const uint32_t (&u0)[8], const uint32_t (&u1)[8], const uint32_t (&u2)[8],
+                                          uint16_t* __restrict__ o, bool vec, int cnt) {
   constexpr uint32_t m = static_cast<uint32_t>(crt_modulus(L));
   constexpr uint32_t h = m / 2u;
-  uint32_t hb[8];
+  uint32_t f[8];   // float bit patterns of the residues (exact small integers)
   if constexpr (m == 256u) {
 #pragma unroll
-    for (int u = 0; u < 8; ++u) hb[u] = bf16_of_small_int(static_cast<int32_t>((lo[u] & 255u) ^ 128u) - 128);
+    for (int u = 0; u < 8; ++u)
+      f[u] = __float_as_uint(__int_as_float(static_cast<int32_t>(0x4B400000u + ((u0[u] & 255u) ^ 128u) - 128u)) -
+                             12582912.0f);
   } else {
-    constexpr float fm = static_cast<float>(m);
-    constexpr float inv = 1.0f / static_cast<float>(m);
-    constexpr float c1 = static_cast<float>(pow2_mod(14, m)), c2 = static_cast<float>(pow2_mod(28, m)),
-                    c3 = static_cast<float>(pow2_mod(42, m));
-    constexpr float cb = static_cast<float>((h + m - pow2_mod(55, m)) % m);
-    constexpr float fh = static_cast<float>(h);
+    constexpr uint32_t c1 = pow2_mod(20, m), c2 = pow2_mod(40, m);
+    constexpr uint32_t cb = (h + m - pow2_mod(55, m)) % m;
+    constexpr uint32_t M = static_cast<uint32_t>((1ull << 39) / m + 1ull);
+    static_assert(m > 128u, "the quotient step needs m > 128");
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-      const float x = fmaf(f3[u], c3, fmaf(f2[u], c2, fmaf(f1[u], c1, f0[u] + cb)));
-      const float q = floorf(x * inv);
-      float r = fmaf(-q, fm, x);
-      r = r < 0.0f ? r + fm : r;
-      r = r >= fm ? r - fm : r;
-      // rho = r - h: an integer of at most 8 significant bits, so its float's
-      // upper half is its bfloat16 (a zero is +0)
-      hb[u] = __float_as_uint(r - fh) >> 16;
+      const uint32_t v = u2[u] * c2 + u1[u] * c1 + (u0[u] + cb);
+      const uint32_t q = __umulhi(v, M) >> 7;
+      // rho = v - q m - h, placed in the float 1.5 * 2^23 + rho and read back exactly
+      const uint32_t r = (v + (0x4B400000u - h)) - q * m;
+      f[u] = __float_as_uint(__uint_as_float(r) - 12582912.0f);
     }
   }
+  // bfloat16 = upper half of each float
+  const uint4 w = make_uint4(__byte_perm(f[0], f[1], 0x7632), __byte_perm(f[2], f[3], 0x7632),
+                             __byte_perm(f[4], f[5], 0x7632), __byte_perm(f[6], f[7], 0x7632));
   if (vec) {
-    *reinterpret_cast<uint4*>(o) =
-        make_uint4(hb[0] | (hb[1] << 16), hb[2] | (hb[3] << 16), hb[4] | (hb[5] << 16), hb[6] | (hb[7] << 16));
+    *reinterpret_cast<uint4*>(o) = w;
   } else {
 #pragma unroll
     for (int u = 0; u < 8; ++u)
-      if (u < cnt) o[u] = static_cast<uint16_t>(hb[u]);
+      if (u < cnt) o[u] = static_cast<uint16_t>(f[u] >> 16);
   }
 }
 
 template <int... Ls>
-__device__ __forceinline__ void crt_planes(std::integer_sequence<int, Ls...>, int N, const float (&f0)[8],
-                                           const float (&f1)[8], const float (&f2)[8], const float (&f3)[8],
-                                           const uint32_t (&lo)[8], uint16_t* __restrict__ dst, size_t plane,
-                                           bool vec, int cnt) {
-  ((Ls < N ? crt_plane<Ls>(f0, f1, f2, f3, lo, dst + Ls * plane, vec, cnt) : void()), ...);
+__device__ __forceinline__ void crt_planes(std::integer_sequence<int, Ls...>, int N, const uint32_t (&u0)[8],
+                                           const uint32_t (&u1)[8], const uint32_t (&u2)[8],
+                                           uint16_t* __restrict__ dst, size_t plane, bool vec, int cnt) {
+  ((Ls < N ? crt_plane<Ls>(u0, u1, u2, dst + Ls * plane, vec, cnt) : void()), ...);
 }
 
 __device__ __forceinline__ void slice8_crt_store(const uint64_t (&vb)[8], int32_t X, int N, int b,
                                                  uint16_t* __restrict__ dst, size_t plane, int cnt) {
   const bool vec = (cnt == 8) && ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0);
-  float f0[8], f1[8], f2[8], f3[8];
-  uint32_t lo[8];
+  uint32_t u0[8], u1[8], u2[8];
 #pragma unroll
   for (int u = 0; u < 8; ++u) {
-    const uint64_t ub = static_cast<uint64_t>(scaled_rne(vb[u], b - X) + (1ll << 55));
-    lo[u] = static_cast<uint32_t>(ub);
-    f0[u] = small_u2f(static_cast<uint32_t>(ub) & 0x3FFFu);
-    f1[u] = small_u2f(static_cast<uint32_t>(ub >> 14) & 0x3FFFu);
-    f2[u] = small_u2f(static_cast<uint32_t>(ub >> 28) & 0x3FFFu);
-    f3[u] = small_u2f(static_cast<uint32_t>(ub >> 42));
+    const uint64_t ub = biased_rne(vb[u], b - X);
+    u0[u] = static_cast<uint32_t>(ub) & 0xFFFFFu;
+    u1[u] = static_cast<uint32_t>(ub >> 20) & 0xFFFFFu;
+    u2[u] = static_cast<uint32_t>(ub >> 40);
   }
-  crt_planes(std::make_integer_sequence<int, CRT_N_MAX>{}, N, f0, f1, f2, f3, lo, dst, plane, vec, cnt);
+  crt_planes(std::make_integer_sequence<int, CRT_N_MAX>{}, N, u0, u1, u2, dst, plane, vec, cnt);
 }
 
 // Mode 3: the FP64-accuracy form the decision names -- the modular form's
@@ -872,6 +876,22 @@ __global__ void __launch_bounds__(256) grouped_spread_kernel(const GroupedSplitA
   }
 }
 
+// Between the phases, with the modular form allowed: one thread per problem
+// records its decision (fp64_decision on its spreads).
+__global__ void __launch_bounds__(256) grouped_decide_kernel(const GroupedSplitArgs a) {
+  const int count = *a.count_dev;
+  for (int p = static_cast<int>(blockIdx.x * blockDim.x + threadIdx.x); p < count;
+       p += static_cast<int>(gridDim.x * blockDim.x)) {
+    SliceDecision* d = a.probs[p].dec;
+    if (d == nullptr) continue;
+    int b = 0;
+    const int code =
+        fp64_decision(a.probs[p].k, spread_from_room(d->amin_room), spread_from_room(d->bmin_room), true, &b);
+    d->s = code;
+    d->bits = b;
+  }
+}
+
 // Phase 2: slices of A, 256 runs of 8 entries per block taken row after row
 // (so short rows share a block), then of every 64 x 32 block of B.
 template <int MODE>
@@ -890,18 +910,21 @@ __global__ void __launch_bounds__(256) grouped_slice_kernel(const GroupedSplitAr
       const int64_t runs = (g.k + 7) / 8;   // runs of 8 entries per row
       const int64_t u = lb * 256 + threadIdx.x;
       const int64_t row = u / runs, c0 = (u - row * runs) * 8;
-      const int se = decided_slices(g.dec, g.s, g.k, lb == 0);
+      int bits = 0;
+      const int se = (MODE == 3) ? decided_fp64(g.dec, &bits) : decided_slices(g.dec, g.s, g.k, lb == 0);
       if (row < g.m)
-        slice_rows_body<MODE>(g.A, g.m, g.k, g.lda, g.rowmax, se, g.kp, g.slA, g.E, g.perr ? g.perr : a.err, row, c0);
+        slice_rows_body<MODE>(g.A, g.m, g.k, g.lda, g.rowmax, se, g.kp, g.slA, g.E, g.perr ? g.perr : a.err, row, c0,
+                              bits);
     } else {
       const int64_t v = vb - t2;
       const int p = find_problem(off3, count, v);
       const GroupedSplit& g = a.probs[p];
       const int64_t lb = v - off3[p];
       const int64_t nnb = (g.n + 31) / 32;
-      const int se = decided_slices(g.dec, g.s, g.k, false);
+      int bits = 0;
+      const int se = (MODE == 3) ? decided_fp64(g.dec, &bits) : decided_slices(g.dec, g.s, g.k, false);
       slice_cols_body<MODE>(g.B, g.k, g.n, g.ldb, g.colmax, se, g.kp, g.slB, g.F, g.perr ? g.perr : a.err, (lb / nnb) * 64,
-                            (lb % nnb) * 32);
+                            (lb % nnb) * 32, bits);
     }
   }
 }
@@ -1037,6 +1060,24 @@ cudaError_t launch_slice_cols(int mode, const double* B, int64_t k, int64_t n, i
   return cudaGetLastError();
 }
 
+namespace mmdev {
+__global__ void crt_residues_out_kernel(const uint8_t* __restrict__ res, int64_t rplane, int64_t blk, int N,
+                                        int64_t m, int64_t n, uint8_t* __restrict__ out) {
+  const int64_t total = static_cast<int64_t>(N) * m * n;
+  for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < total;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t l = i / (m * n), r = (i / n) % m, c = i % n;
+    out[i] = res[l * rplane + (c >> 3) * blk + r * 8 + (c & 7)];
+  }
+}
+}  // namespace mmdev
+
+cudaError_t launch_crt_residues_out(const uint8_t* res, int64_t rplane, int64_t blk, int N, int64_t m, int64_t n,
+                                   uint8_t* out, cudaStream_t st) {
+  crt_residues_out_kernel<<<1024, 256, 0, st>>>(res, rplane, blk, N, m, n, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_decide_fp64(SliceDecision* dec, int64_t k, cudaStream_t st) {
   decide_fp64_kernel<<<1, 32, 0, st>>>(dec, k);
   return cudaGetLastError();
@@ -1046,14 +1087,19 @@ cudaError_t launch_grouped_split(int mode01, const GroupedSplitArgs& a, int grid
   grouped_absmax_kernel<<<grid, 256, 0, st>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  if (mode01 == 0) {
+  if (mode01 == 0 || mode01 == 3) {
     grouped_spread_kernel<<<grid, 256, 0, st>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  if (mode01 == 0)
+  if (mode01 == 3) {
+    grouped_decide_kernel<<<4, 256, 0, st>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    grouped_slice_kernel<3><<<grid, 256, 0, st>>>(a);
+  } else if (mode01 == 0) {
     grouped_slice_kernel<0><<<grid, 256, 0, st>>>(a);
-  else
+  } else {
     grouped_slice_kernel<1><<<grid, 256, 0, st>>>(a);
+  }
   return cudaGetLastError();
 }
 

@@ -232,3 +232,62 @@ def test_workload_takes_twelve_moduli(h, mm):
     Ah, Bh = A.cpu().numpy(), B.cpu().numpy()
     got = C.cpu().numpy()[rows]
     assert bound_ok(got, oracle.gemm_rows(Ah, Bh, rows), oracle.absprod_rows(Ah, Bh, rows), em.gamma(8192, "fp64_emu"))
+
+
+def test_subnormal_outputs_bit_exact(h, mm):
+    # entries near 2^-530: every product lies below 2^-1022, so the rebuilt
+    # integer is rounded once straight to the subnormal grid (and some rows
+    # reach down to zero)
+    m, n, k = 140, 130, 700
+    A = inputs.uniform(m, k, 17, inputs.STREAM_A) * 2.0 ** -530
+    B = inputs.uniform(k, n, 17, inputs.STREAM_B) * 2.0 ** -530
+    A[5] *= 2.0 ** -40
+    C, code, bits, _, _, _ = h.debug_fp64_product(dev(A), dev(B), residues=False)
+    assert h.sync() == 0
+    assert code > mm.CRT_BASE
+    got = C.cpu().numpy()
+    assert np.all(np.abs(got) < 2.0 ** -1022) and np.any(got != 0.0)
+    rows = [0, 5, 64, 139]
+    assert np.array_equal(got[rows], em.gemm_fp64_crt(A[rows], B, bits, code - mm.CRT_BASE))
+
+
+def test_grouped_modular_form_matches_single(h, mm):
+    # a group in the default scheme: problems that take the modular form, one
+    # that falls back to the digit form (short sums of wide-spread rows), one
+    # that takes the plain kernel (Cauchy rows) and one the single path takes
+    # (k <= 4): every result the same bits as mm_gemm on it alone
+    specs = [("scaled", 200, 300, 700), ("normal", 130, 70, 1500), ("uniform", 33, 520, 64), ("t3", 90, 90, 300),
+             ("spread", 40, 60, 7), ("scaled", 5, 6, 3), ("scaled", 257, 129, 2100)]
+    probs = []
+    for i, (name, m, n, k) in enumerate(specs):
+        A, B = _case(name, m, n, k, 50 + i)
+        probs.append((A, B, dev(A), dev(B), torch.full((m, n), np.nan, dtype=torch.float64, device="cuda")))
+    A, B = inputs.cauchy(64, 900, 3, 1), inputs.cauchy(900, 40, 3, 2)
+    probs.append((A, B, dev(A), dev(B), torch.full((64, 40), np.nan, dtype=torch.float64, device="cuda")))
+    h.grouped([(a, b, c) for _, _, a, b, c in probs], precision=mm.FP64_EMU)
+    assert h.sync() == 0
+    codes = []
+    for A, B, Ad, Bd, Cd in probs:
+        alone = h.gemm(Ad, Bd, precision=mm.FP64_EMU)
+        assert h.sync() == 0
+        got = Cd.cpu().numpy()
+        assert np.array_equal(got, alone.cpu().numpy())
+        k = A.shape[1]
+        assert bound_ok(got, oracle.gemm(A, B), oracle.absprod(A, B), em.gamma(k, "fp64_emu"))
+        if k > 4:
+            codes.append(h.debug_fp64_product(Ad, Bd, residues=False)[1])
+    assert any(c > mm.CRT_BASE for c in codes) and any(c <= 7 for c in codes) and 8 in codes, codes
+
+
+def test_served_requests_take_the_modular_form(h, mm):
+    A, B = _case("scaled", 300, 260, 1100, 9)
+    Ad, Bd = dev(A), dev(B)
+    Cd = torch.full((300, 260), np.nan, dtype=torch.float64, device="cuda")
+    t = h.serve_submit(Ad, Bd, Cd, precision=mm.FP64_EMU)
+    h.serve_drain()
+    rc, _ = h.serve_poll(t)
+    assert rc == 0
+    alone = h.gemm(Ad, Bd, precision=mm.FP64_EMU)
+    assert h.sync() == 0
+    assert np.array_equal(Cd.cpu().numpy(), alone.cpu().numpy())
+    assert h.debug_fp64_product(Ad, Bd, residues=False)[1] > mm.CRT_BASE

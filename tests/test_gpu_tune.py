@@ -106,7 +106,6 @@ def group_bucket(probs):
 def test_autotune_grouped_same_bits(mm):
     probs = make_group(30, 16, 400, 63)
     with mm.Handle(0) as h0:
-        h0.set_option(mm.OPT_FP64_SCHEME, 1)   # the digit form, as grouped products take it
         ref = [run(h0, A, B, mm.FP64_EMU) for A, B in probs]
     with mm.Handle(0) as h:
         h.set_option(mm.OPT_AUTOTUNE, 1)
@@ -129,7 +128,6 @@ def test_grouped_wide_tiles_from_loaded_table(mm, tmp_path, prec):
     path.write_text("# mm tune table v1: kind precision b0 b1 b2 bn cg kern ms\n"
                     f"1 {prec} {b_cnt} {b_d} 0 256 1 0 1.0\n")
     with mm.Handle(0) as h:
-        h.set_option(mm.OPT_FP64_SCHEME, 1)   # the digit form, as grouped products take it
         ref = [run(h, A, B, prec) for A, B in probs]
         h.tune_load(str(path))
         assert h.tune_lookup(prec, cnt, d, grouped=True) == (256, 1, 0)
