@@ -32,7 +32,8 @@
  *                modulo its modulus, the exact integer product rebuilt by the
  *                Chinese remainder theorem and rounded once: N products
  *                instead of s(s+1)/2 (11 against 15 at M = N = K = 8192 on
- *                the benchmark inputs); see mm_crt_rule and MM_OPT_FP64_SCHEME.
+ *                the benchmark inputs) for products with m*n*k >= 2^33; see
+ *                mm_crt_rule and MM_OPT_FP64_SCHEME.
  *   MM_FP32_EMU  FP32-accuracy emulation: three bfloat16 slices per scaled
  *                entry and the six slice products with index sum <= 2, FP32
  *                accumulation on tcgen05. Bound 4k*2^-24 * (|A||B|).
@@ -241,8 +242,11 @@ enum {
                                      products always use the default. */
     MM_OPT_FP64_SCHEME = 12       /* FP64-accuracy products with the automatic slice count
                                      (MM_OPT_SLICES = 0), single, grouped and served: 0 = the
-                                     modular form wherever mm_crt_rule fits, else the digit form
-                                     (default); 1 = the digit form only. */
+                                     modular form where mm_crt_rule fits and m*n*k >= 2^33, else
+                                     the digit form (default: smaller products run faster on the
+                                     digit form, whose split is shorter and whose epilogue a CTA
+                                     with few tiles need not overlap); 1 = the digit form only;
+                                     2 = the modular form wherever mm_crt_rule fits. */
 };
 
 /* Kernel classes for mm_profile_read. */

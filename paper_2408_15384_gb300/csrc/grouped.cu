@@ -90,6 +90,7 @@ struct EmuPlan {
     int s_floor;    // smallest count the automatic rule can give for this k
     int64_t kp, ldr;
     size_t colmax, rowmax, E, F, dec, part, sa, sb, res;
+    bool crt;       // the modular form allowed for this problem
   };
   std::vector<Prob> p;
   std::vector<TileCost> tiles;
@@ -97,7 +98,7 @@ struct EmuPlan {
   size_t colmax_bytes = 0, ws_bytes = 0;
   int bn = 128;   // output tile width of the group's slice GEMM (one CTA per 128 x bn tile)
   bool any_auto = false;
-  bool crt = false;               // the modular form allowed (FP64-accuracy, automatic counts)
+  bool crt = false;               // some problem may take the modular form
   int auto_floor = SLICE_S_MAX;   // smallest s_floor over the automatic problems
   void build(mm_handle_s* h, const std::vector<int>& idx, const mm_problem* probs, bool fp64, int bn_) {
     bn = bn_;
@@ -107,7 +108,6 @@ struct EmuPlan {
     ftiles.clear();
     any_auto = false;
     auto_floor = SLICE_S_MAX;
-    crt = fp64 && crt_allowed(h, MM_FP64_EMU, h->opt_slices);
     const int FT = fp64_tile_size();
     size_t cm = 0, o = 0;
     for (int i = 0; i < count; ++i) {
@@ -115,7 +115,9 @@ struct EmuPlan {
       Prob& r = p[i];
       r.s = emu_slices(h, fp64 ? MM_FP64_EMU : MM_FP32_EMU, q.k, 0);
       r.s_floor = r.s > 0 ? r.s : std::max(SLICE_S_MIN, slice_count_floor(q.k));
-      const int planes = crt ? std::max(CRT_N_MAX, SLICE_S_MAX) : emu_planes(r.s);
+      r.crt = fp64 && crt_allowed(h, MM_FP64_EMU, r.s, q.m, q.n, q.k);
+      crt = crt || r.crt;
+      const int planes = r.crt ? std::max(CRT_N_MAX, SLICE_S_MAX) : emu_planes(r.s);
       r.kp = static_cast<int64_t>(align_up(static_cast<size_t>(q.k), 8));
       r.ldr = static_cast<int64_t>(align_up(static_cast<size_t>(std::max<int64_t>(q.n, 1)), 16));
       // column maxima and decision records in the region zeroed before each launch
@@ -127,12 +129,12 @@ struct EmuPlan {
       r.part = o; o = align_up(o + (r.s == 0 ? 8 * static_cast<size_t>(launch_absmax_parts(q.k)) * q.n : 0), 256);
       r.sa = o; o = align_up(o + 2 * static_cast<size_t>(planes) * q.m * r.kp, 1024);
       r.sb = o; o = align_up(o + 2 * static_cast<size_t>(planes) * q.n * r.kp, 1024);
-      r.res = o; o = align_up(o + (crt ? static_cast<size_t>(CRT_N_MAX) * q.m * r.ldr : 0), 256);
+      r.res = o; o = align_up(o + (r.crt ? static_cast<size_t>(CRT_N_MAX) * q.m * r.ldr : 0), 256);
       const int tm = static_cast<int>((q.m + 127) / 128), tn = static_cast<int>((q.n + bn - 1) / bn);
       const int64_t nkb = (q.k + 63) / 64;
       // products a tile runs (for the cost order): the modular form's typical
       // 12 moduli, the digit form's pairs at its smallest count
-      const int64_t pairs = crt ? 12 : fp64 ? static_cast<int64_t>(r.s_floor) * (r.s_floor + 1) / 2 : (r.s == 2 ? 3 : 6);
+      const int64_t pairs = r.crt ? 12 : fp64 ? static_cast<int64_t>(r.s_floor) * (r.s_floor + 1) / 2 : (r.s == 2 ? 3 : 6);
       for (int a = 0; a < tm; ++a)
         for (int b = 0; b < tn; ++b)
           tiles.push_back({nkb * pairs, i, a * tn + b, TileRef{i, static_cast<int16_t>(a), static_cast<int16_t>(b)}});
@@ -177,10 +179,10 @@ static int fill_emu_blob(mm_handle_s* h, const EmuPlan& plan, const EmuLayout& L
   for (int i = 0; i < count; ++i) {
     const mm_problem& q = probs[idx[i]];
     const EmuPlan::Prob& r = plan.p[i];
-    const int planes = plan.crt ? std::max(CRT_N_MAX, SLICE_S_MAX) : emu_planes(r.s);
+    const int planes = r.crt ? std::max(CRT_N_MAX, SLICE_S_MAX) : emu_planes(r.s);
     GroupedSplit& g = gs[i];
     g.m = q.m; g.n = q.n; g.k = q.k; g.lda = q.lda; g.ldb = q.ldb; g.kp = r.kp;
-    g.A = q.A; g.B = q.B; g.s = r.s > 0 ? r.s : SLICE_S_MAX; g.pad = 0;
+    g.A = q.A; g.B = q.B; g.s = r.s > 0 ? r.s : SLICE_S_MAX; g.crt = r.crt ? 1 : 0;
     g.rowmax = reinterpret_cast<uint64_t*>(wsp + r.rowmax);
     g.colmax = reinterpret_cast<uint64_t*>(ws + r.colmax);
     g.E = reinterpret_cast<int32_t*>(wsp + r.E);
@@ -208,7 +210,7 @@ static int fill_emu_blob(mm_handle_s* h, const EmuPlan& plan, const EmuLayout& L
     P.tiles_m = static_cast<int>((q.m + 127) / 128);
     P.tiles_n = static_cast<int>((q.n + plan.bn - 1) / plan.bn);
     P.E = g.E; P.F = g.F; P.C = q.C; P.ldc = q.ldc; P.levels = nullptr;
-    if (plan.crt) {
+    if (r.crt) {
       P.res = reinterpret_cast<uint8_t*>(wsp + r.res);
       P.ldr = q.m * 8;
       P.rplane = q.m * r.ldr;

@@ -68,7 +68,8 @@ struct mm_handle_s {
   int opt_cta_pair = 0;
   int opt_tile_n = 0;        // FP64-accuracy tile width (0 = automatic, 128, 192, 240, 256)
   bool opt_int8 = false;     // FP64-accuracy single products on INT8-form digits (mma.sync s8)
-  int opt_fp64_scheme = 0;   // 0: modular form where it fits (single products), else digits; 1: digits only
+  int opt_fp64_scheme = 0;   // 0: modular form for products of m n k >= CRT_MIN_WORK where it fits; 1: digits
+                             // only; 2: modular form wherever it fits
   int max_pairs_fp32 = 0, max_pairs_fp64 = 0, max_pairs_crt = 0;   // co-resident CTA pairs of the pair kernels
   int max_clusters4_fp32 = 0, max_clusters4_fp64 = 0;   // co-resident clusters of two pairs (cg = 4)
 
@@ -159,8 +160,13 @@ struct SplitLayout {
 // mode: a launch_slice_rows mode (3 for a layout with crt)
 int run_split(mm_handle_s* h, int mode, const SplitLayout& L, char* ws, const double* A, int64_t lda,
               const double* B, int64_t ldb, cudaStream_t st);
-// whether a single FP64-accuracy product may take the modular form
-bool crt_allowed(const mm_handle_s* h, int precision, int s);
+// Whether an FP64-accuracy product of m x k by k x n may take the modular form
+// (automatic slice count; the scheme option; below CRT_MIN_WORK the digit
+// form is faster: the modular form's longer split and its rebuild, which a
+// product with few tiles a CTA cannot overlap with tensor-core work, cost more
+// than its fewer products save).
+constexpr double CRT_MIN_WORK = 8589934592.0;   // m n k >= 2^33 (2048^3)
+bool crt_allowed(const mm_handle_s* h, int precision, int s, int64_t m, int64_t n, int64_t k);
 
 // tune.cu: the autotuner. Keys are shape buckets (ceil(log2) of the single
 // product's m, n, k; of a group's problem count and mean dimension).

@@ -203,7 +203,7 @@ struct GroupedSplit {
   const double* A;
   const double* B;
   int s;                  // slices (FP64-accuracy, when dec is null) or 3
-  int pad;
+  int crt;                // 1: the modular form allowed (splitting mode 3)
   uint64_t* rowmax;
   uint64_t* colmax;
   int32_t* E;

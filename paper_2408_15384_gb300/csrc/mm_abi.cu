@@ -241,8 +241,10 @@ int run_split(mm_handle_s* h, int mode01, const SplitLayout& L, char* ws, const 
   return MM_OK;
 }
 
-bool crt_allowed(const mm_handle_s* h, int precision, int s) {
-  return precision == MM_FP64_EMU && s == 0 && h->opt_fp64_scheme != 1;
+bool crt_allowed(const mm_handle_s* h, int precision, int s, int64_t m, int64_t n, int64_t k) {
+  if (precision != MM_FP64_EMU || s != 0 || h->opt_fp64_scheme == 1) return false;
+  return h->opt_fp64_scheme == 2 ||
+         static_cast<double>(m) * static_cast<double>(n) * static_cast<double>(k) >= CRT_MIN_WORK;
 }
 
 int emu_slices(mm_handle_s* h, int precision, int64_t k, int s_override) {
@@ -402,7 +404,7 @@ int run_emulated(mm_handle_s* h, int precision, int64_t m, int64_t n, int64_t k,
   const bool fp64 = (precision == MM_FP64_EMU);
   const int s = emu_slices(h, precision, k, s_override);
   SplitLayout L;
-  L.plan(m, n, k, s, 2, !levels && crt_allowed(h, precision, s));
+  L.plan(m, n, k, s, 2, !levels && crt_allowed(h, precision, s, m, n, k));
   void* wsv = nullptr;
   int rc = ws_alloc(h, L.bytes, st, &wsv);
   if (rc != MM_OK) return rc;
@@ -646,7 +648,7 @@ int gemm_host_pipelined(mm_handle_s* h, int64_t m, int64_t n, int64_t k, const d
   const bool fp64 = precision == MM_FP64_EMU;
   const int s = emu_slices(h, precision, k, 0);
   SplitLayout L;
-  L.plan(m, n, k, s, 2, crt_allowed(h, precision, s));
+  L.plan(m, n, k, s, 2, crt_allowed(h, precision, s, m, n, k));
   const int smode = !fp64 ? 1 : (L.crt ? 3 : 0);
   void* wsv = nullptr;
   int rc = ws_alloc(h, L.bytes, st, &wsv);
@@ -842,7 +844,7 @@ int mm_set_option(mm_handle h, int option, int64_t value) {
       h->opt_int8 = value != 0;
       return MM_OK;
     case MM_OPT_FP64_SCHEME:
-      if (value != 0 && value != 1) return MM_ERR_INVALID_ARG;
+      if (value < 0 || value > 2) return MM_ERR_INVALID_ARG;
       h->opt_fp64_scheme = static_cast<int>(value);
       return MM_OK;
     default: return MM_ERR_INVALID_ARG;
@@ -1016,7 +1018,7 @@ int mm_debug_fp64_product(mm_handle h, int64_t m, int64_t n, int64_t k, const do
   DeviceGuard g(h->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   SplitLayout L;
-  L.plan(m, n, k, 0, 2, h->opt_fp64_scheme != 1);
+  L.plan(m, n, k, 0, 2, crt_allowed(h, MM_FP64_EMU, 0, m, n, k));
   void* wsv = nullptr;
   rc = ws_alloc(h, L.bytes, st, &wsv);
   if (rc != MM_OK) return rc;

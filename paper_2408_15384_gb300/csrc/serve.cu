@@ -120,7 +120,7 @@ static size_t request_charge(mm_handle_s* h, const mm_request& r) {
   if (r.precision != MM_FP64 && p.k > 0) {
     // slice planes (seven for the automatic count, fourteen with the modular
     // form allowed, which also keeps its residue bytes), scan and spread records
-    const bool crt = crt_allowed(h, r.precision, h->opt_slices);
+    const bool crt = crt_allowed(h, r.precision, h->opt_slices, p.m, p.n, p.k);
     const int s = crt ? CRT_N_MAX : (r.precision == MM_FP64_EMU) ? emu_planes(h->opt_slices) : 3;
     const size_t kp = align_up(static_cast<size_t>(p.k), 8);
     bytes += 2 * static_cast<size_t>(s) * (p.m + p.n) * kp + 16 * static_cast<size_t>(p.m + p.n) +

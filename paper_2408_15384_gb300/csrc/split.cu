@@ -876,8 +876,9 @@ __global__ void __launch_bounds__(256) grouped_spread_kernel(const GroupedSplitA
   }
 }
 
-// Between the phases, with the modular form allowed: one thread per problem
-// records its decision (fp64_decision on its spreads).
+// Between the phases, with the modular form allowed for some problem: one
+// thread per problem records its decision (fp64_decision on its spreads, the
+// modular form only where the problem allows it).
 __global__ void __launch_bounds__(256) grouped_decide_kernel(const GroupedSplitArgs a) {
   const int count = *a.count_dev;
   for (int p = static_cast<int>(blockIdx.x * blockDim.x + threadIdx.x); p < count;
@@ -885,8 +886,8 @@ __global__ void __launch_bounds__(256) grouped_decide_kernel(const GroupedSplitA
     SliceDecision* d = a.probs[p].dec;
     if (d == nullptr) continue;
     int b = 0;
-    const int code =
-        fp64_decision(a.probs[p].k, spread_from_room(d->amin_room), spread_from_room(d->bmin_room), true, &b);
+    const int code = fp64_decision(a.probs[p].k, spread_from_room(d->amin_room), spread_from_room(d->bmin_room),
+                                   a.probs[p].crt != 0, &b);
     d->s = code;
     d->bits = b;
   }

@@ -37,7 +37,10 @@ def mm():
 
 @pytest.fixture(scope="module")
 def h(mm):
+    # the modular form wherever it fits, small products included (by default
+    # only products of m n k >= 2^33 take it)
     with mm.Handle(0) as hh:
+        hh.set_option(mm.OPT_FP64_SCHEME, 2)
         yield hh
 
 
@@ -205,7 +208,7 @@ def test_digit_form_option(h, mm):
         C, code, _, _, _, _ = h.debug_fp64_product(dev(A), dev(B), residues=False)
         assert h.sync() == 0
     finally:
-        h.set_option(mm.OPT_FP64_SCHEME, 0)
+        h.set_option(mm.OPT_FP64_SCHEME, 2)
     assert code == em.slice_count(A, B)
     s = code
     E, sA = em.fp64_slices_A(A, s)
@@ -214,7 +217,7 @@ def test_digit_form_option(h, mm):
     Ce = em.recombine_exact(em.level_products(sA[:, rows], sB, s), E[rows], F, s)
     assert np.array_equal(C.cpu().numpy()[rows], Ce)
     with pytest.raises(mm.MMError):
-        h.set_option(mm.OPT_FP64_SCHEME, 2)
+        h.set_option(mm.OPT_FP64_SCHEME, 3)
 
 
 def test_workload_takes_twelve_moduli(h, mm):
@@ -291,3 +294,19 @@ def test_served_requests_take_the_modular_form(h, mm):
     assert h.sync() == 0
     assert np.array_equal(Cd.cpu().numpy(), alone.cpu().numpy())
     assert h.debug_fp64_product(Ad, Bd, residues=False)[1] > mm.CRT_BASE
+
+
+def test_default_scheme_by_size(mm):
+    # the default takes the modular form from m n k >= 2^33 on (where it is the
+    # faster form), the digit form below
+    with mm.Handle(0) as hd:
+        assert hd.get_option(mm.OPT_FP64_SCHEME) == 0
+        small = _case("scaled", 1000, 1000, 1000, 4)
+        big = (inputs.row_scaled(2048, 2048, 4), inputs.col_scaled(2048, 2048, 4))
+        for (A, B), modular in ((small, False), (big, True)):
+            C, code, bits, _, _, _ = hd.debug_fp64_product(dev(A), dev(B), residues=False)
+            assert hd.sync() == 0
+            assert (code > mm.CRT_BASE) == modular, (A.shape, code)
+            rows = [0, 999]
+            assert bound_ok(C.cpu().numpy()[rows], oracle.gemm_rows(A, B, rows), oracle.absprod_rows(A, B, rows),
+                            em.gamma(A.shape[1], "fp64_emu"))

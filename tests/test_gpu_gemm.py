@@ -31,12 +31,13 @@ def mm():
     return mm
 
 
-@pytest.fixture(scope="module", params=["auto", "digits"])
+@pytest.fixture(scope="module", params=["modular", "digits"])
 def h(mm, request):
-    # "auto": FP64-accuracy single products take the modular form where it fits
-    # (the default); "digits": the digit form only (MM_OPT_FP64_SCHEME = 1)
+    # "modular": FP64-accuracy products take the modular form wherever it fits
+    # (MM_OPT_FP64_SCHEME = 2; by default only products of m n k >= 2^33 do,
+    # larger than these); "digits": the digit form only (= 1)
     with mm.Handle(0) as hh:
-        hh.set_option(mm.OPT_FP64_SCHEME, 0 if request.param == "auto" else 1)
+        hh.set_option(mm.OPT_FP64_SCHEME, 2 if request.param == "modular" else 1)
         yield hh
 
 
@@ -170,7 +171,7 @@ def test_fp64_emu_within_bound_and_exact(h, mm, m, n, k):
     if k <= 4:
         return
     _, code, bits, _, _, _ = h.debug_fp64_product(dev(A), dev(B))
-    want = em.fp64_scheme(A, B, modular=h.get_option(mm.OPT_FP64_SCHEME) == 0)
+    want = em.fp64_scheme(A, B, modular=h.get_option(mm.OPT_FP64_SCHEME) == 2)
     if want[0] == "crt":
         # the modular form: the exact integer product of the scaled entries, rounded once
         assert (code, bits) == (mm.CRT_BASE + want[2], want[1])
