@@ -122,7 +122,8 @@ def measured_peaks():
         return {}
 
 
-SLICE_GEMM_SOURCES = ("slice_gemm_kernel.cuh", "slice_gemm.cu", "slice_gemm_fold.cu", "slice_gemm_carry.cu")
+SLICE_GEMM_SOURCES = ("slice_gemm_kernel.cuh", "slice_gemm.cu", "slice_gemm_fold.cu", "slice_gemm_carry.cu",
+                      "slice_gemm_crt.cu")
 
 
 def code_of(text: str) -> str:
