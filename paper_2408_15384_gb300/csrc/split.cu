@@ -137,10 +137,14 @@ __device__ __forceinline__ uint16_t bf16_rne_take(int64_t& M, int e) {
   return static_cast<uint16_t>(sgn | (static_cast<uint32_t>(biased) << 7) | static_cast<uint32_t>(q - 128));
 }
 
-__device__ __forceinline__ void fp32_slices3(uint64_t bits, int E, uint32_t& s0, uint32_t& s1, uint32_t& s2) {
+// The first S (2 or 3) FP32-accuracy slices of one entry (the third is not
+// formed for two slices).
+template <int S>
+__device__ __forceinline__ void fp32_slices(uint64_t bits, int E, uint32_t& s0, uint32_t& s1, uint32_t& s2) {
   uint64_t ab = bits & ABS_MASK;
+  s2 = 0u;
   if (ab == 0) {
-    s0 = s1 = s2 = 0u;
+    s0 = s1 = 0u;
     return;
   }
   uint64_t mant;
@@ -163,7 +167,7 @@ __device__ __forceinline__ void fp32_slices3(uint64_t bits, int E, uint32_t& s0,
     s0 = bf16_rne_take(M, e);
   }
   s1 = bf16_rne_take(M, e);
-  s2 = bf16_rne_take(M, e);
+  if (S >= 3) s2 = bf16_rne_take(M, e);
 }
 
 // Slice modes: 0 FP64-accuracy digits as bfloat16, 1 FP32-accuracy bfloat16
@@ -249,8 +253,13 @@ __device__ __forceinline__ void slice8_store(const uint64_t (&vb)[8], int32_t X,
     }
   } else {
     uint32_t h[3][8];
+    if (s >= 3) {
 #pragma unroll
-    for (int u = 0; u < 8; ++u) fp32_slices3(vb[u], X, h[0][u], h[1][u], h[2][u]);
+      for (int u = 0; u < 8; ++u) fp32_slices<3>(vb[u], X, h[0][u], h[1][u], h[2][u]);
+    } else {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) fp32_slices<2>(vb[u], X, h[0][u], h[1][u], h[2][u]);
+    }
 #pragma unroll
     for (int P = 0; P < 3; ++P) {
       if (P >= s) break;   // two slices: the third is not stored
@@ -417,6 +426,14 @@ __device__ __forceinline__ SpreadAcc spread_merge(const SpreadAcc& a, const Spre
 __device__ __forceinline__ float spread_final(const SpreadAcc& a, uint64_t mx, int64_t k) {
   if (mx == 0 || mx >= INF_BITS) return __uint_as_float(0x7F800000u);
   return a.sum * pow2f(a.ref - 1023 - (floor_log2_bits(mx) + 2)) / static_cast<float>(k);
+}
+
+// A warp's row spread (every lane holds it), merged into the decision word
+// *dst as its distance below +inf by lane 0 (no block barrier: the minimum
+// does not depend on the order).
+__device__ __forceinline__ void warp_min_to(float v, uint32_t* dst) {
+  if ((threadIdx.x & 31u) == 0 && v < __uint_as_float(0x7F800000u))
+    atomicMax(dst, 0x7F800000u - __float_as_uint(v));
 }
 
 // Minimum over the block's threads of v (non-negative), merged into the
@@ -668,9 +685,10 @@ __global__ void __launch_bounds__(256) row_absmax_kernel(const double* __restric
                                                          int64_t lda, uint64_t* __restrict__ rowmax,
                                                          uint32_t* __restrict__ amin) {
   const int64_t row = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  float al = __uint_as_float(0x7F800000u);
-  if (row < m) al = row_absmax_body<SPREAD>(A, k, lda, row, rowmax);
-  if constexpr (SPREAD) block_min_to(al, amin);
+  if (row < m) {
+    const float al = row_absmax_body<SPREAD>(A, k, lda, row, rowmax);
+    if constexpr (SPREAD) warp_min_to(al, amin);
+  }
 }
 
 template <bool SPREAD>
@@ -699,9 +717,10 @@ __global__ void __launch_bounds__(256) absmax_both_kernel(const double* __restri
   const int b = static_cast<int>(blockIdx.x);
   if (b < row_blocks) {
     const int64_t row = static_cast<int64_t>(b) * 8 + (threadIdx.x >> 5);
-    float al = __uint_as_float(0x7F800000u);
-    if (row < m) al = row_absmax_body<SPREAD>(A, k, lda, row, rowmax);
-    if constexpr (SPREAD) block_min_to(al, amin);
+    if (row < m) {
+      const float al = row_absmax_body<SPREAD>(A, k, lda, row, rowmax);
+      if constexpr (SPREAD) warp_min_to(al, amin);
+    }
     return;
   }
   const int cb = b - row_blocks;
@@ -798,9 +817,7 @@ __global__ void __launch_bounds__(256) grouped_absmax_kernel(const GroupedSplitA
       const GroupedSplit& g = a.probs[p];
       const int64_t row = (vb - off0[p]) * 8 + (threadIdx.x >> 5);
       if (g.dec != nullptr) {
-        float al = __uint_as_float(0x7F800000u);
-        if (row < g.m) al = row_absmax_body<true>(g.A, g.k, g.lda, row, g.rowmax);
-        block_min_to(al, &g.dec->amin_room);
+        if (row < g.m) warp_min_to(row_absmax_body<true>(g.A, g.k, g.lda, row, g.rowmax), &g.dec->amin_room);
       } else if (row < g.m) {
         row_absmax_body<false>(g.A, g.k, g.lda, row, g.rowmax);
       }
