@@ -319,7 +319,7 @@ def ours(args):
         h.gemm(A, B, C, precision=mm.FP64_EMU)
     torch.cuda.synchronize(dev)
     h.set_option(mm.OPT_PROFILE, 1)
-    for kcls in (mm.KERNEL_SLICE_GEMM, mm.KERNEL_SPLIT):
+    for kcls in (mm.KERNEL_SLICE_GEMM, mm.KERNEL_SPLIT, mm.KERNEL_REBUILD):
         h.profile_read(kcls, reset=True)
     launches0 = h.stats()
     try:
@@ -349,6 +349,7 @@ def ours(args):
     status = h.sync()
     gemm_ms, gemm_n = h.profile_read(mm.KERNEL_SLICE_GEMM, reset=True)
     split_ms, split_n = h.profile_read(mm.KERNEL_SPLIT, reset=True)
+    rebuild_ms, _ = h.profile_read(mm.KERNEL_REBUILD, reset=True)
     h.set_option(mm.OPT_PROFILE, 0)
     t_ms = slowest_rank_ms(t_ms, dist, dev)
     ms_step = t_ms / args.steps
@@ -505,13 +506,16 @@ def ours(args):
             "config": workload_config(N, ws),
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_note": peak_note,
-                         "kernel": "slice_gemm (tcgen05 bf16 slice products, FP64-accuracy epilogue)",
+                         "kernel": ("slice_gemm (tcgen05 bf16 residue products; the epilogue stores the sums "
+                                    "modulo each modulus, C is rebuilt by a pass of its own)" if s is None else
+                                    "slice_gemm (tcgen05 bf16 slice products, FP64-accuracy epilogue)"),
                          "kernel_ms": kernel_ms, "algorithmic": f"2*N^3*{pairs} slice flop per launch",
                          "fp64_form": form},
             "step_ms_median_ci95": {"median": med, "lo": lo, "hi": hi, "n": args.steps,
                                     "tflops_at_median": flop / (med * 1e-3) / 1e12 if med else None,
                                     "method": "order-statistic interval of the per-step device times (CUDA events)"},
             "split_kernels_ms_per_step": split_ms / max(args.steps, 1),
+            "rebuild_kernel_ms_per_step": rebuild_ms / max(args.steps, 1),
             "clocks": clocks, "gpu_launches": launches, "device_status": status,
         }
         line.update(extra)

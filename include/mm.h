@@ -31,7 +31,7 @@
  *                residue product per modulus on tcgen05, each product reduced
  *                modulo its modulus, the exact integer product rebuilt by the
  *                Chinese remainder theorem and rounded once: N products
- *                instead of s(s+1)/2 (11 against 15 at M = N = K = 8192 on
+ *                instead of s(s+1)/2 (12 against 15 at M = N = K = 8192 on
  *                the benchmark inputs) for products with m*n*k >= 2^33; see
  *                mm_crt_rule and MM_OPT_FP64_SCHEME.
  *   MM_FP32_EMU  FP32-accuracy emulation: three bfloat16 slices per scaled
@@ -253,7 +253,9 @@ enum {
 enum {
     MM_KERNEL_SLICE_GEMM = 0,     /* tcgen05 slice products + recombination (emulated modes) */
     MM_KERNEL_SPLIT = 1,          /* exponent scan and slicing of both operands */
-    MM_KERNEL_FP64_GEMM = 2       /* plain FP64 tile kernel */
+    MM_KERNEL_FP64_GEMM = 2,      /* plain FP64 tile kernel */
+    MM_KERNEL_REBUILD = 3         /* the modular form's rebuild of C from the residue bytes (single
+                                     products; grouped launches rebuild inside the slice GEMM) */
 };
 int mm_set_option(mm_handle h, int option, int64_t value);
 int mm_get_option(mm_handle h, int option, int64_t *value);
@@ -349,6 +351,20 @@ int mm_debug_slice_count(mm_handle h, int64_t m, int64_t n, int64_t k,
  * pointers; synchronous. */
 int mm_debug_crt_residues(mm_handle h, int which, int N, int bits, int64_t rows, int64_t cols,
                           const double *X, int64_t ldx, int32_t *exps, uint16_t *planes, void *stream);
+
+/* The modular form's rebuild pass alone, as it follows the slice GEMM of a
+ * single product (Ozaki scheme II, the Chinese-remainder step): C[i][j] =
+ * round-to-nearest(Y_ij 2^(E_i + F_j - 2 bits)), Y_ij the integer in
+ * [-M_N/2, M_N/2) congruent to res's byte of (i, j) modulo the l-th modulus
+ * for l < N (any byte value; it is taken modulo its modulus). res: the slice
+ * GEMM's layout, plane l at res + l * m * 8 * ceil(n/8), within a plane
+ * ceil(n/8) blocks of 8 columns, each block the m rows' 8-byte records in row
+ * order. E (m), F (n): int32 exponents; an exponent of -1000000 marks a
+ * non-finite row or column (NaN out). Device pointers; synchronous.
+ * MM_ERR_INVALID_ARG for N outside 1..14, bits outside 1..53, m or n <= 0,
+ * null pointers or ldc < n. */
+int mm_debug_crt_rebuild(mm_handle h, int64_t m, int64_t n, int N, int bits, const uint8_t *res,
+                         const int32_t *E, const int32_t *F, double *C, int64_t ldc, void *stream);
 
 /* One automatic FP64-accuracy product (k > 4) as mm_gemm runs it, with the
  * device's decision: *code = SLICE count 3..7 (digit form), 8 (plain FP64

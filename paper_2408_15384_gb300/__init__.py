@@ -28,7 +28,7 @@ OPT_TILE_N = 9
 OPT_INT8_SLICES = 11
 OPT_FP64_SCHEME = 12
 CRT_BASE = 16   # decision code of the modular form: CRT_BASE + N
-KERNEL_SLICE_GEMM, KERNEL_SPLIT, KERNEL_FP64_GEMM = 0, 1, 2
+KERNEL_SLICE_GEMM, KERNEL_SPLIT, KERNEL_FP64_GEMM, KERNEL_REBUILD = 0, 1, 2, 3
 
 
 class MMError(RuntimeError):
@@ -294,6 +294,28 @@ class Handle:
         if rc not in (OK, 4):
             raise MMError(rc, "mm_debug_crt_residues")
         return exps, pl, rc
+
+    def debug_crt_rebuild(self, res, E, F, N: int, bits: int, stream=None):
+        """The modular form's rebuild pass alone: C (m x n float64) from
+        residue bytes res (uint8 [N][m][n], device), row exponents E (int32 m)
+        and column exponents F (int32 n), N moduli, b = bits."""
+        import torch
+        if res.dtype != torch.uint8 or res.dim() != 3 or res.shape[0] != N:
+            raise ValueError("res must be uint8 [N][m][n]")
+        _, m, n = res.shape
+        n8 = (n + 7) // 8
+        # the slice GEMM's layout: per plane, blocks of 8 columns of the rows' 8-byte records
+        pad = torch.zeros((N, m, 8 * n8), dtype=torch.uint8, device=res.device)
+        pad[:, :, :n] = res
+        lay = pad.reshape(N, m, n8, 8).permute(0, 2, 1, 3).contiguous()
+        E = E.to(device=res.device, dtype=torch.int32).contiguous()
+        F = F.to(device=res.device, dtype=torch.int32).contiguous()
+        C = torch.empty((m, n), dtype=torch.float64, device=res.device)
+        rc = self.lib.mm_debug_crt_rebuild(self.h, m, n, N, bits, lay.data_ptr(), E.data_ptr(), F.data_ptr(),
+                                           C.data_ptr(), n, _stream_handle(stream))
+        if rc != OK:
+            raise MMError(rc, "mm_debug_crt_rebuild")
+        return C
 
     def debug_fp64_product(self, A, B, C=None, residues=True, stream=None):
         """One automatic FP64-accuracy product as mm_gemm runs it: (C, code,

@@ -75,9 +75,9 @@ struct mm_handle_s {
 
   // profiling: (start, end) event pairs per kernel class, drained by mm_profile_read
   std::mutex prof_mu;
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_pending[3];
-  double prof_ms[3] = {0, 0, 0};
-  uint64_t prof_count[3] = {0, 0, 0};
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_pending[4];
+  double prof_ms[4] = {0, 0, 0, 0};
+  uint64_t prof_count[4] = {0, 0, 0, 0};
 
   std::mutex grouped_mu;
   mmhost::GroupedCache* grouped = nullptr;

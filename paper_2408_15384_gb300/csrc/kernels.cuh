@@ -318,6 +318,10 @@ struct SliceGemmArgs {
   uint32_t* err;
   uint64_t timeout_ns;
   int s_lo, s_hi;                  // with s_dev: only tiles of problems with s in [s_lo, s_hi] (s_hi > 0)
+  // SLICE_CRT, single products: 1 = store the residue bytes only (the rebuild
+  // is a pass of its own, crt_rebuild) and split the last, partial round of
+  // tiles by moduli among the walkers
+  int crt_defer;
 };
 
 // bn: tile width (columns of C); cg: CTAs per tile (1, or 2 for a CTA pair on
@@ -337,6 +341,10 @@ int slice_gemm_max_pairs(int mode);
 int slice_gemm_max_clusters4(int mode);
 // whether launch_slice_gemm has a kernel for (mode, tile width, CTAs per tile)
 bool slice_gemm_tile_ok(int mode, int bn, int cg);
+// The modular form's rebuild of P's outputs (C) from its residue bytes, after
+// a slice GEMM of P launched with crt_defer; returns at once for a product
+// whose decision record names the digit form.
+cudaError_t slice_rebuild_crt(const SliceProblem& P, int sm_count, cudaStream_t st);
 
 // ------------------------------------------------------------- int8_gemm.cu
 // FP64-accuracy product from INT8-form digit planes on mma.sync m16n8k32 s8.

@@ -357,12 +357,19 @@ static int slice_gemm_launch(mm_handle_s* h, const SplitLayout& L, char* ws, int
   const int clusters4 = fp64 ? h->max_clusters4_fp64 : h->max_clusters4_fp32;
   const int grid = (sl.cg == 4) ? 4 * std::min(ntiles / 2, clusters4)
                    : (sl.cg == 2) ? 2 * std::min(ntiles, pairs_avail) : std::min(ntiles, h->sm_count);
+  // the modular form: the slice GEMM stores residue bytes, a pass of its own rebuilds C
+  a.crt_defer = (sl.mode == SLICE_CRT) ? 1 : 0;
   cudaError_t e;
   {
     ProfScope ps(h, MM_KERNEL_SLICE_GEMM, st);
     e = launch_slice_gemm(sl.mode, sl.bn, sl.cg, &tmA, &tmB, a, grid, st);
   }
   count_launch(h, 1);
+  if (e == cudaSuccess && a.crt_defer) {
+    ProfScope ps(h, MM_KERNEL_REBUILD, st);
+    e = slice_rebuild_crt(P, h->sm_count, st);
+    count_launch(h, 1);
+  }
   return cuda_status(e, "slice gemm");
 }
 
@@ -1009,6 +1016,32 @@ int mm_debug_crt_residues(mm_handle h, int which, int N, int bits, int64_t rows,
   return read_and_clear_err(h, st);
 }
 
+int mm_debug_crt_rebuild(mm_handle h, int64_t m, int64_t n, int N, int bits, const uint8_t* res, const int32_t* E,
+                         const int32_t* F, double* C, int64_t ldc, void* stream) {
+  if (!h || m <= 0 || n <= 0 || N < 1 || N > CRT_N_MAX || bits < 1 || bits > CRT_B_MAX) return MM_ERR_INVALID_ARG;
+  if (!res || !E || !F || !C || ldc < n) return MM_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  SliceProblem P;
+  memset(&P, 0, sizeof(P));
+  P.m = m;
+  P.n = n;
+  P.s = N;               // no decision record: N and b from the host
+  P.fix_shift = bits;
+  P.res = const_cast<uint8_t*>(res);
+  P.ldr = m * 8;
+  P.rplane = m * 8 * ((n + 7) / 8);
+  P.E = E;
+  P.F = F;
+  P.C = C;
+  P.ldc = ldc;
+  cudaError_t e = slice_rebuild_crt(P, h->sm_count, st);
+  count_launch(h, 1);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_status(e, "debug rebuild");
+  return read_and_clear_err(h, st);
+}
+
 int mm_debug_fp64_product(mm_handle h, int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
                           int64_t ldb, double* C, int64_t ldc, uint8_t* res, int* code, int* bits, float* alpha_min,
                           float* beta_min, void* stream) {
@@ -1139,7 +1172,7 @@ int mm_stats(mm_handle h, uint64_t* kernel_launches) {
 }
 
 int mm_profile_read(mm_handle h, int kernel, double* total_ms, uint64_t* launches, int reset) {
-  if (!h || kernel < 0 || kernel > 2 || !total_ms || !launches) return MM_ERR_INVALID_ARG;
+  if (!h || kernel < 0 || kernel > 3 || !total_ms || !launches) return MM_ERR_INVALID_ARG;
   DeviceGuard g(h->device);
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pend;
   {

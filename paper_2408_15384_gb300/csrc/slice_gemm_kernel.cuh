@@ -201,13 +201,13 @@ __device__ __forceinline__ void walk_level(int nkb, int& chunk, Fn& f) {
 }
 
 // Walk the pipeline steps of one tile in order; f(Step, chunk offset in tile).
-// The steps of the modular form: for each modulus l, K chunks of 16 blocks
-// (at most 1024 terms of at most 2^14: exact f32 sums), one residue pair
-// (l, l) a K block, PPS consecutive K blocks a step.
+// The steps of the modular form: for each modulus l of the unit's range
+// [l0, l1), K chunks of 16 blocks (at most 1024 terms of at most 2^14: exact
+// f32 sums), one residue pair (l, l) a K block, PPS consecutive K blocks a step.
 template <int PPS, typename Fn>
-__device__ __forceinline__ void walk_crt(int N, int nkb, Fn& f) {
+__device__ __forceinline__ void walk_crt(int l0, int l1, int nkb, Fn& f) {
   int chunk = 0;
-  for (int l = 0; l < N; ++l) {
+  for (int l = l0; l < l1; ++l) {
     for (int kb0 = 0; kb0 < nkb; kb0 += 16, ++chunk) {
       const int kb1 = min(kb0 + 16, nkb);
       for (int kb = kb0; kb < kb1; kb += PPS) {
@@ -219,9 +219,9 @@ __device__ __forceinline__ void walk_crt(int N, int nkb, Fn& f) {
 }
 
 template <int MODE, int PPS, typename Fn>
-__device__ __forceinline__ void for_each_step(int s, int nkb, Fn&& f) {
+__device__ __forceinline__ void for_each_step(int s, int nkb, Fn&& f, int l0 = 0, int l1 = 0) {
   if (MODE == SLICE_CRT) {
-    walk_crt<PPS>(s, nkb, f);
+    walk_crt<PPS>(l0, l1, nkb, f);
   } else if (MODE == SLICE_FP32EMU) {
     // pairs (p, q), p + q <= 2 (three slices) or p + q <= 1 (s = 2), smallest
     // products first (the same order whether a step carries one pair or two)
@@ -267,7 +267,7 @@ __device__ __forceinline__ void for_each_step(int s, int nkb, Fn&& f) {
 template <int MODE>
 __device__ __forceinline__ int chunks_per_tile(int s, int nkb) {
   if (MODE == SLICE_FP32EMU) return 1;
-  if (MODE == SLICE_CRT) return s * ((nkb + 15) / 16);
+  if (MODE == SLICE_CRT) return s * ((nkb + 15) / 16);   // s: the unit's modulus count
   int c = 0;
   for (int d = 2; d <= s + 1; ++d) {
     const int kc = chunk_blocks(d);
@@ -308,6 +308,37 @@ __device__ __forceinline__ void resolve_slices(const SliceGemmArgs& a, const Sli
   }
 }
 
+// The units a launch's walkers take in turn: unit u < nfull is tile u with all
+// its moduli; the last, partial round of tiles (single modular-form products
+// whose rebuild is a pass of its own) is split by moduli, `parts` units a
+// tile, so that round ends after about N / parts moduli instead of N while
+// the other walkers would idle. Every role maps a unit the same way.
+struct Units {
+  int nfull, parts, units;
+};
+__device__ __forceinline__ Units whole_tiles(int ntiles) { return Units{ntiles, 1, ntiles}; }
+__device__ __forceinline__ Units split_tail(int ntiles, int walkers, int N) {
+  const int tail = ntiles % walkers;
+  int parts = tail > 0 ? walkers / tail : 1;
+  if (parts > N) parts = N;
+  if (parts < 2) return whole_tiles(ntiles);
+  return Units{ntiles - tail, parts, ntiles - tail + tail * parts};
+}
+__device__ __forceinline__ int unit_tile(const Units& U, int u) {
+  return u < U.nfull ? u : U.nfull + (u - U.nfull) / U.parts;
+}
+// the unit's moduli [l0, l1) of the tile's N
+__device__ __forceinline__ void unit_moduli(const Units& U, int u, int N, int& l0, int& l1) {
+  if (u < U.nfull) {
+    l0 = 0;
+    l1 = N;
+  } else {
+    const int part = (u - U.nfull) % U.parts;
+    l0 = part * N / U.parts;
+    l1 = (part + 1) * N / U.parts;
+  }
+}
+
 // col_pairs = 2 (clusters of two CTA pairs): t numbers pairs of horizontally
 // adjacent tiles and the cluster's pair `pair_col` takes tile column
 // 2 * (pair of columns) + pair_col; single products only.
@@ -341,25 +372,101 @@ __device__ __forceinline__ TileJob get_job(const SliceGemmArgs& a, const CUtenso
   return j;
 }
 
-// Rebuild of 4 outputs of a modular-form product: row `row`, columns c4 ..
-// c4 + 3 (c4 a multiple of 4), from the residue bytes of its N products.
-// S = sum_l c_l W_l is formed as four 64-bit column sums of 32-bit words (W4:
-// whether W_l needs its fourth word, M_N >= 2^96); q = round(S / M) from a
+// The rebuild constants of N moduli as one output's rebuild reads them: M_N
+// as 32-bit words and as two 64-bit words, M_N / 2, the quotient window's
+// shift and scale. NW: how many 32-bit words M_N (and every W_l) needs; the
+// words above are zero, and with a compile-time NW the arithmetic on them
+// folds away.
+struct CrtK {
+  uint32_t m0, m1, m2, m3;
+  uint64_t Ml, Mh, Hl, Hh;
+  int wsh;
+  float qscale;
+};
+template <int NW>
+__device__ __forceinline__ CrtK crt_k(int N) {
+  CrtK k;
+  k.m0 = c_crt.M[N][0];
+  k.m1 = NW > 1 ? c_crt.M[N][1] : 0u;
+  k.m2 = NW > 2 ? c_crt.M[N][2] : 0u;
+  k.m3 = NW > 3 ? c_crt.M[N][3] : 0u;
+  k.Ml = (static_cast<uint64_t>(k.m1) << 32) | k.m0;
+  k.Mh = (static_cast<uint64_t>(k.m3) << 32) | k.m2;
+  k.Hl = c_crt.H[N][0];
+  k.Hh = NW > 2 ? c_crt.H[N][1] : 0ull;
+  k.wsh = c_crt.wsh[N];
+  k.qscale = c_crt.qscale[N];
+  return k;
+}
+
+// One output of a modular-form product from the column sums T0..T3 of
+// S = sum_l c_l W_l (T_i: the 64-bit sum of the products of the residues with
+// the W_l's 32-bit word i; S < 14 * 2^8 * M < 2^123). q = round(S / M) from a
 // float estimate good to 2^-11; Y = S - q M moved into [-M/2, M/2) (one step
 // at most) is the exact integer product; it is rounded to double once and
-// scaled by 2^(E_i + F_j - 2b). Kept out of line: it runs at modulus ends,
-// between chunk drains, and gets the whole register budget.
+// scaled by 2^e (e = E_i + F_j - 2b). Returns the double's bits.
+template <int NW>
+__device__ __forceinline__ uint64_t crt_output(uint64_t T0, uint64_t T1, uint64_t T2, uint64_t T3, const CrtK& k,
+                                               int e) {
+  if (NW < 2) T1 = 0ull;
+  if (NW < 3) T2 = 0ull;
+  if (NW < 4) T3 = 0ull;
+  // carries: S = hi:lo
+  const uint64_t t1 = T1 + (T0 >> 32);
+  const uint64_t t2 = T2 + (t1 >> 32);
+  const uint64_t t3 = T3 + (t2 >> 32);
+  const uint64_t lo = (t1 << 32) | (T0 & 0xFFFFFFFFull);
+  const uint64_t hi = (t3 << 32) | (t2 & 0xFFFFFFFFull);
+  // q = round(S / M) from the window S >> wsh (< 2^32)
+  const int wsh = k.wsh;
+  const uint64_t win = wsh >= 64 ? (hi >> (wsh - 64)) : (wsh == 0 ? lo : ((lo >> wsh) | (hi << (64 - wsh))));
+  const float qf = __uint2float_rn(static_cast<uint32_t>(win)) * k.qscale;
+  const uint32_t q = __float_as_uint(qf + 8388608.0f) - 0x4B000000u;   // round to nearest
+  // q M in 32-bit words, then Y = S - q M (two's complement, 128 bits)
+  const uint64_t p0 = static_cast<uint64_t>(q) * k.m0;
+  const uint64_t p1 = static_cast<uint64_t>(q) * k.m1 + (p0 >> 32);
+  const uint64_t p2 = static_cast<uint64_t>(q) * k.m2 + (p1 >> 32);
+  const uint64_t p3 = static_cast<uint64_t>(q) * k.m3 + (p2 >> 32);
+  const uint64_t qml = (p1 << 32) | (p0 & 0xFFFFFFFFull), qmh = (p3 << 32) | (p2 & 0xFFFFFFFFull);
+  uint64_t yl = lo - qml;
+  uint64_t yh = hi - qmh - (lo < qml ? 1ull : 0ull);
+  // Y >= M/2: Y - M; Y < -M/2: Y + M
+  const uint64_t th = yh - k.Hh - (yl < k.Hl ? 1ull : 0ull);
+  if (static_cast<int64_t>(th) >= 0) {
+    const uint64_t nl = yl - k.Ml;
+    yh = yh - k.Mh - (yl < k.Ml ? 1ull : 0ull);
+    yl = nl;
+  } else {
+    const uint64_t ul = yl + k.Hl;
+    const uint64_t uh = yh + k.Hh + (ul < yl ? 1ull : 0ull);
+    if (static_cast<int64_t>(uh) < 0) {
+      const uint64_t nl = yl + k.Ml;
+      yh = yh + k.Mh + (nl < yl ? 1ull : 0ull);
+      yl = nl;
+    }
+  }
+  // |Y| < 2^127: one rounding to double
+  const bool neg = static_cast<int64_t>(yh) < 0;
+  if (neg) {
+    yl = ~yl + 1ull;
+    yh = ~yh + (yl == 0ull ? 1ull : 0ull);
+  }
+  return rn_double_bits(yh, yl, e, neg);
+}
+
+// Rebuild of 4 outputs of a modular-form product inside the slice GEMM's
+// epilogue: row `row`, columns c4 .. c4 + 3 (c4 a multiple of 4), from the
+// residue bytes of its N products (crt_output each; W4: whether M_N needs a
+// fourth 32-bit word). Kept out of line: it runs at modulus ends, between
+// chunk drains, and gets the whole register budget.
 template <bool W4>
 static __device__ __noinline__ void crt_rebuild4(const SliceProblem& P, int64_t row, int64_t c4, int N, int bits) {
+  constexpr int NW = W4 ? 4 : 3;
   const int64_t n = P.n;
   const int32_t Ei = P.E[row];
   double* const crow = P.C + row * P.ldc;
   const uint8_t* const rb = P.res + row * 8 + (c4 >> 3) * P.ldr + (c4 & 4);
-  const uint32_t m0 = c_crt.M[N][0], m1 = c_crt.M[N][1], m2 = c_crt.M[N][2], m3 = c_crt.M[N][3];
-  const uint64_t Ml = (static_cast<uint64_t>(m1) << 32) | m0, Mh = (static_cast<uint64_t>(m3) << 32) | m2;
-  const uint64_t Hl = c_crt.H[N][0], Hh = c_crt.H[N][1];
-  const int wsh = c_crt.wsh[N];
-  const float qscale = c_crt.qscale[N];
+  const CrtK k = crt_k<NW>(N);
   const int ebase = Ei - 2 * bits;
   // every modulus's bytes of the 4 columns, all loads in flight together
   uint32_t wc[CRT_N_MAX];
@@ -393,48 +500,10 @@ static __device__ __noinline__ void crt_rebuild4(const SliceProblem& P, int64_t 
   uint64_t ob[4];
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    // carries: S = hi:lo (S < 14 * 2^8 * M < 2^123)
-    const uint64_t t1 = T[j][1] + (T[j][0] >> 32);
-    const uint64_t t2 = T[j][2] + (t1 >> 32);
-    const uint64_t t3 = T[j][3] + (t2 >> 32);
-    const uint64_t lo = (t1 << 32) | (T[j][0] & 0xFFFFFFFFull);
-    const uint64_t hi = (t3 << 32) | (t2 & 0xFFFFFFFFull);
-    // q = round(S / M) from the window S >> wsh (< 2^32)
-    const uint64_t win = wsh >= 64 ? (hi >> (wsh - 64)) : (wsh == 0 ? lo : ((lo >> wsh) | (hi << (64 - wsh))));
-    const float qf = __uint2float_rn(static_cast<uint32_t>(win)) * qscale;
-    const uint32_t q = __float_as_uint(qf + 8388608.0f) - 0x4B000000u;   // round to nearest
-    // q M in 32-bit words, then Y = S - q M (two's complement, 128 bits)
-    const uint64_t p0 = static_cast<uint64_t>(q) * m0;
-    const uint64_t p1 = static_cast<uint64_t>(q) * m1 + (p0 >> 32);
-    const uint64_t p2 = static_cast<uint64_t>(q) * m2 + (p1 >> 32);
-    const uint64_t p3 = static_cast<uint64_t>(q) * m3 + (p2 >> 32);
-    const uint64_t qml = (p1 << 32) | (p0 & 0xFFFFFFFFull), qmh = (p3 << 32) | (p2 & 0xFFFFFFFFull);
-    uint64_t yl = lo - qml;
-    uint64_t yh = hi - qmh - (lo < qml ? 1ull : 0ull);
-    // Y >= M/2: Y - M; Y < -M/2: Y + M
-    const uint64_t th = yh - Hh - (yl < Hl ? 1ull : 0ull);
-    if (static_cast<int64_t>(th) >= 0) {
-      const uint64_t nl = yl - Ml;
-      yh = yh - Mh - (yl < Ml ? 1ull : 0ull);
-      yl = nl;
-    } else {
-      const uint64_t ul = yl + Hl;
-      const uint64_t uh = yh + Hh + (ul < yl ? 1ull : 0ull);
-      if (static_cast<int64_t>(uh) < 0) {
-        const uint64_t nl = yl + Ml;
-        yh = yh + Mh + (nl < yl ? 1ull : 0ull);
-        yl = nl;
-      }
-    }
-    // |Y| < 2^127: one rounding to double, scaled by 2^(E_i + F_j - 2b)
-    const bool neg = static_cast<int64_t>(yh) < 0;
-    if (neg) {
-      yl = ~yl + 1ull;
-      yh = ~yh + (yl == 0ull ? 1ull : 0ull);
-    }
     const int32_t Fj = j == 0 ? f4.x : j == 1 ? f4.y : j == 2 ? f4.z : f4.w;
-    ob[j] = (Ei == EXP_NONFINITE || Fj == EXP_NONFINITE) ? 0x7FF8000000000000ull
-                                                         : rn_double_bits(yh, yl, ebase + Fj, neg);
+    ob[j] = (Ei == EXP_NONFINITE || Fj == EXP_NONFINITE)
+                ? 0x7FF8000000000000ull
+                : crt_output<NW>(T[j][0], T[j][1], T[j][2], T[j][3], k, ebase + Fj);
   }
   if (c4 + 3 < n && ((reinterpret_cast<uintptr_t>(crow + c4) & 15u) == 0)) {
     double2* const op = reinterpret_cast<double2*>(crow + c4);
@@ -485,6 +554,16 @@ __global__ void __launch_bounds__(Cfg<BN, MODE, CG>::NUM_THREADS, 1)
   const int walker = (CG >= 2) ? static_cast<int>(cluster_id_x()) : static_cast<int>(blockIdx.x);
   const int walkers = (CG >= 2) ? static_cast<int>(cluster_count_x()) : static_cast<int>(gridDim.x);
   const bool leader = (rank == 0);
+  // a single modular-form product whose rebuild is deferred: the last round
+  // of tiles split by moduli (N from the decision record)
+  Units U = whole_tiles(ntiles);
+  if constexpr (MODE == SLICE_CRT) {
+    if (args.probs == nullptr && args.crt_defer) {
+      TileJob j0;
+      resolve_slices(args, args.single, j0);
+      U = split_tail(ntiles, walkers, j0.s);
+    }
+  }
 
   WaitCtl wc;
   wc.abort = &abort_flag;
@@ -532,9 +611,11 @@ __global__ void __launch_bounds__(Cfg<BN, MODE, CG>::NUM_THREADS, 1)
     if (lane == 0) {
       int it = 0;
       bool ok = true;
-      for (int t = walker; t < ntiles && ok; t += walkers) {
-        const TileJob job = get_job(args, &tmA, &tmB, t, COL_PAIRS, pair_col);
+      for (int u = walker; u < U.units && ok; u += walkers) {
+        const TileJob job = get_job(args, &tmA, &tmB, unit_tile(U, u), COL_PAIRS, pair_col);
         if (job.skip) continue;
+        int l0, l1;
+        unit_moduli(U, u, job.s, l0, l1);
         const int ya = job.tm * C_::TILE_M + static_cast<int>(rank) * BM;
         const int yb = job.tn * BN + static_cast<int>(rank) * (BN / C_::PAIR);
         for_each_step<MODE, C_::PPS>(job.s, job.P->nkb, [&](const Step& st, int) {
@@ -580,7 +661,7 @@ __global__ void __launch_bounds__(Cfg<BN, MODE, CG>::NUM_THREADS, 1)
             }
           }
           ++it;
-        });
+        }, l0, l1);
       }
       if (!ok) {
         // copies already issued must land before the CTA exits
@@ -598,9 +679,11 @@ __global__ void __launch_bounds__(Cfg<BN, MODE, CG>::NUM_THREADS, 1)
       int chunk_base = 0;
       bool ok = true;
       bool issued_any = false;
-      for (int t = walker; t < ntiles && ok; t += walkers) {
-        const TileJob job = get_job(args, &tmA, &tmB, t, COL_PAIRS, pair_col);
+      for (int u = walker; u < U.units && ok; u += walkers) {
+        const TileJob job = get_job(args, &tmA, &tmB, unit_tile(U, u), COL_PAIRS, pair_col);
         if (job.skip) continue;
+        int l0, l1;
+        unit_moduli(U, u, job.s, l0, l1);
         const int s = job.s, nkb = job.P->nkb;
         for_each_step<MODE, C_::PPS>(s, nkb, [&](const Step& st, int cofs) {
           if (!ok) return;
@@ -650,8 +733,8 @@ __global__ void __launch_bounds__(Cfg<BN, MODE, CG>::NUM_THREADS, 1)
             if (st.last) umma_commit(&accf_bar[slot]);
           }
           ++it;
-        });
-        chunk_base += chunks_per_tile<MODE>(s, nkb);
+        }, l0, l1);
+        chunk_base += chunks_per_tile<MODE>(MODE == SLICE_CRT ? l1 - l0 : s, nkb);
       }
       if (!ok && issued_any) {
         if constexpr (CG >= 2)
@@ -693,9 +776,12 @@ __global__ void __launch_bounds__(Cfg<BN, MODE, CG>::NUM_THREADS, 1)
       if (++pend_g == G4) pend_t = -1;
     };
     (void)crt_step;
-    for (int t = walker; t < ntiles && ok; t += walkers) {
+    for (int u = walker; u < U.units && ok; u += walkers) {
+      const int t = unit_tile(U, u);
       const TileJob job = get_job(args, &tmA, &tmB, t, COL_PAIRS, pair_col);
       if (job.skip) continue;
+      int l0, l1;
+      unit_moduli(U, u, job.s, l0, l1);
       const SliceProblem& P = *job.P;
       const int64_t row = static_cast<int64_t>(job.tm) * C_::TILE_M + static_cast<int64_t>(rank) * BM + row_in_tile;
       const int64_t col0 = static_cast<int64_t>(job.tn) * BN + col_off;
@@ -741,9 +827,11 @@ __global__ void __launch_bounds__(Cfg<BN, MODE, CG>::NUM_THREADS, 1)
         // Modular form. For each modulus the thread keeps int32 sums of its
         // columns over the K chunks (reduced modulo m at every int32 segment
         // end: a segment adds at most SEG_CHUNKS 2^24 < 2^31) and stores their
-        // remainders in [0, m) as bytes; the tile's outputs are rebuilt from
-        // them (crt_rebuild4) 4 columns at a time at the next tile's modulus
-        // ends, so the rebuild overlaps the tensor cores' work.
+        // remainders in [0, m) as bytes. Grouped launches rebuild the tile's
+        // outputs from them (crt_rebuild4) 4 columns at a time at the next
+        // tile's modulus ends, so the rebuild overlaps the tensor cores' work;
+        // single products (crt_defer) leave it to a pass of its own, which
+        // keeps the epilogue warps off the issue slots the MMA thread needs.
         const int N = job.s;
         const int nkb = P.nkb;
         const int nch = (nkb + 15) / 16;
@@ -776,7 +864,7 @@ __global__ void __launch_bounds__(Cfg<BN, MODE, CG>::NUM_THREADS, 1)
             return r < 0 ? r + static_cast<int32_t>(mdl) : r;
           }
         };
-        for (int l = 0; l < N && ok; ++l) {
+        for (int l = l0; l < l1 && ok; ++l) {
           for (int c = 0; c < nch; ++c, ++chunk) {
             const int slot = chunk & 1;
             if (!mbar_wait(&accf_bar[slot], static_cast<uint32_t>(chunk >> 1) & 1u, wc)) { ok = false; break; }
@@ -828,7 +916,7 @@ __global__ void __launch_bounds__(Cfg<BN, MODE, CG>::NUM_THREADS, 1)
         if (ok) {
           // the previous tile's rebuild, what is left of it, then this tile's
           while (pend_t >= 0) crt_step();
-          pend_t = t;
+          pend_t = args.crt_defer ? -1 : t;
           pend_g = 0;
         }
       } else if constexpr (C_::REG_SUMS) {

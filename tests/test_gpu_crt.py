@@ -310,3 +310,89 @@ def test_default_scheme_by_size(mm):
             rows = [0, 999]
             assert bound_ok(C.cpu().numpy()[rows], oracle.gemm_rows(A, B, rows), oracle.absprod_rows(A, B, rows),
                             em.gamma(A.shape[1], "fp64_emu"))
+
+
+# ------------------------------------------------------------- rebuild pass
+def _rebuild_case(N, m, n, seed):
+    """Integers Y (object array) chosen across [-M/2, M/2): uniform, small,
+    0 and +-1, next to +-M/2, exact halves between doubles (ties) and one
+    unit off them; their residues as bytes (some as an unreduced
+    representative c + m_l < 256); exponents E, F spanning normal,
+    subnormal and overflowing results."""
+    import random
+    rng = random.Random(seed)
+    M = em.crt_modulus_product(N)
+    lo, hi = -(M // 2), M - M // 2          # Y in [lo, hi)
+    lb = (M // 2).bit_length()              # 2^(lb-1) <= M/2
+    Y = np.empty((m, n), dtype=object)
+    for i in range(m):
+        for j in range(n):
+            kind = rng.randrange(8)
+            if kind == 0:
+                y = rng.randrange(lo, hi)
+            elif kind == 1:
+                y = rng.randrange(max(lo, -2 ** 20), min(hi, 2 ** 20))
+            elif kind == 2:
+                y = rng.choice((0, 1, -1))
+            elif kind == 3:
+                y = rng.choice((hi - 1 - rng.randrange(4), lo + rng.randrange(4)))
+            elif kind == 4 and lb > 56:
+                # (2^52 + r) 2^(t+1) + 2^t: exactly half way between doubles, +-1
+                t = rng.randrange(0, lb - 55)
+                y = ((2 ** 52 + rng.randrange(2 ** 52)) << (t + 1)) + (1 << t) + rng.choice((0, 0, 1, -1))
+                y = y if rng.random() < 0.5 else -y
+            else:
+                y = rng.randrange(-(1 << rng.randrange(0, lb)), 1 << rng.randrange(0, lb))
+            Y[i, j] = y
+    res = np.zeros((N, m, n), dtype=np.uint8)
+    for l in range(N):
+        ml = em.CRT_MODULI[l]
+        for i in range(m):
+            for j in range(n):
+                c = Y[i, j] % ml
+                if c + ml < 256 and rng.random() < 0.1:
+                    c += ml
+                res[l, i, j] = c
+    bits = rng.randrange(24, 54)
+    E = np.array([rng.randrange(-520, 480) for _ in range(m)], dtype=np.int32)
+    F = np.array([rng.randrange(-520, 480) for _ in range(n)], dtype=np.int32)
+    E[1] = -1022 - lb + 2 * bits            # rows of subnormal, underflowing and normal results
+    E[3] = 1024 - lb + 2 * bits             # rows of overflowing and normal results
+    E[9] = -1022 - lb + 2 * bits + 40
+    return Y, res, E, F, bits
+
+
+NONFINITE = -1000000
+
+
+@pytest.mark.parametrize("N", list(range(1, 15)))
+def test_rebuild_pass_every_modulus_count(h, mm, N):
+    m, n = 70, 150           # three row blocks of 32 and three column blocks of 64, both ragged
+    Y, res, E, F, bits = _rebuild_case(N, m, n, 1000 + N)
+    # the oracle's textbook CRT sum gives the chosen integers back
+    Yo = em.crt_reconstruct(res)
+    assert all(Yo[i, j] == Y[i, j] for i in range(m) for j in range(n))
+    En, Fn = E.copy(), F.copy()
+    En[5], Fn[6] = NONFINITE, NONFINITE
+    got = h.debug_crt_rebuild(torch.from_numpy(res).cuda(), torch.from_numpy(En), torch.from_numpy(Fn), N,
+                              bits).cpu().numpy()
+    from fractions import Fraction
+    big = Fraction(2 ** 1024 - 2 ** 970)   # round-to-nearest overflows at and above this
+    fin = np.ones((m, n), dtype=bool)
+    fin[5, :] = False
+    fin[:, 6] = False
+    want = np.zeros((m, n))
+    for i in range(m):
+        for j in range(n):
+            if not fin[i, j]:
+                continue
+            v = Fraction(int(Yo[i, j])) * Fraction(2) ** (int(E[i]) + int(F[j]) - 2 * bits)
+            want[i, j] = (np.inf if v > 0 else -np.inf) if abs(v) >= big else \
+                em.crt_round(Yo[i:i + 1, j:j + 1], E[i:i + 1], F[j:j + 1], bits)[0, 0]
+    assert np.all(np.isnan(got[~fin]))
+    gb, wb = got[fin].view(np.uint64), want[fin].view(np.uint64)
+    bad = np.flatnonzero(gb != wb)
+    assert bad.size == 0, (bad.size, got[fin][bad[:4]], want[fin][bad[:4]])
+    # the cases reach every branch: subnormal and overflowing results, ties
+    w = want[fin]
+    assert np.any((w != 0) & (np.abs(w) < 2.0 ** -1022)) and np.any(np.isinf(w))
