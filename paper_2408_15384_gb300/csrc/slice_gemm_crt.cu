@@ -82,97 +82,129 @@ __host__ __device__ constexpr int bit_length(u128 x) {
   return b;
 }
 
-// Compile-time constants of N <= 12 moduli (M_N < 2^95): M_N and M_N / 2 as
-// 32-bit words, and the quotient window: S < 2^12 M_N, so S >> SH (SH = bit
-// length of M_N minus 11) is below 2^23 and QS = 2^SH / M_N scales it to S / M_N
-// within 2^-10.
+// Compile-time constants of N <= 12 moduli (M_N < 2^95) as 32-bit words:
+// M_N, H = M_N / 2, NM = 2^96 - M_N (so S - q M = S + q NM modulo 2^96), H2
+// = the top word of H, and the quotient window: S < 2^12 M_N, so S >> SH (SH
+// = bit length of M_N minus 11) is below 2^23 and QS = 2^SH / M_N scales it to
+// S / M_N within 2^-10.
 template <int N>
 struct Crt96 {
   static constexpr u128 M = modulus_product(N);
+  static constexpr u128 H = M >> 1;
+  static constexpr u128 NM = ((u128(1) << 96) - M) & ((u128(1) << 96) - 1);
   static constexpr int BITS = bit_length(M);
   static constexpr uint32_t m0 = static_cast<uint32_t>(M), m1 = static_cast<uint32_t>(M >> 32),
                             m2 = static_cast<uint32_t>(M >> 64);
-  static constexpr uint64_t Mlo = static_cast<uint64_t>(M), Hlo = static_cast<uint64_t>(M >> 1);
-  static constexpr uint32_t Mhi = static_cast<uint32_t>(M >> 64), Hhi = static_cast<uint32_t>(M >> 65);
+  static constexpr uint32_t h0 = static_cast<uint32_t>(H), h1 = static_cast<uint32_t>(H >> 32),
+                            h2 = static_cast<uint32_t>(H >> 64);
+  static constexpr uint32_t n0 = static_cast<uint32_t>(NM), n1 = static_cast<uint32_t>(NM >> 32),
+                            n2 = static_cast<uint32_t>(NM >> 64);
   static constexpr int SH = BITS > 11 ? BITS - 11 : 0;
   static constexpr float QS = static_cast<float>(static_cast<double>(u128(1) << SH) / static_cast<double>(M));
 };
 
+// 96-bit two's-complement words (least significant first) with the carry flag.
+__device__ __forceinline__ void add96(uint32_t& a0, uint32_t& a1, uint32_t& a2, uint32_t b0, uint32_t b1,
+                                      uint32_t b2) {
+  asm("add.cc.u32 %0, %0, %3;\n\taddc.cc.u32 %1, %1, %4;\n\taddc.u32 %2, %2, %5;"
+      : "+r"(a0), "+r"(a1), "+r"(a2)
+      : "r"(b0), "r"(b1), "r"(b2));
+}
+__device__ __forceinline__ void sub96(uint32_t& a0, uint32_t& a1, uint32_t& a2, uint32_t b0, uint32_t b1,
+                                      uint32_t b2) {
+  asm("sub.cc.u32 %0, %0, %3;\n\tsubc.cc.u32 %1, %1, %4;\n\tsubc.u32 %2, %2, %5;"
+      : "+r"(a0), "+r"(a1), "+r"(a2)
+      : "r"(b0), "r"(b1), "r"(b2));
+}
+
 // One output of a product with N <= 12 moduli from the column sums T0..T2 of
 // S = sum_l c_l W_l (the same value as crt_output, specialised): Y = S - q M
-// is kept modulo 2^96 (|Y| < M_N < 2^95 before the one correction step), and a
+// is kept modulo 2^96 (|Y| <= 0.501 M_N < 2^94 before the correction), and a
 // result in the normal range is rounded from the 96-bit magnitude directly;
 // the rest (subnormal or overflowing results) take rn_double_bits.
 template <int N>
 __device__ __forceinline__ uint64_t crt_output96(uint64_t T0, uint64_t T1, uint64_t T2, int e) {
   using K = Crt96<N>;
-  // S = hi 2^64 + a
-  const uint64_t t1s = T1 << 32;
-  const uint64_t a = T0 + t1s;
-  const uint64_t hi = T2 + (T1 >> 32) + (a < t1s ? 1ull : 0ull);
-  // q = round(S / M) from the top 23 bits of S
+  // S = T0 + T1 2^32 + T2 2^64 as words s0..s3 (s3 < 2^12)
+  const uint32_t s0 = static_cast<uint32_t>(T0);
+  uint32_t s1, s2, s3;
+  asm("add.cc.u32 %0, %3, %4;\n\taddc.cc.u32 %1, %5, %6;\n\taddc.u32 %2, %7, 0;"
+      : "=r"(s1), "=r"(s2), "=r"(s3)
+      : "r"(static_cast<uint32_t>(T0 >> 32)), "r"(static_cast<uint32_t>(T1)), "r"(static_cast<uint32_t>(T1 >> 32)),
+        "r"(static_cast<uint32_t>(T2)), "r"(static_cast<uint32_t>(T2 >> 32)));
+  // q = round(S / M) from the 23 bits of S from bit SH up
   uint32_t win;
-  if constexpr (K::SH >= 64)
-    win = static_cast<uint32_t>(hi >> (K::SH - 64));
-  else if constexpr (K::SH > 0)
-    win = static_cast<uint32_t>((a >> K::SH) | (hi << (64 - K::SH)));
-  else
-    win = static_cast<uint32_t>(a);
+  {
+    constexpr int w = K::SH / 32, r = K::SH % 32;
+    const uint32_t wd[5] = {s0, s1, s2, s3, 0u};
+    win = r == 0 ? wd[w] : __funnelshift_r(wd[w], wd[w + 1], r);
+  }
   const float wf = __uint_as_float(0x4B000000u | win) - 8388608.0f;   // exact: win < 2^23
   const uint32_t q = __float_as_uint(fmaf(wf, K::QS, 8388608.0f)) - 0x4B000000u;
-  // Y = S - q M modulo 2^96: (yh, yl), yh the top 32 bits as signed
-  const uint64_t p0 = static_cast<uint64_t>(q) * K::m0;
-  const uint64_t p1 = static_cast<uint64_t>(q) * K::m1 + (p0 >> 32);
-  const uint32_t p2 = q * K::m2 + static_cast<uint32_t>(p1 >> 32);
-  const uint64_t qml = (p1 << 32) | (p0 & 0xFFFFFFFFull);
-  uint64_t yl = a - qml;
-  int32_t yh = static_cast<int32_t>(static_cast<uint32_t>(hi) - p2 - (a < qml ? 1u : 0u));
-  // Y >= M/2: Y - M; Y < -M/2: Y + M (u = Y + M/2 outside [0, M))
-  {
-    const uint64_t ul = yl + K::Hlo;
-    const int32_t uh = yh + static_cast<int32_t>(K::Hhi) + (ul < yl ? 1 : 0);
-    if (uh < 0) {
-      const uint64_t nl = yl + K::Mlo;
-      yh = yh + static_cast<int32_t>(K::Mhi) + (nl < yl ? 1 : 0);
-      yl = nl;
-    } else if (static_cast<uint32_t>(uh) > K::Mhi || (static_cast<uint32_t>(uh) == K::Mhi && ul >= K::Mlo)) {
-      const uint64_t nl = yl - K::Mlo;
-      yh = yh - static_cast<int32_t>(K::Mhi) - (yl < K::Mlo ? 1 : 0);
-      yl = nl;
+  // Y = S + q (2^96 - M) modulo 2^96
+  uint32_t y0, y1, y2;
+  asm("mad.lo.cc.u32 %0, %3, %4, %7;\n\t"
+      "madc.hi.cc.u32 %1, %3, %4, %8;\n\t"
+      "madc.hi.u32 %2, %3, %5, %9;\n\t"
+      "mad.lo.cc.u32 %1, %3, %5, %1;\n\t"
+      "madc.lo.u32 %2, %3, %6, %2;"
+      : "=r"(y0), "=r"(y1), "=r"(y2)
+      : "r"(q), "r"(K::n0), "r"(K::n1), "r"(K::n2), "r"(s0), "r"(s1), "r"(s2));
+  // Y in [-M/2, M/2) for sure when its top word lies in [-h2, h2); else the
+  // exact correction (Y + H outside [0, M): Y + M or Y - M)
+  if (!(K::h2 > 0u && static_cast<uint32_t>(y2 + K::h2) < 2u * K::h2)) {
+    uint32_t u0 = y0, u1 = y1, u2 = y2;
+    add96(u0, u1, u2, K::h0, K::h1, K::h2);
+    if (static_cast<int32_t>(u2) < 0) {
+      add96(y0, y1, y2, K::m0, K::m1, K::m2);
+    } else {
+      sub96(u0, u1, u2, K::m0, K::m1, K::m2);
+      if (static_cast<int32_t>(u2) >= 0) sub96(y0, y1, y2, K::m0, K::m1, K::m2);
     }
   }
-  const bool neg = yh < 0;
-  uint32_t u2 = static_cast<uint32_t>(yh);
-  if (neg) {
-    yl = ~yl + 1ull;
-    u2 = ~u2 + (yl == 0ull ? 1u : 0u);
-  }
-  // |Y| = u2 2^64 + yl < 2^95: its leading 64 bits t (bit 63 set), the
-  // exponent L of its leading bit, and whether any bit below t is set
-  uint64_t t;
+  // |Y| and its sign
+  const uint32_t sg = static_cast<uint32_t>(static_cast<int32_t>(y2) >> 31);
+  y0 ^= sg;
+  y1 ^= sg;
+  y2 ^= sg;
+  add96(y0, y1, y2, sg & 1u, 0u, 0u);
+  const bool neg = sg != 0u;
+  // the leading 64 bits th:tl of |Y| (bit 63 set), the exponent L of its
+  // leading bit, and the bits below them (rest)
+  uint32_t th, tl, rest;
   int L;
-  bool below;
-  if (u2 != 0u) {
-    const int sft = __clz(static_cast<int>(u2));   // 1 .. 31
-    t = (static_cast<uint64_t>(u2) << (32 + sft)) | (yl >> (32 - sft));
-    below = (static_cast<uint32_t>(yl) << sft) != 0u;
+  if (y2 != 0u) {
+    const int sft = __clz(static_cast<int>(y2));
+    th = __funnelshift_l(y1, y2, sft);
+    tl = __funnelshift_l(y0, y1, sft);
+    rest = y0 << sft;
     L = 95 - sft;
-  } else {
-    if (yl == 0ull) return 0ull;
-    const int sft = __clzll(static_cast<long long>(yl));
-    t = yl << sft;
-    below = false;
+  } else if (y1 != 0u) {
+    const int sft = __clz(static_cast<int>(y1));
+    th = __funnelshift_l(y0, y1, sft);
+    tl = y0 << sft;
+    rest = 0u;
     L = 63 - sft;
+  } else {
+    if (y0 == 0u) return 0ull;
+    const int sft = __clz(static_cast<int>(y0));
+    th = y0 << sft;
+    tl = 0u;
+    rest = 0u;
+    L = 31 - sft;
   }
   const int E = L + e;
-  if (E < -1021 || E > 1022)   // subnormal, overflowing, or rounding up to the edge: the general path
-    return rn_double_bits(static_cast<uint64_t>(u2), yl, e, neg);
-  uint64_t mant = t >> 11;                                       // 53 bits, leading bit set
-  const bool rbit = (t >> 10) & 1ull;
-  const bool sticky = below || (t & 0x3FFull) != 0ull;
-  mant += (rbit && (sticky || (mant & 1ull))) ? 1ull : 0ull;
-  const int Ef = E + static_cast<int>(mant >> 53);               // a carry out of the 53 bits
-  return (neg ? (1ull << 63) : 0ull) | (static_cast<uint64_t>(Ef + 1023) << 52) | (mant & 0xFFFFFFFFFFFFFull);
+  if (E < -1022 || E > 1022)   // subnormal, underflowing or overflowing: the general path
+    return rn_double_bits(y2, (static_cast<uint64_t>(y1) << 32) | y0, e, neg);
+  // 53 bits mh:ml (leading bit at bit 20 of mh), rounded to nearest even
+  uint32_t mh = th >> 11, ml = __funnelshift_r(tl, th, 11);
+  const uint32_t rbit = (tl >> 10) & 1u;
+  const uint32_t sticky = ((tl & 0x3FFu) | rest) != 0u ? 1u : 0u;
+  const uint32_t inc = rbit & (sticky | (ml & 1u));
+  asm("add.cc.u32 %0, %0, %2;\n\taddc.u32 %1, %1, 0;" : "+r"(ml), "+r"(mh) : "r"(inc));
+  // the leading bit (and a carry out of the 53 bits) adds to the exponent field
+  const uint32_t hw = (static_cast<uint32_t>(E + 1022) << 20) + mh + (neg ? 0x80000000u : 0u);
+  return (static_cast<uint64_t>(hw) << 32) | ml;
 }
 
 template <int N>
@@ -188,18 +220,27 @@ __device__ __forceinline__ void rebuild_tile(const SliceProblem& P, int bits, in
     for (int l = 0; l < N; ++l) rec[l] = *reinterpret_cast<const uint2*>(rb + static_cast<int64_t>(l) * P.rplane);
     const int32_t Ei = P.E[row];
     const int ebase = Ei - 2 * bits;
+    int32_t Fv[8];
+    if (cb + 7 < P.n && (reinterpret_cast<uintptr_t>(P.F + cb) & 15u) == 0) {
+      const int4 f0 = __ldg(reinterpret_cast<const int4*>(P.F + cb)), f1 = __ldg(reinterpret_cast<const int4*>(P.F + cb) + 1);
+      Fv[0] = f0.x; Fv[1] = f0.y; Fv[2] = f0.z; Fv[3] = f0.w;
+      Fv[4] = f1.x; Fv[5] = f1.y; Fv[6] = f1.z; Fv[7] = f1.w;
+    } else {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) Fv[j] = cb + j < P.n ? __ldg(P.F + cb + j) : 0;
+    }
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       uint64_t T0 = 0ull, T1 = 0ull, T2 = 0ull, T3 = 0ull;
 #pragma unroll
       for (int l = 0; l < N; ++l) {
-        const uint32_t cl = ((j < 4 ? rec[l].x : rec[l].y) >> (8 * (j & 3))) & 255u;
+        const uint32_t cl = __byte_perm(j < 4 ? rec[l].x : rec[l].y, 0u, 0x4440u | static_cast<uint32_t>(j & 3));
         T0 += static_cast<uint64_t>(cl) * c_crt.W[N][l][0];
         if (NW > 1) T1 += static_cast<uint64_t>(cl) * c_crt.W[N][l][1];
         if (NW > 2) T2 += static_cast<uint64_t>(cl) * c_crt.W[N][l][2];
         if (NW > 3) T3 += static_cast<uint64_t>(cl) * c_crt.W[N][l][3];
       }
-      const int32_t Fj = cb + j < P.n ? __ldg(P.F + cb + j) : 0;
+      const int32_t Fj = Fv[j];
       uint64_t o;
       if (Ei == EXP_NONFINITE || Fj == EXP_NONFINITE)
         o = 0x7FF8000000000000ull;
