@@ -481,12 +481,22 @@ int mm_serve_bench(mm_handle h, const mm_serve_load *load, mm_serve_load_result 
  * Errors: MM_ERR_INVALID_ARG (as mm_gemm, or another precision),
  * MM_ERR_BUDGET (the problem's split operands need more than the fixed
  * scratch: about 14*(m+n)*k bytes for FP64-accuracy, 6*(m+n)*k for
- * FP32-accuracy), MM_ERR_CUDA. The device-side status is not reported to the
- * caller: Inf/NaN inputs give NaN in the affected rows/columns of C, and a
- * device wait that runs out (after 2 s) leaves C incomplete, both silently. */
+ * FP32-accuracy), MM_ERR_CUDA. The call does not wait for its kernels, so
+ * their device-side status (Inf/NaN inputs, which give NaN in the affected
+ * rows/columns of C; a device wait that ran out after 2 s, which leaves C
+ * incomplete) is read afterwards with mm_gemm_emu_static_status. */
 int mm_gemm_emu_static(int64_t m, int64_t n, int64_t k,
                        const double *A, int64_t lda, const double *B, int64_t ldb,
                        double *C, int64_t ldc, int precision, void *stream);
+
+/* The device-side status of the last mm_gemm_emu_static call on the calling
+ * thread's current device (each call clears the scratch's status word when it
+ * starts, in stream order): synchronises `stream` (the stream that call ran
+ * on), reads the word and clears it. MM_OK; MM_ERR_NONFINITE (A or B held Inf
+ * or NaN); MM_ERR_TIMEOUT (a device wait ran out, C is incomplete);
+ * MM_ERR_CUDA. Calls on other streams that overlap race on the same word,
+ * as they do on the scratch. */
+int mm_gemm_emu_static_status(void *stream);
 
 #ifdef __cplusplus
 }

@@ -75,6 +75,7 @@ SIGNATURES = {
     "mm_debug_slice_count": (c_int, [c_vp, c_i64, c_i64, c_i64, c_vp, c_i64, c_vp, c_i64, ctypes.POINTER(c_int),
                                      ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float), c_vp]),
     "mm_debug_crt_residues": (c_int, [c_vp, c_int, c_int, c_int, c_i64, c_i64, c_vp, c_i64, c_vp, c_vp, c_vp]),
+    "mm_gemm_emu_static_status": (c_int, [c_vp]),
     "mm_debug_crt_rebuild": (c_int, [c_vp, c_i64, c_i64, c_int, c_int, c_vp, c_vp, c_vp, c_vp, c_i64, c_vp]),
     "mm_debug_fp64_product": (c_int, [c_vp, c_i64, c_i64, c_i64, c_vp, c_i64, c_vp, c_i64, c_vp, c_i64, c_vp,
                                       ctypes.POINTER(c_int), ctypes.POINTER(c_int), ctypes.POINTER(ctypes.c_float),

@@ -89,9 +89,13 @@ int mm_gemm_emu_static(int64_t m, int64_t n, int64_t k, const double* A, int64_t
   std::call_once(d.once, setup_device, std::ref(d));
   if (d.status != MM_OK) return d.status;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  uint32_t* err = reinterpret_cast<uint32_t*>(d.scratch);
 
-  if (k == 0) return cuda_status(launch_zero_c(C, m, n, ldc, st), "zero C");
-  if (precision == MM_FP64_EMU && k <= 4) {
+  if (k == 0 || (precision == MM_FP64_EMU && k <= 4)) {
+    // the status word covers this call too (nothing below sets it)
+    cudaError_t e = cudaMemsetAsync(err, 0, sizeof(uint32_t), st);
+    if (e != cudaSuccess) return cuda_status(e, "status word");
+    if (k == 0) return cuda_status(launch_zero_c(C, m, n, ldc, st), "zero C");
     // same rule as mm_gemm: short sums go to the FP64 kernel (no scratch)
     Fp64GemmArgs a{m, n, k, A, lda, B, ldb, C, ldc};
     return cuda_status(launch_fp64_gemm(2, a, st), "fp64 gemm");
@@ -104,7 +108,6 @@ int mm_gemm_emu_static(int64_t m, int64_t n, int64_t k, const double* A, int64_t
   const size_t status_bytes = 256;
   if (status_bytes + L.bytes > NOALLOC_SCRATCH_BYTES) return MM_ERR_BUDGET;   // larger than the fixed scratch
 
-  uint32_t* err = reinterpret_cast<uint32_t*>(d.scratch);
   char* ws = reinterpret_cast<char*>(d.scratch + status_bytes);
   SliceDecision* dec = L.dec(ws);
   cudaError_t e = cudaMemsetAsync(err, 0, sizeof(uint32_t), st);
@@ -154,4 +157,22 @@ int mm_gemm_emu_static(int64_t m, int64_t n, int64_t k, const double* A, int64_t
     e = launch_fp64_gemm(2, f, st);
   }
   return cuda_status(e, "slice gemm");
+}
+
+int mm_gemm_emu_static_status(void* stream) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return MM_ERR_CUDA;
+  NoAllocDevice& d = g_dev[dev];
+  std::call_once(d.once, setup_device, std::ref(d));
+  if (d.status != MM_OK) return d.status;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  uint32_t* err = reinterpret_cast<uint32_t*>(d.scratch);
+  uint32_t v = 0;
+  cudaError_t e = cudaMemcpyAsync(&v, err, sizeof(v), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess && v != 0u) e = cudaMemsetAsync(err, 0, sizeof(uint32_t), st);
+  if (e != cudaSuccess) return cuda_status(e, "static status word");
+  if (v & MM_DEV_ERR_TIMEOUT_H) return MM_ERR_TIMEOUT;
+  if (v & MM_DEV_ERR_NONFINITE_H) return MM_ERR_NONFINITE;
+  return MM_OK;
 }

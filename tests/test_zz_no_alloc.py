@@ -67,6 +67,7 @@ def test_static_scratch_matches_mm_gemm_twice(mm, prec, mode):
             for _ in range(2):   # the second call meets the first one's scratch contents
                 rc, Cs = call_static(h.lib, Ad, Bd, prec)
                 assert rc == 0
+                assert h.lib.mm_gemm_emu_static_status(torch.cuda.current_stream().cuda_stream) == 0
                 Cg = h.gemm(Ad, Bd, precision=prec)
                 assert h.sync() == 0
                 cs, cg = Cs.cpu().numpy(), Cg.cpu().numpy()
@@ -89,3 +90,36 @@ def test_static_scratch_rejects_oversize(mm):
     rc, _ = call_static(lib, A, B, 1)
     assert rc == 3  # MM_ERR_BUDGET: larger than the fixed scratch
     assert lib.mm_gemm_emu_static(8, 8, 8, None, 8, None, 8, None, 8, 0, None) == 2   # plain FP64 is not offered
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_static_status_reports_nonfinite_and_clears(mm, prec):
+    lib = mm._lib.load()
+    stream = torch.cuda.current_stream().cuda_stream
+    A, B = _operands(70, 50, 300, 11, "scaled")
+    Bd = torch.from_numpy(B).cuda()
+
+    def run(Am):
+        rc, C = call_static(lib, torch.from_numpy(Am).cuda(), Bd, prec)
+        assert rc == 0   # the call itself does not wait for its kernels
+        return C.cpu().numpy()
+
+    bad = A.copy()
+    bad[5, 7] = np.nan
+    assert np.all(np.isnan(run(bad)[5]))
+    assert lib.mm_gemm_emu_static_status(stream) == 4   # MM_ERR_NONFINITE
+    assert lib.mm_gemm_emu_static_status(stream) == 0   # read and cleared
+    # the word covers the last call: a clean call clears what an earlier one left
+    bad[5, 7] = np.inf
+    run(bad)
+    run(A)
+    assert lib.mm_gemm_emu_static_status(stream) == 0
+    # ... also on the paths that take no split (k = 0; FP64-accuracy k <= 4)
+    run(bad)
+    for k in (0, 3):
+        rc, _ = call_static(lib, torch.zeros((8, k), dtype=torch.float64, device="cuda"),
+                            torch.zeros((k, 8), dtype=torch.float64, device="cuda"), prec)
+        assert rc == 0
+        assert lib.mm_gemm_emu_static_status(stream) == 0
+        run(bad)
+    assert lib.mm_gemm_emu_static_status(stream) == 4
