@@ -24,7 +24,7 @@ def lib():
     return _lib.load()
 
 
-def test_header_declares_the_north_star_calls():
+def test_header_declares_the_boundary_calls():
     fns = header_functions()
     for f in ("mm_create", "mm_gemm", "mm_gemm_grouped", "mm_serve_submit", "mm_serve_poll", "mm_destroy"):
         assert f in fns
